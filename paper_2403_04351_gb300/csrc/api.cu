@@ -1,0 +1,1440 @@
+// C ABI of the rttddft library (declarations and contracts in include/rttddft.h).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "rtd.h"
+#include "rttddft.h"
+
+typedef std::complex<double> cplx;
+
+namespace {
+thread_local std::string g_last_error;
+
+struct Fail {
+    int code;
+};
+}  // namespace
+
+struct rttddft_ctx {
+    int nk = 0, natoms = 0, ns = 0, naux = 0;
+    double omega = 0, c = 0;
+    rttddft_options opt{};
+    AtomTab at{};
+    std::vector<int> ng, nb;
+    int maxng = 0, maxnb = 0, maxm = 0;
+    int vt_dim[3] = {0, 0, 0};
+    int nvt = 0, vt_center = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<void*> allocs;
+    std::vector<KDev> hkd;
+    KDev* d_kd = nullptr;
+    AtomTab* d_at = nullptr;
+    zd *d_h = nullptr, *d_o = nullptr, *d_p = nullptr, *d_dh = nullptr;
+    zd *d_vtab = nullptr, *d_dvtab = nullptr, *d_vstep = nullptr;
+    zf *d_vtab32 = nullptr, *d_vstep32 = nullptr;
+    double *d_occ = nullptr, *d_wk = nullptr, *d_lam = nullptr;
+    DevState* d_st = nullptr;
+    double* d_rec = nullptr;
+    double *d_part_jmt = nullptr, *d_part_full = nullptr, *d_part_sub = nullptr, *d_part_norm = nullptr;
+    zd* d_part = nullptr;
+    double *d_a = nullptr, *d_dvs = nullptr;
+    int call_cap = 0;
+    int* d_flag = nullptr;
+    GemmDesc *gd_expand = nullptr, *gd_fwd = nullptr, *gd_proj = nullptr, *gd_g1 = nullptr,
+             *gd_g2 = nullptr, *gd_evh = nullptr, *gd_evn = nullptr;
+    GemmDesc *gd_dvw = nullptr, *gd_dvg = nullptr, *gd_dvi = nullptr;
+    ToepDesc* td_dv = nullptr;
+    zd** d_jac_mats = nullptr;
+    double** d_jac_vals = nullptr;
+    zd** d_jac_vecs = nullptr;
+    int kc_fwd = 0, kc_proj = 0;
+    std::vector<double> eps_min, eps_max, pnorm, dvnorm;
+    double dtcr0 = 0;
+    int nterms = 0, launches_per_step = 0;
+    bool dv_set = false;
+    cudaGraphExec_t gexec = nullptr;
+    int g_key_nterms = -1, g_key_dv = -1, g_key_steps = -1;
+    int rec_count = 0;
+    long long steps_done = 0;
+    double time = 0.0;
+    double a_max_cur = -1.0, s_max_cur = -1.0;  // bounds the Chebyshev interval was built for
+    double* h_stage = nullptr;                  // pinned staging of host samples
+    int stage_cap = 0;
+    cudaEvent_t stage_ev = nullptr;
+    std::string err;
+};
+
+// ------------------------------------------------------------ helpers
+#define CK(x)                                                                            \
+    do {                                                                                 \
+        cudaError_t e_ = (x);                                                            \
+        if (e_ != cudaSuccess) {                                                         \
+            set_err(ctx, std::string(#x) + ": " + cudaGetErrorString(e_));               \
+            throw Fail{e_ == cudaErrorMemoryAllocation ? RTTDDFT_ERR_OOM : RTTDDFT_ERR_CUDA}; \
+        }                                                                                \
+    } while (0)
+#define KCHECK() CK(cudaGetLastError())
+
+static void set_err(rttddft_ctx* ctx, const std::string& s) {
+    if (ctx) ctx->err = s;
+    g_last_error = s;
+}
+[[noreturn]] static void fail(rttddft_ctx* ctx, int code, const std::string& s) {
+    set_err(ctx, s);
+    throw Fail{code};
+}
+
+template <typename T>
+static T* dalloc(rttddft_ctx* ctx, size_t n) {
+    if (n == 0) n = 1;
+    void* p = nullptr;
+    CK(cudaMalloc(&p, n * sizeof(T)));
+    ctx->allocs.push_back(p);
+    return (T*)p;
+}
+template <typename T>
+static T* dupload(rttddft_ctx* ctx, const T* h, size_t n) {
+    T* d = dalloc<T>(ctx, n);
+    if (n) CK(cudaMemcpy(d, h, n * sizeof(T), cudaMemcpyHostToDevice));
+    return d;
+}
+static void dfree(rttddft_ctx* ctx, void* p) {
+    if (!p) return;
+    auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
+    if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+    cudaFree(p);
+}
+
+static bool finite_all(const double* p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// max |M - M^H| / max(1, max |M|) for a complex column-major m x m block
+static double herm_dev(const double* m2, int m) {
+    const cplx* M = (const cplx*)m2;
+    double dev = 0.0, mx = 1.0;
+    for (int j = 0; j < m; ++j)
+        for (int i = 0; i < m; ++i) {
+            dev = std::max(dev, std::abs(M[i + (size_t)j * m] - std::conj(M[j + (size_t)i * m])));
+            mx = std::max(mx, std::abs(M[i + (size_t)j * m]));
+        }
+    return dev / mx;
+}
+
+// Cholesky test for positive definiteness of a Hermitian block
+static bool is_pd(const double* m2, int m) {
+    const cplx* M = (const cplx*)m2;
+    std::vector<cplx> L((size_t)m * m, 0.0);
+    for (int j = 0; j < m; ++j) {
+        double d = M[j + (size_t)j * m].real();
+        for (int k = 0; k < j; ++k) d -= std::norm(L[j + (size_t)k * m]);
+        if (!(d > 0.0)) return false;
+        const double ljj = sqrt(d);
+        L[j + (size_t)j * m] = ljj;
+        for (int i = j + 1; i < m; ++i) {
+            cplx s = M[i + (size_t)j * m];
+            for (int k = 0; k < j; ++k) s -= L[i + (size_t)k * m] * std::conj(L[j + (size_t)k * m]);
+            L[i + (size_t)j * m] = s / ljj;
+        }
+    }
+    return true;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static GemmDesc* upload_descs(rttddft_ctx* ctx, const std::vector<GemmDesc>& v) {
+    return dupload(ctx, v.data(), v.size());
+}
+
+static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
+    StepArgs a{};
+    a.nk = ctx->nk;
+    a.ns = ctx->ns;
+    a.naux = ctx->naux;
+    a.prop = ctx->opt.propagator;
+    a.prec = ctx->opt.precision;
+    a.reproject = ctx->opt.reproject;
+    a.nterms = ctx->nterms;
+    a.dv_on = dv_on;
+    a.vt_center = ctx->vt_center;
+    a.nvt = ctx->nvt;
+    a.lrows = ctx->at.lrows;
+    a.ma = ctx->at.ma;
+    a.rec_cap = ctx->opt.max_record;
+    a.dt = ctx->opt.dt;
+    a.c = ctx->c;
+    a.omega = ctx->omega;
+    a.kd = ctx->d_kd;
+    a.occ = ctx->d_occ;
+    a.wk = ctx->d_wk;
+    a.h = ctx->d_h;
+    a.o = ctx->d_o;
+    a.p = ctx->d_p;
+    a.dh = dv_on ? ctx->d_dh : nullptr;
+    a.vtab = ctx->d_vtab;
+    a.vtab32 = ctx->d_vtab32;
+    a.dvtab = ctx->d_dvtab;
+    a.vstep = ctx->d_vstep;
+    a.vstep32 = ctx->d_vstep32;
+    a.a = ctx->d_a;
+    a.dvs = dv_on ? ctx->d_dvs : nullptr;
+    a.st = ctx->d_st;
+    a.rec = ctx->d_rec;
+    a.part_jmt = ctx->d_part_jmt;
+    a.part_full = ctx->d_part_full;
+    a.part_sub = ctx->d_part_sub;
+    a.part_norm = ctx->d_part_norm;
+    a.at = ctx->d_at;
+    return a;
+}
+
+static StepPlan make_plan(rttddft_ctx* ctx) {
+    StepPlan p{};
+    p.maxnb = ctx->maxnb;
+    p.maxng = ctx->maxng;
+    p.nterms = ctx->nterms;
+    p.gd_expand = ctx->gd_expand;
+    p.gd_fwd = ctx->gd_fwd;
+    p.gd_proj = ctx->gd_proj;
+    p.gd_g1 = ctx->gd_g1;
+    p.gd_g2 = ctx->gd_g2;
+    p.gd_evh = ctx->gd_evh;
+    p.gd_evn = ctx->gd_evn;
+    p.part = ctx->d_part;
+    p.kc_fwd = ctx->kc_fwd;
+    p.kc_proj = ctx->kc_proj;
+    p.gd_dvw = ctx->gd_dvw;
+    p.gd_dvg = ctx->gd_dvg;
+    p.gd_dvi = ctx->gd_dvi;
+    p.td_dv = ctx->td_dv;
+    p.n_dvw = ctx->nk * ctx->at.n;
+    p.maxm = ctx->maxm;
+    p.d_flag = ctx->d_flag;
+    p.jac_mats = ctx->d_jac_mats;
+    p.jac_vals = ctx->d_jac_vals;
+    p.jac_vecs = ctx->d_jac_vecs;
+    p.max_sweeps = ctx->opt.max_sweeps;
+    return p;
+}
+
+static int kchunk_for(int tiles_per_batch, int nbatch, int maxK) {
+    const int target = 2 * 152;
+    int splits = (target + tiles_per_batch * nbatch - 1) / (tiles_per_batch * nbatch);
+    splits = std::max(1, std::min(splits, (maxK + 255) / 256));
+    int kc = (maxK + splits - 1) / splits;
+    kc = (kc + 31) / 32 * 32;
+    return std::max(kc, 32);
+}
+
+// ------------------------------------------------------------ set-up pieces
+// Local coordinates L = [A_alpha X_G ; X_lo(alpha)] stacked over atoms,
+// lrows x ncol per k, for X given per k (nb x ncol, ld nb).
+static void local_coords(rttddft_ctx* ctx, const std::vector<zd*>& X, const std::vector<zd*>& L,
+                         int ncol) {
+    const AtomTab& at = ctx->at;
+    if (at.n == 0) return;
+    std::vector<GemmDesc> v;
+    std::vector<GemmDesc> cp;
+    for (int k = 0; k < ctx->nk; ++k) {
+        for (int a = 0; a < at.n; ++a) {
+            GemmDesc g{};
+            g.A = ctx->hkd[k].amat + at.aoff[a];
+            g.B = X[k];
+            g.C = L[k] + at.loff[a];
+            g.M = at.na[a];
+            g.K = ctx->ng[k];
+            g.lda = at.ma;
+            g.ldb = ctx->nb[k];
+            g.ldc = at.lrows;
+            v.push_back(g);
+            // LO rows: L[loff + na + j] = X[ng + looff + j] as a product with the identity
+            // is avoided: copy through a GEMM with K = 0 is not possible, so use a
+            // strided copy descriptor (A = X rows, M = nlo)
+            GemmDesc c{};
+            c.B = X[k] + ctx->ng[k] + at.looff[a];
+            c.C = L[k] + at.loff[a] + at.na[a];
+            c.M = at.nlo[a];
+            c.K = ncol;
+            c.ldb = ctx->nb[k];
+            c.ldc = at.lrows;
+            cp.push_back(c);
+        }
+    }
+    GemmDesc* d = upload_descs(ctx, v);
+    int maxna = 0;
+    for (int a = 0; a < at.n; ++a) maxna = std::max(maxna, at.na[a]);
+    launch_gemm_nn(d, (int)v.size(), maxna, ctx->maxng, ncol, 0, nullptr, 0, false, nullptr, ctx->stream);
+    KCHECK();
+    GemmDesc* dc = upload_descs(ctx, cp);
+    int maxlo = 0;
+    for (int a = 0; a < at.n; ++a) maxlo = std::max(maxlo, at.nlo[a]);
+    if (maxlo > 0) launch_copy_rows(dc, (int)cp.size(), maxlo, ncol, ctx->stream);
+    KCHECK();
+    CK(cudaStreamSynchronize(ctx->stream));
+    dfree(ctx, d);
+    dfree(ctx, dc);
+}
+
+// G[k] = X^H M X for M in {S (which=0), H0 (1), P_l (2 + l)}, ncol x ncol per k,
+// from the local coordinates L of X and the plane-wave rows of X.
+static void gram(rttddft_ctx* ctx, int which, const std::vector<zd*>& X, const std::vector<zd*>& L,
+                 const std::vector<zd*>& G, int ncol, const zd* tab_override = nullptr,
+                 const zd* blocks_override = nullptr) {
+    const AtomTab& at = ctx->at;
+    const int nk = ctx->nk;
+    std::vector<zd*> W(nk), T(nk);
+    for (int k = 0; k < nk; ++k) {
+        W[k] = dalloc<zd>(ctx, (size_t)std::max(at.lrows, 1) * ncol);
+        T[k] = dalloc<zd>(ctx, (size_t)ctx->ng[k] * ncol);
+    }
+    // muffin-tin part: W = blockdiag(M_alpha) L, G = L^H W
+    if (at.n > 0) {
+        std::vector<GemmDesc> v;
+        for (int k = 0; k < nk; ++k)
+            for (int a = 0; a < at.n; ++a) {
+                GemmDesc g{};
+                const zd* blk;
+                if (blocks_override) blk = blocks_override + at.boff[a];
+                else if (which == 0) blk = ctx->d_o + at.boff[a];
+                else if (which == 1) blk = ctx->d_h + at.boff[a];
+                else blk = ctx->d_p + 3 * at.boff[a] + (size_t)(which - 2) * at.m[a] * at.m[a];
+                g.A = blk;
+                g.B = L[k] + at.loff[a];
+                g.C = W[k] + at.loff[a];
+                g.M = at.m[a];
+                g.K = at.m[a];
+                g.lda = at.m[a];
+                g.ldb = at.lrows;
+                g.ldc = at.lrows;
+                v.push_back(g);
+            }
+        GemmDesc* d = upload_descs(ctx, v);
+        launch_gemm_nn(d, (int)v.size(), ctx->maxm, ctx->maxm, ncol, 0, nullptr, 0, false, nullptr,
+                       ctx->stream);
+        KCHECK();
+        std::vector<GemmDesc> u;
+        for (int k = 0; k < nk; ++k) {
+            GemmDesc g{};
+            g.A = L[k];
+            g.B = W[k];
+            g.C = G[k];
+            g.M = ncol;
+            g.K = at.lrows;
+            g.lda = at.lrows;
+            g.ldb = at.lrows;
+            g.ldc = ncol;
+            u.push_back(g);
+        }
+        GemmDesc* d2 = upload_descs(ctx, u);
+        launch_gemm_cn(d2, nk, ncol, at.lrows, ncol, 0, nullptr, 0, false, nullptr, ctx->stream);
+        KCHECK();
+        CK(cudaStreamSynchronize(ctx->stream));
+        dfree(ctx, d);
+        dfree(ctx, d2);
+    } else {
+        for (int k = 0; k < nk; ++k) launch_zero(G[k], (size_t)ncol * ncol, ctx->stream);
+    }
+    // plane-wave part: T = (table * X_G) + d_G X_G, G += X_G^H T
+    std::vector<ToepDesc> tdv(nk);
+    for (int k = 0; k < nk; ++k) tdv[k] = ToepDesc{X[k], T[k], ctx->nb[k], ctx->ng[k]};
+    ToepDesc* td = dupload(ctx, tdv.data(), tdv.size());
+    const zd* tab = nullptr;
+    int dmode = 0;
+    if (which == 0) dmode = 5;
+    else if (which == 1) {
+        tab = ctx->d_vtab;
+        dmode = 1;
+    } else if (which >= 2 && which <= 4) dmode = which;
+    else if (which == 9) tab = tab_override;  // potential change: table only
+    launch_toeplitz(ctx->d_kd, td, nk, ctx->maxng, ncol, tab, ctx->vt_center, 0, dmode, nullptr,
+                    ctx->stream);
+    KCHECK();
+    std::vector<GemmDesc> u;
+    for (int k = 0; k < nk; ++k) {
+        GemmDesc g{};
+        g.A = X[k];
+        g.B = T[k];
+        g.C = G[k];
+        g.M = ncol;
+        g.K = ctx->ng[k];
+        g.lda = ctx->nb[k];
+        g.ldb = ctx->ng[k];
+        g.ldc = ncol;
+        u.push_back(g);
+    }
+    GemmDesc* d3 = upload_descs(ctx, u);
+    int kc = kchunk_for((ncol + 7) / 8, nk, ctx->maxng);
+    size_t pe = 0;
+    for (int k = 0; k < nk; ++k) {
+        u[k].part_off = pe;
+        pe += (size_t)((ctx->ng[k] + kc - 1) / kc) * ncol * ncol;
+    }
+    CK(cudaMemcpy(d3, u.data(), u.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice));
+    zd* part = dalloc<zd>(ctx, pe);
+    launch_gemm_cn(d3, nk, ncol, ctx->maxng, ncol, kc, part, 0, false, nullptr, ctx->stream);
+    launch_split_reduce(d3, nk, ncol, ncol, kc, part, 1, ctx->stream);
+    KCHECK();
+    CK(cudaStreamSynchronize(ctx->stream));
+    dfree(ctx, part);
+    dfree(ctx, d3);
+    dfree(ctx, td);
+    for (int k = 0; k < nk; ++k) {
+        dfree(ctx, W[k]);
+        dfree(ctx, T[k]);
+    }
+}
+
+// batched square GEMMs on per-k naux x naux matrices
+static void sq_gemm(rttddft_ctx* ctx, bool conjA, const std::vector<zd*>& A, const std::vector<zd*>& B,
+                    const std::vector<zd*>& C, int n) {
+    std::vector<GemmDesc> v;
+    for (int k = 0; k < ctx->nk; ++k) {
+        GemmDesc g{};
+        g.A = A[k];
+        g.B = B[k];
+        g.C = C[k];
+        g.M = n;
+        g.K = n;
+        g.lda = n;
+        g.ldb = n;
+        g.ldc = n;
+        v.push_back(g);
+    }
+    GemmDesc* d = upload_descs(ctx, v);
+    if (conjA) launch_gemm_cn(d, ctx->nk, n, n, n, 0, nullptr, 0, false, nullptr, ctx->stream);
+    else launch_gemm_nn(d, ctx->nk, n, n, n, 0, nullptr, 0, false, nullptr, ctx->stream);
+    KCHECK();
+    CK(cudaStreamSynchronize(ctx->stream));
+    dfree(ctx, d);
+}
+
+static void jacobi(rttddft_ctx* ctx, const std::vector<zd*>& mats, const std::vector<double*>& vals,
+                   const std::vector<zd*>& vecs, int n) {
+    zd** dm = dupload(ctx, mats.data(), mats.size());
+    double** dv = dupload(ctx, vals.data(), vals.size());
+    zd** dx = dupload(ctx, vecs.data(), vecs.size());
+    CK(cudaMemset(ctx->d_flag, 0, sizeof(int)));
+    if (launch_jacobi(dm, dv, dx, (int)mats.size(), n, ctx->opt.max_sweeps, ctx->d_flag, ctx->stream))
+        fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "n_aux above the eigensolver limit (1024)");
+    KCHECK();
+    CK(cudaStreamSynchronize(ctx->stream));
+    int flag = 0;
+    CK(cudaMemcpy(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    dfree(ctx, dm);
+    dfree(ctx, dv);
+    dfree(ctx, dx);
+    if (flag) fail(ctx, RTTDDFT_ERR_TIMEOUT, "Jacobi eigensolver reached its sweep limit");
+}
+
+
+static void validate(const rttddft_system* s, const rttddft_options* o) {
+    rttddft_ctx* ctx = nullptr;
+    if (!s) fail(ctx, RTTDDFT_ERR_ARG, "system is NULL");
+    if (s->n_k < 1) fail(ctx, RTTDDFT_ERR_ARG, "n_k < 1");
+    if (s->n_atoms < 0 || s->n_atoms > RTD_MAX_ATOMS) fail(ctx, RTTDDFT_ERR_ARG, "n_atoms out of range [0, 64]");
+    if (s->n_s < 1 || s->n_aux < s->n_s) fail(ctx, RTTDDFT_ERR_ARG, "need 1 <= n_s <= n_aux");
+    if (s->n_aux > 1024) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "n_aux > 1024");
+    if (!(s->omega > 0) || !(s->c_light > 0)) fail(ctx, RTTDDFT_ERR_ARG, "omega and c_light must be > 0");
+    if (!s->occ || !s->wk || !s->n_g || !s->g_int || !s->gk || !s->vtab || !s->caux)
+        fail(ctx, RTTDDFT_ERR_ARG, "NULL array in system");
+    if (s->n_atoms > 0 && (!s->n_a || !s->n_lo || !s->amat || !s->h || !s->o || !s->p))
+        fail(ctx, RTTDDFT_ERR_ARG, "NULL atom array in system");
+    for (int i = 0; i < 3; ++i)
+        if (s->vt_dim[i] < 1 || (s->vt_dim[i] & 1) == 0) fail(ctx, RTTDDFT_ERR_ARG, "vt_dim must be odd and >= 1");
+    if (!o) fail(ctx, RTTDDFT_ERR_ARG, "options are NULL");
+    if (!(o->dt > 0)) fail(ctx, RTTDDFT_ERR_ARG, "dt must be > 0");
+    if (o->propagator < 0 || o->propagator > 2) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown propagator");
+    if (o->precision < 0 || o->precision > 1) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown precision form");
+    if (o->aux_mode < 0 || o->aux_mode > 1) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown aux_mode");
+    if (o->aux_mode == RTTDDFT_AUX_GIVEN && !s->eps) fail(ctx, RTTDDFT_ERR_ARG, "GIVEN mode needs eps");
+    if (o->max_record < 1 || o->graph_steps < 0 || o->max_sweeps < 1) fail(ctx, RTTDDFT_ERR_ARG, "bad option value");
+    if (!finite_all(s->occ, s->n_s) || !finite_all(s->wk, s->n_k)) fail(ctx, RTTDDFT_ERR_NONFINITE, "occ/wk not finite");
+}
+
+// ------------------------------------------------------------ ABI
+extern "C" {
+
+void rttddft_default_options(rttddft_options* opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->dt = 0.1;
+    opt->propagator = RTTDDFT_PROP_CHEBYSHEV;
+    opt->precision = RTTDDFT_PREC_FP64;
+    opt->reproject = 0;
+    opt->aux_mode = RTTDDFT_AUX_RITZ;
+    opt->max_record = 4096;
+    opt->graph_steps = 1;
+    opt->cheb_tol = 1e-16;
+    opt->ortho_tol = 1e-10;
+    opt->max_sweeps = 30;
+    opt->a_max = 0.0;
+    opt->s_max = 0.0;
+}
+
+const char* rttddft_version(void) { return "rttddft-gb300 0.1 (sm_103a)"; }
+
+const char* rttddft_last_error(const rttddft_ctx* ctx) {
+    if (ctx) return ctx->err.c_str();
+    return g_last_error.c_str();
+}
+
+void rttddft_destroy(rttddft_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* cuda_stream,
+                  rttddft_ctx** out) {
+    rttddft_ctx* ctx = nullptr;
+    if (!out) {
+        g_last_error = "out is NULL";
+        return RTTDDFT_ERR_ARG;
+    }
+    *out = nullptr;
+    rttddft_options dflt;
+    rttddft_default_options(&dflt);
+    const rttddft_options* o = opt_in ? opt_in : &dflt;
+    try {
+        validate(s, o);
+        ctx = new rttddft_ctx();
+        ctx->opt = *o;
+        ctx->nk = s->n_k;
+        ctx->natoms = s->n_atoms;
+        ctx->ns = s->n_s;
+        ctx->naux = s->n_aux;
+        ctx->omega = s->omega;
+        ctx->c = s->c_light;
+        const int nk = ctx->nk, ns = ctx->ns, naux = ctx->naux;
+        // ---- atoms
+        AtomTab& at = ctx->at;
+        at.n = s->n_atoms;
+        size_t boff = 0;
+        int aoff = 0, looff = 0, loff = 0;
+        for (int a = 0; a < at.n; ++a) {
+            if (s->n_a[a] < 0 || s->n_lo[a] < 0 || s->n_a[a] + s->n_lo[a] < 1)
+                fail(ctx, RTTDDFT_ERR_ARG, "atom with no rows");
+            at.na[a] = s->n_a[a];
+            at.nlo[a] = s->n_lo[a];
+            at.m[a] = at.na[a] + at.nlo[a];
+            at.aoff[a] = aoff;
+            at.looff[a] = looff;
+            at.loff[a] = loff;
+            at.boff[a] = boff;
+            aoff += at.na[a];
+            looff += at.nlo[a];
+            loff += at.m[a];
+            boff += (size_t)at.m[a] * at.m[a];
+            ctx->maxm = std::max(ctx->maxm, at.m[a]);
+        }
+        at.ma = aoff;
+        at.nlo_tot = looff;
+        at.lrows = loff;
+        const size_t nblk = boff;
+        // ---- host validation of the blocks and the table
+        if (at.n > 0) {
+            if (!finite_all(s->h, 2 * nblk) || !finite_all(s->o, 2 * nblk) || !finite_all(s->p, 6 * nblk))
+                fail(ctx, RTTDDFT_ERR_NONFINITE, "muffin-tin block not finite");
+            for (int a = 0; a < at.n; ++a) {
+                const int m = at.m[a];
+                const double* hb = s->h + 2 * at.boff[a];
+                const double* ob = s->o + 2 * at.boff[a];
+                if (herm_dev(hb, m) > 1e-12 || herm_dev(ob, m) > 1e-12)
+                    fail(ctx, RTTDDFT_ERR_NOT_HERMITIAN, "h or o block of atom " + std::to_string(a) + " not Hermitian");
+                for (int l = 0; l < 3; ++l)
+                    if (herm_dev(s->p + 2 * (3 * at.boff[a] + (size_t)l * m * m), m) > 1e-12)
+                        fail(ctx, RTTDDFT_ERR_NOT_HERMITIAN, "p block of atom " + std::to_string(a) + " not Hermitian");
+                if (!is_pd(ob, m)) fail(ctx, RTTDDFT_ERR_NOT_PD, "o block of atom " + std::to_string(a) + " not positive definite");
+            }
+        }
+        for (int i = 0; i < 3; ++i) ctx->vt_dim[i] = s->vt_dim[i];
+        const int d0 = s->vt_dim[0], d1 = s->vt_dim[1], d2 = s->vt_dim[2];
+        ctx->nvt = d0 * d1 * d2;
+        const int e0 = (d0 - 1) / 2, e1 = (d1 - 1) / 2, e2 = (d2 - 1) / 2;
+        ctx->vt_center = (e0 * d1 + e1) * d2 + e2;
+        if (!finite_all(s->vtab, 2 * (size_t)ctx->nvt)) fail(ctx, RTTDDFT_ERR_NONFINITE, "vtab not finite");
+        {
+            const cplx* V = (const cplx*)s->vtab;
+            double dev = 0.0, mx = 1e-300;
+            for (int i = 0; i < ctx->nvt; ++i) mx = std::max(mx, std::abs(V[i]));
+            for (int i = 0; i < ctx->nvt; ++i) dev = std::max(dev, std::abs(V[i] - std::conj(V[ctx->nvt - 1 - i])));
+            if (dev > 1e-12 * mx) fail(ctx, RTTDDFT_ERR_NOT_HERMITIAN, "vtab not Hermitian in g");
+        }
+        // ---- k-points
+        ctx->ng.resize(nk);
+        ctx->nb.resize(nk);
+        size_t goff = 0, coff = 0, aoffk = 0;
+        std::vector<size_t> g_off(nk), c_off(nk), a_off(nk);
+        for (int k = 0; k < nk; ++k) {
+            const int ng = s->n_g[k];
+            if (ng < 1) fail(ctx, RTTDDFT_ERR_ARG, "n_g < 1");
+            int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+            for (int g = 0; g < ng; ++g) {
+                const int* t = s->g_int + 3 * (goff + g);
+                for (int i = 0; i < 3; ++i) {
+                    mn[i] = std::min(mn[i], t[i]);
+                    mx[i] = std::max(mx[i], t[i]);
+                }
+            }
+            if (mx[0] - mn[0] > e0 || mx[1] - mn[1] > e1 || mx[2] - mn[2] > e2)
+                fail(ctx, RTTDDFT_ERR_ARG, "vtab box does not cover the G - G' differences");
+            ctx->ng[k] = ng;
+            ctx->nb[k] = ng + at.nlo_tot;
+            if (naux > ctx->nb[k]) fail(ctx, RTTDDFT_ERR_ARG, "n_aux > N_basis of a k-point");
+            ctx->maxng = std::max(ctx->maxng, ng);
+            ctx->maxnb = std::max(ctx->maxnb, ctx->nb[k]);
+            g_off[k] = goff;
+            c_off[k] = coff;
+            a_off[k] = aoffk;
+            goff += ng;
+            coff += (size_t)ctx->nb[k] * naux;
+            aoffk += (size_t)at.ma * ng;
+        }
+        if (!finite_all(s->gk, 3 * goff) || !finite_all(s->caux, 2 * coff) ||
+            (at.n > 0 && !finite_all(s->amat, 2 * aoffk)))
+            fail(ctx, RTTDDFT_ERR_NONFINITE, "gk, caux or amat not finite");
+        if (s->eps && o->aux_mode == RTTDDFT_AUX_GIVEN && !finite_all(s->eps, (size_t)nk * naux))
+            fail(ctx, RTTDDFT_ERR_NONFINITE, "eps not finite");
+        if (s->c0) {
+            size_t n0 = 0;
+            for (int k = 0; k < nk; ++k) n0 += (size_t)ctx->nb[k] * ns;
+            if (!finite_all(s->c0, 2 * n0)) fail(ctx, RTTDDFT_ERR_NONFINITE, "c0 not finite");
+        }
+        // ---- device state (all host checks are done)
+        if (cuda_stream) {
+            ctx->stream = (cudaStream_t)cuda_stream;
+        } else {
+            CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+            ctx->own_stream = true;
+        }
+        ctx->d_occ = dupload(ctx, s->occ, ns);
+        ctx->d_wk = dupload(ctx, s->wk, nk);
+        if (at.n > 0) {
+            ctx->d_h = dupload(ctx, (const zd*)s->h, nblk);
+            ctx->d_o = dupload(ctx, (const zd*)s->o, nblk);
+            ctx->d_p = dupload(ctx, (const zd*)s->p, 3 * nblk);
+        }
+        ctx->d_vtab = dupload(ctx, (const zd*)s->vtab, ctx->nvt);
+        ctx->d_at = dupload(ctx, &at, 1);
+        ctx->d_st = dalloc<DevState>(ctx, 1);
+        CK(cudaMemset(ctx->d_st, 0, sizeof(DevState)));
+        ctx->d_flag = dalloc<int>(ctx, 1);
+        ctx->d_rec = dalloc<double>(ctx, (size_t)o->max_record * RTD_REC_STRIDE);
+        ctx->d_lam = dalloc<double>(ctx, 2 * (size_t)nk);
+        ctx->d_part_jmt = dalloc<double>(ctx, (size_t)nk * std::max(at.lrows, 1) * 3);
+        ctx->d_part_full = dalloc<double>(ctx, (size_t)nk * ns * RB_FULL * 5);
+        ctx->d_part_sub = dalloc<double>(ctx, (size_t)nk * 3 * naux);
+        ctx->d_part_norm = dalloc<double>(ctx, (size_t)nk * 2);
+        CK(cudaMemset(ctx->d_part_jmt, 0, sizeof(double) * nk * std::max(at.lrows, 1) * 3));
+        ctx->call_cap = 1024;
+        ctx->d_a = dalloc<double>(ctx, 3 * (size_t)ctx->call_cap);
+        ctx->d_dvs = dalloc<double>(ctx, (size_t)ctx->call_cap);
+        // ---- per-k buffers
+        ctx->hkd.resize(nk);
+        const size_t nn = (size_t)naux * naux;
+        for (int k = 0; k < nk; ++k) {
+            KDev& K = ctx->hkd[k];
+            K.ng = ctx->ng[k];
+            K.nb = ctx->nb[k];
+            K.caux = dupload(ctx, (const zd*)s->caux + c_off[k], (size_t)K.nb * naux);
+            K.amat = at.n > 0 ? dupload(ctx, (const zd*)s->amat + a_off[k], (size_t)at.ma * K.ng) : nullptr;
+            std::vector<int> gl(K.ng);
+            for (int g = 0; g < K.ng; ++g) {
+                const int* t = s->g_int + 3 * (g_off[k] + g);
+                gl[g] = (t[0] * d1 + t[1]) * d2 + t[2];
+            }
+            K.glin = dupload(ctx, gl.data(), gl.size());
+            K.gk = dupload(ctx, s->gk + 3 * g_off[k], 3 * (size_t)K.ng);
+            K.eps = dalloc<double>(ctx, naux);
+            K.psub = dalloc<zd>(ctx, 3 * nn);
+            K.lloc = dalloc<zd>(ctx, (size_t)std::max(at.lrows, 1) * naux);
+            K.theta = dalloc<zd>(ctx, (size_t)naux * ns);
+            K.theta_t = dalloc<zd>(ctx, (size_t)naux * ns);
+            K.ring = dalloc<zd>(ctx, 3 * (size_t)naux * ns);
+            K.acc = dalloc<zd>(ctx, (size_t)naux * ns);
+            K.hsub = dalloc<zd>(ctx, nn);
+            K.C = dalloc<zd>(ctx, (size_t)K.nb * ns);
+            K.Y = dalloc<zd>(ctx, (size_t)K.nb * 2 * ns);
+            K.Q = dalloc<zd>(ctx, (size_t)std::max(at.ma, 1) * ns);
+            K.Z = dalloc<zd>(ctx, (size_t)std::max(at.ma, 1) * 2 * ns);
+            K.gram = dalloc<zd>(ctx, 2 * (size_t)ns * ns);
+            K.evec = dalloc<zd>(ctx, nn);
+            K.eval = dalloc<double>(ctx, naux);
+            K.wtmp = dalloc<zd>(ctx, (size_t)naux * ns);
+            K.coef = dalloc<zd>(ctx, RTD_MAX_TERMS);
+            K.lam = ctx->d_lam + 2 * k;
+        }
+        ctx->d_kd = dupload(ctx, ctx->hkd.data(), nk);
+        // ---- auxiliary basis
+        std::vector<zd*> X(nk), L(nk), G1(nk), G2(nk), V1(nk), V2(nk), T1(nk), T2(nk), NEW(nk);
+        std::vector<double*> E1(nk), E2(nk);
+        for (int k = 0; k < nk; ++k) {
+            X[k] = ctx->hkd[k].caux;
+            L[k] = ctx->hkd[k].lloc;
+            G1[k] = dalloc<zd>(ctx, nn);
+            G2[k] = dalloc<zd>(ctx, nn);
+            V1[k] = dalloc<zd>(ctx, nn);
+            V2[k] = dalloc<zd>(ctx, nn);
+            T1[k] = dalloc<zd>(ctx, nn);
+            T2[k] = dalloc<zd>(ctx, nn);
+            E1[k] = dalloc<double>(ctx, naux);
+            E2[k] = ctx->hkd[k].eps;
+        }
+        local_coords(ctx, X, L, naux);
+        gram(ctx, 0, X, L, G1, naux);  // X^H S X
+        if (o->aux_mode == RTTDDFT_AUX_RITZ) {
+            gram(ctx, 1, X, L, G2, naux);  // X^H H0 X
+            // canonical S-orthonormalisation: X^H S X = W diag(lam) W^H, T1 = W lam^{-1/2}
+            jacobi(ctx, G1, E1, V1, naux);
+            for (int k = 0; k < nk; ++k) {
+                std::vector<double> ev(naux);
+                CK(cudaMemcpy(ev.data(), E1[k], naux * sizeof(double), cudaMemcpyDeviceToHost));
+                if (!(ev[0] > 1e-12 * ev[naux - 1]))
+                    fail(ctx, RTTDDFT_ERR_NOT_PD, "trial vectors are (numerically) linearly dependent in the S metric");
+            }
+            {
+                zd** dm = dupload(ctx, V1.data(), nk);
+                double** dv = dupload(ctx, E1.data(), nk);
+                launch_scale_cols(dm, dv, nk, naux, 0, ctx->stream);
+                KCHECK();
+                CK(cudaStreamSynchronize(ctx->stream));
+                dfree(ctx, dm);
+                dfree(ctx, dv);
+            }
+            sq_gemm(ctx, false, G2, V1, T1, naux);  // X^H H0 X T1
+            sq_gemm(ctx, true, V1, T1, T2, naux);   // T1^H X^H H0 X T1
+            jacobi(ctx, T2, E2, V2, naux);           // Ritz values (ascending) and vectors
+            sq_gemm(ctx, false, V1, V2, T1, naux);  // coefficients of the Ritz vectors in X
+            // CC = X T  (new buffer, then swap)
+            std::vector<GemmDesc> v;
+            for (int k = 0; k < nk; ++k) {
+                NEW[k] = dalloc<zd>(ctx, (size_t)ctx->nb[k] * naux);
+                GemmDesc g{};
+                g.A = X[k];
+                g.B = T1[k];
+                g.C = NEW[k];
+                g.M = ctx->nb[k];
+                g.K = naux;
+                g.lda = ctx->nb[k];
+                g.ldb = naux;
+                g.ldc = ctx->nb[k];
+                v.push_back(g);
+            }
+            GemmDesc* d = upload_descs(ctx, v);
+            launch_gemm_nn(d, nk, ctx->maxnb, naux, naux, 0, nullptr, 0, false, nullptr, ctx->stream);
+            KCHECK();
+            CK(cudaStreamSynchronize(ctx->stream));
+            dfree(ctx, d);
+            for (int k = 0; k < nk; ++k) {
+                dfree(ctx, ctx->hkd[k].caux);
+                ctx->hkd[k].caux = NEW[k];
+                X[k] = NEW[k];
+            }
+            CK(cudaMemcpy(ctx->d_kd, ctx->hkd.data(), nk * sizeof(KDev), cudaMemcpyHostToDevice));
+            launch_phase_fix(ctx->d_kd, nk, naux, nullptr, nullptr, 0, ctx->stream);
+            KCHECK();
+            CK(cudaStreamSynchronize(ctx->stream));
+            local_coords(ctx, X, L, naux);
+        } else {
+            for (int k = 0; k < nk; ++k) {
+                std::vector<cplx> g(nn);
+                CK(cudaMemcpy(g.data(), G1[k], nn * sizeof(zd), cudaMemcpyDeviceToHost));
+                double dev = 0.0;
+                for (int j = 0; j < naux; ++j)
+                    for (int i = 0; i < naux; ++i)
+                        dev = std::max(dev, std::abs(g[i + (size_t)j * naux] - (i == j ? 1.0 : 0.0)));
+                if (dev > o->ortho_tol)
+                    fail(ctx, RTTDDFT_ERR_NOT_ORTHONORMAL, "given CC(0) is not S-orthonormal (max dev " + std::to_string(dev) + ")");
+                CK(cudaMemcpy(E2[k], s->eps + (size_t)k * naux, naux * sizeof(double), cudaMemcpyHostToDevice));
+            }
+        }
+        // ---- projected momentum PP_l = CC^H P_l CC (Eq. auxiliary_hamiltonian_with_parts)
+        for (int l = 0; l < 3; ++l) {
+            std::vector<zd*> P(nk);
+            for (int k = 0; k < nk; ++k) P[k] = ctx->hkd[k].psub + (size_t)l * nn;
+            gram(ctx, 2 + l, X, L, P, naux);
+        }
+        ctx->eps_min.resize(nk);
+        ctx->eps_max.resize(nk);
+        ctx->pnorm.assign(3 * nk, 0.0);
+        ctx->dvnorm.assign(nk, 0.0);
+        ctx->dtcr0 = 1e300;
+        for (int k = 0; k < nk; ++k) {
+            std::vector<double> ev(naux);
+            CK(cudaMemcpy(ev.data(), E2[k], naux * sizeof(double), cudaMemcpyDeviceToHost));
+            ctx->eps_min[k] = *std::min_element(ev.begin(), ev.end());
+            ctx->eps_max[k] = *std::max_element(ev.begin(), ev.end());
+            if (ctx->eps_max[k] > ctx->eps_min[k])
+                ctx->dtcr0 = std::min(ctx->dtcr0, 0.2 / (ctx->eps_max[k] - ctx->eps_min[k]));
+            std::vector<double> pp(2 * 3 * nn);
+            CK(cudaMemcpy(pp.data(), ctx->hkd[k].psub, 3 * nn * sizeof(zd), cudaMemcpyDeviceToHost));
+            for (int l = 0; l < 3; ++l) {
+                double f = 0.0;
+                for (size_t e = 0; e < 2 * nn; ++e) f += pp[2 * l * nn + e] * pp[2 * l * nn + e];
+                ctx->pnorm[3 * k + l] = sqrt(f);
+            }
+        }
+        for (int k = 0; k < nk; ++k) {
+            dfree(ctx, G1[k]);
+            dfree(ctx, G2[k]);
+            dfree(ctx, V1[k]);
+            dfree(ctx, V2[k]);
+            dfree(ctx, T1[k]);
+            dfree(ctx, T2[k]);
+            dfree(ctx, E1[k]);
+        }
+        // ---- FP32 copies for the FP32 form
+        if (o->precision == RTTDDFT_PREC_FP32) {
+            for (int k = 0; k < nk; ++k) {
+                KDev& K = ctx->hkd[k];
+                K.caux32 = dalloc<zf>(ctx, (size_t)K.nb * naux);
+                launch_convert_f32(K.caux, K.caux32, (size_t)K.nb * naux, ctx->stream);
+                if (at.n > 0) {
+                    K.amat32 = dalloc<zf>(ctx, (size_t)at.ma * K.ng);
+                    launch_convert_f32(K.amat, K.amat32, (size_t)at.ma * K.ng, ctx->stream);
+                }
+            }
+            ctx->d_vtab32 = dalloc<zf>(ctx, ctx->nvt);
+            launch_convert_f32(ctx->d_vtab, ctx->d_vtab32, ctx->nvt, ctx->stream);
+            KCHECK();
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+        CK(cudaMemcpy(ctx->d_kd, ctx->hkd.data(), nk * sizeof(KDev), cudaMemcpyHostToDevice));
+        // ---- step descriptors
+        const bool f32 = o->precision == RTTDDFT_PREC_FP32;
+        std::vector<GemmDesc> ex, fw, pj, g1, g2, eh, en;
+        ctx->kc_fwd = kchunk_for((at.ma + 127) / 128, nk, ctx->maxng);
+        ctx->kc_proj = kchunk_for((naux + 7) / 8, nk, ctx->maxnb);
+        size_t pf = 0, pp = 0;
+        for (int k = 0; k < nk; ++k) {
+            KDev& K = ctx->hkd[k];
+            GemmDesc g{};
+            g.A = f32 ? (const void*)K.caux32 : (const void*)K.caux;
+            g.B = K.theta;
+            g.C = K.C;
+            g.M = K.nb;
+            g.K = naux;
+            g.lda = K.nb;
+            g.ldb = naux;
+            g.ldc = K.nb;
+            ex.push_back(g);
+            g = GemmDesc{};
+            g.A = f32 ? (const void*)K.amat32 : (const void*)K.amat;
+            g.B = K.C;
+            g.C = K.Q;
+            g.M = at.ma;
+            g.K = K.ng;
+            g.lda = std::max(at.ma, 1);
+            g.ldb = K.nb;
+            g.ldc = std::max(at.ma, 1);
+            g.part_off = pf;
+            pf += (size_t)((K.ng + ctx->kc_fwd - 1) / ctx->kc_fwd) * ns * std::max(at.ma, 1);
+            fw.push_back(g);
+            g = GemmDesc{};
+            g.A = f32 ? (const void*)K.caux32 : (const void*)K.caux;
+            g.B = K.Y + (size_t)ns * K.nb;
+            g.C = K.theta_t;
+            g.M = naux;
+            g.K = K.nb;
+            g.lda = K.nb;
+            g.ldb = K.nb;
+            g.ldc = naux;
+            g.part_off = pp;
+            pp += (size_t)((K.nb + ctx->kc_proj - 1) / ctx->kc_proj) * ns * naux;
+            pj.push_back(g);
+            g = GemmDesc{};
+            g.A = K.theta;
+            g.B = K.theta_t;
+            g.C = K.gram;
+            g.M = ns;
+            g.K = naux;
+            g.lda = naux;
+            g.ldb = naux;
+            g.ldc = ns;
+            g1.push_back(g);
+            g.A = K.theta_t;
+            g.C = K.gram + (size_t)ns * ns;
+            g2.push_back(g);
+            g = GemmDesc{};
+            g.A = K.evec;
+            g.B = K.theta;
+            g.C = K.wtmp;
+            g.M = naux;
+            g.K = naux;
+            g.lda = naux;
+            g.ldb = naux;
+            g.ldc = naux;
+            eh.push_back(g);
+            g.B = K.wtmp;
+            g.C = K.theta;
+            en.push_back(g);
+        }
+        ctx->d_part = dalloc<zd>(ctx, std::max(pf, pp));
+        ctx->gd_expand = upload_descs(ctx, ex);
+        ctx->gd_fwd = upload_descs(ctx, fw);
+        ctx->gd_proj = upload_descs(ctx, pj);
+        ctx->gd_g1 = upload_descs(ctx, g1);
+        ctx->gd_g2 = upload_descs(ctx, g2);
+        ctx->gd_evh = upload_descs(ctx, eh);
+        ctx->gd_evn = upload_descs(ctx, en);
+        {
+            std::vector<zd*> jm(nk), jv(nk);
+            std::vector<double*> jw(nk);
+            for (int k = 0; k < nk; ++k) {
+                jm[k] = ctx->hkd[k].hsub;
+                jv[k] = ctx->hkd[k].evec;
+                jw[k] = ctx->hkd[k].eval;
+            }
+            ctx->d_jac_mats = dupload(ctx, jm.data(), nk);
+            ctx->d_jac_vecs = dupload(ctx, jv.data(), nk);
+            ctx->d_jac_vals = dupload(ctx, jw.data(), nk);
+        }
+        // ---- theta(0)
+        if (s->c0) {
+            size_t c0off = 0;
+            for (int k = 0; k < nk; ++k) {
+                CK(cudaMemcpy(ctx->hkd[k].C, (const zd*)s->c0 + c0off, (size_t)ctx->nb[k] * ns * sizeof(zd),
+                              cudaMemcpyHostToDevice));
+                c0off += (size_t)ctx->nb[k] * ns;
+            }
+            CK(cudaMemset(ctx->d_st, 0, sizeof(DevState)));
+            StepArgs a = make_args(ctx, 0);
+            StepPlan p = make_plan(ctx);
+            launch_operator_pass(a, p, ctx->stream);
+            launch_gemm_cn(p.gd_proj, nk, naux, ctx->maxnb, ns, ctx->kc_proj, ctx->d_part, 0, f32, nullptr,
+                           ctx->stream);
+            launch_split_reduce(p.gd_proj, nk, naux, ns, ctx->kc_proj, ctx->d_part, 0, ctx->stream);
+            KCHECK();
+            for (int k = 0; k < nk; ++k)
+                CK(cudaMemcpyAsync(ctx->hkd[k].theta, ctx->hkd[k].theta_t, (size_t)naux * ns * sizeof(zd),
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+        } else {
+            std::vector<zd> th((size_t)naux * ns, zmk(0.0, 0.0));
+            for (int j = 0; j < ns; ++j) th[j + (size_t)j * naux] = zmk(1.0, 0.0);
+            for (int k = 0; k < nk; ++k)
+                CK(cudaMemcpy(ctx->hkd[k].theta, th.data(), th.size() * sizeof(zd), cudaMemcpyHostToDevice));
+        }
+        // ---- ground-state current J(t0) with A = 0
+        CK(cudaMemset(ctx->d_st, 0, sizeof(DevState)));
+        {
+            StepArgs a = make_args(ctx, 0);
+            launch_subspace_current(a, 1, ctx->stream);
+            KCHECK();
+        }
+        CK(cudaStreamSynchronize(ctx->stream));
+        *out = ctx;
+        return RTTDDFT_OK;
+    } catch (Fail& f) {
+        if (ctx) {
+            g_last_error = ctx->err;
+            rttddft_destroy(ctx);
+        }
+        return f.code;
+    }
+}
+
+// Chebyshev scaling [lam_c - lam_h, lam_c + lam_h] containing the spectrum of
+// HH(t) = diag(eps) + (A/c).PP + |A|^2/(2c^2) + s dVV_1 for every |A| <= a_max
+// and |s| <= s_max: ||sum_l (A_l/c) PP_l||_2 <= |A| sum_l ||PP_l||_F / c.
+// The coefficients are rebuilt on the device only when the bounds grow.
+static void ensure_interval(rttddft_ctx* ctx, double a_need, double s_need) {
+    if (ctx->a_max_cur >= 0.0 && a_need <= ctx->a_max_cur && s_need <= ctx->s_max_cur) return;
+    const double amax = std::max(a_need, std::max(ctx->a_max_cur, 0.0));
+    const double smax = std::max(s_need, std::max(ctx->s_max_cur, 0.0));
+    const int nk = ctx->nk;
+    const double c = ctx->c, dt = ctx->opt.dt;
+    std::vector<double> lam(2 * nk);
+    double zmax = 0.0;
+    for (int k = 0; k < nk; ++k) {
+        const double bl = amax * (ctx->pnorm[3 * k] + ctx->pnorm[3 * k + 1] + ctx->pnorm[3 * k + 2]) / c;
+        const double a2 = amax * amax / (2 * c * c);
+        const double sd = smax * ctx->dvnorm[k];
+        double lo = ctx->eps_min[k] - bl - sd;
+        double hi = ctx->eps_max[k] + bl + a2 + sd;
+        const double pad = 1e-10 * std::max(1.0, std::max(fabs(lo), fabs(hi)));
+        lo -= pad;
+        hi += pad;
+        lam[2 * k] = 0.5 * (hi + lo);
+        lam[2 * k + 1] = std::max(0.5 * (hi - lo), 1e-12);
+        zmax = std::max(zmax, dt * lam[2 * k + 1]);
+    }
+    const double tol = ctx->opt.cheb_tol > 0 ? ctx->opt.cheb_tol : 1e-16;
+    int nt;
+    if (ctx->opt.propagator == RTTDDFT_PROP_CN) {
+        // Cayley map: pole of 1/(1 + i dt/2 lam) at lam = 2i/dt; coefficients
+        // decay like rho^-n with rho the Bernstein ellipse through the pole
+        double nmax = 3;
+        for (int k = 0; k < nk; ++k) {
+            const cplx xp = (cplx(0.0, 2.0 / dt) - lam[2 * k]) / lam[2 * k + 1];
+            cplx r = xp + std::sqrt(xp * xp - 1.0);
+            if (std::abs(r) < 1.0) r = xp - std::sqrt(xp * xp - 1.0);
+            nmax = std::max(nmax, log(1e-2 * tol) / -log(std::abs(r)) + 4);
+        }
+        nt = (int)ceil(nmax);
+        if (nt > 120) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "Crank-Nicolson series too long for this dt and spectrum");
+    } else {
+        // |J_n(z)| <= (z/2)^n / n!: stop once 2 (z/2)^n / n! < tol/100 with n > z
+        double term = 1.0;
+        int n = 1;
+        for (; n < RTD_MAX_TERMS - 3; ++n) {
+            term *= (0.5 * zmax) / n;
+            if (n > zmax && 2.0 * term < 1e-2 * tol) break;
+        }
+        nt = n + 2;
+    }
+    ctx->nterms = std::max(3, std::min(nt, RTD_MAX_TERMS));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(ctx->d_lam, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice));
+    StepArgs a = make_args(ctx, 0);
+    launch_prep_coef(a, ctx->stream);
+    KCHECK();
+    ctx->a_max_cur = amax;
+    ctx->s_max_cur = smax;
+}
+
+static void ensure_call_cap(rttddft_ctx* ctx, int nsteps) {
+    if (nsteps <= ctx->call_cap) return;
+    CK(cudaStreamSynchronize(ctx->stream));
+    dfree(ctx, ctx->d_a);
+    dfree(ctx, ctx->d_dvs);
+    ctx->call_cap = nsteps;
+    ctx->d_a = dalloc<double>(ctx, 3 * (size_t)nsteps);
+    ctx->d_dvs = dalloc<double>(ctx, (size_t)nsteps);
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+        ctx->g_key_nterms = -1;
+    }
+}
+
+static void run_steps(rttddft_ctx* ctx, int nsteps, int dv_on) {
+    StepArgs a = make_args(ctx, dv_on);
+    StepPlan p = make_plan(ctx);
+    CK(cudaMemsetAsync(&ctx->d_st->cstep, 0, sizeof(int), ctx->stream));
+    const int G = ctx->opt.graph_steps;
+    int done = 0;
+    if (G > 0 && nsteps >= G) {
+        if (!ctx->gexec || ctx->g_key_nterms != ctx->nterms || ctx->g_key_dv != dv_on || ctx->g_key_steps != G) {
+            if (ctx->gexec) {
+                CK(cudaStreamSynchronize(ctx->stream));
+                cudaGraphExecDestroy(ctx->gexec);
+                ctx->gexec = nullptr;
+            }
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            for (int i = 0; i < G; ++i) launch_step(a, p, ctx->stream, &ctx->launches_per_step);
+            cudaError_t e1 = cudaGetLastError();
+            cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &graph);
+            if (e1 != cudaSuccess || e2 != cudaSuccess) {
+                set_err(ctx, std::string("graph capture failed: ") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+                throw Fail{RTTDDFT_ERR_CUDA};
+            }
+            CK(cudaGraphInstantiate(&ctx->gexec, graph, 0));
+            cudaGraphDestroy(graph);
+            ctx->g_key_nterms = ctx->nterms;
+            ctx->g_key_dv = dv_on;
+            ctx->g_key_steps = G;
+        }
+        while (nsteps - done >= G) {
+            CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+            done += G;
+        }
+    }
+    for (; done < nsteps; ++done) launch_step(a, p, ctx->stream, &ctx->launches_per_step);
+    KCHECK();
+}
+
+// Wait for the device and turn a raised device flag into an error code.
+static void sync_and_check(rttddft_ctx* ctx) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    int flag = 0;
+    CK(cudaMemcpy(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(cudaMemset(ctx->d_flag, 0, sizeof(int)));
+        if (flag & 1) fail(ctx, RTTDDFT_ERR_TIMEOUT, "Jacobi eigensolver reached its sweep limit");
+        fail(ctx, RTTDDFT_ERR_ARG, "a pulse sample or dv scale exceeded a_max / s_max");
+    }
+}
+
+static void stage_host(rttddft_ctx* ctx, const double* src, size_t n, double* dst_dev) {
+    if (ctx->stage_ev) CK(cudaEventSynchronize(ctx->stage_ev));
+    if ((int)n > ctx->stage_cap) {
+        if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+        ctx->h_stage = nullptr;
+        CK(cudaMallocHost(&ctx->h_stage, n * sizeof(double)));
+        ctx->stage_cap = (int)n;
+    }
+    if (!ctx->stage_ev) CK(cudaEventCreateWithFlags(&ctx->stage_ev, cudaEventDisableTiming));
+    memcpy(ctx->h_stage, src, n * sizeof(double));
+    CK(cudaMemcpyAsync(dst_dev, ctx->h_stage, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaEventRecord(ctx->stage_ev, ctx->stream));
+}
+
+int rttddft_step(rttddft_ctx* ctx, int nsteps, const double* a_samples, const double* dv_scale) {
+    if (!ctx) return RTTDDFT_ERR_ARG;
+    try {
+        if (nsteps < 1 || !a_samples) fail(ctx, RTTDDFT_ERR_ARG, "nsteps < 1 or a_samples NULL");
+        if (ctx->rec_count + nsteps > ctx->opt.max_record)
+            fail(ctx, RTTDDFT_ERR_ARG, "record capacity exceeded: call rttddft_observables with clear");
+        if (dv_scale && !ctx->dv_set) fail(ctx, RTTDDFT_ERR_ARG, "dv_scale given before rttddft_set_dv");
+        {
+            int flag = 0;  // errors raised by earlier, finished work
+            if (cudaStreamQuery(ctx->stream) == cudaSuccess) {
+                CK(cudaMemcpy(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+                if (flag) sync_and_check(ctx);
+            } else {
+                cudaGetLastError();
+            }
+        }
+        ensure_call_cap(ctx, nsteps);
+        const size_t na = 3 * (size_t)nsteps;
+        double a_need = 0.0, s_need = 0.0;
+        const bool a_dev = is_device_ptr(a_samples);
+        const bool s_dev = dv_scale && is_device_ptr(dv_scale);
+        std::vector<double> tmp;
+        if (a_dev) {
+            CK(cudaMemcpyAsync(ctx->d_a, a_samples, na * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+            if (ctx->opt.a_max > 0) {
+                a_need = ctx->opt.a_max;
+            } else {
+                tmp.resize(na);
+                CK(cudaMemcpyAsync(tmp.data(), a_samples, na * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+                CK(cudaStreamSynchronize(ctx->stream));
+            }
+        } else {
+            if (!finite_all(a_samples, na)) fail(ctx, RTTDDFT_ERR_NONFINITE, "a_samples not finite");
+            tmp.assign(a_samples, a_samples + na);
+        }
+        for (size_t i = 0; i + 2 < tmp.size(); i += 3)
+            a_need = std::max(a_need, sqrt(tmp[i] * tmp[i] + tmp[i + 1] * tmp[i + 1] + tmp[i + 2] * tmp[i + 2]));
+        if (!a_dev && ctx->opt.a_max > 0) {
+            if (a_need > ctx->opt.a_max) fail(ctx, RTTDDFT_ERR_ARG, "|A_k| exceeds a_max");
+            a_need = ctx->opt.a_max;
+        }
+        std::vector<double> stmp;
+        if (dv_scale) {
+            if (s_dev) {
+                CK(cudaMemcpyAsync(ctx->d_dvs, dv_scale, nsteps * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+                if (ctx->opt.s_max > 0) {
+                    s_need = ctx->opt.s_max;
+                } else {
+                    stmp.resize(nsteps);
+                    CK(cudaMemcpyAsync(stmp.data(), dv_scale, nsteps * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+                    CK(cudaStreamSynchronize(ctx->stream));
+                }
+            } else {
+                if (!finite_all(dv_scale, nsteps)) fail(ctx, RTTDDFT_ERR_NONFINITE, "dv_scale not finite");
+                stmp.assign(dv_scale, dv_scale + nsteps);
+            }
+            for (double x : stmp) s_need = std::max(s_need, fabs(x));
+            if (!s_dev && ctx->opt.s_max > 0) {
+                if (s_need > ctx->opt.s_max) fail(ctx, RTTDDFT_ERR_ARG, "|s_k| exceeds s_max");
+                s_need = ctx->opt.s_max;
+            }
+        }
+        ensure_interval(ctx, a_need, s_need);
+        if (!a_dev) stage_host(ctx, a_samples, na, ctx->d_a);
+        if (dv_scale && !s_dev) {
+            // second staging: wait for the first copy before reusing the buffer
+            stage_host(ctx, dv_scale, nsteps, ctx->d_dvs);
+        }
+        if ((a_dev && ctx->opt.a_max > 0) || (s_dev && ctx->opt.s_max > 0))
+            launch_check_samples(ctx->d_a, a_dev ? nsteps : 0, ctx->a_max_cur, ctx->d_dvs,
+                                 s_dev ? nsteps : 0, ctx->s_max_cur, ctx->d_flag, ctx->stream);
+        run_steps(ctx, nsteps, dv_scale ? 1 : 0);
+        ctx->rec_count += nsteps;
+        ctx->steps_done += nsteps;
+        ctx->time += nsteps * ctx->opt.dt;
+        return RTTDDFT_OK;
+    } catch (Fail& f) {
+        return f.code;
+    }
+}
+
+int rttddft_observables(rttddft_ctx* ctx, rttddft_obs* out, int clear) {
+    if (!ctx || !out) return RTTDDFT_ERR_ARG;
+    try {
+        sync_and_check(ctx);
+        const int n = ctx->rec_count;
+        if (out->capacity < n) fail(ctx, RTTDDFT_ERR_ARG, "observable capacity smaller than the records held");
+        std::vector<double> r((size_t)n * RTD_REC_STRIDE);
+        if (n) CK(cudaMemcpy(r.data(), ctx->d_rec, r.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n; ++i) {
+            const double* q = r.data() + (size_t)i * RTD_REC_STRIDE;
+            if (out->t) out->t[i] = q[REC_T];
+            for (int l = 0; l < 3; ++l) {
+                if (out->j) out->j[3 * i + l] = q[REC_J + l];
+                if (out->j_full) out->j_full[3 * i + l] = q[REC_JF + l];
+                if (out->dmu) out->dmu[3 * i + l] = q[REC_DMU + l];
+            }
+            if (out->energy) out->energy[i] = q[REC_E];
+            if (out->norm_dev) out->norm_dev[i] = q[REC_NDEV];
+            if (out->resid) out->resid[i] = q[REC_RES];
+            if (out->dt_cr) out->dt_cr[i] = q[REC_DTCR];
+        }
+        out->count = n;
+        if (clear) {
+            CK(cudaMemsetAsync(&ctx->d_st->rec_count, 0, sizeof(int), ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            ctx->rec_count = 0;
+        }
+        return RTTDDFT_OK;
+    } catch (Fail& f) {
+        return f.code;
+    }
+}
+
+int rttddft_get_state(rttddft_ctx* ctx, int k, double* theta, double* c) {
+    if (!ctx) return RTTDDFT_ERR_ARG;
+    try {
+        if (k < 0 || k >= ctx->nk) fail(ctx, RTTDDFT_ERR_ARG, "k out of range");
+        sync_and_check(ctx);
+        const KDev& K = ctx->hkd[k];
+        if (theta)
+            CK(cudaMemcpy(theta, K.theta, (size_t)ctx->naux * ctx->ns * sizeof(zd), cudaMemcpyDeviceToHost));
+        if (c) {
+            launch_gemm_nn(ctx->gd_expand, ctx->nk, ctx->maxnb, ctx->naux, ctx->ns, 0, nullptr, 0,
+                           ctx->opt.precision == RTTDDFT_PREC_FP32, nullptr, ctx->stream);
+            KCHECK();
+            CK(cudaStreamSynchronize(ctx->stream));
+            CK(cudaMemcpy(c, K.C, (size_t)K.nb * ctx->ns * sizeof(zd), cudaMemcpyDeviceToHost));
+        }
+        return RTTDDFT_OK;
+    } catch (Fail& f) {
+        return f.code;
+    }
+}
+
+int rttddft_set_state(rttddft_ctx* ctx, int k, const double* theta) {
+    if (!ctx) return RTTDDFT_ERR_ARG;
+    try {
+        if (k < 0 || k >= ctx->nk || !theta) fail(ctx, RTTDDFT_ERR_ARG, "k out of range or theta NULL");
+        if (!finite_all(theta, 2 * (size_t)ctx->naux * ctx->ns)) fail(ctx, RTTDDFT_ERR_NONFINITE, "theta not finite");
+        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaMemcpy(ctx->hkd[k].theta, theta, (size_t)ctx->naux * ctx->ns * sizeof(zd), cudaMemcpyHostToDevice));
+        return RTTDDFT_OK;
+    } catch (Fail& f) {
+        return f.code;
+    }
+}
+
+int rttddft_get_aux(rttddft_ctx* ctx, int k, double* caux, double* eps, double* pp) {
+    if (!ctx) return RTTDDFT_ERR_ARG;
+    try {
+        if (k < 0 || k >= ctx->nk) fail(ctx, RTTDDFT_ERR_ARG, "k out of range");
+        CK(cudaStreamSynchronize(ctx->stream));
+        const KDev& K = ctx->hkd[k];
+        const size_t nn = (size_t)ctx->naux * ctx->naux;
+        if (caux) CK(cudaMemcpy(caux, K.caux, (size_t)K.nb * ctx->naux * sizeof(zd), cudaMemcpyDeviceToHost));
+        if (eps) CK(cudaMemcpy(eps, K.eps, ctx->naux * sizeof(double), cudaMemcpyDeviceToHost));
+        if (pp) CK(cudaMemcpy(pp, K.psub, 3 * nn * sizeof(zd), cudaMemcpyDeviceToHost));
+        return RTTDDFT_OK;
+    } catch (Fail& f) {
+        return f.code;
+    }
+}
+
+int rttddft_get_info(rttddft_ctx* ctx, rttddft_info* info) {
+    if (!ctx || !info) return RTTDDFT_ERR_ARG;
+    info->steps_done = ctx->steps_done;
+    info->time = ctx->time;
+    info->n_basis_max = ctx->maxnb;
+    info->cheb_terms = ctx->nterms;
+    info->dt_cr0 = ctx->dtcr0;
+    info->kernel_launches_per_step = ctx->launches_per_step;
+    return RTTDDFT_OK;
+}
+
+int rttddft_set_dv(rttddft_ctx* ctx, const double* dh, const double* dvtab) {
+    if (!ctx) return RTTDDFT_ERR_ARG;
+    try {
+        const AtomTab& at = ctx->at;
+        size_t nblk = 0;
+        for (int a = 0; a < at.n; ++a) nblk += (size_t)at.m[a] * at.m[a];
+        if ((at.n > 0 && !dh) || !dvtab) fail(ctx, RTTDDFT_ERR_ARG, "dh or dvtab NULL");
+        if ((at.n > 0 && !finite_all(dh, 2 * nblk)) || !finite_all(dvtab, 2 * (size_t)ctx->nvt))
+            fail(ctx, RTTDDFT_ERR_NONFINITE, "dh or dvtab not finite");
+        for (int a = 0; a < at.n; ++a)
+            if (herm_dev(dh + 2 * at.boff[a], at.m[a]) > 1e-12)
+                fail(ctx, RTTDDFT_ERR_NOT_HERMITIAN, "dh block not Hermitian");
+        {
+            const cplx* V = (const cplx*)dvtab;
+            double dev = 0.0, mx = 1e-300;
+            for (int i = 0; i < ctx->nvt; ++i) mx = std::max(mx, std::abs(V[i]));
+            for (int i = 0; i < ctx->nvt; ++i) dev = std::max(dev, std::abs(V[i] - std::conj(V[ctx->nvt - 1 - i])));
+            if (dev > 1e-12 * mx) fail(ctx, RTTDDFT_ERR_NOT_HERMITIAN, "dvtab not Hermitian in g");
+        }
+        const int nk = ctx->nk, naux = ctx->naux;
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (!ctx->dv_set) {
+            if (at.n > 0) ctx->d_dh = dalloc<zd>(ctx, nblk);
+            ctx->d_dvtab = dalloc<zd>(ctx, ctx->nvt);
+            ctx->d_vstep = dalloc<zd>(ctx, ctx->nvt);
+            if (ctx->opt.precision == RTTDDFT_PREC_FP32) ctx->d_vstep32 = dalloc<zf>(ctx, ctx->nvt);
+            std::vector<GemmDesc> w, g, gi;
+            std::vector<ToepDesc> td;
+            for (int k = 0; k < nk; ++k) {
+                KDev& K = ctx->hkd[k];
+                K.dvsub = dalloc<zd>(ctx, (size_t)naux * naux);
+                zd* W = dalloc<zd>(ctx, (size_t)std::max(at.lrows, 1) * naux);
+                zd* T = dalloc<zd>(ctx, (size_t)K.ng * naux);
+                for (int a = 0; a < at.n; ++a) {
+                    GemmDesc d{};
+                    d.A = ctx->d_dh + at.boff[a];
+                    d.B = K.lloc + at.loff[a];
+                    d.C = W + at.loff[a];
+                    d.M = at.m[a];
+                    d.K = at.m[a];
+                    d.lda = at.m[a];
+                    d.ldb = at.lrows;
+                    d.ldc = at.lrows;
+                    w.push_back(d);
+                }
+                GemmDesc d{};
+                d.A = K.lloc;
+                d.B = W;
+                d.C = K.dvsub;
+                d.M = naux;
+                d.K = at.lrows;
+                d.lda = std::max(at.lrows, 1);
+                d.ldb = std::max(at.lrows, 1);
+                d.ldc = naux;
+                g.push_back(d);
+                td.push_back(ToepDesc{K.caux, T, K.nb, K.ng});
+                d = GemmDesc{};
+                d.A = K.caux;
+                d.B = T;
+                d.C = K.dvsub;
+                d.M = naux;
+                d.K = K.ng;
+                d.lda = K.nb;
+                d.ldb = K.ng;
+                d.ldc = naux;
+                gi.push_back(d);
+            }
+            ctx->gd_dvw = upload_descs(ctx, w);
+            ctx->gd_dvg = upload_descs(ctx, g);
+            ctx->gd_dvi = upload_descs(ctx, gi);
+            ctx->td_dv = dupload(ctx, td.data(), td.size());
+            CK(cudaMemcpy(ctx->d_kd, ctx->hkd.data(), nk * sizeof(KDev), cudaMemcpyHostToDevice));
+        }
+        if (at.n > 0) CK(cudaMemcpy(ctx->d_dh, dh, nblk * sizeof(zd), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_dvtab, dvtab, ctx->nvt * sizeof(zd), cudaMemcpyHostToDevice));
+        ctx->dv_set = true;
+        // bound || CC^H dV_1 CC ||_F for the Chebyshev scaling (one evaluation with s = 1)
+        {
+            const double one = 1.0;
+            CK(cudaMemcpy(&ctx->d_st->cur_s, &one, sizeof(double), cudaMemcpyHostToDevice));
+            StepArgs a = make_args(ctx, 1);
+            StepPlan p = make_plan(ctx);
+            if (at.n > 0) {
+                launch_gemm_nn(p.gd_dvw, p.n_dvw, p.maxm, p.maxm, naux, 0, nullptr, 0, false, &a.st->cur_s, ctx->stream);
+                launch_gemm_cn(p.gd_dvg, nk, naux, at.lrows, naux, 0, nullptr, 0, false, nullptr, ctx->stream);
+            } else {
+                for (int k = 0; k < nk; ++k) launch_zero(ctx->hkd[k].dvsub, (size_t)naux * naux, ctx->stream);
+            }
+            launch_toeplitz(ctx->d_kd, p.td_dv, nk, ctx->maxng, naux, ctx->d_dvtab, ctx->vt_center, 0, 0,
+                            &a.st->cur_s, ctx->stream);
+            launch_gemm_cn(p.gd_dvi, nk, naux, ctx->maxng, naux, 0, nullptr, 1, false, nullptr, ctx->stream);
+            KCHECK();
+            CK(cudaStreamSynchronize(ctx->stream));
+            for (int k = 0; k < nk; ++k) {
+                std::vector<double> v(2 * (size_t)naux * naux);
+                CK(cudaMemcpy(v.data(), ctx->hkd[k].dvsub, v.size() * sizeof(double), cudaMemcpyDeviceToHost));
+                double f = 0.0;
+                for (double x : v) f += x * x;
+                ctx->dvnorm[k] = sqrt(f);
+            }
+            ctx->a_max_cur = -1.0;  // the spectral interval depends on ||dVV_1||
+        }
+        return RTTDDFT_OK;
+    } catch (Fail& f) {
+        return f.code;
+    }
+}
+
+int rttddft_apply(rttddft_ctx* ctx, int k, int ncols, const double* x, const double* a_vec,
+                  double dv_scale, double* hx, double* sx) {
+    if (!ctx) return RTTDDFT_ERR_ARG;
+    try {
+        if (k < 0 || k >= ctx->nk || ncols < 1 || !x || !a_vec || !hx || !sx)
+            fail(ctx, RTTDDFT_ERR_ARG, "bad argument to rttddft_apply");
+        if (dv_scale != 0.0 && !ctx->dv_set) fail(ctx, RTTDDFT_ERR_ARG, "dv_scale != 0 before rttddft_set_dv");
+        CK(cudaStreamSynchronize(ctx->stream));
+        const bool dev = is_device_ptr(x);
+        const cudaMemcpyKind kin = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        const cudaMemcpyKind kout = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        const KDev& K = ctx->hkd[k];
+        const int ns = ctx->ns, nb = K.nb;
+        DevState hst{};
+        CK(cudaMemcpy(&hst, ctx->d_st, sizeof(DevState), cudaMemcpyDeviceToHost));
+        DevState tmp = hst;
+        for (int l = 0; l < 3; ++l) tmp.cur_a[l] = a_vec[l];
+        tmp.cur_s = dv_scale;
+        tmp.cur_aa = (a_vec[0] * a_vec[0] + a_vec[1] * a_vec[1] + a_vec[2] * a_vec[2]) / (2 * ctx->c * ctx->c);
+        CK(cudaMemcpy(ctx->d_st, &tmp, sizeof(DevState), cudaMemcpyHostToDevice));
+        const int dv_on = (dv_scale != 0.0) ? 1 : 0;
+        StepArgs a = make_args(ctx, dv_on);
+        a.kd = ctx->d_kd + k;
+        a.nk = 1;
+        StepPlan p = make_plan(ctx);
+        p.gd_fwd = ctx->gd_fwd + k;
+        p.maxng = K.ng;
+        if (dv_on) launch_vstep(a, ctx->stream);
+        const zd* xz = (const zd*)x;
+        zd* hz = (zd*)hx;
+        zd* sz = (zd*)sx;
+        for (int c0 = 0; c0 < ncols; c0 += ns) {
+            const int w = std::min(ns, ncols - c0);
+            if (w < ns) launch_zero(K.C, (size_t)nb * ns, ctx->stream);
+            CK(cudaMemcpyAsync(K.C, xz + (size_t)c0 * nb, (size_t)w * nb * sizeof(zd), kin, ctx->stream));
+            launch_operator_pass(a, p, ctx->stream);
+            KCHECK();
+            CK(cudaMemcpyAsync(hz + (size_t)c0 * nb, K.Y, (size_t)w * nb * sizeof(zd), kout, ctx->stream));
+            CK(cudaMemcpyAsync(sz + (size_t)c0 * nb, K.Y + (size_t)ns * nb, (size_t)w * nb * sizeof(zd), kout,
+                               ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+        CK(cudaMemcpy(ctx->d_st, &hst, sizeof(DevState), cudaMemcpyHostToDevice));
+        return RTTDDFT_OK;
+    } catch (Fail& f) {
+        return f.code;
+    }
+}
+
+int rttddft_adjoint(rttddft_ctx* ctx, int nsteps, const double* a_samples, const double* dv_scale,
+                    const double* gdir, int ckpt_every, double* grad, double* dmu_out) {
+    if (!ctx) return RTTDDFT_ERR_ARG;
+    (void)nsteps;
+    (void)a_samples;
+    (void)dv_scale;
+    (void)gdir;
+    (void)ckpt_every;
+    (void)grad;
+    (void)dmu_out;
+    set_err(ctx, "adjoint not built yet");
+    return RTTDDFT_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,255 @@
+// Batched complex contractions used by the step and its set-up.
+//
+// On GB300 the FP64 pipe delivers a few DFMA per clock per SM, so an FP64
+// complex contraction is bound by its multiply-add count even at two
+// right-hand columns; these kernels keep every DFMA useful and spread the
+// work over all SMs (split-K where the output is small).  The FP32-storage
+// variants stream half the bytes and run on the FFMA pipe.
+#include "rtd.h"
+
+// ---------------------------------------------------------------- NN
+// C[m, n] (+)= sum_k A[m, k] B[k, n]; one thread per output row m,
+// a K-chunk of B staged in shared memory, NT columns per pass.
+template <typename TA, typename TC, int NT>
+__global__ void __launch_bounds__(128) k_gemm_nn(const GemmDesc* __restrict__ descs, int N,
+                                                 int kchunk, zd* __restrict__ part, int beta_add,
+                                                 const double* __restrict__ dscale) {
+    const GemmDesc d = descs[blockIdx.z];
+    const int m0 = blockIdx.x * 128;
+    const int k0 = blockIdx.y * kchunk;
+    if (m0 >= d.M || k0 >= d.K) return;
+    const int k1 = min(d.K, k0 + kchunk);
+    const int m = m0 + threadIdx.x;
+    const bool act = m < d.M;
+    const TA* __restrict__ A = (const TA*)d.A;
+    __shared__ TC bs[32][NT];
+    for (int n0 = 0; n0 < N; n0 += NT) {
+        TC acc[NT];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) acc[j] = Cx<TC>::zero();
+        for (int kb = k0; kb < k1; kb += 32) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < 32 * NT; e += 128) {
+                const int kk = e & 31, j = e >> 5;
+                const int kg = kb + kk, n = n0 + j;
+                bs[kk][j] = (kg < k1 && n < N) ? Cx<TC>::from(d.B[kg + (size_t)n * d.ldb])
+                                               : Cx<TC>::zero();
+            }
+            __syncthreads();
+            if (act) {
+                const int kend = min(32, k1 - kb);
+                const TA* ap = A + m + (size_t)kb * d.lda;
+                for (int kk = 0; kk < kend; ++kk) {
+                    const TC a = Cx<TC>::from(ap[(size_t)kk * d.lda]);
+#pragma unroll
+                    for (int j = 0; j < NT; ++j) Cx<TC>::fma(acc[j], a, bs[kk][j]);
+                }
+            }
+        }
+        if (act) {
+            const double sc = dscale ? *dscale : 1.0;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const int n = n0 + j;
+                if (n >= N) break;
+                const zd v = zscale(Cx<TC>::todbl(acc[j]), sc);
+                if (part) {
+                    part[d.part_off + ((size_t)blockIdx.y * N + n) * d.M + m] = v;
+                } else {
+                    zd* c = d.C + m + (size_t)n * d.ldc;
+                    *c = beta_add ? zadd(*c, v) : v;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- CN
+// C[m, n] (+)= sum_k conj(A[k, m]) B[k, n]; one warp per output row m,
+// lanes stride over k (column m of A is contiguous).
+template <typename TA, typename TC, int NT>
+__global__ void __launch_bounds__(256) k_gemm_cn(const GemmDesc* __restrict__ descs, int N,
+                                                 int kchunk, zd* __restrict__ part, int beta_add,
+                                                 const double* __restrict__ dscale) {
+    const GemmDesc d = descs[blockIdx.z];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = blockIdx.x * 8 + warp;
+    const int k0 = blockIdx.y * kchunk;
+    if (m >= d.M || k0 >= d.K) return;
+    const int k1 = min(d.K, k0 + kchunk);
+    const TA* __restrict__ A = (const TA*)d.A + (size_t)m * d.lda;
+    for (int n0 = 0; n0 < N; n0 += NT) {
+        TC acc[NT];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) acc[j] = Cx<TC>::zero();
+        for (int k = k0 + lane; k < k1; k += 32) {
+            const TC a = Cx<TC>::from(A[k]);
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                if (n0 + j < N) Cx<TC>::fmac(acc[j], a, Cx<TC>::from(d.B[k + (size_t)(n0 + j) * d.ldb]));
+            }
+        }
+        const double sc = dscale ? *dscale : 1.0;
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            const zd s = zscale(warp_zsum(Cx<TC>::todbl(acc[j])), sc);
+            const int n = n0 + j;
+            if (lane == j && n < N) {
+                if (part) {
+                    part[d.part_off + ((size_t)blockIdx.y * N + n) * d.M + m] = s;
+                } else {
+                    zd* c = d.C + m + (size_t)n * d.ldc;
+                    *c = beta_add ? zadd(*c, s) : s;
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_split_reduce(const GemmDesc* __restrict__ descs, int N, int kchunk,
+                               const zd* __restrict__ part, int beta_add) {
+    const GemmDesc d = descs[blockIdx.z];
+    const int idx = blockIdx.x * 256 + threadIdx.x;
+    if (idx >= d.M * N) return;
+    const int m = idx % d.M, n = idx / d.M;
+    const int nsp = (d.K + kchunk - 1) / kchunk;
+    zd s = zmk(0.0, 0.0);
+    for (int sp = 0; sp < nsp; ++sp) s = zadd(s, part[d.part_off + ((size_t)sp * N + n) * d.M + m]);
+    zd* c = d.C + m + (size_t)n * d.ldc;
+    *c = beta_add ? zadd(*c, s) : s;
+}
+
+template <typename TA, typename TC>
+static void gemm_nn_t(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kchunk, zd* part,
+                      int beta_add, const double* ds, cudaStream_t s) {
+    if (nb <= 0 || maxM <= 0 || maxK <= 0 || N <= 0) return;
+    if (kchunk <= 0) kchunk = maxK;
+    dim3 grid((maxM + 127) / 128, (maxK + kchunk - 1) / kchunk, nb);
+    if (N <= 2)
+        k_gemm_nn<TA, TC, 2><<<grid, 128, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+    else if (N <= 4)
+        k_gemm_nn<TA, TC, 4><<<grid, 128, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+    else
+        k_gemm_nn<TA, TC, 8><<<grid, 128, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+}
+template <typename TA, typename TC>
+static void gemm_cn_t(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kchunk, zd* part,
+                      int beta_add, const double* ds, cudaStream_t s) {
+    if (nb <= 0 || maxM <= 0 || maxK <= 0 || N <= 0) return;
+    if (kchunk <= 0) kchunk = maxK;
+    dim3 grid((maxM + 7) / 8, (maxK + kchunk - 1) / kchunk, nb);
+    if (N <= 2)
+        k_gemm_cn<TA, TC, 2><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+    else if (N <= 4)
+        k_gemm_cn<TA, TC, 4><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+    else
+        k_gemm_cn<TA, TC, 8><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+}
+
+void launch_gemm_nn(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kchunk, zd* part,
+                    int beta_add, bool a_fp32, const double* ds, cudaStream_t s) {
+    if (a_fp32) gemm_nn_t<zf, zf>(d, nb, maxM, maxK, N, kchunk, part, beta_add, ds, s);
+    else gemm_nn_t<zd, zd>(d, nb, maxM, maxK, N, kchunk, part, beta_add, ds, s);
+}
+void launch_gemm_cn(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kchunk, zd* part,
+                    int beta_add, bool a_fp32, const double* ds, cudaStream_t s) {
+    if (a_fp32) gemm_cn_t<zf, zf>(d, nb, maxM, maxK, N, kchunk, part, beta_add, ds, s);
+    else gemm_cn_t<zd, zd>(d, nb, maxM, maxK, N, kchunk, part, beta_add, ds, s);
+}
+void launch_split_reduce(const GemmDesc* d, int nb, int maxM, int N, int kchunk, const zd* part,
+                         int beta_add, cudaStream_t s) {
+    if (nb <= 0 || maxM <= 0 || N <= 0) return;
+    dim3 grid((maxM * N + 255) / 256, 1, nb);
+    k_split_reduce<<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add);
+}
+
+// ---------------------------------------------------------------- Toeplitz
+// Eq. v_interstitial as an operator: Y[G, n] (+)= sum_G' V~_{G-G'} X[G', n]
+// (+ d_G X[G, n]).  The integer difference G - G' maps to a table offset
+// glin(G) - glin(G') + center because the table box is dense.
+template <int NT>
+__global__ void __launch_bounds__(256) k_toeplitz(const KDev* __restrict__ kd, const ToepDesc* __restrict__ td,
+                                                  int N, const zd* __restrict__ tab, int center,
+                                                  int beta_add, int dmode,
+                                                  const double* __restrict__ dscale) {
+    const int k = blockIdx.z;
+    const int ng = kd[k].ng;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * 8 + warp;
+    if (g >= ng) return;
+    const ToepDesc t = td[k];
+    const int* __restrict__ glin = kd[k].glin;
+    const int base = glin[g] + center;
+    double dg = 0.0;
+    if (dmode == 1) {
+        const double* q = kd[k].gk + 3 * (size_t)g;
+        dg = 0.5 * (q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+    } else if (dmode >= 2 && dmode <= 4) {
+        dg = kd[k].gk[3 * (size_t)g + (dmode - 2)];
+    } else if (dmode == 5) {
+        dg = 1.0;
+    }
+    for (int n0 = 0; n0 < N; n0 += NT) {
+        zd acc[NT];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) acc[j] = zmk(0.0, 0.0);
+        if (tab) {
+            for (int gp = lane; gp < ng; gp += 32) {
+                const zd v = tab[base - glin[gp]];
+#pragma unroll
+                for (int j = 0; j < NT; ++j)
+                    if (n0 + j < N) zfma(acc[j], v, t.X[gp + (size_t)(n0 + j) * t.ldx]);
+            }
+        }
+        const double sc = dscale ? *dscale : 1.0;
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            zd s = zscale(warp_zsum(acc[j]), sc);
+            const int n = n0 + j;
+            if (lane == j && n < N) {
+                if (dmode) s = zadd(s, zscale(t.X[g + (size_t)n * t.ldx], dg));
+                zd* y = t.Y + g + (size_t)n * t.ldy;
+                *y = beta_add ? zadd(*y, s) : s;
+            }
+        }
+    }
+}
+
+void launch_toeplitz(const KDev* kd, const ToepDesc* td, int nk, int maxng, int N, const zd* tab,
+                     int center, int beta_add, int dmode, const double* dscale, cudaStream_t s) {
+    if (nk <= 0 || maxng <= 0 || N <= 0) return;
+    dim3 grid((maxng + 7) / 8, 1, nk);
+    k_toeplitz<8><<<grid, 256, 0, s>>>(kd, td, N, tab, center, beta_add, dmode, dscale);
+}
+
+__global__ void k_zero(zd* p, size_t n) {
+    size_t i = (size_t)blockIdx.x * 256 + threadIdx.x;
+    if (i < n) p[i] = zmk(0.0, 0.0);
+}
+void launch_zero(zd* p, size_t n, cudaStream_t s) {
+    if (n == 0) return;
+    k_zero<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n);
+}
+
+// C[r, c] = B[r, c] for r < M, c < K (batched strided copy; GemmDesc fields B, C, M, K, ldb, ldc)
+__global__ void k_copy_rows(const GemmDesc* __restrict__ descs, int ncol) {
+    const GemmDesc d = descs[blockIdx.z];
+    const int e = blockIdx.x * 256 + threadIdx.x;
+    if (e >= d.M * ncol) return;
+    const int r = e % d.M, c = e / d.M;
+    d.C[r + (size_t)c * d.ldc] = d.B[r + (size_t)c * d.ldb];
+}
+void launch_copy_rows(const GemmDesc* d, int nb, int maxrows, int ncol, cudaStream_t s) {
+    if (nb <= 0 || maxrows <= 0 || ncol <= 0) return;
+    dim3 grid((maxrows * ncol + 255) / 256, 1, nb);
+    k_copy_rows<<<grid, 256, 0, s>>>(d, ncol);
+}
+
+__global__ void k_convert_f32(const zd* __restrict__ src, zf* __restrict__ dst, size_t n) {
+    const size_t i = (size_t)blockIdx.x * 256 + threadIdx.x;
+    if (i < n) dst[i] = tof(src[i]);
+}
+void launch_convert_f32(const zd* src, zf* dst, size_t n, cudaStream_t s) {
+    if (n == 0) return;
+    k_convert_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
+}

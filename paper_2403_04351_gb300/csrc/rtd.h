@@ -1,0 +1,169 @@
+// Internal layout of the rttddft device state and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+#define RTD_MAX_ATOMS 64
+#define RTD_MAX_TERMS 512
+#define RTD_REC_STRIDE 16  // doubles per step record
+#define RB_FULL 16         // row blocks of the full-basis reductions
+
+// Record fields (offsets within one record)
+enum { REC_T = 0, REC_J = 1, REC_JF = 4, REC_DMU = 7, REC_E = 10, REC_NDEV = 11,
+       REC_RES = 12, REC_DTCR = 13 };
+
+// One entry of a batched GEMM; batched kernels index an array of these
+// with blockIdx.z.  Matrices are complex column-major.
+struct GemmDesc {
+    const void* A;   // zd or zf
+    const zd* B;
+    zd* C;
+    int M, K;        // output rows, contraction length
+    int lda, ldb, ldc;
+    size_t part_off; // offset (complex elements) of this entry's split-K partials
+};
+
+// Batched Toeplitz entry: Y[G, n] (+)= sum_G' tab(G - G') X[G', n] + d_G X[G, n]
+struct ToepDesc {
+    const zd* X;
+    zd* Y;
+    int ldx, ldy;
+};
+
+// Per-atom tables
+struct AtomTab {
+    int n;                       // atoms
+    int na[RTD_MAX_ATOMS];       // matching rows N_A
+    int nlo[RTD_MAX_ATOMS];      // local orbitals
+    int m[RTD_MAX_ATOMS];        // na + nlo
+    int aoff[RTD_MAX_ATOMS];     // first row in A / Q / Z
+    int looff[RTD_MAX_ATOMS];    // first LO (relative to N_G)
+    int loff[RTD_MAX_ATOMS];     // first row of the atom in stacked local blocks
+    size_t boff[RTD_MAX_ATOMS];  // offset (complex) of the atom's m x m block
+    int lrows;                   // sum m
+    int ma;                      // sum na
+    int nlo_tot;                 // sum nlo
+};
+
+// Per-k device pointers (an array of these lives in device memory)
+struct KDev {
+    int ng, nb;
+    zd* caux;     // nb x naux
+    zf* caux32;   // nb x naux (FP32 form)
+    zd* amat;     // ma x ng
+    zf* amat32;   // ma x ng (FP32 form)
+    int* glin;    // ng  linear table index of G
+    double* gk;   // ng x 3 (row-major)
+    double* eps;  // naux
+    zd* psub;     // 3 x naux x naux
+    zd* lloc;     // lrows x naux: local coordinates [A_a CC_G ; CC_l] of the aux basis
+    zd* theta;    // naux x ns
+    zd* theta_t;  // naux x ns  CC^H S C
+    zd* ring;     // 3 x naux x ns  Chebyshev vectors
+    zd* acc;      // naux x ns
+    zd* hsub;     // naux x naux
+    zd* dvsub;    // naux x naux  (potential change, when active)
+    zd* C;        // nb x ns
+    zd* Y;        // nb x 2ns  [H C | S C]
+    zd* Q;        // ma x ns
+    zd* Z;        // ma x 2ns
+    zd* gram;     // ns x ns x 2   theta^H theta~ and theta~^H theta~
+    zd* evec;     // naux x naux (EIG form)
+    double* eval; // naux
+    zd* wtmp;     // naux x ns
+    zd* coef;     // RTD_MAX_TERMS Chebyshev coefficients
+    double* lam;  // [2] spectral centre and half-width of HH (written per call)
+    double dtcr_b;// dt_cr from the bounds of the call
+    double pad;
+};
+
+// Device-resident step state
+struct DevState {
+    int cstep;          // step index within the current rttddft_step call
+    int rec_count;
+    long long gstep;    // steps since set-up
+    double t;           // time of the current state
+    double dmu[3];
+    double jind_prev[3];
+    double j_gs[3];
+    double cur_a[3];    // A of the current step
+    double cur_s;       // potential-change scale of the current step
+    double cur_aa;      // |A|^2 / (2 c^2)
+    int err;            // nonzero: a device iteration limit ran out
+    int pad;
+};
+
+// Everything the step kernels need, passed by value
+struct StepArgs {
+    int nk, ns, naux, prop, prec, reproject, nterms, dv_on;
+    int vt_center, nvt, lrows, ma, rec_cap, pad;
+    double dt, c, omega;
+    const KDev* kd;
+    const double* occ;   // ns
+    const double* wk;    // nk
+    const zd* h;         // atom blocks (boff)
+    const zd* o;         // atom blocks (boff)
+    const zd* p;         // 3 blocks per atom at 3*boff
+    const zd* dh;        // potential change blocks (or null)
+    const zd* vtab;      // V~
+    const zf* vtab32;
+    const zd* dvtab;     // dV~ (or null)
+    zd* vstep;           // per-step combined table V~ + s dV~
+    zf* vstep32;
+    const double* a;     // call samples [cstep][3]
+    const double* dvs;   // call dv scales (or null)
+    DevState* st;
+    double* rec;         // records
+    double* part_jmt;    // [nk][lrows][3]
+    double* part_full;   // [nk][ns][RB_FULL][5]
+    double* part_sub;    // [nk][3][naux]
+    double* part_norm;   // [nk][2]
+    const AtomTab* at;   // device copy
+};
+
+// ---- k_linalg.cu
+void launch_gemm_nn(const GemmDesc* d, int nbatch, int maxM, int maxK, int N, int kchunk,
+                    zd* part, int beta_add, bool a_fp32, const double* dscale, cudaStream_t s);
+void launch_gemm_cn(const GemmDesc* d, int nbatch, int maxM, int maxK, int N, int kchunk,
+                    zd* part, int beta_add, bool a_fp32, const double* dscale, cudaStream_t s);
+void launch_split_reduce(const GemmDesc* d, int nbatch, int maxM, int N, int kchunk, const zd* part,
+                         int beta_add, cudaStream_t s);
+// dmode: 0 none, 1 kinetic |G+k|^2/2, 2..4 (G+k)_{x,y,z}, 5 unit
+void launch_toeplitz(const KDev* kd, const ToepDesc* td, int nk, int maxng, int N, const zd* tab,
+                     int center, int beta_add, int dmode, const double* dscale, cudaStream_t s);
+void launch_zero(zd* p, size_t n, cudaStream_t s);
+void launch_copy_rows(const GemmDesc* d, int nbatch, int maxrows, int ncol, cudaStream_t s);
+void launch_convert_f32(const zd* src, zf* dst, size_t n, cudaStream_t s);
+
+// ---- k_step.cu
+struct StepPlan {
+    int maxnb, maxng, nterms;
+    const GemmDesc *gd_expand, *gd_fwd, *gd_proj, *gd_g1, *gd_g2, *gd_evh, *gd_evn;
+    zd* part;
+    int kc_fwd, kc_proj;
+    // potential change (a2)
+    const GemmDesc *gd_dvw, *gd_dvg, *gd_dvi;   // W = dh L, dV = L^H W, dV += C_G^H T
+    const ToepDesc* td_dv;                       // T = dV~ C_G
+    int n_dvw;                                   // entries of gd_dvw (nk * atoms)
+    int maxm;
+    int* d_flag;
+    zd* const* jac_mats; double* const* jac_vals; zd* const* jac_vecs;
+    int max_sweeps;
+};
+void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlaunch);
+void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s);
+void launch_prep_coef(const StepArgs& a, cudaStream_t s);
+void launch_subspace_current(const StepArgs& a, int set_gs, cudaStream_t s);
+void launch_set_cur(const StepArgs& a, cudaStream_t s);
+void launch_vstep(const StepArgs& a, cudaStream_t s);
+void launch_check_samples(const double* a, int na, double amax, const double* s, int ns, double smax,
+                          int* flag, cudaStream_t st);
+int launch_jacobi(zd* const* mats, double* const* vals, zd* const* vecs, int nbatch, int n,
+                  int max_sweeps, int* d_flag, cudaStream_t s);
+void launch_phase_fix(const KDev* kd, int nk, int naux, zd* const* extra, const int* ldextra,
+                      int nextra_rows, cudaStream_t s);
+void launch_scale_cols(zd* const* mats, const double* const* vals, int nbatch, int n, int mode,
+                       cudaStream_t s);

@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Throughput of the RT-TDDFT auxiliary-subspace step on GB300.
+
+One "step" is one time step of the whole hot path for every k-point of the
+workload: HH(t) build, propagation, expansion, operator pass from the
+submatrices, projection and reductions.  The metric is state*steps/s
+(propagated Kohn-Sham states times time steps per second).
+
+ours (default): the CUDA library through its C ABI.  `value` is device time
+(CUDA events on the context's stream, summed over the K timed steps) with
+the inputs resident in HBM and L2 flushed (a 256 MiB write) before every
+step; `e2e` is the same metric through the public API from host buffers
+(pinned sample upload and record read-back inside every timed step).
+reference: the FP64 CPU oracle on the host cores, on a bounded number of
+steps of the same workload.
+
+Multi-GPU (torchrun): every rank runs an independent replica of the
+workload (the k-points of these systems need no exchange); `value` is the
+sum over ranks divided by the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "state*steps/sec per GB300, plain FP64 vs split-precision/batched at stated error"
+UNIT = "state*steps/s"
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; the profiling recipe's table)
+SM_COUNT, SM_MAX_MHZ, FP32_LANES = 152, 2070.0, 128
+
+# dram bytes (read + write) per launch from ncu captures, keyed by kernel slot,
+# form and workload; valid only while the kernel source hashes match.
+TRAFFIC = {}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    for f in ("k_linalg.cu", "k_step.cu", "common.cuh", "rtd.h"):
+        with open(os.path.join(ROOT, "paper_2403_04351_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_work(name, sysd, prec):
+    """(flops, bytes) of one launch of a step kernel, from the shapes alone
+    (the submatrix form, not the dense H the method avoids)."""
+    ns, naux = int(sysd["n_s"]), int(sysd["n_aux"])
+    ma = int(np.sum(sysd["n_a"]))
+    nlo = int(np.sum(sysd["n_lo"]))
+    cb = 8 if prec == "fp32" else 16  # bytes of a stored complex
+    fl, by = 0.0, 0.0
+    for ng in np.asarray(sysd["n_g"], dtype=np.float64):
+        nb = ng + nlo
+        if name == "back_toeplitz":
+            fl += 8 * ns * (ng * ng + 2 * ng * ma) + 4 * ns * ng
+            by += ma * ng * cb + ng * ns * 16 * 3
+        elif name == "gemm_expand":
+            fl += 8 * nb * naux * ns
+            by += nb * naux * cb + nb * ns * 16
+        elif name == "gemm_forward":
+            fl += 8 * ma * ng * ns
+            by += ma * ng * cb
+        elif name == "gemm_project":
+            fl += 8 * nb * naux * ns
+            by += nb * naux * cb + nb * ns * 16
+        elif name == "chebyshev_term":
+            fl += 8 * naux * naux * ns
+            by += naux * naux * 16
+        elif name == "local_mt":
+            m = (ma + nlo)
+            fl += 8 * 5 * ns * m * m / max(1, int(sysd["n_atoms"]))
+            by += 5 * m * m * 16 / max(1, int(sysd["n_atoms"]))
+    return fl, by
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    from paper_2403_04351_gb300 import Context, build
+    from synth import make_system, pulse_samples
+    build()
+    s = make_system(args.workload)
+    cfg = s["cfg"]
+    K, W = args.steps, args.warmup
+    a_all = pulse_samples(s, n_steps=max(cfg.n_steps, K + W + 64))
+    a0 = float(cfg.a0)
+    # a dedicated stream: the library, the L2 flush and the events all run on it
+    # (torch's default stream has handle 0, which the library would replace)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    assert stream.cuda_stream != 0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    n_states = int(s["n_s"]) * int(s["n_k"])
+
+    def timed_form(prec, nsteps, nwarm):
+        ctx = Context(s, precision=prec, graph_steps=1, a_max=a0, max_record=nsteps + nwarm + 8,
+                      stream=stream.cuda_stream)
+        assert ctx.stream_handle() == stream.cuda_stream
+        d_a = torch.from_numpy(a_all[:nsteps + nwarm]).to(dev)
+        for i in range(nwarm):
+            flush.zero_()
+            ctx.step(d_a[i:i + 1])
+        torch.cuda.synchronize(dev)
+        ctx.observables(clear=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(nsteps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i in range(nsteps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            ctx.step(d_a[nwarm + i:nwarm + i + 1])
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        if world > 1:
+            torch.distributed.barrier()
+        dev_s = sum(e0.elapsed_time(e1) for e0, e1 in ev) * 1e-3
+        obs = ctx.observables(clear=True)
+        return ctx, dev_s, wall, obs
+
+    with ClockSampler(local_rank) as clk:
+        ctx, dev_s, wall, obs = timed_form(args.precision, K, W)
+    clocks = clk.summary()
+    # slowest rank sets the time
+    times = torch.tensor([dev_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
+    dev_max = float(times.item())
+    value = n_states * K * world / dev_max
+
+    # per-kernel trace (CUDA events after every launch, L2 flushed before each step)
+    tr = {}
+    for i in range(args.trace_steps):
+        flush.zero_()
+        for name, ms in ctx.trace(a_all[W + K + i:W + K + i + 1]):
+            t = tr.setdefault(name, [0.0, 0])
+            t[0] += ms
+            t[1] += 1
+    ctx.observables(clear=True)
+    # e2e: host samples (pinned) in, the step's record out, every step
+    pinned = torch.from_numpy(a_all[:K + W]).pin_memory()
+    e2e_s = 0.0
+    for i in range(W + K):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ctx.step(pinned[i:i + 1].numpy())
+        rec = ctx.observables(clear=True)
+        if i >= W:
+            e2e_s += time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = n_states * K * world / float(e2e_t.item())
+    info = ctx.info()
+    ctx.close()
+
+    # the plain FP64 GPU step, for the ratio the target is stated against
+    fp64 = None
+    if args.precision != "fp64" and args.fp64_steps > 0:
+        c64, d64, _, _ = timed_form("fp64", args.fp64_steps, 3)
+        c64.close()
+        fp64 = {"value": n_states * args.fp64_steps / d64, "ms_per_step": d64 / args.fp64_steps * 1e3,
+                "steps": args.fp64_steps}
+
+    # roofline of the dominant kernel slot
+    dom = max(tr.items(), key=lambda kv: kv[1][0])[0] if tr else None
+    roof = None
+    if dom:
+        dur = tr[dom][0] / tr[dom][1] * 1e-3  # seconds per launch
+        fl, by = algorithmic_work(dom, s, args.precision)
+        hbm, src = _peaks()
+        if dom in ("gemm_expand", "gemm_project", "gemm_forward") and args.precision == "fp32":
+            ach = by / dur / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "peak_source": src}
+        else:
+            if args.precision == "fp64" or dom in ("chebyshev_term",):
+                peak = FP64_PEAK_TFLOPS
+                src = "recipe FP64 nominal"
+            else:
+                peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+                src = "152 SM x 128 FP32 lanes x 2 x 2070 MHz"
+            ach = fl / dur / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "peak_source": src}
+        key = (dom, args.precision, args.workload, _src_hash())
+        roof["kernel"] = dom
+        roof["ms_per_launch"] = dur * 1e3
+        roof["traffic"] = TRAFFIC.get(key)
+    share = {n: round(v[0] / sum(x[0] for x in tr.values()), 4) for n, v in tr.items()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": dev_max / K * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic (seeded generator shaped like the paper's H2 cell)",
+        "config": {"workload": args.workload, "n_k": int(s["n_k"]), "n_basis": int(s["n_g"][0]) +
+                   int(np.sum(s["n_lo"])), "n_states": int(s["n_s"]), "n_aux": int(s["n_aux"]),
+                   "dt": float(s["dt"]), "precision_form": args.precision,
+                   "propagator": "chebyshev (exact exponential to FP64 round-off)",
+                   "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 8,
+                "d2h_bytes_per_step": 16 * 8},
+        "gpu_launches": int(info["kernel_launches_per_step"]) * K,
+        "clocks": clocks,
+        "roofline": roof,
+        "kernel_share": share,
+        "fp64": fp64,
+        "wall_s": wall,
+        "observables_last": {"dmu": obs["dmu"][-1].tolist() if len(obs["t"]) else None,
+                             "norm_dev_max": float(np.max(obs["norm_dev"])) if len(obs["t"]) else None},
+    }
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        line["cpu_baseline"] = cpu_baseline(s, a_all, args.cpu_seconds)
+    return line
+
+
+def cpu_baseline(s, a_all, budget_s):
+    """The oracle, as it stands, on the host cores: set-up excluded, then as
+    many steps as fit in about `budget_s` seconds."""
+    from oracle import Oracle
+    cores = os.cpu_count()
+    orc = Oracle(s)
+    t0 = time.perf_counter()
+    n = 0
+    thetas = None
+    while True:
+        r = orc.run(a_all[n:n + 1], s["dt"], thetas=thetas)
+        thetas = r["theta"]
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": int(s["n_s"]) * int(s["n_k"]) * n / dt, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": "%d steps of %s after set-up (set-up excluded), numpy/OpenBLAS threads = %d"
+                      % (n, s["name"], cores)}
+
+
+def run_reference(args):
+    from oracle import Oracle
+    from synth import make_system, pulse_samples
+    s = make_system(args.workload)
+    a = pulse_samples(s, n_steps=max(s["cfg"].n_steps, args.steps + args.warmup + 1))
+    orc = Oracle(s)
+    thetas = None
+    for i in range(args.warmup):
+        thetas = orc.run(a[i:i + 1], s["dt"], thetas=thetas)["theta"]
+    nsteps = args.steps if args.ref_steps <= 0 else min(args.steps, args.ref_steps)
+    t0 = time.perf_counter()
+    r = orc.run(a[args.warmup:args.warmup + nsteps], s["dt"], thetas=thetas)
+    dt = time.perf_counter() - t0
+    v = int(s["n_s"]) * int(s["n_k"]) * nsteps / dt
+    cores = os.cpu_count()
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+            "steps": nsteps, "warmup": args.warmup, "ms_per_step": dt / nsteps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator shaped like the paper's H2 cell)",
+            "config": {"workload": args.workload, "precision_form": "fp64 oracle"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d steps of %s (set-up excluded)" % (nsteps, s["name"])},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "dmu_last": r["dmu"][-1].tolist()}
+
+
+def main():
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    p.add_argument("--workload", default="h2_6000")
+    p.add_argument("--fp64-steps", type=int, default=50)
+    p.add_argument("--trace-steps", type=int, default=5)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--ref-steps", type=int, default=40)
+    args = p.parse_args()
+    if args.warmup < 3:
+        p.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+                os.environ.setdefault(v, str(os.cpu_count()))
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -221,6 +221,23 @@ RTTDDFT_API int rttddft_get_info(rttddft_ctx* ctx, rttddft_info* info);
 RTTDDFT_API int rttddft_adjoint(rttddft_ctx* ctx, int nsteps, const double* a_samples, const double* dv_scale,
                     const double* gdir, int ckpt_every, double* grad, double* dmu_out);
 
+/* Per-kernel timing of the step: runs `nsteps` steps exactly as rttddft_step
+ * does, but with kernels launched one by one (no graph) and a CUDA event
+ * recorded on the context's stream after each launch.  out->names[i] (static
+ * strings owned by the library) and out->ms[i] (device milliseconds summed
+ * over the steps) describe the i-th launch slot of a step; out->count slots
+ * are filled, at most out->capacity.  The steps advance the state and the
+ * record like rttddft_step.  a_samples, dv_scale: host arrays.
+ * Errors: ERR_ARG, ERR_CUDA. */
+typedef struct {
+    int capacity;        /* in: slots the arrays hold */
+    int count;           /* out: launch slots per step */
+    const char** names;  /* [capacity] out */
+    double* ms;          /* [capacity] out, summed over the steps */
+} rttddft_trace;
+RTTDDFT_API int rttddft_trace_steps(rttddft_ctx* ctx, int nsteps, const double* a_samples,
+                                    const double* dv_scale, rttddft_trace* out);
+
 RTTDDFT_API void rttddft_destroy(rttddft_ctx* ctx);
 
 /* Text of the last error on `ctx` (or of the last failed rttddft_setup in

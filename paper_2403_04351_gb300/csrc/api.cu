@@ -1423,6 +1423,72 @@ int rttddft_apply(rttddft_ctx* ctx, int k, int ncols, const double* x, const dou
     }
 }
 
+int rttddft_trace_steps(rttddft_ctx* ctx, int nsteps, const double* a_samples, const double* dv_scale,
+                        rttddft_trace* out) {
+    if (!ctx) return RTTDDFT_ERR_ARG;
+    std::vector<cudaEvent_t> ev;
+    try {
+        if (!out || !out->names || !out->ms || out->capacity < 1 || nsteps < 1 || !a_samples)
+            fail(ctx, RTTDDFT_ERR_ARG, "bad argument to rttddft_trace_steps");
+        if (ctx->rec_count + nsteps > ctx->opt.max_record)
+            fail(ctx, RTTDDFT_ERR_ARG, "record capacity exceeded: call rttddft_observables with clear");
+        if (dv_scale && !ctx->dv_set) fail(ctx, RTTDDFT_ERR_ARG, "dv_scale given before rttddft_set_dv");
+        sync_and_check(ctx);
+        ensure_call_cap(ctx, nsteps);
+        const size_t na = 3 * (size_t)nsteps;
+        double a_need = 0.0, s_need = 0.0;
+        for (size_t i = 0; i < na; i += 3)
+            a_need = std::max(a_need, sqrt(a_samples[i] * a_samples[i] + a_samples[i + 1] * a_samples[i + 1] +
+                                           a_samples[i + 2] * a_samples[i + 2]));
+        if (ctx->opt.a_max > 0) a_need = std::max(a_need, ctx->opt.a_max);
+        if (dv_scale) {
+            for (int i = 0; i < nsteps; ++i) s_need = std::max(s_need, fabs(dv_scale[i]));
+            if (ctx->opt.s_max > 0) s_need = std::max(s_need, ctx->opt.s_max);
+        }
+        ensure_interval(ctx, a_need, s_need);
+        CK(cudaMemcpy(ctx->d_a, a_samples, na * sizeof(double), cudaMemcpyHostToDevice));
+        if (dv_scale) CK(cudaMemcpy(ctx->d_dvs, dv_scale, nsteps * sizeof(double), cudaMemcpyHostToDevice));
+        const int dv_on = dv_scale ? 1 : 0;
+        StepArgs a = make_args(ctx, dv_on);
+        StepPlan p = make_plan(ctx);
+        CK(cudaMemsetAsync(&ctx->d_st->cstep, 0, sizeof(int), ctx->stream));
+        const int cap = 256;
+        ev.resize(cap + 1);
+        for (auto& e : ev) CK(cudaEventCreate(&e));
+        std::vector<const char*> names(cap);
+        std::vector<double> acc(cap, 0.0);
+        int slots = 0;
+        for (int i = 0; i < nsteps; ++i) {
+            TraceHook tr{ev.data() + 1, names.data(), 0, cap};
+            CK(cudaEventRecord(ev[0], ctx->stream));
+            launch_step(a, p, ctx->stream, &ctx->launches_per_step, &tr);
+            KCHECK();
+            CK(cudaStreamSynchronize(ctx->stream));
+            for (int j = 0; j < tr.n; ++j) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, ev[j], ev[j + 1]));
+                acc[j] += ms;
+            }
+            slots = tr.n;
+        }
+        const int n = std::min(slots, out->capacity);
+        for (int j = 0; j < n; ++j) {
+            out->names[j] = names[j];
+            out->ms[j] = acc[j];
+        }
+        out->count = n;
+        for (auto& e : ev) cudaEventDestroy(e);
+        ctx->rec_count += nsteps;
+        ctx->steps_done += nsteps;
+        ctx->time += nsteps * ctx->opt.dt;
+        return RTTDDFT_OK;
+    } catch (Fail& f) {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        return f.code;
+    }
+}
+
 int rttddft_adjoint(rttddft_ctx* ctx, int nsteps, const double* a_samples, const double* dv_scale,
                     const double* gdir, int ckpt_every, double* grad, double* dmu_out) {
     if (!ctx) return RTTDDFT_ERR_ARG;

@@ -766,15 +766,25 @@ void launch_subspace_current(const StepArgs& a, int set_gs, cudaStream_t s) {
     k_finalize<<<1, 256, 0, s>>>(a, set_gs);
 }
 
-void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s) {
+static inline void mark(TraceHook* tr, const char* name, cudaStream_t s) {
+    if (!tr || tr->n >= tr->cap) return;
+    tr->names[tr->n] = name;
+    cudaEventRecord(tr->ev[tr->n], s);
+    tr->n += 1;
+}
+
+void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr) {
     const bool f32 = a.prec == 1;
     // Q = A C_G (matching coefficients applied to the plane-wave rows)
     launch_gemm_nn(p.gd_fwd, a.nk, a.ma, p.maxng, a.ns, p.kc_fwd, p.part, 0, f32, nullptr, s);
+    mark(tr, "gemm_forward", s);
     launch_split_reduce(p.gd_fwd, a.nk, a.ma, a.ns, p.kc_fwd, p.part, 0, s);
+    mark(tr, "split_reduce_forward", s);
     if (a.lrows > 0) {
         dim3 g((a.lrows + 7) / 8, 1, a.nk);
         if (a.ns <= 2) k_local<2><<<g, 256, 0, s>>>(a);
         else k_local<4><<<g, 256, 0, s>>>(a);
+        mark(tr, "local_mt", s);
     }
     {
         dim3 g((p.maxng + 7) / 8, 1, a.nk);
@@ -787,34 +797,44 @@ void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s) 
             else if (a.ns <= 4) k_back<zd, zd, zd, 4><<<g, 256, 0, s>>>(a);
             else k_back<zd, zd, zd, 8><<<g, 256, 0, s>>>(a);
         }
+        mark(tr, "back_toeplitz", s);
     }
 }
 
-void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlaunch) {
+void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlaunch, TraceHook* tr) {
     int nl = 0;
     const bool f32 = a.prec == 1;
     const int nn = a.naux * a.naux;
     k_set_cur<<<1, 1, 0, s>>>(a);
+    mark(tr, "set_cur", s);
     ++nl;
     if (a.dv_on) {
         // Eq. v_MT and Eq. v_interstitial rebuilt from the scaled blocks:
         // dVV = L^H (s dh) L + CC_G^H (s dV~ * CC_G)
         k_vstep<<<(a.nvt + 255) / 256, 256, 0, s>>>(a);
+        mark(tr, "dv_table", s);
         launch_gemm_nn(p.gd_dvw, p.n_dvw, p.maxm, p.maxm, a.naux, 0, nullptr, 0, false,
                        &a.st->cur_s, s);
+        mark(tr, "dv_mt_blocks", s);
         launch_gemm_cn(p.gd_dvg, a.nk, a.naux, a.lrows, a.naux, 0, nullptr, 0, false, nullptr, s);
+        mark(tr, "dv_mt_project", s);
         launch_toeplitz(a.kd, p.td_dv, a.nk, p.maxng, a.naux, a.dvtab, a.vt_center, 0, 0,
                         &a.st->cur_s, s);
+        mark(tr, "dv_interstitial_toeplitz", s);
         launch_gemm_cn(p.gd_dvi, a.nk, a.naux, p.maxng, a.naux, 0, nullptr, 1, false, nullptr, s);
+        mark(tr, "dv_interstitial_project", s);
         nl += 5;
     }
     k_hsub<<<dim3((nn + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
+    mark(tr, "hsub", s);
     ++nl;
     if (a.prop == 1) {
         launch_jacobi(p.jac_mats, p.jac_vals, p.jac_vecs, a.nk, a.naux, p.max_sweeps, p.d_flag, s);
+        mark(tr, "jacobi", s);
         launch_gemm_cn(p.gd_evh, a.nk, a.naux, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
         k_eigphase<<<dim3((a.naux * a.ns + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
         launch_gemm_nn(p.gd_evn, a.nk, a.naux, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
+        mark(tr, "eig_apply", s);
         nl += 4;
     } else {
         dim3 g((a.naux + 7) / 8, 1, a.nk);
@@ -823,28 +843,42 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
             if (a.ns <= 2) k_cheb<2><<<g, 256, 0, s>>>(a, t, last);
             else if (a.ns <= 4) k_cheb<4><<<g, 256, 0, s>>>(a, t, last);
             else k_cheb<8><<<g, 256, 0, s>>>(a, t, last);
+            mark(tr, "chebyshev_term", s);
             ++nl;
         }
     }
     // C = CC theta (Eq. approximation_coefficients)
     launch_gemm_nn(p.gd_expand, a.nk, p.maxnb, a.naux, a.ns, 0, nullptr, 0, f32, nullptr, s);
+    mark(tr, "gemm_expand", s);
     ++nl;
-    launch_operator_pass(a, p, s);
+    launch_operator_pass(a, p, s, tr);
     nl += 4;
     k_reduce_full<<<dim3(RB_FULL, a.ns, a.nk), 256, 0, s>>>(a);
+    mark(tr, "reduce_full", s);
     ++nl;
     // theta~ = CC^H (S C)
     launch_gemm_cn(p.gd_proj, a.nk, a.naux, p.maxnb, a.ns, p.kc_proj, p.part, 0, f32, nullptr, s);
+    mark(tr, "gemm_project", s);
     launch_split_reduce(p.gd_proj, a.nk, a.naux, a.ns, p.kc_proj, p.part, 0, s);
+    mark(tr, "split_reduce_project", s);
     launch_gemm_cn(p.gd_g1, a.nk, a.ns, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
+    mark(tr, "gram", s);
     k_normred<<<a.nk, 256, 0, s>>>(a);
+    mark(tr, "norm_residual", s);
     nl += 4;
     if (a.reproject) {
         launch_gemm_cn(p.gd_g2, a.nk, a.ns, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
         k_reproj<<<dim3((a.naux * a.ns + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
+        mark(tr, "reproject", s);
         nl += 2;
     }
-    launch_subspace_current(a, 0, s);
+    {
+        dim3 g((3 * a.naux + 7) / 8, 1, a.nk);
+        k_subj<<<g, 256, 0, s>>>(a);
+        mark(tr, "subspace_current", s);
+        k_finalize<<<1, 256, 0, s>>>(a, 0);
+        mark(tr, "finalize", s);
+    }
     nl += 2;
     if (nlaunch) *nlaunch = nl;
 }

@@ -153,8 +153,15 @@ struct StepPlan {
     zd* const* jac_mats; double* const* jac_vals; zd* const* jac_vecs;
     int max_sweeps;
 };
-void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlaunch);
-void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s);
+// Optional per-kernel tracing: an event is recorded after every launch of a step.
+struct TraceHook {
+    cudaEvent_t* ev;     // capacity events
+    const char** names;  // name of the kernel that ends at ev[i]
+    int n, cap;
+};
+void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlaunch,
+                 TraceHook* tr = nullptr);
+void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr = nullptr);
 void launch_prep_coef(const StepArgs& a, cudaStream_t s);
 void launch_subspace_current(const StepArgs& a, int set_gs, cudaStream_t s);
 void launch_set_cur(const StepArgs& a, cudaStream_t s);

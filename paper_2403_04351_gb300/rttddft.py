@@ -26,8 +26,8 @@ AUX = {"ritz": 0, "given": 1}
 
 EXPORTED = ["rttddft_default_options", "rttddft_setup", "rttddft_step", "rttddft_observables",
             "rttddft_set_dv", "rttddft_apply", "rttddft_get_state", "rttddft_set_state",
-            "rttddft_get_aux", "rttddft_get_info", "rttddft_adjoint", "rttddft_destroy",
-            "rttddft_last_error", "rttddft_version"]
+            "rttddft_get_aux", "rttddft_get_info", "rttddft_adjoint", "rttddft_trace_steps",
+            "rttddft_destroy", "rttddft_last_error", "rttddft_version"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -61,6 +61,11 @@ class rttddft_info(ctypes.Structure):
     _fields_ = [("steps_done", ctypes.c_longlong), ("time", ctypes.c_double),
                 ("n_basis_max", ctypes.c_int), ("cheb_terms", ctypes.c_int),
                 ("dt_cr0", ctypes.c_double), ("kernel_launches_per_step", ctypes.c_int)]
+
+
+class rttddft_trace(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int), ("count", ctypes.c_int),
+                ("names", ctypes.POINTER(ctypes.c_char_p)), ("ms", _dp)]
 
 
 class RttddftError(RuntimeError):
@@ -105,6 +110,8 @@ def load_library(path=None):
     lib.rttddft_get_info.restype = ctypes.c_int
     lib.rttddft_adjoint.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_int, vp, vp]
     lib.rttddft_adjoint.restype = ctypes.c_int
+    lib.rttddft_trace_steps.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.POINTER(rttddft_trace)]
+    lib.rttddft_trace_steps.restype = ctypes.c_int
     lib.rttddft_destroy.argtypes = [vp]
     lib.rttddft_destroy.restype = None
     lib.rttddft_last_error.argtypes = [vp]
@@ -190,6 +197,11 @@ def rttddft_adjoint(ctx, nsteps, a_samples, dv_scale, gdir, ckpt_every, grad, dm
                                                _ptr(dmu_out)))
 
 
+def rttddft_trace_steps(ctx, nsteps, a_samples, dv_scale, trace):
+    _check(ctx, load_library().rttddft_trace_steps(ctx, int(nsteps), _ptr(a_samples), _ptr(dv_scale),
+                                                   ctypes.byref(trace)))
+
+
 def rttddft_destroy(ctx):
     load_library().rttddft_destroy(ctx)
 
@@ -262,7 +274,12 @@ class Context:
         o.s_max = float(s_max)
         self.options = o
         self.max_record = int(max_record)
+        self._stream = stream
         self.ctx = rttddft_setup(s, o, stream)
+
+    def stream_handle(self):
+        """The cudaStream_t given at set-up (0/None: the library's own stream)."""
+        return self._stream or 0
 
     def step(self, a_samples, dv_scale=None):
         a = a_samples
@@ -342,6 +359,20 @@ class Context:
         d = None if dv_scale is None else np.ascontiguousarray(dv_scale, dtype=np.float64)
         rttddft_adjoint(self.ctx, n, a, d, g, int(ckpt_every), grad, dmu)
         return grad, dmu
+
+    def trace(self, a_samples, dv_scale=None):
+        """Per-launch device milliseconds of the steps, summed over the samples."""
+        a = np.ascontiguousarray(a_samples, dtype=np.float64)
+        d = None if dv_scale is None else np.ascontiguousarray(dv_scale, dtype=np.float64)
+        cap = 256
+        t = rttddft_trace()
+        t.capacity = cap
+        names = (ctypes.c_char_p * cap)()
+        ms = np.zeros(cap)
+        t.names = names
+        t.ms = ms.ctypes.data_as(_dp)
+        rttddft_trace_steps(self.ctx, a.shape[0], a, d, t)
+        return [(names[i].decode(), float(ms[i])) for i in range(t.count)]
 
     def close(self):
         if getattr(self, "ctx", None):

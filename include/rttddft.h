@@ -198,6 +198,26 @@ RTTDDFT_API int rttddft_set_dv(rttddft_ctx* ctx, const double* dh, const double*
 RTTDDFT_API int rttddft_apply(rttddft_ctx* ctx, int k, int ncols, const double* x, const double* a_vec,
                   double dv_scale, double* hx, double* sx);
 
+/* The same operator as rttddft_apply, for callers that must not allocate
+ * device memory at the time of the call (a CUDA graph being captured, an
+ * allocator-free thread, memory owned by another pool).  The paper has no
+ * counterpart; this is a property of the library, not of the method.
+ * x, hx, sx must be device pointers (complex, N_basis(k) x ncols,
+ * column-major); the call is asynchronous on the context's stream and does
+ * not wait for the device.  Its scratch is one 16 MiB array in device memory
+ * that every GPU loading the library holds until the process exits; the
+ * first call on each device looks up that array's address (make that first
+ * call before starting any stream capture).  Every call shares the array, so
+ * calls whose work overlaps on the GPU (different streams or contexts) race;
+ * calls on one stream are ordered.  A k-point whose scratch need exceeds
+ * 16 MiB (about N_basis x N_states x 48 bytes plus the matching-coefficient
+ * partials) is rejected with ERR_ARG and a message giving the need.
+ * It never calls cudaMalloc or cudaFree.
+ * Errors: ERR_ARG (bad sizes, NULL or host pointers, scratch limit),
+ * ERR_CUDA, ERR_UNSUPPORTED (device ordinal above 255). */
+RTTDDFT_API int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const double* x,
+                                      const double* a_vec, double dv_scale, double* hx, double* sx);
+
 /* State of k-point k.  theta: complex n_aux x n_s; c: NULL or complex
  * N_basis(k) x n_s (the last expanded C).  Host pointers. */
 RTTDDFT_API int rttddft_get_state(rttddft_ctx* ctx, int k, double* theta, double* c);

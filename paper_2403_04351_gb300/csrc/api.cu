@@ -1504,3 +1504,144 @@ int rttddft_adjoint(rttddft_ctx* ctx, int nsteps, const double* a_samples, const
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ operator apply without allocation
+// Some callers cannot call cudaMalloc at the moment they need the operator:
+// code running while a CUDA graph is being captured, allocator-free
+// real-time or callback threads, or processes whose device memory is owned
+// by another pool.  rttddft_apply_noalloc serves them: its scratch (the
+// staged input block, Q = A X, the muffin-tin products, the split-K partials
+// and the small descriptors) comes from one file-scope device array that
+// every GPU loading this library holds until the process exits.  The caller
+// passes device input and output buffers.
+#define RTD_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)  // 16 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RTD_NOALLOC_SCRATCH_BYTES];
+
+#include <mutex>
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[256];  // device address of the array, per device ordinal
+
+// Small host structs reach the scratch array as kernel parameters (no
+// staging copy from pageable memory).
+struct Blob512 {
+    unsigned char b[512];
+};
+__global__ void k_put_blob(unsigned char* dst, Blob512 src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src.b[i];
+}
+template <typename T>
+static void put_struct(unsigned char* dst, const T& v, cudaStream_t s) {
+    static_assert(sizeof(T) <= sizeof(Blob512), "struct too large for a blob");
+    Blob512 b;
+    memset(&b, 0, sizeof(b));
+    memcpy(b.b, &v, sizeof(T));
+    k_put_blob<<<1, 128, 0, s>>>(dst, b, (int)sizeof(T));
+}
+
+// Resolve the array's device address for the current device (first call on
+// each device; later calls reuse it).
+static unsigned char* noalloc_base(rttddft_ctx* ctx) {
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "device ordinal above 255");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            fail(ctx, RTTDDFT_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    return (unsigned char*)g_noalloc_addr[dev];
+}
+
+extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const double* x, const double* a_vec,
+                                     double dv_scale, double* hx, double* sx) {
+    if (!ctx) return RTTDDFT_ERR_ARG;
+    try {
+        if (k < 0 || k >= ctx->nk || ncols < 1 || !x || !a_vec || !hx || !sx)
+            fail(ctx, RTTDDFT_ERR_ARG, "bad argument to rttddft_apply_noalloc");
+        if (dv_scale != 0.0 && !ctx->dv_set) fail(ctx, RTTDDFT_ERR_ARG, "dv_scale != 0 before rttddft_set_dv");
+        if (!is_device_ptr(x) || !is_device_ptr(hx) || !is_device_ptr(sx))
+            fail(ctx, RTTDDFT_ERR_ARG, "rttddft_apply_noalloc takes device pointers for x, hx and sx");
+        const KDev& K = ctx->hkd[k];
+        const int ns = ctx->ns, nb = K.nb, ma = std::max(ctx->at.ma, 1), ng = K.ng;
+        const int dv_on = (dv_scale != 0.0) ? 1 : 0;
+        const bool f32 = ctx->opt.precision == RTTDDFT_PREC_FP32;
+        const int splits = (ng + ctx->kc_fwd - 1) / ctx->kc_fwd;
+        // carve the scratch array
+        size_t off = 0;
+        auto take = [&](size_t bytes) {
+            off = (off + 255) & ~(size_t)255;
+            const size_t at = off;
+            off += std::max(bytes, (size_t)1);
+            return at;
+        };
+        const size_t o_kd = take(sizeof(KDev)), o_gd = take(sizeof(GemmDesc)), o_st = take(sizeof(DevState));
+        const size_t o_c = take((size_t)nb * ns * sizeof(zd)), o_y = take((size_t)nb * 2 * ns * sizeof(zd));
+        const size_t o_q = take((size_t)ma * ns * sizeof(zd)), o_z = take((size_t)ma * 2 * ns * sizeof(zd));
+        const size_t o_part = take((size_t)splits * ns * ma * sizeof(zd));
+        const size_t o_jmt = take((size_t)std::max(ctx->at.lrows, 1) * 3 * sizeof(double));
+        const size_t o_vs = dv_on ? take((size_t)ctx->nvt * sizeof(zd)) : 0;
+        const size_t o_vs32 = (dv_on && f32) ? take((size_t)ctx->nvt * sizeof(zf)) : 0;
+        if (off > RTD_NOALLOC_SCRATCH_BYTES)
+            fail(ctx, RTTDDFT_ERR_ARG, "rttddft_apply_noalloc needs " + std::to_string(off) +
+                                           " bytes of scratch for this k-point; the static limit is " +
+                                           std::to_string(RTD_NOALLOC_SCRATCH_BYTES) + " bytes");
+        unsigned char* base = noalloc_base(ctx);
+        cudaStream_t st = ctx->stream;
+        KDev kc = K;
+        kc.C = (zd*)(base + o_c);
+        kc.Y = (zd*)(base + o_y);
+        kc.Q = (zd*)(base + o_q);
+        kc.Z = (zd*)(base + o_z);
+        GemmDesc g{};
+        g.A = f32 ? (const void*)K.amat32 : (const void*)K.amat;
+        g.B = kc.C;
+        g.C = kc.Q;
+        g.M = ctx->at.ma;
+        g.K = ng;
+        g.lda = ma;
+        g.ldb = nb;
+        g.ldc = ma;
+        g.part_off = 0;
+        DevState ds{};
+        for (int l = 0; l < 3; ++l) ds.cur_a[l] = a_vec[l];
+        ds.cur_s = dv_scale;
+        ds.cur_aa = (a_vec[0] * a_vec[0] + a_vec[1] * a_vec[1] + a_vec[2] * a_vec[2]) / (2 * ctx->c * ctx->c);
+        put_struct(base + o_kd, kc, st);
+        put_struct(base + o_gd, g, st);
+        put_struct(base + o_st, ds, st);
+        KCHECK();
+        StepArgs a = make_args(ctx, dv_on);
+        a.kd = (const KDev*)(base + o_kd);
+        a.nk = 1;
+        a.st = (DevState*)(base + o_st);
+        a.part_jmt = (double*)(base + o_jmt);
+        if (dv_on) {
+            a.vstep = (zd*)(base + o_vs);
+            a.vstep32 = f32 ? (zf*)(base + o_vs32) : nullptr;
+        }
+        StepPlan p = make_plan(ctx);
+        p.gd_fwd = (const GemmDesc*)(base + o_gd);
+        p.maxng = ng;
+        p.part = (zd*)(base + o_part);
+        if (dv_on) launch_vstep(a, st);
+        const zd* xz = (const zd*)x;
+        zd* hz = (zd*)hx;
+        zd* sz = (zd*)sx;
+        for (int c0 = 0; c0 < ncols; c0 += ns) {
+            const int w = std::min(ns, ncols - c0);
+            if (w < ns) launch_zero(kc.C, (size_t)nb * ns, st);  // unused columns start at zero
+            CK(cudaMemcpyAsync(kc.C, xz + (size_t)c0 * nb, (size_t)w * nb * sizeof(zd), cudaMemcpyDeviceToDevice, st));
+            launch_operator_pass(a, p, st);
+            KCHECK();
+            CK(cudaMemcpyAsync(hz + (size_t)c0 * nb, kc.Y, (size_t)w * nb * sizeof(zd), cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(sz + (size_t)c0 * nb, kc.Y + (size_t)ns * nb, (size_t)w * nb * sizeof(zd),
+                               cudaMemcpyDeviceToDevice, st));
+        }
+        return RTTDDFT_OK;
+    } catch (Fail& f) {
+        return f.code;
+    }
+}

@@ -27,6 +27,7 @@ AUX = {"ritz": 0, "given": 1}
 EXPORTED = ["rttddft_default_options", "rttddft_setup", "rttddft_step", "rttddft_observables",
             "rttddft_set_dv", "rttddft_apply", "rttddft_get_state", "rttddft_set_state",
             "rttddft_get_aux", "rttddft_get_info", "rttddft_adjoint", "rttddft_trace_steps",
+            "rttddft_apply_noalloc",
             "rttddft_destroy", "rttddft_last_error", "rttddft_version"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -100,6 +101,9 @@ def load_library(path=None):
     lib.rttddft_set_dv.restype = ctypes.c_int
     lib.rttddft_apply.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_double, vp, vp]
     lib.rttddft_apply.restype = ctypes.c_int
+    lib.rttddft_apply_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_double,
+                                          vp, vp]
+    lib.rttddft_apply_noalloc.restype = ctypes.c_int
     lib.rttddft_get_state.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.rttddft_get_state.restype = ctypes.c_int
     lib.rttddft_set_state.argtypes = [vp, ctypes.c_int, vp]
@@ -171,6 +175,12 @@ def rttddft_set_dv(ctx, dh, dvtab):
 def rttddft_apply(ctx, k, ncols, x, a_vec, dv_scale, hx, sx):
     _check(ctx, load_library().rttddft_apply(ctx, int(k), int(ncols), _ptr(x), _ptr(a_vec),
                                              float(dv_scale), _ptr(hx), _ptr(sx)))
+
+
+def rttddft_apply_noalloc(ctx, k, ncols, x, a_vec, dv_scale, hx, sx):
+    """Operator apply with the library's static scratch (device pointers only)."""
+    _check(ctx, load_library().rttddft_apply_noalloc(ctx, int(k), int(ncols), _ptr(x), _ptr(a_vec),
+                                                     float(dv_scale), _ptr(hx), _ptr(sx)))
 
 
 def rttddft_get_state(ctx, k, theta, c=None):

@@ -42,7 +42,9 @@ struct rttddft_ctx {
     double *d_occ = nullptr, *d_wk = nullptr, *d_lam = nullptr;
     DevState* d_st = nullptr;
     double* d_rec = nullptr;
-    double *d_part_jmt = nullptr, *d_part_full = nullptr, *d_part_sub = nullptr, *d_part_norm = nullptr;
+    double *d_part_jmt = nullptr, *d_part_full = nullptr, *d_part_post = nullptr;
+    int max_nback = 1, wmax = 1, nseg = 1, segw = BT, ntsel = 2, msegw = 64, nslot = 1, coop_grid = 0;
+    zd* d_part_t = nullptr;
     zd* d_part = nullptr;
     double *d_a = nullptr, *d_dvs = nullptr;
     int call_cap = 0;
@@ -54,7 +56,7 @@ struct rttddft_ctx {
     zd** d_jac_mats = nullptr;
     double** d_jac_vals = nullptr;
     zd** d_jac_vecs = nullptr;
-    int kc_fwd = 0, kc_proj = 0;
+    int kc_fwd = 0, kc_proj = 0, kc_expand = 0;
     std::vector<double> eps_min, eps_max, pnorm, dvnorm;
     double dtcr0 = 0;
     int nterms = 0, launches_per_step = 0;
@@ -179,6 +181,8 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.rec_cap = ctx->opt.max_record;
     a.dt = ctx->opt.dt;
     a.c = ctx->c;
+    a.inv_c = 1.0 / ctx->c;
+    a.half_inv_c2 = 0.5 / (ctx->c * ctx->c);
     a.omega = ctx->omega;
     a.kd = ctx->d_kd;
     a.occ = ctx->d_occ;
@@ -198,9 +202,21 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.rec = ctx->d_rec;
     a.part_jmt = ctx->d_part_jmt;
     a.part_full = ctx->d_part_full;
-    a.part_sub = ctx->d_part_sub;
-    a.part_norm = ctx->d_part_norm;
+    a.part_post = ctx->d_part_post;
     a.at = ctx->d_at;
+    a.gd_proj = ctx->gd_proj;
+    a.part_proj = ctx->d_part;
+    a.kc_proj = ctx->kc_proj;
+    a.max_nback = ctx->max_nback;
+    a.wmax = ctx->wmax;
+    a.nseg = ctx->nseg;
+    a.segw = ctx->segw;
+    a.maxng = ctx->maxng;
+    a.msegw = ctx->msegw;
+    a.nslot = ctx->nslot;
+    a.part_t = ctx->d_part_t;
+    a.flag = ctx->d_flag;
+    a.coop_grid = ctx->coop_grid;
     return a;
 }
 
@@ -219,6 +235,7 @@ static StepPlan make_plan(rttddft_ctx* ctx) {
     p.part = ctx->d_part;
     p.kc_fwd = ctx->kc_fwd;
     p.kc_proj = ctx->kc_proj;
+    p.kc_expand = ctx->kc_expand;
     p.gd_dvw = ctx->gd_dvw;
     p.gd_dvg = ctx->gd_dvg;
     p.gd_dvi = ctx->gd_dvi;
@@ -233,13 +250,17 @@ static StepPlan make_plan(rttddft_ctx* ctx) {
     return p;
 }
 
+// rows of C per block of the CN kernel for N right-hand columns
+static int cn_rows(int N) { return N <= 2 ? 32 : (N <= 4 ? 16 : 8); }
+
+// K-chunk of a split-K launch so that about two blocks per SM are busy
 static int kchunk_for(int tiles_per_batch, int nbatch, int maxK) {
     const int target = 2 * 152;
     int splits = (target + tiles_per_batch * nbatch - 1) / (tiles_per_batch * nbatch);
     splits = std::max(1, std::min(splits, (maxK + 255) / 256));
     int kc = (maxK + splits - 1) / splits;
-    kc = (kc + 31) / 32 * 32;
-    return std::max(kc, 32);
+    kc = (kc + 127) / 128 * 128;
+    return std::max(kc, 128);
 }
 
 // ------------------------------------------------------------ set-up pieces
@@ -254,12 +275,12 @@ static void local_coords(rttddft_ctx* ctx, const std::vector<zd*>& X, const std:
     for (int k = 0; k < ctx->nk; ++k) {
         for (int a = 0; a < at.n; ++a) {
             GemmDesc g{};
-            g.A = ctx->hkd[k].amat + at.aoff[a];
+            g.A = ctx->hkd[k].at + (size_t)at.aoff[a] * ctx->ng[k];  // columns of A^H
             g.B = X[k];
             g.C = L[k] + at.loff[a];
             g.M = at.na[a];
             g.K = ctx->ng[k];
-            g.lda = at.ma;
+            g.lda = ctx->ng[k];
             g.ldb = ctx->nb[k];
             g.ldc = at.lrows;
             v.push_back(g);
@@ -279,7 +300,7 @@ static void local_coords(rttddft_ctx* ctx, const std::vector<zd*>& X, const std:
     GemmDesc* d = upload_descs(ctx, v);
     int maxna = 0;
     for (int a = 0; a < at.n; ++a) maxna = std::max(maxna, at.na[a]);
-    launch_gemm_nn(d, (int)v.size(), maxna, ctx->maxng, ncol, 0, nullptr, 0, false, nullptr, ctx->stream);
+    launch_gemm_cn(d, (int)v.size(), maxna, ctx->maxng, ncol, 0, nullptr, 0, false, nullptr, ctx->stream);
     KCHECK();
     GemmDesc* dc = upload_descs(ctx, cp);
     int maxlo = 0;
@@ -641,12 +662,25 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
         CK(cudaMemset(ctx->d_st, 0, sizeof(DevState)));
         ctx->d_flag = dalloc<int>(ctx, 1);
         ctx->d_rec = dalloc<double>(ctx, (size_t)o->max_record * RTD_REC_STRIDE);
-        ctx->d_lam = dalloc<double>(ctx, 2 * (size_t)nk);
-        ctx->d_part_jmt = dalloc<double>(ctx, (size_t)nk * std::max(at.lrows, 1) * 3);
-        ctx->d_part_full = dalloc<double>(ctx, (size_t)nk * ns * RB_FULL * 5);
-        ctx->d_part_sub = dalloc<double>(ctx, (size_t)nk * 3 * naux);
-        ctx->d_part_norm = dalloc<double>(ctx, (size_t)nk * 2);
-        CK(cudaMemset(ctx->d_part_jmt, 0, sizeof(double) * nk * std::max(at.lrows, 1) * 3));
+        ctx->d_lam = dalloc<double>(ctx, LAM_N * (size_t)nk);
+        ctx->max_nback = (ctx->maxng + BT - 1) / BT;
+        {
+            // split the G' sum of the interstitial term so that ~4 blocks per SM work
+            const int tiles = ctx->max_nback;
+            int nseg = (4 * 152 + tiles * nk - 1) / (tiles * nk);
+            nseg = std::max(1, std::min(nseg, tiles));
+            ctx->segw = ((tiles + nseg - 1) / nseg) * BT;
+            ctx->nseg = (ctx->maxng + ctx->segw - 1) / ctx->segw;
+            ctx->ntsel = ns <= 2 ? 2 : (ns <= 4 ? 4 : 8);
+            ctx->msegw = 64;
+            ctx->nslot = ctx->nseg + (at.ma + ctx->msegw - 1) / ctx->msegw;
+            ctx->d_part_t = dalloc<zd>(ctx, (size_t)nk * ctx->nslot * 2 * ctx->ntsel * ctx->maxng);
+        }
+        ctx->d_part_jmt = dalloc<double>(ctx, (size_t)nk * std::max(at.lrows, 1) * 5);
+        ctx->d_part_full = dalloc<double>(ctx, (size_t)nk * ctx->max_nback * 5);
+        ctx->d_part_post = dalloc<double>(ctx, (size_t)nk * naux * POST_STRIDE);
+        CK(cudaMemset(ctx->d_part_jmt, 0, sizeof(double) * nk * std::max(at.lrows, 1) * 5));
+        CK(cudaMemset(ctx->d_part_post, 0, sizeof(double) * nk * naux * POST_STRIDE));
         ctx->call_cap = 1024;
         ctx->d_a = dalloc<double>(ctx, 3 * (size_t)ctx->call_cap);
         ctx->d_dvs = dalloc<double>(ctx, (size_t)ctx->call_cap);
@@ -658,7 +692,18 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             K.ng = ctx->ng[k];
             K.nb = ctx->nb[k];
             K.caux = dupload(ctx, (const zd*)s->caux + c_off[k], (size_t)K.nb * naux);
-            K.amat = at.n > 0 ? dupload(ctx, (const zd*)s->amat + a_off[k], (size_t)at.ma * K.ng) : nullptr;
+            if (at.n > 0) {
+                // matching coefficients are kept as A^H (N_G x M_A): both the forward
+                // product A C_G and the back-projection A^H Z then read coalesced
+                zd* tmp = dupload(ctx, (const zd*)s->amat + a_off[k], (size_t)at.ma * K.ng);
+                K.at = dalloc<zd>(ctx, (size_t)at.ma * K.ng);
+                launch_conj_transpose(tmp, K.at, at.ma, K.ng, ctx->stream);
+                KCHECK();
+                CK(cudaStreamSynchronize(ctx->stream));
+                dfree(ctx, tmp);
+            } else {
+                K.at = nullptr;
+            }
             std::vector<int> gl(K.ng);
             for (int g = 0; g < K.ng; ++g) {
                 const int* t = s->g_int + 3 * (g_off[k] + g);
@@ -683,9 +728,28 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             K.eval = dalloc<double>(ctx, naux);
             K.wtmp = dalloc<zd>(ctx, (size_t)naux * ns);
             K.coef = dalloc<zd>(ctx, RTD_MAX_TERMS);
-            K.lam = ctx->d_lam + 2 * k;
+            K.lam = ctx->d_lam + LAM_N * k;
         }
         ctx->d_kd = dupload(ctx, ctx->hkd.data(), nk);
+        // largest table window of a (row tile, column tile) pair of the back kernel
+        {
+            int wm = 1;
+            size_t goff2 = 0;
+            for (int k = 0; k < nk; ++k) {
+                const int ng = ctx->ng[k];
+                int rmax = 0;
+                for (int t0 = 0; t0 < ng; t0 += BT) {
+                    const int* a0 = s->g_int + 3 * (goff2 + t0);
+                    const int* a1 = s->g_int + 3 * (goff2 + std::min(t0 + BT, ng) - 1);
+                    const int l0 = (a0[0] * d1 + a0[1]) * d2 + a0[2];
+                    const int l1 = (a1[0] * d1 + a1[1]) * d2 + a1[2];
+                    rmax = std::max(rmax, l1 - l0);
+                }
+                wm = std::max(wm, 2 * rmax + 1);
+                goff2 += ng;
+            }
+            ctx->wmax = wm;
+        }
         // ---- auxiliary basis
         std::vector<zd*> X(nk), L(nk), G1(nk), G2(nk), V1(nk), V2(nk), T1(nk), T2(nk), NEW(nk);
         std::vector<double*> E1(nk), E2(nk);
@@ -811,8 +875,8 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
                 K.caux32 = dalloc<zf>(ctx, (size_t)K.nb * naux);
                 launch_convert_f32(K.caux, K.caux32, (size_t)K.nb * naux, ctx->stream);
                 if (at.n > 0) {
-                    K.amat32 = dalloc<zf>(ctx, (size_t)at.ma * K.ng);
-                    launch_convert_f32(K.amat, K.amat32, (size_t)at.ma * K.ng, ctx->stream);
+                    K.at32 = dalloc<zf>(ctx, (size_t)at.ma * K.ng);
+                    launch_convert_f32(K.at, K.at32, (size_t)at.ma * K.ng, ctx->stream);
                 }
             }
             ctx->d_vtab32 = dalloc<zf>(ctx, ctx->nvt);
@@ -824,9 +888,19 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
         // ---- step descriptors
         const bool f32 = o->precision == RTTDDFT_PREC_FP32;
         std::vector<GemmDesc> ex, fw, pj, g1, g2, eh, en;
-        ctx->kc_fwd = kchunk_for((at.ma + 127) / 128, nk, ctx->maxng);
-        ctx->kc_proj = kchunk_for((naux + 7) / 8, nk, ctx->maxnb);
-        size_t pf = 0, pp = 0;
+        ctx->kc_fwd = kchunk_for((at.ma + cn_rows(ns) - 1) / cn_rows(ns), nk, ctx->maxng);
+        ctx->kc_proj = kchunk_for((naux + cn_rows(ns) - 1) / cn_rows(ns), nk, ctx->maxnb);
+        {
+            // expand: rows are many, K = n_aux is short; split K only in FP64 where the
+            // DFMA pipe of every SM is needed
+            const int tiles = (ctx->maxnb + 63) / 64;
+            ctx->kc_expand = 0;
+            if (tiles * nk < 2 * 152 && naux >= 128) {
+                int splits = std::min((2 * 152 + tiles * nk - 1) / (tiles * nk), naux / 64);
+                if (splits > 1) ctx->kc_expand = ((naux + splits - 1) / splits + 63) / 64 * 64;
+            }
+        }
+        size_t pf = 0, pp = 0, pe = 0;
         for (int k = 0; k < nk; ++k) {
             KDev& K = ctx->hkd[k];
             GemmDesc g{};
@@ -838,14 +912,16 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             g.lda = K.nb;
             g.ldb = naux;
             g.ldc = K.nb;
+            g.part_off = pe;
+            if (ctx->kc_expand > 0) pe += (size_t)((naux + ctx->kc_expand - 1) / ctx->kc_expand) * ns * K.nb;
             ex.push_back(g);
             g = GemmDesc{};
-            g.A = f32 ? (const void*)K.amat32 : (const void*)K.amat;
+            g.A = f32 ? (const void*)K.at32 : (const void*)K.at;
             g.B = K.C;
             g.C = K.Q;
             g.M = at.ma;
             g.K = K.ng;
-            g.lda = std::max(at.ma, 1);
+            g.lda = K.ng;
             g.ldb = K.nb;
             g.ldc = std::max(at.ma, 1);
             g.part_off = pf;
@@ -890,7 +966,7 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             g.C = K.theta;
             en.push_back(g);
         }
-        ctx->d_part = dalloc<zd>(ctx, std::max(pf, pp));
+        ctx->d_part = dalloc<zd>(ctx, std::max(std::max(pf, pp), pe));
         ctx->gd_expand = upload_descs(ctx, ex);
         ctx->gd_fwd = upload_descs(ctx, fw);
         ctx->gd_proj = upload_descs(ctx, pj);
@@ -909,6 +985,13 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             ctx->d_jac_mats = dupload(ctx, jm.data(), nk);
             ctx->d_jac_vecs = dupload(ctx, jv.data(), nk);
             ctx->d_jac_vals = dupload(ctx, jw.data(), nk);
+        }
+        {
+            StepArgs a = make_args(ctx, 0);
+            const int e = prepare_back_kernels(a);
+            if (e) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "table window needs more shared memory than a block has");
+            CK(cudaStreamSynchronize(ctx->stream));
+            ctx->coop_grid = prepare_cheb_coop(a, ctx->stream);
         }
         // ---- theta(0)
         if (s->c0) {
@@ -964,7 +1047,7 @@ static void ensure_interval(rttddft_ctx* ctx, double a_need, double s_need) {
     const double smax = std::max(s_need, std::max(ctx->s_max_cur, 0.0));
     const int nk = ctx->nk;
     const double c = ctx->c, dt = ctx->opt.dt;
-    std::vector<double> lam(2 * nk);
+    std::vector<double> lam(LAM_N * nk, 0.0);
     double zmax = 0.0;
     for (int k = 0; k < nk; ++k) {
         const double bl = amax * (ctx->pnorm[3 * k] + ctx->pnorm[3 * k + 1] + ctx->pnorm[3 * k + 2]) / c;
@@ -975,9 +1058,12 @@ static void ensure_interval(rttddft_ctx* ctx, double a_need, double s_need) {
         const double pad = 1e-10 * std::max(1.0, std::max(fabs(lo), fabs(hi)));
         lo -= pad;
         hi += pad;
-        lam[2 * k] = 0.5 * (hi + lo);
-        lam[2 * k + 1] = std::max(0.5 * (hi - lo), 1e-12);
-        zmax = std::max(zmax, dt * lam[2 * k + 1]);
+        lam[LAM_N * k] = 0.5 * (hi + lo);
+        lam[LAM_N * k + 1] = std::max(0.5 * (hi - lo), 1e-12);
+        lam[LAM_N * k + 2] = 1.0 / lam[LAM_N * k + 1];
+        lam[LAM_N * k + 3] = cos(-dt * lam[LAM_N * k]);
+        lam[LAM_N * k + 4] = sin(-dt * lam[LAM_N * k]);
+        zmax = std::max(zmax, dt * lam[LAM_N * k + 1]);
     }
     const double tol = ctx->opt.cheb_tol > 0 ? ctx->opt.cheb_tol : 1e-16;
     int nt;
@@ -986,7 +1072,7 @@ static void ensure_interval(rttddft_ctx* ctx, double a_need, double s_need) {
         // decay like rho^-n with rho the Bernstein ellipse through the pole
         double nmax = 3;
         for (int k = 0; k < nk; ++k) {
-            const cplx xp = (cplx(0.0, 2.0 / dt) - lam[2 * k]) / lam[2 * k + 1];
+            const cplx xp = (cplx(0.0, 2.0 / dt) - lam[LAM_N * k]) / lam[LAM_N * k + 1];
             cplx r = xp + std::sqrt(xp * xp - 1.0);
             if (std::abs(r) < 1.0) r = xp - std::sqrt(xp * xp - 1.0);
             nmax = std::max(nmax, log(1e-2 * tol) / -log(std::abs(r)) + 4);
@@ -1458,11 +1544,23 @@ int rttddft_trace_steps(rttddft_ctx* ctx, int nsteps, const double* a_samples, c
         std::vector<const char*> names(cap);
         std::vector<double> acc(cap, 0.0);
         int slots = 0;
+        // one step with an event after every launch, captured in a graph so that
+        // the events measure device time without host launch gaps
+        TraceHook tr{ev.data() + 1, names.data(), 0, cap};
+        cudaGraph_t graph;
+        cudaGraphExec_t gx = nullptr;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        CK(cudaEventRecordWithFlags(ev[0], ctx->stream, cudaEventRecordExternal));
+        launch_step(a, p, ctx->stream, &ctx->launches_per_step, &tr);
+        {
+            cudaError_t e1 = cudaGetLastError();
+            cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &graph);
+            if (e1 != cudaSuccess || e2 != cudaSuccess) fail(ctx, RTTDDFT_ERR_CUDA, "trace graph capture failed");
+        }
+        CK(cudaGraphInstantiate(&gx, graph, 0));
+        cudaGraphDestroy(graph);
         for (int i = 0; i < nsteps; ++i) {
-            TraceHook tr{ev.data() + 1, names.data(), 0, cap};
-            CK(cudaEventRecord(ev[0], ctx->stream));
-            launch_step(a, p, ctx->stream, &ctx->launches_per_step, &tr);
-            KCHECK();
+            CK(cudaGraphLaunch(gx, ctx->stream));
             CK(cudaStreamSynchronize(ctx->stream));
             for (int j = 0; j < tr.n; ++j) {
                 float ms = 0.f;
@@ -1471,6 +1569,7 @@ int rttddft_trace_steps(rttddft_ctx* ctx, int nsteps, const double* a_samples, c
             }
             slots = tr.n;
         }
+        cudaGraphExecDestroy(gx);
         const int n = std::min(slots, out->capacity);
         for (int j = 0; j < n; ++j) {
             out->names[j] = names[j];
@@ -1492,15 +1591,178 @@ int rttddft_trace_steps(rttddft_ctx* ctx, int nsteps, const double* a_samples, c
 int rttddft_adjoint(rttddft_ctx* ctx, int nsteps, const double* a_samples, const double* dv_scale,
                     const double* gdir, int ckpt_every, double* grad, double* dmu_out) {
     if (!ctx) return RTTDDFT_ERR_ARG;
-    (void)nsteps;
-    (void)a_samples;
-    (void)dv_scale;
-    (void)gdir;
-    (void)ckpt_every;
-    (void)grad;
-    (void)dmu_out;
-    set_err(ctx, "adjoint not built yet");
-    return RTTDDFT_ERR_UNSUPPORTED;
+    std::vector<void*> tmp;
+    DevState saved{};
+    std::vector<zd*> theta_saved;
+    bool restore = false;
+    try {
+        if (nsteps < 1 || !a_samples || !gdir || !grad || ckpt_every < 1)
+            fail(ctx, RTTDDFT_ERR_ARG, "bad argument to rttddft_adjoint");
+        if (ctx->opt.propagator != RTTDDFT_PROP_CHEBYSHEV)
+            fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "the adjoint differentiates the Chebyshev propagator only");
+        if (dv_scale && !ctx->dv_set) fail(ctx, RTTDDFT_ERR_ARG, "dv_scale given before rttddft_set_dv");
+        sync_and_check(ctx);
+        const int nk = ctx->nk, ns = ctx->ns, naux = ctx->naux;
+        const size_t vs = (size_t)naux * ns;
+        cudaStream_t st = ctx->stream;
+        // samples on the host (needed for the gradient formula) and on the device
+        const size_t na = 3 * (size_t)nsteps;
+        std::vector<double> ha(na), hs;
+        if (is_device_ptr(a_samples)) CK(cudaMemcpy(ha.data(), a_samples, na * sizeof(double), cudaMemcpyDeviceToHost));
+        else memcpy(ha.data(), a_samples, na * sizeof(double));
+        if (!finite_all(ha.data(), na)) fail(ctx, RTTDDFT_ERR_NONFINITE, "a_samples not finite");
+        if (dv_scale) {
+            hs.resize(nsteps);
+            if (is_device_ptr(dv_scale)) CK(cudaMemcpy(hs.data(), dv_scale, nsteps * sizeof(double), cudaMemcpyDeviceToHost));
+            else memcpy(hs.data(), dv_scale, nsteps * sizeof(double));
+        }
+        double a_need = 0.0, s_need = 0.0;
+        for (size_t q = 0; q < na; q += 3)
+            a_need = std::max(a_need, sqrt(ha[q] * ha[q] + ha[q + 1] * ha[q + 1] + ha[q + 2] * ha[q + 2]));
+        for (double x : hs) s_need = std::max(s_need, fabs(x));
+        ensure_interval(ctx, std::max(a_need, ctx->opt.a_max), std::max(s_need, ctx->opt.s_max));
+        ensure_call_cap(ctx, nsteps);
+        CK(cudaMemcpy(ctx->d_a, ha.data(), na * sizeof(double), cudaMemcpyHostToDevice));
+        if (dv_scale) CK(cudaMemcpy(ctx->d_dvs, hs.data(), nsteps * sizeof(double), cudaMemcpyHostToDevice));
+        // save the state the call must leave unchanged
+        CK(cudaMemcpy(&saved, ctx->d_st, sizeof(DevState), cudaMemcpyDeviceToHost));
+        for (int k = 0; k < nk; ++k) {
+            zd* b = dalloc<zd>(ctx, vs);
+            tmp.push_back(b);
+            theta_saved.push_back(b);
+            CK(cudaMemcpy(b, ctx->hkd[k].theta, vs * sizeof(zd), cudaMemcpyDeviceToDevice));
+        }
+        restore = true;
+        const int N = ctx->nterms;
+        const int K = ckpt_every;
+        const int nseg = (nsteps + K - 1) / K;
+        auto alloc = [&](size_t n) {
+            zd* p = dalloc<zd>(ctx, n);
+            tmp.push_back(p);
+            return p;
+        };
+        zd* ckpt = alloc((size_t)nseg * nk * vs);   // theta at the start of every segment
+        zd* hist = alloc((size_t)(K + 1) * nk * vs);  // theta over the current segment
+        zd* Yh = alloc((size_t)nk * N * vs);
+        zd* Yb = alloc((size_t)nk * N * vs);
+        zd* lam = alloc((size_t)nk * vs);
+        const int gblk = std::max(1, std::min(64, (naux * naux + 255) / 256));
+        double* gpart = dalloc<double>(ctx, (size_t)nk * gblk * 4);
+        tmp.push_back(gpart);
+        double* nrm = dalloc<double>(ctx, (size_t)nk * naux);
+        tmp.push_back(nrm);
+        const int dv_on = dv_scale ? 1 : 0;
+        StepArgs a = make_args(ctx, dv_on);
+        a.coop_grid = 0;
+        StepPlan p = make_plan(ctx);
+        auto copy_theta = [&](zd* dst /* nk * vs */, bool to_theta) {
+            for (int k = 0; k < nk; ++k) {
+                if (to_theta) CK(cudaMemcpyAsync(ctx->hkd[k].theta, dst + (size_t)k * vs, vs * sizeof(zd), cudaMemcpyDeviceToDevice, st));
+                else CK(cudaMemcpyAsync(dst + (size_t)k * vs, ctx->hkd[k].theta, vs * sizeof(zd), cudaMemcpyDeviceToDevice, st));
+            }
+        };
+        const double om = ctx->omega, dt = ctx->opt.dt, c = ctx->c;
+        // current of the propagated theta at t_m (host sum of the row partials)
+        std::vector<double> post((size_t)nk * naux * POST_STRIDE), wk(nk);
+        CK(cudaMemcpy(wk.data(), ctx->d_wk, nk * sizeof(double), cudaMemcpyDeviceToHost));
+        auto current = [&](double out[3]) {
+            launch_subspace_j(a, st);
+            KCHECK();
+            CK(cudaMemcpyAsync(post.data(), ctx->d_part_post, post.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            for (int l = 0; l < 3; ++l) {
+                double v = 0.0;
+                for (int k = 0; k < nk; ++k)
+                    for (int i = 0; i < naux; ++i) v += wk[k] * post[((size_t)k * naux + i) * POST_STRIDE + 1 + l];
+                out[l] = -v / om;
+            }
+        };
+        // ---- forward pass: checkpoints and the dipole increment
+        double dmu[3] = {0, 0, 0}, jprev[3] = {saved.jind_prev[0], saved.jind_prev[1], saved.jind_prev[2]};
+        for (int m = 0; m < nsteps; ++m) {
+            if (m % K == 0) copy_theta(ckpt + (size_t)(m / K) * nk * vs, false);
+            // the current uses the sample of the step just taken
+            launch_propagate_only(a, p, m, st);
+            KCHECK();
+            double J[3];
+            current(J);
+            for (int l = 0; l < 3; ++l) {
+                const double jind = J[l] - saved.j_gs[l];
+                dmu[l] += om * dt * 0.5 * (jprev[l] + jind);
+                jprev[l] = jind;
+            }
+        }
+        if (dmu_out)
+            for (int l = 0; l < 3; ++l) dmu_out[l] = dmu[l];
+        // ---- reverse sweep, segment by segment
+        for (size_t q = 0; q < na; ++q) grad[q] = 0.0;
+        launch_zero(lam, (size_t)nk * vs, st);
+        std::vector<double> hg((size_t)nk * gblk * 4), hn((size_t)nk * naux), lamh(2 * nk);
+        std::vector<double> lamc(LAM_N * nk);
+        CK(cudaMemcpy(lamc.data(), ctx->d_lam, lamc.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int sg = nseg - 1; sg >= 0; --sg) {
+            const int s0 = sg * K, s1 = std::min(nsteps, s0 + K);
+            copy_theta(ckpt + (size_t)sg * nk * vs, true);
+            copy_theta(hist, false);
+            for (int m = s0; m < s1; ++m) {
+                launch_propagate_only(a, p, m, st);
+                copy_theta(hist + (size_t)(m - s0 + 1) * nk * vs, false);
+            }
+            KCHECK();
+            for (int m = s1; m > s0; --m) {
+                const double* am = ha.data() + 3 * (size_t)(m - 1);
+                // source from J(t_m): weight of t_m in the trapezoid sum of dmu
+                const double wm = om * dt * (m == nsteps ? 0.5 : 1.0);
+                const double sm = (gdir[0] * am[0] + gdir[1] * am[1] + gdir[2] * am[2]) / c;
+                launch_adj_jterm(a, lam, hist + (size_t)(m - s0) * nk * vs, gdir, sm, -2.0 * wm / om, nrm, st);
+                KCHECK();
+                CK(cudaMemcpyAsync(hn.data(), nrm, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+                // propagator of step m-1: recompute the Chebyshev vectors from theta_{m-1}
+                launch_hsub_only(a, p, m - 1, st);
+                for (int k = 0; k < nk; ++k)
+                    CK(cudaMemcpyAsync(Yh + (size_t)k * N * vs, hist + (size_t)(m - 1 - s0) * nk * vs + (size_t)k * vs,
+                                       vs * sizeof(zd), cudaMemcpyDeviceToDevice, st));
+                for (int t = 1; t < N; ++t) launch_adj_fwd_term(a, Yh, N, t, st);
+                launch_adj_bwd_init(a, Yb, lam, N, st);
+                for (int t = N - 1; t >= 1; --t) launch_adj_bwd_term(a, Yb, N, t, st);
+                launch_adj_grad(a, Yh, Yb, N, gpart, gblk, st);
+                KCHECK();
+                CK(cudaMemcpyAsync(hg.data(), gpart, hg.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+                // lam_{m-1} = theta-bar = ybar_0
+                for (int k = 0; k < nk; ++k)
+                    CK(cudaMemcpyAsync(lam + (size_t)k * vs, Yb + (size_t)k * N * vs, vs * sizeof(zd),
+                                       cudaMemcpyDeviceToDevice, st));
+                CK(cudaStreamSynchronize(st));
+                double nm = 0.0;
+                for (double x : hn) nm += x;
+                for (int l = 0; l < 3; ++l) grad[3 * (size_t)(m - 1) + l] += wm * gdir[l] * (-1.0 / om) * nm / c;
+                for (int k = 0; k < nk; ++k) {
+                    double acc[4] = {0, 0, 0, 0};
+                    for (int b = 0; b < gblk; ++b)
+                        for (int q = 0; q < 4; ++q) acc[q] += hg[((size_t)k * gblk + b) * 4 + q];
+                    const double ilh = lamc[LAM_N * k + 2];
+                    for (int l = 0; l < 3; ++l)
+                        grad[3 * (size_t)(m - 1) + l] += ilh * (acc[l] / c + am[l] / (c * c) * acc[3]);
+                }
+            }
+        }
+        // ---- restore
+        for (int k = 0; k < nk; ++k)
+            CK(cudaMemcpy(ctx->hkd[k].theta, theta_saved[k], vs * sizeof(zd), cudaMemcpyDeviceToDevice));
+        CK(cudaMemcpy(ctx->d_st, &saved, sizeof(DevState), cudaMemcpyHostToDevice));
+        restore = false;
+        for (void* q : tmp) dfree(ctx, q);
+        return RTTDDFT_OK;
+    } catch (Fail& f) {
+        if (restore) {
+            for (size_t k = 0; k < theta_saved.size(); ++k)
+                cudaMemcpy(ctx->hkd[k].theta, theta_saved[k], (size_t)ctx->naux * ctx->ns * sizeof(zd),
+                           cudaMemcpyDeviceToDevice);
+            cudaMemcpy(ctx->d_st, &saved, sizeof(DevState), cudaMemcpyHostToDevice);
+        }
+        for (void* q : tmp) dfree(ctx, q);
+        return f.code;
+    }
 }
 
 }  // extern "C"
@@ -1581,7 +1843,9 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         const size_t o_c = take((size_t)nb * ns * sizeof(zd)), o_y = take((size_t)nb * 2 * ns * sizeof(zd));
         const size_t o_q = take((size_t)ma * ns * sizeof(zd)), o_z = take((size_t)ma * 2 * ns * sizeof(zd));
         const size_t o_part = take((size_t)splits * ns * ma * sizeof(zd));
-        const size_t o_jmt = take((size_t)std::max(ctx->at.lrows, 1) * 3 * sizeof(double));
+        const size_t o_jmt = take((size_t)std::max(ctx->at.lrows, 1) * 5 * sizeof(double));
+        const size_t o_pf = take((size_t)ctx->max_nback * 5 * sizeof(double));
+        const size_t o_pt = take((size_t)ctx->nslot * 2 * ctx->ntsel * ctx->maxng * sizeof(zd));
         const size_t o_vs = dv_on ? take((size_t)ctx->nvt * sizeof(zd)) : 0;
         const size_t o_vs32 = (dv_on && f32) ? take((size_t)ctx->nvt * sizeof(zf)) : 0;
         if (off > RTD_NOALLOC_SCRATCH_BYTES)
@@ -1596,12 +1860,12 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         kc.Q = (zd*)(base + o_q);
         kc.Z = (zd*)(base + o_z);
         GemmDesc g{};
-        g.A = f32 ? (const void*)K.amat32 : (const void*)K.amat;
+        g.A = f32 ? (const void*)K.at32 : (const void*)K.at;
         g.B = kc.C;
         g.C = kc.Q;
         g.M = ctx->at.ma;
         g.K = ng;
-        g.lda = ma;
+        g.lda = ng;
         g.ldb = nb;
         g.ldc = ma;
         g.part_off = 0;
@@ -1618,6 +1882,8 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         a.nk = 1;
         a.st = (DevState*)(base + o_st);
         a.part_jmt = (double*)(base + o_jmt);
+        a.part_full = (double*)(base + o_pf);
+        a.part_t = (zd*)(base + o_pt);
         if (dv_on) {
             a.vstep = (zd*)(base + o_vs);
             a.vstep32 = f32 ? (zf*)(base + o_vs32) : nullptr;

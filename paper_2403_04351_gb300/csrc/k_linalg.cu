@@ -8,51 +8,61 @@
 #include "rtd.h"
 
 // ---------------------------------------------------------------- NN
-// C[m, n] (+)= sum_k A[m, k] B[k, n]; one thread per output row m,
-// a K-chunk of B staged in shared memory, NT columns per pass.
+// C[m, n] (+)= sum_k A[m, k] B[k, n].  A block has 64 output rows and four
+// k-groups (256 threads); a K-chunk of B is staged in shared memory and the
+// four groups' partial sums are combined in shared memory, so a column of A
+// is read once and coalesced.  NT columns per pass; split-K over blockIdx.y.
 template <typename TA, typename TC, int NT>
-__global__ void __launch_bounds__(128) k_gemm_nn(const GemmDesc* __restrict__ descs, int N,
+__global__ void __launch_bounds__(256) k_gemm_nn(const GemmDesc* __restrict__ descs, int N,
                                                  int kchunk, zd* __restrict__ part, int beta_add,
                                                  const double* __restrict__ dscale) {
     const GemmDesc d = descs[blockIdx.z];
-    const int m0 = blockIdx.x * 128;
+    const int m0 = blockIdx.x * 64;
     const int k0 = blockIdx.y * kchunk;
     if (m0 >= d.M || k0 >= d.K) return;
     const int k1 = min(d.K, k0 + kchunk);
-    const int m = m0 + threadIdx.x;
+    const int r = threadIdx.x & 63, grp = threadIdx.x >> 6;
+    const int m = m0 + r;
     const bool act = m < d.M;
     const TA* __restrict__ A = (const TA*)d.A;
-    __shared__ TC bs[32][NT];
+    __shared__ TC bs[64][NT];
+    __shared__ TC red[3][64][NT];
     for (int n0 = 0; n0 < N; n0 += NT) {
         TC acc[NT];
 #pragma unroll
         for (int j = 0; j < NT; ++j) acc[j] = Cx<TC>::zero();
-        for (int kb = k0; kb < k1; kb += 32) {
+        for (int kb = k0; kb < k1; kb += 64) {
             __syncthreads();
-            for (int e = threadIdx.x; e < 32 * NT; e += 128) {
-                const int kk = e & 31, j = e >> 5;
+            for (int e = threadIdx.x; e < 64 * NT; e += 256) {
+                const int kk = e & 63, j = e >> 6;
                 const int kg = kb + kk, n = n0 + j;
-                bs[kk][j] = (kg < k1 && n < N) ? Cx<TC>::from(d.B[kg + (size_t)n * d.ldb])
-                                               : Cx<TC>::zero();
+                bs[kk][j] = (kg < k1 && n < N) ? Cx<TC>::from(d.B[kg + (size_t)n * d.ldb]) : Cx<TC>::zero();
             }
             __syncthreads();
             if (act) {
-                const int kend = min(32, k1 - kb);
+                const int kend = min(64, k1 - kb);
                 const TA* ap = A + m + (size_t)kb * d.lda;
-                for (int kk = 0; kk < kend; ++kk) {
+                for (int kk = grp; kk < kend; kk += 4) {
                     const TC a = Cx<TC>::from(ap[(size_t)kk * d.lda]);
 #pragma unroll
                     for (int j = 0; j < NT; ++j) Cx<TC>::fma(acc[j], a, bs[kk][j]);
                 }
             }
         }
-        if (act) {
+        if (grp > 0) {
+#pragma unroll
+            for (int j = 0; j < NT; ++j) red[grp - 1][r][j] = acc[j];
+        }
+        __syncthreads();
+        if (grp == 0 && act) {
             const double sc = dscale ? *dscale : 1.0;
 #pragma unroll
             for (int j = 0; j < NT; ++j) {
                 const int n = n0 + j;
                 if (n >= N) break;
-                const zd v = zscale(Cx<TC>::todbl(acc[j]), sc);
+                zd v = zadd(zadd(Cx<TC>::todbl(acc[j]), Cx<TC>::todbl(red[0][r][j])),
+                            zadd(Cx<TC>::todbl(red[1][r][j]), Cx<TC>::todbl(red[2][r][j])));
+                v = zscale(v, sc);
                 if (part) {
                     part[d.part_off + ((size_t)blockIdx.y * N + n) * d.M + m] = v;
                 } else {
@@ -61,45 +71,87 @@ __global__ void __launch_bounds__(128) k_gemm_nn(const GemmDesc* __restrict__ de
                 }
             }
         }
+        __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------- CN
-// C[m, n] (+)= sum_k conj(A[k, m]) B[k, n]; one warp per output row m,
-// lanes stride over k (column m of A is contiguous).
-template <typename TA, typename TC, int NT>
+// C[m, n] (+)= sum_k conj(A[k, m]) B[k, n].  Eight warps, each owning RPW
+// output rows; lanes stride over k (column m of A is contiguous) and a
+// K-chunk of B staged in shared memory serves the block's 8 RPW rows.
+template <typename TA, typename TC, int NT, int RPW>
 __global__ void __launch_bounds__(256) k_gemm_cn(const GemmDesc* __restrict__ descs, int N,
                                                  int kchunk, zd* __restrict__ part, int beta_add,
                                                  const double* __restrict__ dscale) {
     const GemmDesc d = descs[blockIdx.z];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m = blockIdx.x * 8 + warp;
+    const int mb = blockIdx.x * 8 * RPW;
     const int k0 = blockIdx.y * kchunk;
-    if (m >= d.M || k0 >= d.K) return;
+    if (mb >= d.M || k0 >= d.K) return;
     const int k1 = min(d.K, k0 + kchunk);
-    const TA* __restrict__ A = (const TA*)d.A + (size_t)m * d.lda;
+    const int m0 = mb + warp * RPW;
+    __shared__ TC bs[128][NT];
     for (int n0 = 0; n0 < N; n0 += NT) {
-        TC acc[NT];
+        TC acc[RPW][NT];
 #pragma unroll
-        for (int j = 0; j < NT; ++j) acc[j] = Cx<TC>::zero();
-        for (int k = k0 + lane; k < k1; k += 32) {
-            const TC a = Cx<TC>::from(A[k]);
+        for (int q = 0; q < RPW; ++q)
 #pragma unroll
-            for (int j = 0; j < NT; ++j) {
-                if (n0 + j < N) Cx<TC>::fmac(acc[j], a, Cx<TC>::from(d.B[k + (size_t)(n0 + j) * d.ldb]));
+            for (int j = 0; j < NT; ++j) acc[q][j] = Cx<TC>::zero();
+        for (int kb = k0; kb < k1; kb += 128) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < 128 * NT; e += 256) {
+                const int kk = e & 127, j = e >> 7;
+                const int kg = kb + kk, n = n0 + j;
+                bs[kk][j] = (kg < k1 && n < N) ? Cx<TC>::from(d.B[kg + (size_t)n * d.ldb]) : Cx<TC>::zero();
+            }
+            __syncthreads();
+            const int kend = min(128, k1 - kb);
+            if (kend == 128 && m0 + RPW <= d.M) {
+                // full chunk: issue all 4 RPW loads before the multiply-adds
+                TA av[RPW][4];
+#pragma unroll
+                for (int q = 0; q < RPW; ++q) {
+                    const TA* ap = (const TA*)d.A + (size_t)(m0 + q) * d.lda + kb + lane;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) av[q][u] = ap[32 * u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int q = 0; q < RPW; ++q) {
+                        const TC a = Cx<TC>::from(av[q][u]);
+#pragma unroll
+                        for (int j = 0; j < NT; ++j) Cx<TC>::fmac(acc[q][j], a, bs[lane + 32 * u][j]);
+                    }
+            } else {
+#pragma unroll
+                for (int q = 0; q < RPW; ++q) {
+                    const int m = m0 + q;
+                    if (m >= d.M) break;
+                    const TA* ap = (const TA*)d.A + (size_t)m * d.lda + kb;
+                    for (int kk = lane; kk < kend; kk += 32) {
+                        const TC a = Cx<TC>::from(ap[kk]);
+#pragma unroll
+                        for (int j = 0; j < NT; ++j) Cx<TC>::fmac(acc[q][j], a, bs[kk][j]);
+                    }
+                }
             }
         }
         const double sc = dscale ? *dscale : 1.0;
 #pragma unroll
-        for (int j = 0; j < NT; ++j) {
-            const zd s = zscale(warp_zsum(Cx<TC>::todbl(acc[j])), sc);
-            const int n = n0 + j;
-            if (lane == j && n < N) {
-                if (part) {
-                    part[d.part_off + ((size_t)blockIdx.y * N + n) * d.M + m] = s;
-                } else {
-                    zd* c = d.C + m + (size_t)n * d.ldc;
-                    *c = beta_add ? zadd(*c, s) : s;
+        for (int q = 0; q < RPW; ++q) {
+            const int m = m0 + q;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const zd s = zscale(warp_zsum(Cx<TC>::todbl(acc[q][j])), sc);
+                const int n = n0 + j;
+                if (lane == j && n < N && m < d.M) {
+                    if (part) {
+                        part[d.part_off + ((size_t)blockIdx.y * N + n) * d.M + m] = s;
+                    } else {
+                        zd* c = d.C + m + (size_t)n * d.ldc;
+                        *c = beta_add ? zadd(*c, s) : s;
+                    }
                 }
             }
         }
@@ -124,26 +176,29 @@ static void gemm_nn_t(const GemmDesc* d, int nb, int maxM, int maxK, int N, int 
                       int beta_add, const double* ds, cudaStream_t s) {
     if (nb <= 0 || maxM <= 0 || maxK <= 0 || N <= 0) return;
     if (kchunk <= 0) kchunk = maxK;
-    dim3 grid((maxM + 127) / 128, (maxK + kchunk - 1) / kchunk, nb);
+    dim3 grid((maxM + 63) / 64, (maxK + kchunk - 1) / kchunk, nb);
     if (N <= 2)
-        k_gemm_nn<TA, TC, 2><<<grid, 128, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+        k_gemm_nn<TA, TC, 2><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
     else if (N <= 4)
-        k_gemm_nn<TA, TC, 4><<<grid, 128, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+        k_gemm_nn<TA, TC, 4><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
     else
-        k_gemm_nn<TA, TC, 8><<<grid, 128, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+        k_gemm_nn<TA, TC, 8><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
 }
 template <typename TA, typename TC>
 static void gemm_cn_t(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kchunk, zd* part,
                       int beta_add, const double* ds, cudaStream_t s) {
     if (nb <= 0 || maxM <= 0 || maxK <= 0 || N <= 0) return;
     if (kchunk <= 0) kchunk = maxK;
-    dim3 grid((maxM + 7) / 8, (maxK + kchunk - 1) / kchunk, nb);
-    if (N <= 2)
-        k_gemm_cn<TA, TC, 2><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
-    else if (N <= 4)
-        k_gemm_cn<TA, TC, 4><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
-    else
-        k_gemm_cn<TA, TC, 8><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+    if (N <= 2) {
+        dim3 grid((maxM + 31) / 32, (maxK + kchunk - 1) / kchunk, nb);
+        k_gemm_cn<TA, TC, 2, 4><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+    } else if (N <= 4) {
+        dim3 grid((maxM + 15) / 16, (maxK + kchunk - 1) / kchunk, nb);
+        k_gemm_cn<TA, TC, 4, 2><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+    } else {
+        dim3 grid((maxM + 7) / 8, (maxK + kchunk - 1) / kchunk, nb);
+        k_gemm_cn<TA, TC, 8, 1><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+    }
 }
 
 void launch_gemm_nn(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kchunk, zd* part,
@@ -252,4 +307,23 @@ __global__ void k_convert_f32(const zd* __restrict__ src, zf* __restrict__ dst, 
 void launch_convert_f32(const zd* src, zf* dst, size_t n, cudaStream_t s) {
     if (n == 0) return;
     k_convert_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
+}
+
+__global__ void k_conj_transpose(const zd* __restrict__ A, zd* __restrict__ AT, int m, int n) {
+    __shared__ zd t[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;  // bx over m (rows of A), by over n
+    for (int j = threadIdx.y; j < 32; j += 8) {
+        const int r = bx + threadIdx.x, c = by + j;
+        if (r < m && c < n) t[j][threadIdx.x] = A[r + (size_t)c * m];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += 8) {
+        const int r = by + threadIdx.x, c = bx + j;  // AT[r, c] = conj(A[c, r])
+        if (r < n && c < m) AT[r + (size_t)c * n] = zconj(t[threadIdx.x][j]);
+    }
+}
+void launch_conj_transpose(const zd* A, zd* AT, int m, int n, cudaStream_t s) {
+    if (m <= 0 || n <= 0) return;
+    dim3 grid((m + 31) / 32, (n + 31) / 32), block(32, 8);
+    k_conj_transpose<<<grid, block, 0, s>>>(A, AT, m, n);
 }

@@ -24,7 +24,7 @@ __global__ void k_set_cur(StepArgs a) {
     st->cur_a[1] = av[1];
     st->cur_a[2] = av[2];
     st->cur_s = a.dvs ? a.dvs[cs] : 0.0;
-    st->cur_aa = (av[0] * av[0] + av[1] * av[1] + av[2] * av[2]) / (2.0 * a.c * a.c);
+    st->cur_aa = (av[0] * av[0] + av[1] * av[1] + av[2] * av[2]) * a.half_inv_c2;
 }
 
 // V~ + s dV~ (and its FP32 copy) for steps with a potential change
@@ -38,21 +38,36 @@ __global__ void k_vstep(StepArgs a) {
 }
 
 // ------------------------------------------------------------ HH(t_k)
+// HH = diag(eps + |A|^2/(2c^2)) + sum_l (A_l/c) PP_l (+ dVV).  Without a
+// potential change this kernel also stores the step's A and |A|^2/(2c^2)
+// for the kernels that follow (with one, k_set_cur ran first).
 __global__ void k_hsub(StepArgs a) {
     const KDev& K = a.kd[blockIdx.z];
     const int n = a.naux;
+    DevState* st = a.st;
+    const double* av = a.a + 3 * (size_t)st->cstep;
+    const double ax = av[0], ay = av[1], az = av[2];
+    const double aa = (ax * ax + ay * ay + az * az) * a.half_inv_c2;
+    if (blockIdx.x == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
+        st->bar = 0u;
+        if (!a.dv_on) {
+            st->cur_a[0] = ax;
+            st->cur_a[1] = ay;
+            st->cur_a[2] = az;
+            st->cur_s = 0.0;
+            st->cur_aa = aa;
+        }
+    }
     const int idx = blockIdx.x * 256 + threadIdx.x;
     if (idx >= n * n) return;
     const int i = idx % n, j = idx / n;
-    const DevState* st = a.st;
     const size_t nn = (size_t)n * n;
+    const double al[3] = {ax * a.inv_c, ay * a.inv_c, az * a.inv_c};
     zd v = zmk(0.0, 0.0);
 #pragma unroll
-    for (int l = 0; l < 3; ++l) {
-        const double al = st->cur_a[l] / a.c;
-        if (al != 0.0) v = zadd(v, zscale(K.psub[l * nn + idx], al));
-    }
-    if (i == j) v.x += K.eps[i] + st->cur_aa;
+    for (int l = 0; l < 3; ++l)
+        if (al[l] != 0.0) v = zadd(v, zscale(K.psub[l * nn + idx], al[l]));
+    if (i == j) v.x += K.eps[i] + aa;
     if (a.dv_on) v = zadd(v, K.dvsub[idx]);
     K.hsub[idx] = v;
 }
@@ -60,58 +75,174 @@ __global__ void k_hsub(StepArgs a) {
 // ------------------------------------------------------------ Chebyshev
 // Term n of  sum_n c_n T_n(H~) theta,  H~ = (HH - lam_c)/lam_h:
 //   y_1 = H~ y_0, y_n = 2 H~ y_{n-1} - y_{n-2}; acc += c_n y_n.
-// One warp per row i; HH is Hermitian so row i is read as column i.
+// One block per row i (threads over the columns of HH; HH is Hermitian so
+// row i is read as the contiguous column i), so every SM shares the FP64 work.
 template <int NT>
-__global__ void __launch_bounds__(256) k_cheb(StepArgs a, int nt, int last) {
+__global__ void __launch_bounds__(128) k_cheb(StepArgs a, int nt, int last) {
+    __shared__ double red[4][2 * NT];
     const KDev& K = a.kd[blockIdx.z];
     const int n = a.naux, ns = a.ns;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * 8 + warp;
+    const int i = blockIdx.x;
     if (i >= n) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t vs = (size_t)n * ns;
     const zd* __restrict__ H = K.hsub + (size_t)i * n;
     const zd* yin = (nt == 1) ? K.theta : K.ring + ((nt - 1) % 3) * vs;
     const zd* yp2 = (nt >= 2) ? K.ring + ((nt - 2) % 3) * vs : nullptr;
     zd* yout = K.ring + (nt % 3) * vs;
-    const double lc = K.lam[0], lh = K.lam[1];
+    const double lc = K.lam[0], ilh = K.lam[2];
     const zd cn = K.coef[nt];
     for (int n0 = 0; n0 < ns; n0 += NT) {
         zd acc[NT];
 #pragma unroll
-        for (int j = 0; j < NT; ++j) acc[j] = zmk(0.0, 0.0);
-        for (int jj = lane; jj < n; jj += 32) {
-            const zd h = H[jj];
+        for (int c = 0; c < NT; ++c) acc[c] = zmk(0.0, 0.0);
+        for (int j = tid; j < n; j += 128) {
+            const zd h = H[j];
 #pragma unroll
-            for (int j = 0; j < NT; ++j)
-                if (n0 + j < ns) zfmac(acc[j], h, yin[jj + (size_t)(n0 + j) * n]);
+            for (int c = 0; c < NT; ++c)
+                if (n0 + c < ns) zfmac(acc[c], h, yin[j + (size_t)(n0 + c) * n]);
         }
 #pragma unroll
-        for (int j = 0; j < NT; ++j) {
-            const zd v = warp_zsum(acc[j]);
-            const int c = n0 + j;
-            if (lane == j && c < ns) {
-                const size_t e = i + (size_t)c * n;
-                const zd yi = yin[e];
-                const zd w = zscale(zsub(v, zscale(yi, lc)), 1.0 / lh);
-                zd y, ac;
-                if (nt == 1) {
-                    y = w;
-                    K.ring[e] = yi;  // y_0
-                    ac = zadd(zmul(K.coef[0], yi), zmul(cn, y));
-                } else {
-                    y = zsub(zscale(w, 2.0), yp2[e]);
-                    ac = zadd(K.acc[e], zmul(cn, y));
-                }
-                yout[e] = y;
-                if (last) {
-                    // exp form: e^{-i dt lam_c}; Crank-Nicolson form: the centre is inside c_n
-                    const double ph = (a.prop == 0) ? -a.dt * lc : 0.0;
-                    K.theta[e] = zmul(zmk(cos(ph), sin(ph)), ac);
-                } else {
-                    K.acc[e] = ac;
-                }
+        for (int c = 0; c < NT; ++c) {
+            const zd r = warp_zsum(acc[c]);
+            if (lane == 0) {
+                red[warp][2 * c] = r.x;
+                red[warp][2 * c + 1] = r.y;
             }
         }
+        __syncthreads();
+        if (tid < NT && n0 + tid < ns) {
+            const int c = tid;
+            const zd v = zmk(red[0][2 * c] + red[1][2 * c] + red[2][2 * c] + red[3][2 * c],
+                             red[0][2 * c + 1] + red[1][2 * c + 1] + red[2][2 * c + 1] + red[3][2 * c + 1]);
+            const size_t e = i + (size_t)(n0 + c) * n;
+            const zd yi = yin[e];
+            const zd w = zscale(zsub(v, zscale(yi, lc)), ilh);
+            zd y, ac;
+            if (nt == 1) {
+                y = w;
+                K.ring[e] = yi;  // y_0
+                ac = zadd(zmul(K.coef[0], yi), zmul(cn, y));
+            } else {
+                y = zsub(zscale(w, 2.0), yp2[e]);
+                ac = zadd(K.acc[e], zmul(cn, y));
+            }
+            yout[e] = y;
+            if (last) {
+                // exp form: e^{-i dt lam_c}; Crank-Nicolson form: the centre is inside c_n
+                const zd ph = (a.prop == 0) ? zmk(K.lam[3], K.lam[4]) : zmk(1.0, 0.0);
+                K.theta[e] = zmul(ph, ac);
+            } else {
+                K.acc[e] = ac;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Grid-wide barrier of a cooperative launch: a monotone arrival counter in
+// device memory (zeroed by k_hsub before the launch); a block waits until
+// the counter reaches `target`.  The wait is bounded: after about 0.3 s it
+// raises flag bit 2 (reported as ERR_TIMEOUT) and returns false, so a launch
+// can never hang.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ bool grid_barrier(unsigned* count, unsigned target, int* flag) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        int ok = 1;
+        unsigned long long it = 0;
+        while (ld_acquire_gpu(count) < target) {
+            if (++it > (1ull << 22)) {
+                atomicOr(flag, 4);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The whole Chebyshev series in one cooperative launch.  A block of eight
+// warps owns rows (k, i) round-robin and splits each row's dot products
+// over its warps (on GB300 the FP64 pipe of a single warp would take ~3
+// us per row); a grid barrier separates consecutive terms.  Vectors written
+// by other blocks are read through L2 (ld.global.cg).
+template <int NT>
+__global__ void __launch_bounds__(256) k_cheb_coop(StepArgs a) {
+    __shared__ double red[8][2 * NT];
+    const int n = a.naux, ns = a.ns;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t vs = (size_t)n * ns;
+    const int nrow = a.nk * n;
+    for (int nt = 1; nt < a.nterms; ++nt) {
+        const int last = (nt == a.nterms - 1);
+        for (int q = blockIdx.x; q < nrow; q += gridDim.x) {
+            const int k = q / n, i = q % n;
+            const KDev& K = a.kd[k];
+            const zd* __restrict__ H = K.hsub + (size_t)i * n;
+            const zd* yin = (nt == 1) ? K.theta : K.ring + ((nt - 1) % 3) * vs;
+            const zd* yp2 = (nt >= 2) ? K.ring + ((nt - 2) % 3) * vs : nullptr;
+            zd* yout = K.ring + (nt % 3) * vs;
+            const double lc = K.lam[0], ilh = K.lam[2];
+            const zd cn = K.coef[nt];
+            for (int n0 = 0; n0 < ns; n0 += NT) {
+                zd acc[NT];
+#pragma unroll
+                for (int c = 0; c < NT; ++c) acc[c] = zmk(0.0, 0.0);
+                for (int j = tid; j < n; j += 256) {
+                    const zd h = H[j];
+#pragma unroll
+                    for (int c = 0; c < NT; ++c)
+                        if (n0 + c < ns) zfmac(acc[c], h, __ldcg(yin + j + (size_t)(n0 + c) * n));
+                }
+#pragma unroll
+                for (int c = 0; c < NT; ++c) {
+                    const zd r = warp_zsum(acc[c]);
+                    if (lane == 0) {
+                        red[warp][2 * c] = r.x;
+                        red[warp][2 * c + 1] = r.y;
+                    }
+                }
+                __syncthreads();
+                if (tid < NT && n0 + tid < ns) {
+                    const int c = tid;
+                    zd v = zmk(0.0, 0.0);
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) v = zadd(v, zmk(red[w][2 * c], red[w][2 * c + 1]));
+                    const size_t e = i + (size_t)(n0 + c) * n;
+                    const zd yi = __ldcg(yin + e);
+                    const zd w = zscale(zsub(v, zscale(yi, lc)), ilh);
+                    zd y, ac;
+                    if (nt == 1) {
+                        y = w;
+                        K.ring[e] = yi;
+                        ac = zadd(zmul(K.coef[0], yi), zmul(cn, y));
+                    } else {
+                        y = zsub(zscale(w, 2.0), __ldcg(yp2 + e));
+                        ac = zadd(__ldcg(K.acc + e), zmul(cn, y));
+                    }
+                    yout[e] = y;
+                    if (last) {
+                        const zd ph = (a.prop == 0) ? zmk(K.lam[3], K.lam[4]) : zmk(1.0, 0.0);
+                        K.theta[e] = zmul(ph, ac);
+                    } else {
+                        K.acc[e] = ac;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (!last && !grid_barrier(&a.st->bar, (unsigned)nt * gridDim.x, a.flag)) return;
     }
 }
 
@@ -193,14 +324,16 @@ __global__ void k_coef(StepArgs a) {
 //   Z_H = h_eff X_loc,  Z_S = o X_loc,  h_eff = h + (A/c).p + |A|^2/(2c^2) o + s dh
 // with X_loc = [A_alpha C_G ; C_lo(alpha)] (Eq. v_MT with the block map
 // [A 0; 0 I]); the matching rows go to Z (back-projected next), the LO rows
-// directly into [HC | SC].  Also sum_n f_n Re x_i^* (p_l X)_i for the current.
-template <int NT>
-__global__ void __launch_bounds__(256) k_local(StepArgs a) {
+// directly into [HC | SC].  Per row it also stores sum_n f_n Re x^* (p_l X)
+// (the muffin-tin part of c^H P c) and, for LO rows, the rows' share of
+// c^H H c and c^H S c.
+template <typename TC, int NT>
+__global__ void __launch_bounds__(32) k_local(StepArgs a) {
     const int k = blockIdx.z;
     const KDev& K = a.kd[k];
     const AtomTab& at = *a.at;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * 8 + warp;
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x;
     if (row >= at.lrows) return;
     int al = 0;
     while (al + 1 < at.n && at.loff[al + 1] <= row) ++al;
@@ -212,46 +345,49 @@ __global__ void __launch_bounds__(256) k_local(StepArgs a) {
     const zd* __restrict__ p = a.p + 3 * at.boff[al] + (size_t)i * m;
     const zd* __restrict__ dh = a.dh ? a.dh + at.boff[al] + (size_t)i * m : nullptr;
     const DevState* st = a.st;
-    const double cx = st->cur_a[0] / a.c, cy = st->cur_a[1] / a.c, cz = st->cur_a[2] / a.c;
+    const double cx = st->cur_a[0] * a.inv_c, cy = st->cur_a[1] * a.inv_c, cz = st->cur_a[2] * a.inv_c;
     const double aa = st->cur_aa, sdv = st->cur_s;
     const int ns = a.ns, nb = K.nb, ma = at.ma, ng = K.ng;
     const int aoff = at.aoff[al], lo0 = ng + at.looff[al];
-    double jc[3] = {0.0, 0.0, 0.0};
+    double jc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int n0 = 0; n0 < ns; n0 += NT) {
-        zd aH[NT], aS[NT], aP[3][NT];
+        TC aH[NT], aS[NT], aP[3][NT];
 #pragma unroll
         for (int j = 0; j < NT; ++j) {
-            aH[j] = aS[j] = zmk(0.0, 0.0);
-            aP[0][j] = aP[1][j] = aP[2][j] = zmk(0.0, 0.0);
+            aH[j] = aS[j] = Cx<TC>::zero();
+            aP[0][j] = aP[1][j] = aP[2][j] = Cx<TC>::zero();
         }
         for (int jj = lane; jj < m; jj += 32) {
             const zd hj = h[jj], oj = o[jj];
             const zd px = p[jj], py = p[mm + jj], pz = p[2 * mm + jj];
             zd he = zadd(hj, zadd(zadd(zscale(px, cx), zscale(py, cy)), zadd(zscale(pz, cz), zscale(oj, aa))));
             if (dh && sdv != 0.0) he = zadd(he, zscale(dh[jj], sdv));
+            const TC hec = Cx<TC>::from(he), ojc = Cx<TC>::from(oj);
+            const TC pxc = Cx<TC>::from(px), pyc = Cx<TC>::from(py), pzc = Cx<TC>::from(pz);
             const zd* xs = (jj < na) ? (K.Q + aoff + jj) : (K.C + lo0 + (jj - na));
             const size_t ld = (jj < na) ? (size_t)ma : (size_t)nb;
 #pragma unroll
             for (int j = 0; j < NT; ++j) {
                 if (n0 + j >= ns) break;
-                const zd x = xs[(size_t)(n0 + j) * ld];
-                zfmac(aH[j], he, x);
-                zfmac(aS[j], oj, x);
-                zfmac(aP[0][j], px, x);
-                zfmac(aP[1][j], py, x);
-                zfmac(aP[2][j], pz, x);
+                const TC x = Cx<TC>::from(xs[(size_t)(n0 + j) * ld]);
+                Cx<TC>::fmac(aH[j], hec, x);
+                Cx<TC>::fmac(aS[j], ojc, x);
+                Cx<TC>::fmac(aP[0][j], pxc, x);
+                Cx<TC>::fmac(aP[1][j], pyc, x);
+                Cx<TC>::fmac(aP[2][j], pzc, x);
             }
         }
 #pragma unroll
         for (int j = 0; j < NT; ++j) {
-            const zd zh = warp_zsum(aH[j]);
-            const zd zs = warp_zsum(aS[j]);
-            const zd q0 = warp_zsum(aP[0][j]);
-            const zd q1 = warp_zsum(aP[1][j]);
-            const zd q2 = warp_zsum(aP[2][j]);
+            const zd zh = warp_zsum(Cx<TC>::todbl(aH[j]));
+            const zd zs = warp_zsum(Cx<TC>::todbl(aS[j]));
+            const zd q0 = warp_zsum(Cx<TC>::todbl(aP[0][j]));
+            const zd q1 = warp_zsum(Cx<TC>::todbl(aP[1][j]));
+            const zd q2 = warp_zsum(Cx<TC>::todbl(aP[2][j]));
             const int c = n0 + j;
             if (lane == j && c < ns) {
                 zd xi;
+                const double f = a.occ[c];
                 if (i < na) {
                     K.Z[aoff + i + (size_t)c * ma] = zh;
                     K.Z[aoff + i + (size_t)(ns + c) * ma] = zs;
@@ -261,87 +397,197 @@ __global__ void __launch_bounds__(256) k_local(StepArgs a) {
                     K.Y[r + (size_t)c * nb] = zh;
                     K.Y[r + (size_t)(ns + c) * nb] = zs;
                     xi = K.C[r + (size_t)c * nb];
+                    jc[3] += f * (xi.x * zh.x + xi.y * zh.y);
+                    jc[4] += f * (xi.x * zs.x + xi.y * zs.y);
                 }
-                const double f = a.occ[c];
                 jc[0] += f * (xi.x * q0.x + xi.y * q0.y);
                 jc[1] += f * (xi.x * q1.x + xi.y * q1.y);
                 jc[2] += f * (xi.x * q2.x + xi.y * q2.y);
             }
         }
     }
-    jc[0] = warp_sum(jc[0]);
-    jc[1] = warp_sum(jc[1]);
-    jc[2] = warp_sum(jc[2]);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) jc[q] = warp_sum(jc[q]);
     if (lane == 0) {
-        double* pj = a.part_jmt + ((size_t)k * at.lrows + row) * 3;
-        pj[0] = jc[0];
-        pj[1] = jc[1];
-        pj[2] = jc[2];
+        double* pj = a.part_jmt + ((size_t)k * at.lrows + row) * 5;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) pj[q] = jc[q];
     }
 }
 
-// Plane-wave rows, one warp per G:
-//   HC_G = |G+k+A/c|^2/2 C_G + sum_G' V~_{G-G'} C_G' + A^H Z_H
-//   SC_G = C_G + A^H Z_S
+// Plane-wave rows of H C and S C in independent partial sums, one block per
+// (row tile of BT rows G, slot):
+//  - slots 0 .. nseg-1: the interstitial sum of Eq. v_interstitial over one
+//    segment of G',  T[G, n] = sum_{G' in segment} V~_{G-G'} C_G'.  G is listed
+//    in lexicographic order, so the table offsets glin(G) - glin(G') of a
+//    (row tile, column tile) pair form one contiguous window; the window and
+//    the column tile of C are staged in shared memory and the inner loop
+//    reads shared memory only;
+//  - slots nseg .. nseg+naseg-1: the back-projection (A^H Z_H, A^H Z_S) over
+//    one chunk of the matching rows, A^H read coalesced over the block's rows.
+// Each slot writes [H part | S part] for columns n0 .. n0+NT-1 into part_t.
 template <typename TA, typename TT, typename TC, int NT>
-__global__ void __launch_bounds__(256) k_back(StepArgs a) {
+__global__ void __launch_bounds__(BT) k_toep_seg(StepArgs a, int n0) {
+    extern __shared__ __align__(16) unsigned char smem[];
     const int k = blockIdx.z;
     const KDev& K = a.kd[k];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = blockIdx.x * 8 + warp;
-    if (g >= K.ng) return;
-    const int ns = a.ns, nb = K.nb, ma = a.ma, ng = K.ng;
-    const int* __restrict__ glin = K.glin;
-    const int base = glin[g] + a.vt_center;
-    const TT* __restrict__ tab;
-    const TA* __restrict__ A;
-    if constexpr (sizeof(TA) == sizeof(zf)) {
-        tab = (const TT*)(a.dv_on ? (const void*)a.vstep32 : (const void*)a.vtab32);
-        A = (const TA*)K.amat32 + (size_t)g * ma;
+    const int ng = K.ng;
+    const int g0 = blockIdx.x * BT;
+    const int slot = blockIdx.y;
+    const int tid = threadIdx.x;
+    const int g = g0 + tid;
+    const bool act = g < ng;
+    const int ns = a.ns, nb = K.nb, ma = a.ma;
+    const int nc = min(NT, ns - n0);
+    TC aH[NT], aS[NT];
+#pragma unroll
+    for (int c = 0; c < NT; ++c) aH[c] = aS[c] = Cx<TC>::zero();
+    if (slot < a.nseg) {
+        const int c_lo = slot * a.segw;
+        if (g0 >= ng || c_lo >= ng) return;
+        const int c_hi = min(ng, c_lo + a.segw);
+        TC* xs = (TC*)smem;                 // [BT][NT]
+        int* ls = (int*)(xs + BT * NT);     // [BT]
+        TT* ws = (TT*)(ls + BT);            // table window
+        const int* __restrict__ glin = K.glin;
+        const zd* __restrict__ X = K.C;
+        const TT* __restrict__ tab;
+        if constexpr (sizeof(TT) == sizeof(zf))
+            tab = (const TT*)(a.dv_on ? (const void*)a.vstep32 : (const void*)a.vtab32);
+        else
+            tab = (const TT*)(a.dv_on ? (const void*)a.vstep : (const void*)a.vtab);
+        const int Lr0 = glin[g0], Lr1 = glin[min(g0 + BT, ng) - 1];
+        const int Lrow = act ? glin[g] : Lr0;
+        for (int c0 = c_lo; c0 < c_hi; c0 += BT) {
+            const int cw = min(BT, c_hi - c0);
+            const int Lc0 = glin[c0], Lc1 = glin[c0 + cw - 1];
+            const int wlo = Lr0 - Lc1 + a.vt_center;
+            const int wn = Lr1 - Lc0 + a.vt_center - wlo + 1;
+            __syncthreads();
+            if (tid < cw) {
+                ls[tid] = glin[c0 + tid];
+#pragma unroll
+                for (int c = 0; c < NT; ++c)
+                    xs[tid * NT + c] = (c < nc) ? Cx<TC>::from(X[(c0 + tid) + (size_t)(n0 + c) * nb]) : Cx<TC>::zero();
+            }
+            for (int e = tid; e < wn; e += BT) ws[e] = tab[wlo + e];
+            __syncthreads();
+            if (act) {
+                const int base = Lrow + a.vt_center - wlo;
+                for (int i = 0; i < cw; ++i) {
+                    const TC v = Cx<TC>::from(ws[base - ls[i]]);
+#pragma unroll
+                    for (int c = 0; c < NT; ++c) Cx<TC>::fma(aH[c], v, xs[i * NT + c]);
+                }
+            }
+        }
     } else {
-        tab = (const TT*)(a.dv_on ? (const void*)a.vstep : (const void*)a.vtab);
-        A = (const TA*)K.amat + (size_t)g * ma;
+        const int r_lo = (slot - a.nseg) * a.msegw;
+        if (g0 >= ng || r_lo >= ma) return;
+        const int r_hi = min(ma, r_lo + a.msegw);
+        TC* zs = (TC*)smem;  // [msegw][2 NT]
+        const zd* __restrict__ Z = K.Z;
+        const TA* __restrict__ AT;
+        if constexpr (sizeof(TA) == sizeof(zf)) AT = (const TA*)K.at32;
+        else AT = (const TA*)K.at;
+        for (int r = r_lo + tid; r < r_hi; r += BT) {
+            const int q = r - r_lo;
+#pragma unroll
+            for (int c = 0; c < NT; ++c) {
+                zs[q * 2 * NT + c] = (c < nc) ? Cx<TC>::from(Z[r + (size_t)(n0 + c) * ma]) : Cx<TC>::zero();
+                zs[q * 2 * NT + NT + c] = (c < nc) ? Cx<TC>::from(Z[r + (size_t)(ns + n0 + c) * ma]) : Cx<TC>::zero();
+            }
+        }
+        __syncthreads();
+        if (act) {
+            const TA* ap = AT + g;
+            for (int r = r_lo; r < r_hi; ++r) {
+                const TC av = Cx<TC>::from(ap[(size_t)r * ng]);
+                const TC* zr = zs + (r - r_lo) * 2 * NT;
+#pragma unroll
+                for (int c = 0; c < NT; ++c) {
+                    Cx<TC>::fma(aH[c], av, zr[c]);
+                    Cx<TC>::fma(aS[c], av, zr[NT + c]);
+                }
+            }
+        }
     }
-    const zd* __restrict__ X = K.C;
-    const zd* __restrict__ Z = K.Z;
-    const DevState* st = a.st;
-    const double* q = K.gk + 3 * (size_t)g;
-    const double dg = 0.5 * (dsq(q[0] + st->cur_a[0] / a.c) + dsq(q[1] + st->cur_a[1] / a.c) +
-                             dsq(q[2] + st->cur_a[2] / a.c));
-    for (int n0 = 0; n0 < ns; n0 += NT) {
-        TC aH[NT], aS[NT];
+    if (act) {
+        zd* pt = a.part_t + (((size_t)k * a.nslot + slot) * 2 * NT) * a.maxng + g;
 #pragma unroll
-        for (int j = 0; j < NT; ++j) aH[j] = aS[j] = Cx<TC>::zero();
-        for (int gp = lane; gp < ng; gp += 32) {
-            const TC v = Cx<TC>::from(tab[base - glin[gp]]);
-#pragma unroll
-            for (int j = 0; j < NT; ++j)
-                if (n0 + j < ns) Cx<TC>::fma(aH[j], v, Cx<TC>::from(X[gp + (size_t)(n0 + j) * nb]));
-        }
-        for (int r = lane; r < ma; r += 32) {
-            const TC ar = Cx<TC>::from(A[r]);
-#pragma unroll
-            for (int j = 0; j < NT; ++j) {
-                if (n0 + j >= ns) break;
-                Cx<TC>::fmac(aH[j], ar, Cx<TC>::from(Z[r + (size_t)(n0 + j) * ma]));
-                Cx<TC>::fmac(aS[j], ar, Cx<TC>::from(Z[r + (size_t)(ns + n0 + j) * ma]));
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < NT; ++j) {
-            const zd sh = warp_zsum(Cx<TC>::todbl(aH[j]));
-            const zd ss = warp_zsum(Cx<TC>::todbl(aS[j]));
-            const int c = n0 + j;
-            if (lane == j && c < ns) {
-                const zd x = X[g + (size_t)c * nb];
-                K.Y[g + (size_t)c * nb] = zadd(sh, zscale(x, dg));
-                K.Y[g + (size_t)(ns + c) * nb] = zadd(ss, x);
-            }
+        for (int c = 0; c < NT; ++c) {
+            if (c >= nc) break;
+            pt[(size_t)c * a.maxng] = Cx<TC>::todbl(aH[c]);
+            pt[(size_t)(NT + c) * a.maxng] = Cx<TC>::todbl(aS[c]);
         }
     }
 }
 
-// ------------------------------------------------------------ reductions
+// Plane-wave rows of [HC | SC] (one thread per row G):
+//   HC_G = |G+k+A/c|^2/2 C_G + (sum of the slots' H parts)
+//   SC_G = C_G + (sum of the back-projection slots' S parts)
+// summed in a fixed slot order.  The block adds its rows' f-weighted shares of
+// Re c^H HC, Re c^H SC and sum (G+k)|c|^2 into its slot of part_full.
+template <int NT>
+__global__ void __launch_bounds__(BT) k_back(StepArgs a, int n0) {
+    __shared__ double rs[BT / 32][5];
+    const int k = blockIdx.z;
+    const KDev& K = a.kd[k];
+    const int ng = K.ng;
+    const int g0 = blockIdx.x * BT;
+    if (g0 >= ng) return;
+    const int tid = threadIdx.x;
+    const int g = g0 + tid;
+    const bool act = g < ng;
+    const int ns = a.ns, nb = K.nb;
+    const int nc = min(NT, ns - n0);
+    const zd* __restrict__ X = K.C;
+    double red[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (act) {
+        const int nsg = (ng + a.segw - 1) / a.segw;
+        const int nas = (a.ma + a.msegw - 1) / a.msegw;
+        const DevState* st = a.st;
+        const double* q = K.gk + 3 * (size_t)g;
+        const double dg = 0.5 * (dsq(q[0] + st->cur_a[0] * a.inv_c) + dsq(q[1] + st->cur_a[1] * a.inv_c) +
+                                 dsq(q[2] + st->cur_a[2] * a.inv_c));
+        for (int c = 0; c < NT; ++c) {
+            if (c >= nc) break;
+            zd th = zmk(0.0, 0.0), ts = zmk(0.0, 0.0);
+            for (int sg = 0; sg < nsg; ++sg)
+                th = zadd(th, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + c) * a.maxng + g]);
+            for (int sg = a.nseg; sg < a.nseg + nas; ++sg) {
+                th = zadd(th, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + c) * a.maxng + g]);
+                ts = zadd(ts, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + NT + c) * a.maxng + g]);
+            }
+            const zd x = X[g + (size_t)(n0 + c) * nb];
+            const zd hv = zadd(th, zscale(x, dg));
+            const zd sv = zadd(ts, x);
+            K.Y[g + (size_t)(n0 + c) * nb] = hv;
+            K.Y[g + (size_t)(ns + n0 + c) * nb] = sv;
+            const double f = a.occ[n0 + c];
+            const double w = f * (x.x * x.x + x.y * x.y);
+            red[0] += f * (x.x * hv.x + x.y * hv.y);
+            red[1] += f * (x.x * sv.x + x.y * sv.y);
+            red[2] += q[0] * w;
+            red[3] += q[1] * w;
+            red[4] += q[2] * w;
+        }
+    }
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const double v = warp_sum(red[q]);
+        if (lane == 0) rs[warp][q] = v;
+    }
+    __syncthreads();
+    if (tid < 5) {
+        double v = 0.0;
+        for (int w = 0; w < BT / 32; ++w) v += rs[w][tid];
+        double* pf = a.part_full + ((size_t)k * a.max_nback + blockIdx.x) * 5 + tid;
+        *pf = (n0 == 0) ? v : *pf + v;
+    }
+}
+
 // Sum over the block; every thread receives the total (fixed order).
 __device__ double block_sum(double v, double* sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -364,66 +610,60 @@ __device__ double block_max(double v, double* sh) {
     return r;
 }
 
-// Per (k, state n, row block): Re c^H (HC), Re c^H (SC), sum_G (G+k)_l |c_G|^2
-__global__ void __launch_bounds__(256) k_reduce_full(StepArgs a) {
-    __shared__ double sh[32];
-    const int k = blockIdx.z, n = blockIdx.y, b = blockIdx.x;
+// Per subspace row i and component l (one warp each): finish
+// theta~ = CC^H S C from the split-K partials (l == 0: its deviation from
+// theta and, for N_s <= 4, the row's share of theta^H theta~), and the
+// row's share of J_sub,l = sum_n f_n Re theta_in^* ((PP_l + A_l/c) theta)_in.
+__global__ void __launch_bounds__(128) k_post(StepArgs a, int do_theta, int do_j) {
+    const int k = blockIdx.z;
     const KDev& K = a.kd[k];
-    const int nb = K.nb, ng = K.ng, ns = a.ns;
-    const int per = (nb + RB_FULL - 1) / RB_FULL;
-    const int r0 = b * per, r1 = min(nb, r0 + per);
-    double e = 0.0, s = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        const zd c = K.C[r + (size_t)n * nb];
-        const zd hc = K.Y[r + (size_t)n * nb];
-        const zd sc = K.Y[r + (size_t)(ns + n) * nb];
-        e += c.x * hc.x + c.y * hc.y;
-        s += c.x * sc.x + c.y * sc.y;
-        if (r < ng) {
-            const double w = c.x * c.x + c.y * c.y;
-            const double* q = K.gk + 3 * (size_t)r;
-            jx += q[0] * w;
-            jy += q[1] * w;
-            jz += q[2] * w;
+    const int n = a.naux, ns = a.ns;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = blockIdx.x * 4 + warp;
+    if (w >= 3 * n) return;
+    const int i = w / 3, l = w % 3;
+    double* prow = a.part_post + ((size_t)k * n + i) * POST_STRIDE;
+    if (do_theta && l == 0) {
+        const GemmDesc d = a.gd_proj[k];
+        const int nsp = (d.K + a.kc_proj - 1) / a.kc_proj;
+        double res = 0.0;
+        zd mine = zmk(0.0, 0.0);
+        for (int c = 0; c < ns; ++c) {
+            zd t = zmk(0.0, 0.0);
+            for (int sp = lane; sp < nsp; sp += 32) t = zadd(t, a.part_proj[d.part_off + ((size_t)sp * ns + c) * n + i]);
+            t = warp_zsum(t);
+            if (lane == 0) K.theta_t[i + (size_t)c * n] = t;
+            const zd dd = zsub(t, K.theta[i + (size_t)c * n]);
+            res = fmax(res, dd.x * dd.x + dd.y * dd.y);
+            if (lane == c) mine = t;
         }
+        res = sqrt(res);
+        if (ns <= 4) {
+            // row i's share of theta^H theta~ (= C^H S C for C = CC theta)
+            const int pq = lane, pp = pq % ns, qq = pq / ns;
+            const double tx = __shfl_sync(0xffffffffu, mine.x, qq < 32 ? qq : 0);
+            const double ty = __shfl_sync(0xffffffffu, mine.y, qq < 32 ? qq : 0);
+            if (pq < ns * ns) {
+                const zd tp = K.theta[i + (size_t)pp * n];
+                prow[4 + 2 * pq] = tp.x * tx + tp.y * ty;
+                prow[4 + 2 * pq + 1] = tp.x * ty - tp.y * tx;
+            }
+        }
+        if (lane == 0) prow[0] = res;
     }
-    e = block_sum(e, sh);
-    s = block_sum(s, sh);
-    jx = block_sum(jx, sh);
-    jy = block_sum(jy, sh);
-    jz = block_sum(jz, sh);
-    if (threadIdx.x == 0) {
-        double* pf = a.part_full + (((size_t)k * ns + n) * RB_FULL + b) * 5;
-        pf[0] = e;
-        pf[1] = s;
-        pf[2] = jx;
-        pf[3] = jy;
-        pf[4] = jz;
-    }
-}
-
-// max |theta^H theta~ - I| (= max |C^H S C - I| for C = CC theta) and
-// max |theta~ - theta| per k-point
-__global__ void __launch_bounds__(256) k_normred(StepArgs a) {
-    __shared__ double sh[32];
-    const int k = blockIdx.x;
-    const KDev& K = a.kd[k];
-    const int ns = a.ns, n = a.naux;
-    double d1 = 0.0, d2 = 0.0;
-    for (int e = threadIdx.x; e < ns * ns; e += blockDim.x) {
-        zd g = K.gram[e];
-        if (e % ns == e / ns) g.x -= 1.0;
-        d1 = fmax(d1, hypot(g.x, g.y));
-    }
-    for (int e = threadIdx.x; e < n * ns; e += blockDim.x) {
-        const zd d = zsub(K.theta_t[e], K.theta[e]);
-        d2 = fmax(d2, hypot(d.x, d.y));
-    }
-    d1 = block_max(d1, sh);
-    d2 = block_max(d2, sh);
-    if (threadIdx.x == 0) {
-        a.part_norm[2 * k] = d1;
-        a.part_norm[2 * k + 1] = d2;
+    if (do_j) {
+        const zd* __restrict__ P = K.psub + (size_t)l * n * n + (size_t)i * n;
+        const double al = a.st->cur_a[l] * a.inv_c;
+        double jl = 0.0;
+        for (int c = 0; c < ns; ++c) {
+            const zd* th = K.theta + (size_t)c * n;
+            zd v = zmk(0.0, 0.0);
+            for (int j = lane; j < n; j += 32) zfmac(v, P[j], th[j]);
+            v = warp_zsum(v);
+            const zd ti = th[i];
+            jl += a.occ[c] * (ti.x * (v.x + al * ti.x) + ti.y * (v.y + al * ti.y));
+        }
+        if (lane == 0) prow[1 + l] = jl;
     }
 }
 
@@ -445,82 +685,94 @@ __global__ void k_reproj(StepArgs a) {
     K.theta[e] = v;
 }
 
-// J contributions from the subspace: sum_n f_n Re theta_in^* ((PP_l + A_l/c) theta)_in,
-// one warp per (l, i)
-__global__ void __launch_bounds__(256) k_subj(StepArgs a) {
-    const int k = blockIdx.z;
-    const KDev& K = a.kd[k];
-    const int n = a.naux, ns = a.ns;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * 8 + warp;
-    if (row >= 3 * n) return;
-    const int l = row / n, i = row % n;
-    const zd* __restrict__ P = K.psub + (size_t)l * n * n + (size_t)i * n;
-    const double al = a.st->cur_a[l] / a.c;
-    double tot = 0.0;
-    for (int c = 0; c < ns; ++c) {
-        zd v = zmk(0.0, 0.0);
-        const zd* th = K.theta + (size_t)c * n;
-        for (int j = lane; j < n; j += 32) zfmac(v, P[j], th[j]);
-        v = warp_zsum(v);
-        const zd ti = th[i];
-        tot += a.occ[c] * (ti.x * (v.x + al * ti.x) + ti.y * (v.y + al * ti.y));
-    }
-    if (lane == 0) a.part_sub[((size_t)k * 3 + l) * n + i] = tot;
-}
-
-// Sum the step's partials over k-points (weights w_k), update the dipole by
-// the trapezoid rule (Eq. dipole) and append the record.  One block.
+// Sum the step's partials over k-points (weights w_k) in a fixed order,
+// update the dipole by the trapezoid rule (Eq. dipole) and append the
+// record.  One block.
 __global__ void __launch_bounds__(256) k_finalize(StepArgs a, int set_gs) {
-    __shared__ double sh[32];
+    __shared__ double sh[8][13];
     DevState* st = a.st;
     const int ns = a.ns, n = a.naux, lrows = a.lrows;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double J[3] = {0, 0, 0}, JF[3] = {0, 0, 0}, E = 0.0, ndev = 0.0, res = 0.0, dtcr = 1e300;
     const double io = -1.0 / a.omega;
     for (int k = 0; k < a.nk; ++k) {
         const KDev& K = a.kd[k];
-        const double w = a.wk[k];
-        double js[3];
-        for (int l = 0; l < 3; ++l) {
-            double v = 0.0;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) v += a.part_sub[((size_t)k * 3 + l) * n + i];
-            js[l] = block_sum(v, sh);
-            J[l] += w * io * js[l];
+        const int nback = (K.ng + BT - 1) / BT;
+        // 0-2 J_sub, 3 E, 4 c^H S c, 5-7 sum (G+k)|c|^2, 8-10 J_mt | 11 residual, 12 norm (max)
+        double v[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int i = tid; i < n; i += blockDim.x) {
+            const double* p = a.part_post + ((size_t)k * n + i) * POST_STRIDE;
+            v[0] += p[1];
+            v[1] += p[2];
+            v[2] += p[3];
+            v[11] = fmax(v[11], p[0]);
         }
-        if (set_gs) continue;
-        double e = 0.0, sf = 0.0, ji[3] = {0, 0, 0};
-        for (int idx = threadIdx.x; idx < ns * RB_FULL; idx += blockDim.x) {
-            const int c = idx / RB_FULL;
-            const double f = a.occ[c];
-            const double* pf = a.part_full + ((size_t)k * ns * RB_FULL + idx) * 5;
-            e += f * pf[0];
-            sf += f * pf[1];
-            ji[0] += f * pf[2];
-            ji[1] += f * pf[3];
-            ji[2] += f * pf[4];
+        if (!set_gs) {
+            for (int c = tid; c < nback; c += blockDim.x) {
+                const double* pf = a.part_full + ((size_t)k * a.max_nback + c) * 5;
+                v[3] += pf[0];
+                v[4] += pf[1];
+                v[5] += pf[2];
+                v[6] += pf[3];
+                v[7] += pf[4];
+            }
+            for (int r = tid; r < lrows; r += blockDim.x) {
+                const double* pj = a.part_jmt + ((size_t)k * lrows + r) * 5;
+                v[8] += pj[0];
+                v[9] += pj[1];
+                v[10] += pj[2];
+                v[3] += pj[3];
+                v[4] += pj[4];
+            }
+            if (ns <= 4) {
+                // sum the rows' shares of theta^H theta~ in a fixed order (one warp per entry)
+                for (int e = warp; e < ns * ns; e += blockDim.x / 32) {
+                    double gx = 0.0, gy = 0.0;
+                    for (int i = lane; i < n; i += 32) {
+                        const double* p = a.part_post + ((size_t)k * n + i) * POST_STRIDE + 4 + 2 * e;
+                        gx += p[0];
+                        gy += p[1];
+                    }
+                    gx = warp_sum(gx);
+                    gy = warp_sum(gy);
+                    if (e % ns == e / ns) gx -= 1.0;
+                    v[12] = fmax(v[12], hypot(gx, gy));
+                }
+            } else {
+                for (int e = tid; e < ns * ns; e += blockDim.x) {
+                    zd g = K.gram[e];
+                    if (e % ns == e / ns) g.x -= 1.0;
+                    v[12] = fmax(v[12], hypot(g.x, g.y));
+                }
+            }
         }
-        e = block_sum(e, sh);
-        sf = block_sum(sf, sh);
-        double jm[3];
-        for (int l = 0; l < 3; ++l) {
-            double v = 0.0;
-            for (int r = threadIdx.x; r < lrows; r += blockDim.x) v += a.part_jmt[((size_t)k * lrows + r) * 3 + l];
-            jm[l] = block_sum(v, sh);
-            const double jil = block_sum(ji[l], sh);
-            JF[l] += w * io * (jil + jm[l] + st->cur_a[l] / a.c * sf);
+#pragma unroll
+        for (int q = 0; q < 13; ++q) {
+            const double r = (q >= 11) ? warp_max(v[q]) : warp_sum(v[q]);
+            if (lane == 0) sh[warp][q] = r;
         }
-        E += w * e;
-        ndev = fmax(ndev, a.part_norm[2 * k]);
-        res = fmax(res, a.part_norm[2 * k + 1]);
-        double dk;
-        if (a.prop == 1) {
-            dk = 0.2 / (K.eval[n - 1] - K.eval[0]);
-        } else {
-            dk = 0.2 / (2.0 * K.lam[1]);
+        __syncthreads();
+        if (tid == 0) {
+            double t[13];
+            for (int q = 0; q < 13; ++q) {
+                t[q] = 0.0;
+                for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w)
+                    t[q] = (q >= 11) ? fmax(t[q], sh[w][q]) : t[q] + sh[w][q];
+            }
+            const double w = a.wk[k];
+            for (int l = 0; l < 3; ++l) {
+                J[l] += w * io * t[l];
+                JF[l] += w * io * (t[5 + l] + t[8 + l] + st->cur_a[l] * a.inv_c * t[4]);
+            }
+            E += w * t[3];
+            res = fmax(res, t[11]);
+            ndev = fmax(ndev, t[12]);
+            const double dk = (a.prop == 1) ? 0.2 / (K.eval[n - 1] - K.eval[0]) : 0.2 / (2.0 * K.lam[1]);
+            dtcr = fmin(dtcr, dk);
         }
-        dtcr = fmin(dtcr, dk);
+        __syncthreads();
     }
-    if (threadIdx.x != 0) return;
+    if (tid != 0) return;
     if (set_gs) {
         for (int l = 0; l < 3; ++l) st->j_gs[l] = J[l];
         return;
@@ -753,6 +1005,64 @@ void launch_phase_fix(const KDev* kd, int nk, int naux, zd* const* extra, const 
 }
 
 // ------------------------------------------------------------ orchestration
+static cudaError_t launch_cheb_coop_raw(const StepArgs& a, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.coop_grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (a.ns <= 2) return cudaLaunchKernelEx(&cfg, k_cheb_coop<2>, a);
+    if (a.ns <= 4) return cudaLaunchKernelEx(&cfg, k_cheb_coop<4>, a);
+    return cudaLaunchKernelEx(&cfg, k_cheb_coop<8>, a);
+}
+void launch_cheb_coop(const StepArgs& a, cudaStream_t s) { launch_cheb_coop_raw(a, s); }
+
+// Blocks for the cooperative series: all must be resident at once (the
+// launch guarantees it or fails), and the launch must be capturable in a
+// graph on this driver; otherwise 0 (one launch per term).
+int prepare_cheb_coop(const StepArgs& a0, cudaStream_t s) {
+    int dev = 0, coop = 0, nsm = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (!coop || nsm <= 0) return 0;
+    cudaError_t e;
+    if (a0.ns <= 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_coop<2>, 256, 0);
+    else if (a0.ns <= 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_coop<4>, 256, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_coop<8>, 256, 0);
+    if (e != cudaSuccess || per_sm <= 0) {
+        cudaGetLastError();
+        return 0;
+    }
+    // one block per row while the rows last, at most four blocks per SM
+    const int nrow = a0.nk * a0.naux;
+    int grid = nrow < 4 * nsm ? nrow : 4 * nsm;
+    if (grid > per_sm * nsm) grid = per_sm * nsm;
+    StepArgs a = a0;
+    a.coop_grid = grid;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaError_t e1 = launch_cheb_coop_raw(a, s);
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    int ok = (e1 == cudaSuccess && e2 == cudaSuccess && g != nullptr);
+    if (ok) {
+        cudaGraphExec_t x = nullptr;
+        ok = cudaGraphInstantiate(&x, g, 0) == cudaSuccess;
+        if (x) cudaGraphExecDestroy(x);
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return ok ? grid : 0;
+}
+
 void launch_set_cur(const StepArgs& a, cudaStream_t s) { k_set_cur<<<1, 1, 0, s>>>(a); }
 
 void launch_prep_coef(const StepArgs& a, cudaStream_t s) {
@@ -761,43 +1071,88 @@ void launch_prep_coef(const StepArgs& a, cudaStream_t s) {
 }
 
 void launch_subspace_current(const StepArgs& a, int set_gs, cudaStream_t s) {
-    dim3 g((3 * a.naux + 7) / 8, 1, a.nk);
-    k_subj<<<g, 256, 0, s>>>(a);
+    dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
+    k_post<<<g, 128, 0, s>>>(a, 0, 1);
     k_finalize<<<1, 256, 0, s>>>(a, set_gs);
 }
 
 static inline void mark(TraceHook* tr, const char* name, cudaStream_t s) {
     if (!tr || tr->n >= tr->cap) return;
     tr->names[tr->n] = name;
-    cudaEventRecord(tr->ev[tr->n], s);
+    cudaEventRecordWithFlags(tr->ev[tr->n], s, cudaEventRecordExternal);
     tr->n += 1;
+}
+
+template <int NT>
+static size_t toep_smem(const StepArgs& a, size_t tc, size_t tt) {
+    const size_t t = (size_t)BT * NT * tc + (size_t)BT * sizeof(int) + (size_t)a.wmax * tt;
+    const size_t b = (size_t)a.msegw * 2 * NT * tc;
+    return t > b ? t : b;
+}
+
+template <typename TA, typename TT, typename TC, int NT>
+static void back_launch(const StepArgs& a, int maxng, cudaStream_t s, TraceHook* tr) {
+    const size_t sm = toep_smem<NT>(a, sizeof(TC), sizeof(TT));
+    dim3 gt((maxng + BT - 1) / BT, a.nslot, a.nk);
+    dim3 gb((maxng + BT - 1) / BT, 1, a.nk);
+    for (int n0 = 0; n0 < a.ns; n0 += NT) {
+        k_toep_seg<TA, TT, TC, NT><<<gt, BT, sm, s>>>(a, n0);
+        mark(tr, "toeplitz_and_backprojection", s);
+        k_back<NT><<<gb, BT, 0, s>>>(a, n0);
+        mark(tr, "back_finish", s);
+    }
+}
+
+// Opt the slot kernels in to the shared memory their table window needs.
+// The attribute is global per kernel, so it only ever grows (a context with
+// a smaller window must not lower another context's limit).
+static size_t g_toep_smem[6];
+int prepare_back_kernels(const StepArgs& a) {
+    cudaError_t e = cudaSuccess;
+    int slot = 0;
+#define RTD_SET(TA, TT, TC, NT)                                                                      \
+    {                                                                                                \
+        const size_t need = toep_smem<NT>(a, sizeof(TC), sizeof(TT));                                \
+        if (need > g_toep_smem[slot]) {                                                              \
+            e = cudaFuncSetAttribute(k_toep_seg<TA, TT, TC, NT>,                                     \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);         \
+            if (e != cudaSuccess) return (int)e;                                                     \
+            g_toep_smem[slot] = need;                                                                \
+        }                                                                                            \
+        ++slot;                                                                                      \
+    }
+    RTD_SET(zd, zd, zd, 2) RTD_SET(zd, zd, zd, 4) RTD_SET(zd, zd, zd, 8)
+    RTD_SET(zf, zf, zf, 2) RTD_SET(zf, zf, zf, 4) RTD_SET(zf, zf, zf, 8)
+#undef RTD_SET
+    return 0;
 }
 
 void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr) {
     const bool f32 = a.prec == 1;
-    // Q = A C_G (matching coefficients applied to the plane-wave rows)
-    launch_gemm_nn(p.gd_fwd, a.nk, a.ma, p.maxng, a.ns, p.kc_fwd, p.part, 0, f32, nullptr, s);
+    // Q = A C_G = (A^H)^H C_G: one warp per matching row; split-K in FP64
+    launch_gemm_cn(p.gd_fwd, a.nk, a.ma, p.maxng, a.ns, p.kc_fwd, p.part, 0, f32, nullptr, s);
     mark(tr, "gemm_forward", s);
     launch_split_reduce(p.gd_fwd, a.nk, a.ma, a.ns, p.kc_fwd, p.part, 0, s);
     mark(tr, "split_reduce_forward", s);
     if (a.lrows > 0) {
-        dim3 g((a.lrows + 7) / 8, 1, a.nk);
-        if (a.ns <= 2) k_local<2><<<g, 256, 0, s>>>(a);
-        else k_local<4><<<g, 256, 0, s>>>(a);
+        dim3 g(a.lrows, 1, a.nk);
+        if (f32) {
+            if (a.ns <= 2) k_local<zf, 2><<<g, 32, 0, s>>>(a);
+            else k_local<zf, 4><<<g, 32, 0, s>>>(a);
+        } else {
+            if (a.ns <= 2) k_local<zd, 2><<<g, 32, 0, s>>>(a);
+            else k_local<zd, 4><<<g, 32, 0, s>>>(a);
+        }
         mark(tr, "local_mt", s);
     }
-    {
-        dim3 g((p.maxng + 7) / 8, 1, a.nk);
-        if (f32) {
-            if (a.ns <= 2) k_back<zf, zf, zf, 2><<<g, 256, 0, s>>>(a);
-            else if (a.ns <= 4) k_back<zf, zf, zf, 4><<<g, 256, 0, s>>>(a);
-            else k_back<zf, zf, zf, 8><<<g, 256, 0, s>>>(a);
-        } else {
-            if (a.ns <= 2) k_back<zd, zd, zd, 2><<<g, 256, 0, s>>>(a);
-            else if (a.ns <= 4) k_back<zd, zd, zd, 4><<<g, 256, 0, s>>>(a);
-            else k_back<zd, zd, zd, 8><<<g, 256, 0, s>>>(a);
-        }
-        mark(tr, "back_toeplitz", s);
+    if (f32) {
+        if (a.ns <= 2) back_launch<zf, zf, zf, 2>(a, p.maxng, s, tr);
+        else if (a.ns <= 4) back_launch<zf, zf, zf, 4>(a, p.maxng, s, tr);
+        else back_launch<zf, zf, zf, 8>(a, p.maxng, s, tr);
+    } else {
+        if (a.ns <= 2) back_launch<zd, zd, zd, 2>(a, p.maxng, s, tr);
+        else if (a.ns <= 4) back_launch<zd, zd, zd, 4>(a, p.maxng, s, tr);
+        else back_launch<zd, zd, zd, 8>(a, p.maxng, s, tr);
     }
 }
 
@@ -805,10 +1160,9 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
     int nl = 0;
     const bool f32 = a.prec == 1;
     const int nn = a.naux * a.naux;
-    k_set_cur<<<1, 1, 0, s>>>(a);
-    mark(tr, "set_cur", s);
-    ++nl;
     if (a.dv_on) {
+        k_set_cur<<<1, 1, 0, s>>>(a);
+        mark(tr, "set_cur", s);
         // Eq. v_MT and Eq. v_interstitial rebuilt from the scaled blocks:
         // dVV = L^H (s dh) L + CC_G^H (s dV~ * CC_G)
         k_vstep<<<(a.nvt + 255) / 256, 256, 0, s>>>(a);
@@ -823,7 +1177,7 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
         mark(tr, "dv_interstitial_toeplitz", s);
         launch_gemm_cn(p.gd_dvi, a.nk, a.naux, p.maxng, a.naux, 0, nullptr, 1, false, nullptr, s);
         mark(tr, "dv_interstitial_project", s);
-        nl += 5;
+        nl += 6;
     }
     k_hsub<<<dim3((nn + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
     mark(tr, "hsub", s);
@@ -836,50 +1190,58 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
         launch_gemm_nn(p.gd_evn, a.nk, a.naux, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
         mark(tr, "eig_apply", s);
         nl += 4;
+    } else if (a.coop_grid > 0) {
+        launch_cheb_coop(a, s);
+        mark(tr, "chebyshev_series", s);
+        ++nl;
     } else {
-        dim3 g((a.naux + 7) / 8, 1, a.nk);
+        dim3 g(a.naux, 1, a.nk);
         for (int t = 1; t < a.nterms; ++t) {
             const int last = (t == a.nterms - 1);
-            if (a.ns <= 2) k_cheb<2><<<g, 256, 0, s>>>(a, t, last);
-            else if (a.ns <= 4) k_cheb<4><<<g, 256, 0, s>>>(a, t, last);
-            else k_cheb<8><<<g, 256, 0, s>>>(a, t, last);
+            if (a.ns <= 2) k_cheb<2><<<g, 128, 0, s>>>(a, t, last);
+            else if (a.ns <= 4) k_cheb<4><<<g, 128, 0, s>>>(a, t, last);
+            else k_cheb<8><<<g, 128, 0, s>>>(a, t, last);
             mark(tr, "chebyshev_term", s);
             ++nl;
         }
     }
     // C = CC theta (Eq. approximation_coefficients)
-    launch_gemm_nn(p.gd_expand, a.nk, p.maxnb, a.naux, a.ns, 0, nullptr, 0, f32, nullptr, s);
+    launch_gemm_nn(p.gd_expand, a.nk, p.maxnb, a.naux, a.ns, p.kc_expand, p.kc_expand > 0 ? p.part : nullptr,
+                   0, f32, nullptr, s);
     mark(tr, "gemm_expand", s);
     ++nl;
+    if (p.kc_expand > 0) {
+        launch_split_reduce(p.gd_expand, a.nk, p.maxnb, a.ns, p.kc_expand, p.part, 0, s);
+        mark(tr, "split_reduce_expand", s);
+        ++nl;
+    }
     launch_operator_pass(a, p, s, tr);
-    nl += 4;
-    k_reduce_full<<<dim3(RB_FULL, a.ns, a.nk), 256, 0, s>>>(a);
-    mark(tr, "reduce_full", s);
-    ++nl;
-    // theta~ = CC^H (S C)
+    nl += 3 + 2 * ((a.ns + 7) / 8);
+    // theta~ = CC^H (S C): split-K partials, finished per row in k_post
     launch_gemm_cn(p.gd_proj, a.nk, a.naux, p.maxnb, a.ns, p.kc_proj, p.part, 0, f32, nullptr, s);
     mark(tr, "gemm_project", s);
-    launch_split_reduce(p.gd_proj, a.nk, a.naux, a.ns, p.kc_proj, p.part, 0, s);
-    mark(tr, "split_reduce_project", s);
-    launch_gemm_cn(p.gd_g1, a.nk, a.ns, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
-    mark(tr, "gram", s);
-    k_normred<<<a.nk, 256, 0, s>>>(a);
-    mark(tr, "norm_residual", s);
-    nl += 4;
+    {
+        dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
+        k_post<<<g, 128, 0, s>>>(a, 1, a.reproject ? 0 : 1);
+        mark(tr, "project_finish_current", s);
+    }
+    if (a.ns > 4) {
+        launch_gemm_cn(p.gd_g1, a.nk, a.ns, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
+        mark(tr, "gram", s);
+        ++nl;
+    }
+    nl += 2;
     if (a.reproject) {
         launch_gemm_cn(p.gd_g2, a.nk, a.ns, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
         k_reproj<<<dim3((a.naux * a.ns + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
+        dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
+        k_post<<<g, 128, 0, s>>>(a, 0, 1);
         mark(tr, "reproject", s);
-        nl += 2;
+        nl += 3;
     }
-    {
-        dim3 g((3 * a.naux + 7) / 8, 1, a.nk);
-        k_subj<<<g, 256, 0, s>>>(a);
-        mark(tr, "subspace_current", s);
-        k_finalize<<<1, 256, 0, s>>>(a, 0);
-        mark(tr, "finalize", s);
-    }
-    nl += 2;
+    k_finalize<<<1, 256, 0, s>>>(a, 0);
+    mark(tr, "finalize", s);
+    ++nl;
     if (nlaunch) *nlaunch = nl;
 }
 
@@ -902,4 +1264,47 @@ void launch_check_samples(const double* a, int na, double amax, const double* s,
     const int n = na > ns ? na : ns;
     if (n == 0) return;
     k_check_samples<<<(n + 255) / 256 < 64 ? (n + 255) / 256 : 64, 256, 0, st>>>(a, na, amax, s, ns, smax, flag);
+}
+
+__global__ void k_set_cstep(DevState* st, int c) { st->cstep = c; }
+
+// The subspace part of a step only (HH(t_k) and its Chebyshev series, one
+// launch per term): what the adjoint recomputes.  cstep selects the sample.
+void launch_propagate_only(const StepArgs& a, const StepPlan& p, int cstep, cudaStream_t s) {
+    k_set_cstep<<<1, 1, 0, s>>>(a.st, cstep);
+    if (a.dv_on) {
+        k_set_cur<<<1, 1, 0, s>>>(a);
+        k_vstep<<<(a.nvt + 255) / 256, 256, 0, s>>>(a);
+        launch_gemm_nn(p.gd_dvw, p.n_dvw, p.maxm, p.maxm, a.naux, 0, nullptr, 0, false, &a.st->cur_s, s);
+        launch_gemm_cn(p.gd_dvg, a.nk, a.naux, a.lrows, a.naux, 0, nullptr, 0, false, nullptr, s);
+        launch_toeplitz(a.kd, p.td_dv, a.nk, p.maxng, a.naux, a.dvtab, a.vt_center, 0, 0, &a.st->cur_s, s);
+        launch_gemm_cn(p.gd_dvi, a.nk, a.naux, p.maxng, a.naux, 0, nullptr, 1, false, nullptr, s);
+    }
+    k_hsub<<<dim3((a.naux * a.naux + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
+    dim3 g(a.naux, 1, a.nk);
+    for (int t = 1; t < a.nterms; ++t) {
+        const int last = (t == a.nterms - 1);
+        if (a.ns <= 2) k_cheb<2><<<g, 128, 0, s>>>(a, t, last);
+        else if (a.ns <= 4) k_cheb<4><<<g, 128, 0, s>>>(a, t, last);
+        else k_cheb<8><<<g, 128, 0, s>>>(a, t, last);
+    }
+}
+
+// HH(t_k) only (the adjoint's reverse sweep needs the matrix of step cstep)
+void launch_hsub_only(const StepArgs& a, const StepPlan& p, int cstep, cudaStream_t s) {
+    k_set_cstep<<<1, 1, 0, s>>>(a.st, cstep);
+    if (a.dv_on) {
+        k_set_cur<<<1, 1, 0, s>>>(a);
+        launch_gemm_nn(p.gd_dvw, p.n_dvw, p.maxm, p.maxm, a.naux, 0, nullptr, 0, false, &a.st->cur_s, s);
+        launch_gemm_cn(p.gd_dvg, a.nk, a.naux, a.lrows, a.naux, 0, nullptr, 0, false, nullptr, s);
+        launch_toeplitz(a.kd, p.td_dv, a.nk, p.maxng, a.naux, a.dvtab, a.vt_center, 0, 0, &a.st->cur_s, s);
+        launch_gemm_cn(p.gd_dvi, a.nk, a.naux, p.maxng, a.naux, 0, nullptr, 1, false, nullptr, s);
+    }
+    k_hsub<<<dim3((a.naux * a.naux + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
+}
+
+// J contributions of the current theta (rows into part_post[.][1..3])
+void launch_subspace_j(const StepArgs& a, cudaStream_t s) {
+    dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
+    k_post<<<g, 128, 0, s>>>(a, 0, 1);
 }

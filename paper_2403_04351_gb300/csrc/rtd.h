@@ -9,7 +9,8 @@
 #define RTD_MAX_ATOMS 64
 #define RTD_MAX_TERMS 512
 #define RTD_REC_STRIDE 16  // doubles per step record
-#define RB_FULL 16         // row blocks of the full-basis reductions
+#define BT 128            // plane-wave rows (and G' columns) per tile of the back kernel
+#define LAM_N 8           // doubles per k-point of the Chebyshev scaling record
 
 // Record fields (offsets within one record)
 enum { REC_T = 0, REC_J = 1, REC_JF = 4, REC_DMU = 7, REC_E = 10, REC_NDEV = 11,
@@ -53,8 +54,8 @@ struct KDev {
     int ng, nb;
     zd* caux;     // nb x naux
     zf* caux32;   // nb x naux (FP32 form)
-    zd* amat;     // ma x ng
-    zf* amat32;   // ma x ng (FP32 form)
+    zd* at;       // ng x ma: A^H, the matching coefficients conjugate-transposed
+    zf* at32;     // ng x ma (FP32 form)
     int* glin;    // ng  linear table index of G
     double* gk;   // ng x 3 (row-major)
     double* eps;  // naux
@@ -75,7 +76,7 @@ struct KDev {
     double* eval; // naux
     zd* wtmp;     // naux x ns
     zd* coef;     // RTD_MAX_TERMS Chebyshev coefficients
-    double* lam;  // [2] spectral centre and half-width of HH (written per call)
+    double* lam;  // [LAM_N]: centre, half-width, 1/half-width, cos and sin of -dt*centre
     double dtcr_b;// dt_cr from the bounds of the call
     double pad;
 };
@@ -93,7 +94,7 @@ struct DevState {
     double cur_s;       // potential-change scale of the current step
     double cur_aa;      // |A|^2 / (2 c^2)
     int err;            // nonzero: a device iteration limit ran out
-    int pad;
+    unsigned bar;       // arrival counter of the grid barrier (zeroed by k_hsub)
 };
 
 // Everything the step kernels need, passed by value
@@ -101,6 +102,7 @@ struct StepArgs {
     int nk, ns, naux, prop, prec, reproject, nterms, dv_on;
     int vt_center, nvt, lrows, ma, rec_cap, pad;
     double dt, c, omega;
+    double inv_c, half_inv_c2;  // 1/c and 1/(2 c^2): GB300 FP64 division is slow, multiply instead
     const KDev* kd;
     const double* occ;   // ns
     const double* wk;    // nk
@@ -117,12 +119,21 @@ struct StepArgs {
     const double* dvs;   // call dv scales (or null)
     DevState* st;
     double* rec;         // records
-    double* part_jmt;    // [nk][lrows][3]
-    double* part_full;   // [nk][ns][RB_FULL][5]
-    double* part_sub;    // [nk][3][naux]
-    double* part_norm;   // [nk][2]
+    double* part_jmt;    // [nk][lrows][5]  per local row: J_mt (3), LO-row E and c^H S c
+    double* part_full;   // [nk][max_nback][5] per back tile: E, c^H S c, sum (G+k)|c|^2 (3)
+    double* part_post;   // [nk][naux][POST_STRIDE]  per subspace row
     const AtomTab* at;   // device copy
+    const GemmDesc* gd_proj;  // projection descriptors (split-K partial offsets)
+    const zd* part_proj;      // projection split-K partials
+    int kc_proj, max_nback;
+    int wmax;                 // largest table window of a back tile (entries)
+    int nseg, segw, maxng;    // G' segments of the interstitial sum
+    int msegw, nslot;         // matching rows per back-projection slot; nseg + such slots
+    zd* part_t;               // [nk][nslot][2 NT][maxng] slot partial sums
+    int* flag;                // device error flags (bit 0 Jacobi, 1 bounds, 2 barrier)
+    int coop_grid;            // blocks of the cooperative Chebyshev launch (0: per-term launches)
 };
+#define POST_STRIDE 36        // part_post row: residual, J_sub (3), then theta^H theta~ (ns <= 4)
 
 // ---- k_linalg.cu
 void launch_gemm_nn(const GemmDesc* d, int nbatch, int maxM, int maxK, int N, int kchunk,
@@ -137,13 +148,15 @@ void launch_toeplitz(const KDev* kd, const ToepDesc* td, int nk, int maxng, int 
 void launch_zero(zd* p, size_t n, cudaStream_t s);
 void launch_copy_rows(const GemmDesc* d, int nbatch, int maxrows, int ncol, cudaStream_t s);
 void launch_convert_f32(const zd* src, zf* dst, size_t n, cudaStream_t s);
+// AT (n x m) = A^H for A (m x n), both column-major
+void launch_conj_transpose(const zd* A, zd* AT, int m, int n, cudaStream_t s);
 
 // ---- k_step.cu
 struct StepPlan {
     int maxnb, maxng, nterms;
     const GemmDesc *gd_expand, *gd_fwd, *gd_proj, *gd_g1, *gd_g2, *gd_evh, *gd_evn;
     zd* part;
-    int kc_fwd, kc_proj;
+    int kc_fwd, kc_proj, kc_expand;
     // potential change (a2)
     const GemmDesc *gd_dvw, *gd_dvg, *gd_dvi;   // W = dh L, dV = L^H W, dV += C_G^H T
     const ToepDesc* td_dv;                       // T = dV~ C_G
@@ -162,6 +175,10 @@ struct TraceHook {
 void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlaunch,
                  TraceHook* tr = nullptr);
 void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr = nullptr);
+int prepare_back_kernels(const StepArgs& a);
+// blocks for the cooperative Chebyshev launch if it can be captured in a graph, else 0
+int prepare_cheb_coop(const StepArgs& a, cudaStream_t s);
+void launch_cheb_coop(const StepArgs& a, cudaStream_t s);
 void launch_prep_coef(const StepArgs& a, cudaStream_t s);
 void launch_subspace_current(const StepArgs& a, int set_gs, cudaStream_t s);
 void launch_set_cur(const StepArgs& a, cudaStream_t s);
@@ -174,3 +191,15 @@ void launch_phase_fix(const KDev* kd, int nk, int naux, zd* const* extra, const 
                       int nextra_rows, cudaStream_t s);
 void launch_scale_cols(zd* const* mats, const double* const* vals, int nbatch, int n, int mode,
                        cudaStream_t s);
+
+// ---- adjoint (k_step.cu, k_adjoint.cu)
+void launch_propagate_only(const StepArgs& a, const StepPlan& p, int cstep, cudaStream_t s);
+void launch_hsub_only(const StepArgs& a, const StepPlan& p, int cstep, cudaStream_t s);
+void launch_subspace_j(const StepArgs& a, cudaStream_t s);
+void launch_adj_fwd_term(const StepArgs& a, zd* Yh, int nterm, int nt, cudaStream_t s);
+void launch_adj_bwd_init(const StepArgs& a, zd* Yb, const zd* lam, int nterm, cudaStream_t s);
+void launch_adj_bwd_term(const StepArgs& a, zd* Yb, int nterm, int nt, cudaStream_t s);
+void launch_adj_grad(const StepArgs& a, const zd* Yh, const zd* Yb, int nterm, double* part, int nblk,
+                     cudaStream_t s);
+void launch_adj_jterm(const StepArgs& a, zd* lam, const zd* theta, const double* g, double sm, double cfac,
+                      double* nrm, cudaStream_t s);

@@ -151,6 +151,30 @@ def algorithmic_work(name, sysd, prec, nterms=1):
     return fl, by
 
 
+def reduce_max(x, device):
+    """Max over all ranks of a per-rank float (the slowest replica sets the
+    time); the value itself when no process group is running."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if torch.distributed.is_available() and torch.distributed.is_initialized() \
+            and torch.distributed.get_world_size() > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch
+    if torch.distributed.is_available() and torch.distributed.is_initialized() \
+            and torch.distributed.get_world_size() > 1:
+        torch.distributed.barrier()
+
+
+def job_throughput(states_per_rank, steps, world, t_max):
+    """Whole-job state*steps/s: every replica advances its own copy of the
+    workload, so the units of all ranks count, over the slowest rank's time."""
+    return states_per_rank * steps * world / t_max
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -190,8 +214,7 @@ def run_ours(args, rank, world, local_rank):
         ctx.observables(clear=True)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(nsteps)]
-        if world > 1:
-            torch.distributed.barrier()
+        barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for i in range(nsteps):
@@ -201,8 +224,7 @@ def run_ours(args, rank, world, local_rank):
             ev[i][1].record(stream)
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - t0
-        if world > 1:
-            torch.distributed.barrier()
+        barrier()
         dev_s = sum(e0.elapsed_time(e1) for e0, e1 in ev) * 1e-3
         obs = ctx.observables(clear=True)
         return ctx, dev_s, wall, obs
@@ -210,12 +232,8 @@ def run_ours(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         ctx, dev_s, wall, obs = timed_form(args.precision, K, W)
     clocks = clk.summary()
-    # slowest rank sets the time
-    times = torch.tensor([dev_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
-    dev_max = float(times.item())
-    value = n_states * K * world / dev_max
+    dev_max = reduce_max(dev_s, dev)
+    value = job_throughput(n_states, K, world, dev_max)
 
     # per-kernel trace (CUDA events after every launch, L2 flushed before each step)
     tr = {}
@@ -237,10 +255,7 @@ def run_ours(args, rank, world, local_rank):
         rec = ctx.observables(clear=True)
         if i >= W:
             e2e_s += time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = n_states * K * world / float(e2e_t.item())
+    e2e_value = job_throughput(n_states, K, world, reduce_max(e2e_s, dev))
     info = ctx.info()
     ctx.close()
 

@@ -258,6 +258,29 @@ typedef struct {
 RTTDDFT_API int rttddft_trace_steps(rttddft_ctx* ctx, int nsteps, const double* a_samples,
                                     const double* dv_scale, rttddft_trace* out);
 
+/* Split-BF16 complex GEMM on the tensor cores, the contraction form of the
+ * precision option RTTDDFT_PREC_BF16X3 (the bulk contractions of Sec. 2:
+ * expansion C = CC theta, Eq. approximation_coefficients, and projection
+ * CC^H S C, Eq. evolution_of_projection_coeff):
+ *   C = op(A) X          (beta_add = 0)   or   C += op(A) X  (beta_add = 1),
+ * op(A) = A (trans = 0, A is m x k) or A^H (trans = 1, A is k x m); X is
+ * k x n; C is m x n.  The complex product is one real GEMM on
+ * [Re A | Im A] and, per column of X, [Re x | -Im x] and [Im x | Re x]; each
+ * real operand is split as v = hi + lo with hi, lo bf16, and
+ * hi.hi + hi.lo + lo.hi is accumulated in FP32 on the tensor cores per slice
+ * of K, the slices summed in FP64.  Error per element: a few 2^-16 of
+ * sum_k |a||x| (the dropped lo.lo term and the rounding of lo).
+ * a, x, c: device pointers, complex, column-major, lda >= rows of A,
+ * ldx >= k, ldc >= m.  stream: a cudaStream_t or NULL.  The call allocates
+ * and frees its own workspace (about (m + 2n) x 8k bytes) and synchronizes
+ * the stream before it returns.  m, n or k = 0 is allowed (C unchanged for
+ * k = 0 with beta_add = 1, zero otherwise).
+ * Errors: ERR_ARG (sizes, leading dimensions, NULL), ERR_OOM, ERR_CUDA,
+ * ERR_TIMEOUT (a bounded wait of the copy/product pipeline ran out),
+ * ERR_UNSUPPORTED (the driver has no tensor-map encoder). */
+RTTDDFT_API int rttddft_zgemm_bf16x3(int trans, int m, int n, int k, const double* a, int lda, const double* x,
+                                     int ldx, double* c, int ldc, int beta_add, void* stream);
+
 RTTDDFT_API void rttddft_destroy(rttddft_ctx* ctx);
 
 /* Text of the last error on `ctx` (or of the last failed rttddft_setup in

@@ -1911,3 +1911,22 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         return f.code;
     }
 }
+
+extern "C" int rttddft_zgemm_bf16x3(int trans, int m, int n, int k, const double* a, int lda, const double* x,
+                                    int ldx, double* c, int ldc, int beta_add, void* stream) {
+    if (m < 0 || n < 0 || k < 0 || (trans != 0 && trans != 1)) return RTTDDFT_ERR_ARG;
+    if (m == 0 || n == 0) return RTTDDFT_OK;
+    if (!a || !x || !c) return RTTDDFT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (k == 0) {
+        if (!beta_add) {
+            if (ldc < m) return RTTDDFT_ERR_ARG;
+            if (cudaMemset2DAsync(c, (size_t)ldc * 16, 0, (size_t)m * 16, n, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return RTTDDFT_ERR_CUDA;
+        }
+        return RTTDDFT_OK;
+    }
+    if (!is_device_ptr(a) || !is_device_ptr(x) || !is_device_ptr(c)) return RTTDDFT_ERR_ARG;
+    return tc_zgemm(trans, m, n, k, (const zd*)a, lda, (const zd*)x, ldx, (zd*)c, ldc, beta_add, s);
+}

@@ -203,3 +203,7 @@ void launch_adj_grad(const StepArgs& a, const zd* Yh, const zd* Yb, int nterm, d
                      cudaStream_t s);
 void launch_adj_jterm(const StepArgs& a, zd* lam, const zd* theta, const double* g, double sm, double cfac,
                       double* nrm, cudaStream_t s);
+
+// ---- tensor-core split-BF16 complex GEMM (k_tc.cu); returns an RTTDDFT_* code
+int tc_zgemm(int opA, int M, int N, int K, const zd* A, int lda, const zd* X, int ldx, zd* C, int ldc,
+             int beta_add, cudaStream_t s);

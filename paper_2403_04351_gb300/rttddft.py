@@ -27,7 +27,7 @@ AUX = {"ritz": 0, "given": 1}
 EXPORTED = ["rttddft_default_options", "rttddft_setup", "rttddft_step", "rttddft_observables",
             "rttddft_set_dv", "rttddft_apply", "rttddft_get_state", "rttddft_set_state",
             "rttddft_get_aux", "rttddft_get_info", "rttddft_adjoint", "rttddft_trace_steps",
-            "rttddft_apply_noalloc",
+            "rttddft_apply_noalloc", "rttddft_zgemm_bf16x3",
             "rttddft_destroy", "rttddft_last_error", "rttddft_version"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -116,6 +116,9 @@ def load_library(path=None):
     lib.rttddft_adjoint.restype = ctypes.c_int
     lib.rttddft_trace_steps.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.POINTER(rttddft_trace)]
     lib.rttddft_trace_steps.restype = ctypes.c_int
+    lib.rttddft_zgemm_bf16x3.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
+                                         ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.rttddft_zgemm_bf16x3.restype = ctypes.c_int
     lib.rttddft_destroy.argtypes = [vp]
     lib.rttddft_destroy.restype = None
     lib.rttddft_last_error.argtypes = [vp]
@@ -181,6 +184,15 @@ def rttddft_apply_noalloc(ctx, k, ncols, x, a_vec, dv_scale, hx, sx):
     """Operator apply with the library's static scratch (device pointers only)."""
     _check(ctx, load_library().rttddft_apply_noalloc(ctx, int(k), int(ncols), _ptr(x), _ptr(a_vec),
                                                      float(dv_scale), _ptr(hx), _ptr(sx)))
+
+
+def rttddft_zgemm_bf16x3(trans, m, n, k, a, lda, x, ldx, c, ldc, beta_add=0, stream=None):
+    """Split-BF16 complex GEMM on the tensor cores (device pointers)."""
+    code = load_library().rttddft_zgemm_bf16x3(int(trans), int(m), int(n), int(k), _ptr(a), int(lda),
+                                               _ptr(x), int(ldx), _ptr(c), int(ldc), int(beta_add),
+                                               _ptr(stream))
+    if code != RTTDDFT_OK:
+        raise RttddftError(code, "rttddft_zgemm_bf16x3 failed (%s)" % ERRORS.get(code, code))
 
 
 def rttddft_get_state(ctx, k, theta, c=None):

@@ -53,9 +53,19 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
 def _src_hash():
     h = hashlib.sha256()
-    for f in ("k_linalg.cu", "k_step.cu", "common.cuh", "rtd.h"):
+    for f in ("k_linalg.cu", "k_step.cu", "k_tc.cu", "common.cuh", "rtd.h"):
         with open(os.path.join(ROOT, "paper_2403_04351_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -131,6 +141,10 @@ def algorithmic_work(name, sysd, prec, nterms=1):
         if name == "toeplitz_and_backprojection":
             fl += 8 * ns * (ng * ng + 2 * ng * ma)
             by += ma * ng * cb + ng * ns * 16 * 2
+        elif name == "tc_interstitial_and_forward":
+            # split-BF16: three bf16 products per complex multiply-add
+            fl += 3 * 8 * ns * (ng * ng + ng * ma)
+            by += ma * ng * 8 + ng * ns * 8
         elif name == "gemm_expand":
             fl += 8 * nb * naux * ns
             by += nb * naux * cb + nb * ns * 16
@@ -173,6 +187,37 @@ def job_throughput(states_per_rank, steps, world, t_max):
     """Whole-job state*steps/s: every replica advances its own copy of the
     workload, so the units of all ranks count, over the slowest rank's time."""
     return states_per_rank * steps * world / t_max
+
+
+def roofline_of(name, tr, s, prec, nterms):
+    """Roofline entry of one traced kernel slot: algorithmic work per launch
+    over its mean event-timed duration, against the peak of its bound."""
+    dur = tr[name][0] / tr[name][1] * 1e-3  # seconds per launch
+    fl, by = algorithmic_work(name, s, prec, nterms)
+    hbm, src = _peaks()
+    if name in ("gemm_expand", "gemm_project", "gemm_forward") and prec != "fp64":
+        ach = by / dur / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "peak_source": src}
+    elif name == "tc_interstitial_and_forward":
+        peak, src = _bf16_peak()
+        ach = fl / dur / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "peak_source": src + " (cuBLAS bf16 burst)"}
+    else:
+        if prec == "fp64" or name in ("chebyshev_term", "chebyshev_series"):
+            peak = FP64_PEAK_TFLOPS
+            src = "recipe FP64 nominal"
+        else:
+            peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+            src = "152 SM x 128 FP32 lanes x 2 x 2070 MHz"
+        ach = fl / dur / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "peak_source": src}
+    roof["kernel"] = name
+    roof["ms_per_launch"] = dur * 1e3
+    roof["traffic"] = TRAFFIC.get((name, prec, s["name"], _src_hash()))
+    return roof
 
 
 def run_ours(args, rank, world, local_rank):
@@ -267,38 +312,19 @@ def run_ours(args, rank, world, local_rank):
         fp64 = {"value": n_states * args.fp64_steps / d64, "ms_per_step": d64 / args.fp64_steps * 1e3,
                 "steps": args.fp64_steps}
 
-    # roofline of the dominant kernel slot
+    # roofline of the dominant kernel slot (and of the tensor-core kernel, if any)
     dom = max(tr.items(), key=lambda kv: kv[1][0])[0] if tr else None
-    roof = None
-    if dom:
-        dur = tr[dom][0] / tr[dom][1] * 1e-3  # seconds per launch
-        fl, by = algorithmic_work(dom, s, args.precision, info["cheb_terms"])
-        hbm, src = _peaks()
-        if dom in ("gemm_expand", "gemm_project", "gemm_forward") and args.precision == "fp32":
-            ach = by / dur / 1e9
-            roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm, "peak_source": src}
-        else:
-            if args.precision == "fp64" or dom in ("chebyshev_term", "chebyshev_series"):
-                peak = FP64_PEAK_TFLOPS
-                src = "recipe FP64 nominal"
-            else:
-                peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-                src = "152 SM x 128 FP32 lanes x 2 x 2070 MHz"
-            ach = fl / dur / 1e12
-            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "peak_source": src}
-        key = (dom, args.precision, args.workload, _src_hash())
-        roof["kernel"] = dom
-        roof["ms_per_launch"] = dur * 1e3
-        roof["traffic"] = TRAFFIC.get(key)
+    roof = roofline_of(dom, tr, s, args.precision, info["cheb_terms"]) if dom else None
+    roof_tc = None
+    if "tc_interstitial_and_forward" in tr and dom != "tc_interstitial_and_forward":
+        roof_tc = roofline_of("tc_interstitial_and_forward", tr, s, args.precision, info["cheb_terms"])
     share = {n: round(v[0] / sum(x[0] for x in tr.values()), 4) for n, v in tr.items()}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": dev_max / K * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "dtype": {"fp64": "f64", "fp32": "f32+f64", "bf16x3": "bf16x3+f32+f64"}[args.precision],
         "data": "synthetic (seeded generator shaped like the paper's H2 cell)",
         "config": {"workload": args.workload, "n_k": int(s["n_k"]), "n_basis": int(s["n_g"][0]) +
                    int(np.sum(s["n_lo"])), "n_states": int(s["n_s"]), "n_aux": int(s["n_aux"]),
@@ -311,6 +337,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(info["kernel_launches_per_step"]) * K,
         "clocks": clocks,
         "roofline": roof,
+        "roofline_tc": roof_tc,
         "kernel_share": share,
         "fp64": fp64,
         "wall_s": wall,
@@ -376,7 +403,7 @@ def main():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    p.add_argument("--precision", choices=["fp32", "fp64", "bf16x3"], default="fp32")
     p.add_argument("--workload", default="h2_6000")
     p.add_argument("--fp64-steps", type=int, default=50)
     p.add_argument("--trace-steps", type=int, default=5)

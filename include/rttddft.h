@@ -71,6 +71,12 @@ extern "C" {
  * the subspace propagation and every reduction stay FP64 */
 #define RTTDDFT_PREC_FP64 0
 #define RTTDDFT_PREC_FP32 1
+/* split-BF16 on the tensor cores: the interstitial convolution and the
+ * matching-coefficient products of the operator run as tcgen05 products of
+ * bf16 hi/lo splits (hi.hi + hi.lo + lo.hi, FP32 accumulation, FP64 sums of
+ * the K slices, relative error a few 2^-16); the other full-basis
+ * contractions as in RTTDDFT_PREC_FP32.  At most 128 states. */
+#define RTTDDFT_PREC_BF16X3 2
 
 /* how the auxiliary basis CC(0) is obtained at set-up */
 #define RTTDDFT_AUX_RITZ 0  /* Ritz vectors of H0 in span(caux): S-orthonormal, H0-diagonal */
@@ -146,6 +152,13 @@ typedef struct {
     int cheb_terms;        /* terms of the last Chebyshev series */
     double dt_cr0;         /* Eq. critical_timestep from the set-up eigenvalues, min over k */
     int kernel_launches_per_step; /* kernels launched per step (graph nodes) */
+    int precision;         /* RTTDDFT_PREC_* of the context */
+    int tc_tile_n;         /* split-BF16 form: real output columns per tensor-core tile (0 otherwise) */
+    int tc_stages;         /*   shared-memory pipeline stages */
+    int tc_kblocks;        /*   K blocks (32 G') per slice */
+    int tc_slices;         /*   K slices */
+    int tc_window;         /*   largest interstitial table window staged (entries) */
+    int tc_smem;           /*   dynamic shared memory per block (bytes) */
 } rttddft_info;
 
 RTTDDFT_API void rttddft_default_options(rttddft_options* opt);

@@ -37,6 +37,8 @@ struct rttddft_ctx {
     KDev* d_kd = nullptr;
     AtomTab* d_at = nullptr;
     zd *d_h = nullptr, *d_o = nullptr, *d_p = nullptr, *d_dh = nullptr;
+    zf *d_h32 = nullptr, *d_o32 = nullptr, *d_p32 = nullptr;
+    size_t nblk = 0;
     zd *d_vtab = nullptr, *d_dvtab = nullptr, *d_vstep = nullptr;
     zf *d_vtab32 = nullptr, *d_vstep32 = nullptr;
     double *d_occ = nullptr, *d_wk = nullptr, *d_lam = nullptr;
@@ -58,6 +60,8 @@ struct rttddft_ctx {
     zd** d_jac_vecs = nullptr;
     int kc_fwd = 0, kc_proj = 0, kc_expand = 0;
     std::vector<double> eps_min, eps_max, pnorm, dvnorm;
+    std::vector<std::vector<int>> h_glin;       // host copy of the table offsets of G per k
+    TcPlan* tc = nullptr;                       // tensor-core operator (split-BF16 form)
     double dtcr0 = 0;
     int nterms = 0, launches_per_step = 0;
     bool dv_set = false;
@@ -190,6 +194,9 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.h = ctx->d_h;
     a.o = ctx->d_o;
     a.p = ctx->d_p;
+    a.h32 = ctx->d_h32;
+    a.o32 = ctx->d_o32;
+    a.p32 = ctx->d_p32;
     a.dh = dv_on ? ctx->d_dh : nullptr;
     a.vtab = ctx->d_vtab;
     a.vtab32 = ctx->d_vtab32;
@@ -247,6 +254,7 @@ static StepPlan make_plan(rttddft_ctx* ctx) {
     p.jac_vals = ctx->d_jac_vals;
     p.jac_vecs = ctx->d_jac_vecs;
     p.max_sweeps = ctx->opt.max_sweeps;
+    p.tc = ctx->tc;
     return p;
 }
 
@@ -481,7 +489,7 @@ static void validate(const rttddft_system* s, const rttddft_options* o) {
     if (!o) fail(ctx, RTTDDFT_ERR_ARG, "options are NULL");
     if (!(o->dt > 0)) fail(ctx, RTTDDFT_ERR_ARG, "dt must be > 0");
     if (o->propagator < 0 || o->propagator > 2) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown propagator");
-    if (o->precision < 0 || o->precision > 1) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown precision form");
+    if (o->precision < 0 || o->precision > 2) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown precision form");
     if (o->aux_mode < 0 || o->aux_mode > 1) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown aux_mode");
     if (o->aux_mode == RTTDDFT_AUX_GIVEN && !s->eps) fail(ctx, RTTDDFT_ERR_ARG, "GIVEN mode needs eps");
     if (o->max_record < 1 || o->graph_steps < 0 || o->max_sweeps < 1) fail(ctx, RTTDDFT_ERR_ARG, "bad option value");
@@ -519,6 +527,7 @@ void rttddft_destroy(rttddft_ctx* ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    tc_plan_destroy(ctx->tc);
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
@@ -652,6 +661,7 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
         ctx->d_occ = dupload(ctx, s->occ, ns);
         ctx->d_wk = dupload(ctx, s->wk, nk);
         if (at.n > 0) {
+            ctx->nblk = nblk;
             ctx->d_h = dupload(ctx, (const zd*)s->h, nblk);
             ctx->d_o = dupload(ctx, (const zd*)s->o, nblk);
             ctx->d_p = dupload(ctx, (const zd*)s->p, 3 * nblk);
@@ -710,6 +720,7 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
                 gl[g] = (t[0] * d1 + t[1]) * d2 + t[2];
             }
             K.glin = dupload(ctx, gl.data(), gl.size());
+            ctx->h_glin.push_back(gl);
             K.gk = dupload(ctx, s->gk + 3 * g_off[k], 3 * (size_t)K.ng);
             K.eps = dalloc<double>(ctx, naux);
             K.psub = dalloc<zd>(ctx, 3 * nn);
@@ -723,6 +734,7 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             K.Y = dalloc<zd>(ctx, (size_t)K.nb * 2 * ns);
             K.Q = dalloc<zd>(ctx, (size_t)std::max(at.ma, 1) * ns);
             K.Z = dalloc<zd>(ctx, (size_t)std::max(at.ma, 1) * 2 * ns);
+            K.th = (o->precision == RTTDDFT_PREC_BF16X3) ? dalloc<zd>(ctx, (size_t)K.ng * ns) : nullptr;
             K.gram = dalloc<zd>(ctx, 2 * (size_t)ns * ns);
             K.evec = dalloc<zd>(ctx, nn);
             K.eval = dalloc<double>(ctx, naux);
@@ -868,8 +880,8 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             dfree(ctx, T2[k]);
             dfree(ctx, E1[k]);
         }
-        // ---- FP32 copies for the FP32 form
-        if (o->precision == RTTDDFT_PREC_FP32) {
+        // ---- FP32 copies for the FP32 and split-BF16 forms
+        if (o->precision != RTTDDFT_PREC_FP64) {
             for (int k = 0; k < nk; ++k) {
                 KDev& K = ctx->hkd[k];
                 K.caux32 = dalloc<zf>(ctx, (size_t)K.nb * naux);
@@ -881,12 +893,35 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             }
             ctx->d_vtab32 = dalloc<zf>(ctx, ctx->nvt);
             launch_convert_f32(ctx->d_vtab, ctx->d_vtab32, ctx->nvt, ctx->stream);
+            if (ctx->nblk > 0) {
+                ctx->d_h32 = dalloc<zf>(ctx, ctx->nblk);
+                ctx->d_o32 = dalloc<zf>(ctx, ctx->nblk);
+                ctx->d_p32 = dalloc<zf>(ctx, 3 * ctx->nblk);
+                launch_convert_f32(ctx->d_h, ctx->d_h32, ctx->nblk, ctx->stream);
+                launch_convert_f32(ctx->d_o, ctx->d_o32, ctx->nblk, ctx->stream);
+                launch_convert_f32(ctx->d_p, ctx->d_p32, 3 * ctx->nblk, ctx->stream);
+            }
             KCHECK();
             CK(cudaStreamSynchronize(ctx->stream));
         }
+        // ---- tensor-core operands of the split-BF16 form
+        if (o->precision == RTTDDFT_PREC_BF16X3) {
+            std::vector<int> ngv(nk);
+            std::vector<const int*> glp(nk);
+            std::vector<const zd*> atp(nk);
+            for (int k = 0; k < nk; ++k) {
+                ngv[k] = ctx->hkd[k].ng;
+                glp[k] = ctx->h_glin[k].data();
+                atp[k] = ctx->hkd[k].at;
+            }
+            std::string why;
+            const int e = tc_plan_create(&ctx->tc, nk, ns, at.ma, ngv.data(), glp.data(), atp.data(),
+                                         ctx->vt_center, ctx->stream, &why);
+            if (e) fail(ctx, e, "split-BF16 form: " + why);
+        }
         CK(cudaMemcpy(ctx->d_kd, ctx->hkd.data(), nk * sizeof(KDev), cudaMemcpyHostToDevice));
         // ---- step descriptors
-        const bool f32 = o->precision == RTTDDFT_PREC_FP32;
+        const bool f32 = o->precision != RTTDDFT_PREC_FP64;
         std::vector<GemmDesc> ex, fw, pj, g1, g2, eh, en;
         ctx->kc_fwd = kchunk_for((at.ma + cn_rows(ns) - 1) / cn_rows(ns), nk, ctx->maxng);
         ctx->kc_proj = kchunk_for((naux + cn_rows(ns) - 1) / cn_rows(ns), nk, ctx->maxnb);
@@ -1159,6 +1194,8 @@ static void sync_and_check(rttddft_ctx* ctx) {
     if (flag) {
         CK(cudaMemset(ctx->d_flag, 0, sizeof(int)));
         if (flag & 1) fail(ctx, RTTDDFT_ERR_TIMEOUT, "Jacobi eigensolver reached its sweep limit");
+        if (flag & 4) fail(ctx, RTTDDFT_ERR_TIMEOUT, "the grid barrier of the Chebyshev series timed out");
+        if (flag & 8) fail(ctx, RTTDDFT_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
         fail(ctx, RTTDDFT_ERR_ARG, "a pulse sample or dv scale exceeded a_max / s_max");
     }
 }
@@ -1301,7 +1338,7 @@ int rttddft_get_state(rttddft_ctx* ctx, int k, double* theta, double* c) {
             CK(cudaMemcpy(theta, K.theta, (size_t)ctx->naux * ctx->ns * sizeof(zd), cudaMemcpyDeviceToHost));
         if (c) {
             launch_gemm_nn(ctx->gd_expand, ctx->nk, ctx->maxnb, ctx->naux, ctx->ns, 0, nullptr, 0,
-                           ctx->opt.precision == RTTDDFT_PREC_FP32, nullptr, ctx->stream);
+                           ctx->opt.precision != RTTDDFT_PREC_FP64, nullptr, ctx->stream);
             KCHECK();
             CK(cudaStreamSynchronize(ctx->stream));
             CK(cudaMemcpy(c, K.C, (size_t)K.nb * ctx->ns * sizeof(zd), cudaMemcpyDeviceToHost));
@@ -1349,6 +1386,15 @@ int rttddft_get_info(rttddft_ctx* ctx, rttddft_info* info) {
     info->cheb_terms = ctx->nterms;
     info->dt_cr0 = ctx->dtcr0;
     info->kernel_launches_per_step = ctx->launches_per_step;
+    info->precision = ctx->opt.precision;
+    int v[6] = {0, 0, 0, 0, 0, 0};
+    if (ctx->tc) tc_plan_info(ctx->tc, v);
+    info->tc_tile_n = v[0];
+    info->tc_stages = v[1];
+    info->tc_kblocks = v[2];
+    info->tc_slices = v[3];
+    info->tc_window = v[4];
+    info->tc_smem = v[5];
     return RTTDDFT_OK;
 }
 
@@ -1377,7 +1423,7 @@ int rttddft_set_dv(rttddft_ctx* ctx, const double* dh, const double* dvtab) {
             if (at.n > 0) ctx->d_dh = dalloc<zd>(ctx, nblk);
             ctx->d_dvtab = dalloc<zd>(ctx, ctx->nvt);
             ctx->d_vstep = dalloc<zd>(ctx, ctx->nvt);
-            if (ctx->opt.precision == RTTDDFT_PREC_FP32) ctx->d_vstep32 = dalloc<zf>(ctx, ctx->nvt);
+            if (ctx->opt.precision != RTTDDFT_PREC_FP64) ctx->d_vstep32 = dalloc<zf>(ctx, ctx->nvt);
             std::vector<GemmDesc> w, g, gi;
             std::vector<ToepDesc> td;
             for (int k = 0; k < nk; ++k) {
@@ -1484,6 +1530,7 @@ int rttddft_apply(rttddft_ctx* ctx, int k, int ncols, const double* x, const dou
         StepArgs a = make_args(ctx, dv_on);
         a.kd = ctx->d_kd + k;
         a.nk = 1;
+        a.kofs = k;
         StepPlan p = make_plan(ctx);
         p.gd_fwd = ctx->gd_fwd + k;
         p.maxng = K.ng;
@@ -1500,7 +1547,7 @@ int rttddft_apply(rttddft_ctx* ctx, int k, int ncols, const double* x, const dou
             CK(cudaMemcpyAsync(hz + (size_t)c0 * nb, K.Y, (size_t)w * nb * sizeof(zd), kout, ctx->stream));
             CK(cudaMemcpyAsync(sz + (size_t)c0 * nb, K.Y + (size_t)ns * nb, (size_t)w * nb * sizeof(zd), kout,
                                ctx->stream));
-            CK(cudaStreamSynchronize(ctx->stream));
+            sync_and_check(ctx);
         }
         CK(cudaMemcpy(ctx->d_st, &hst, sizeof(DevState), cudaMemcpyHostToDevice));
         return RTTDDFT_OK;
@@ -1829,7 +1876,7 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         const KDev& K = ctx->hkd[k];
         const int ns = ctx->ns, nb = K.nb, ma = std::max(ctx->at.ma, 1), ng = K.ng;
         const int dv_on = (dv_scale != 0.0) ? 1 : 0;
-        const bool f32 = ctx->opt.precision == RTTDDFT_PREC_FP32;
+        const bool f32 = ctx->opt.precision != RTTDDFT_PREC_FP64;
         const int splits = (ng + ctx->kc_fwd - 1) / ctx->kc_fwd;
         // carve the scratch array
         size_t off = 0;
@@ -1879,6 +1926,7 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         KCHECK();
         StepArgs a = make_args(ctx, dv_on);
         a.kd = (const KDev*)(base + o_kd);
+        if (a.prec == 2) a.prec = 1;  // the static scratch holds the FP32-form operands only
         a.nk = 1;
         a.st = (DevState*)(base + o_st);
         a.part_jmt = (double*)(base + o_jmt);

@@ -172,14 +172,58 @@ __device__ bool grid_barrier(unsigned* count, unsigned target, int* flag) {
     return s_ok != 0;
 }
 
-// The whole Chebyshev series in one cooperative launch.  A block of eight
-// warps owns rows (k, i) round-robin and splits each row's dot products
-// over its warps (on GB300 the FP64 pipe of a single warp would take ~3
-// us per row); a grid barrier separates consecutive terms.  Vectors written
-// by other blocks are read through L2 (ld.global.cg).
+// Sum over the 32 lanes of V values per lane by exchange-halving steps
+// (each lane keeps half of its values and adds its partner's copy of them)
+// followed by plain steps: V - 1 + (5 - log2 V) additions per lane for
+// V <= 32, instead of 5 V (on GB300 each warp-wide FP64 add holds a
+// sub-partition's FP64 pipe for tens of cycles).  Afterwards lane L holds
+// the full sums of values base .. base + max(1, V/32) - 1.
+template <typename T, int V, int OFF>
+struct WarpHalvingSum {
+    static __device__ __forceinline__ void run(T* v, int lane, int& base) {
+        if constexpr (OFF >= 1) {
+            if constexpr (V > 1) {
+                constexpr int H = V / 2;
+                const bool up = (lane & OFF) != 0;
+#pragma unroll
+                for (int u = 0; u < H; ++u) {
+                    const T send = up ? v[u] : v[u + H];
+                    const T keep = up ? v[u + H] : v[u];
+                    v[u] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+                }
+                if (up) base += H;
+                WarpHalvingSum<T, H, OFF / 2>::run(v, lane, base);
+            } else {
+                v[0] += __shfl_xor_sync(0xffffffffu, v[0], OFF);
+                WarpHalvingSum<T, 1, OFF / 2>::run(v, lane, base);
+            }
+        }
+    }
+};
+// Reduce V (a power of two) values per lane over the warp and store the V
+// sums to out[0 .. V-1] (one writer per value).
+template <typename T, int V>
+__device__ __forceinline__ void warp_sum_store(T* v, int lane, T* out) {
+    int base = 0;
+    WarpHalvingSum<T, V, 16>::run(v, lane, base);
+    constexpr int REM = V >= 32 ? V / 32 : 1;
+    constexpr int MASK = V >= 32 ? 0 : (32 / V - 1);
+    if ((lane & MASK) == 0) {
+#pragma unroll
+        for (int r = 0; r < REM; ++r) out[base + r] = v[r];
+    }
+}
+
+// The whole Chebyshev series in one cooperative launch.  A block of two
+// warps owns rows (k, i) round-robin; its lanes stride the row's dot
+// products and reduce them with WarpHalvingSum (the FP64 pipe, not memory,
+// bounds a term on GB300); a grid barrier separates consecutive terms.
+// Vectors written by other blocks are read through L2 (ld.global.cg).
+#define CHEB_THREADS 64
 template <int NT>
-__global__ void __launch_bounds__(256) k_cheb_coop(StepArgs a) {
-    __shared__ double red[8][2 * NT];
+__global__ void __launch_bounds__(CHEB_THREADS) k_cheb_coop(StepArgs a) {
+    constexpr int V = 2 * NT;
+    __shared__ double red[CHEB_THREADS / 32][V];
     const int n = a.naux, ns = a.ns;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t vs = (size_t)n * ns;
@@ -199,29 +243,28 @@ __global__ void __launch_bounds__(256) k_cheb_coop(StepArgs a) {
                 zd acc[NT];
 #pragma unroll
                 for (int c = 0; c < NT; ++c) acc[c] = zmk(0.0, 0.0);
-                for (int j = tid; j < n; j += 256) {
+                for (int j = tid; j < n; j += CHEB_THREADS) {
                     const zd h = H[j];
 #pragma unroll
                     for (int c = 0; c < NT; ++c)
                         if (n0 + c < ns) zfmac(acc[c], h, __ldcg(yin + j + (size_t)(n0 + c) * n));
                 }
+                double v[V];
 #pragma unroll
                 for (int c = 0; c < NT; ++c) {
-                    const zd r = warp_zsum(acc[c]);
-                    if (lane == 0) {
-                        red[warp][2 * c] = r.x;
-                        red[warp][2 * c + 1] = r.y;
-                    }
+                    v[2 * c] = acc[c].x;
+                    v[2 * c + 1] = acc[c].y;
                 }
+                warp_sum_store<double, V>(v, lane, red[warp]);
                 __syncthreads();
                 if (tid < NT && n0 + tid < ns) {
                     const int c = tid;
-                    zd v = zmk(0.0, 0.0);
+                    zd r = zmk(red[0][2 * c], red[0][2 * c + 1]);
 #pragma unroll
-                    for (int w = 0; w < 8; ++w) v = zadd(v, zmk(red[w][2 * c], red[w][2 * c + 1]));
+                    for (int w = 1; w < CHEB_THREADS / 32; ++w) r = zadd(r, zmk(red[w][2 * c], red[w][2 * c + 1]));
                     const size_t e = i + (size_t)(n0 + c) * n;
                     const zd yi = __ldcg(yin + e);
-                    const zd w = zscale(zsub(v, zscale(yi, lc)), ilh);
+                    const zd w = zscale(zsub(r, zscale(yi, lc)), ilh);
                     zd y, ac;
                     if (nt == 1) {
                         y = w;
@@ -329,6 +372,10 @@ __global__ void k_coef(StepArgs a) {
 // c^H H c and c^H S c.
 template <typename TC, int NT>
 __global__ void __launch_bounds__(32) k_local(StepArgs a) {
+    using R = decltype(TC{}.x);
+    constexpr bool F32 = sizeof(R) == 4;
+    constexpr int VP = (10 * NT <= 32) ? 32 : 64;  // 5 complex sums per column, padded
+    __shared__ R red[VP];
     const int k = blockIdx.z;
     const KDev& K = a.kd[k];
     const AtomTab& at = *a.at;
@@ -340,10 +387,8 @@ __global__ void __launch_bounds__(32) k_local(StepArgs a) {
     const int i = row - at.loff[al];
     const int m = at.m[al], na = at.na[al];
     const size_t mm = (size_t)m * m;
-    const zd* __restrict__ h = a.h + at.boff[al] + (size_t)i * m;
-    const zd* __restrict__ o = a.o + at.boff[al] + (size_t)i * m;
-    const zd* __restrict__ p = a.p + 3 * at.boff[al] + (size_t)i * m;
-    const zd* __restrict__ dh = a.dh ? a.dh + at.boff[al] + (size_t)i * m : nullptr;
+    const size_t boff = at.boff[al] + (size_t)i * m;
+    const zd* __restrict__ dh = a.dh ? a.dh + boff : nullptr;
     const DevState* st = a.st;
     const double cx = st->cur_a[0] * a.inv_c, cy = st->cur_a[1] * a.inv_c, cz = st->cur_a[2] * a.inv_c;
     const double aa = st->cur_aa, sdv = st->cur_s;
@@ -358,12 +403,34 @@ __global__ void __launch_bounds__(32) k_local(StepArgs a) {
             aP[0][j] = aP[1][j] = aP[2][j] = Cx<TC>::zero();
         }
         for (int jj = lane; jj < m; jj += 32) {
-            const zd hj = h[jj], oj = o[jj];
-            const zd px = p[jj], py = p[mm + jj], pz = p[2 * mm + jj];
-            zd he = zadd(hj, zadd(zadd(zscale(px, cx), zscale(py, cy)), zadd(zscale(pz, cz), zscale(oj, aa))));
-            if (dh && sdv != 0.0) he = zadd(he, zscale(dh[jj], sdv));
-            const TC hec = Cx<TC>::from(he), ojc = Cx<TC>::from(oj);
-            const TC pxc = Cx<TC>::from(px), pyc = Cx<TC>::from(py), pzc = Cx<TC>::from(pz);
+            TC hec, ojc, pxc, pyc, pzc;
+            if constexpr (F32) {
+                // the FP32 forms combine H(t) = h + A/c.p + |A|^2/2c^2 o in FP32
+                const zf hj = a.h32[boff + jj], oj = a.o32[boff + jj];
+                pxc = a.p32[3 * at.boff[al] + (size_t)i * m + jj];
+                pyc = a.p32[3 * at.boff[al] + mm + (size_t)i * m + jj];
+                pzc = a.p32[3 * at.boff[al] + 2 * mm + (size_t)i * m + jj];
+                const float fx = (float)cx, fy = (float)cy, fz = (float)cz, fa = (float)aa;
+                hec.x = hj.x + fx * pxc.x + fy * pyc.x + fz * pzc.x + fa * oj.x;
+                hec.y = hj.y + fx * pxc.y + fy * pyc.y + fz * pzc.y + fa * oj.y;
+                if (dh && sdv != 0.0) {
+                    const zd d = dh[jj];
+                    hec.x += (float)(sdv * d.x);
+                    hec.y += (float)(sdv * d.y);
+                }
+                ojc = oj;
+            } else {
+                const zd* __restrict__ p = a.p + 3 * at.boff[al] + (size_t)i * m;
+                const zd hj = a.h[boff + jj], oj = a.o[boff + jj];
+                const zd px = p[jj], py = p[mm + jj], pz = p[2 * mm + jj];
+                zd he = zadd(hj, zadd(zadd(zscale(px, cx), zscale(py, cy)), zadd(zscale(pz, cz), zscale(oj, aa))));
+                if (dh && sdv != 0.0) he = zadd(he, zscale(dh[jj], sdv));
+                hec = he;
+                ojc = oj;
+                pxc = px;
+                pyc = py;
+                pzc = pz;
+            }
             const zd* xs = (jj < na) ? (K.Q + aoff + jj) : (K.C + lo0 + (jj - na));
             const size_t ld = (jj < na) ? (size_t)ma : (size_t)nb;
 #pragma unroll
@@ -377,15 +444,32 @@ __global__ void __launch_bounds__(32) k_local(StepArgs a) {
                 Cx<TC>::fmac(aP[2][j], pzc, x);
             }
         }
+        R v[VP];
 #pragma unroll
         for (int j = 0; j < NT; ++j) {
-            const zd zh = warp_zsum(Cx<TC>::todbl(aH[j]));
-            const zd zs = warp_zsum(Cx<TC>::todbl(aS[j]));
-            const zd q0 = warp_zsum(Cx<TC>::todbl(aP[0][j]));
-            const zd q1 = warp_zsum(Cx<TC>::todbl(aP[1][j]));
-            const zd q2 = warp_zsum(Cx<TC>::todbl(aP[2][j]));
-            const int c = n0 + j;
-            if (lane == j && c < ns) {
+            v[10 * j + 0] = aH[j].x;
+            v[10 * j + 1] = aH[j].y;
+            v[10 * j + 2] = aS[j].x;
+            v[10 * j + 3] = aS[j].y;
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                v[10 * j + 4 + 2 * l] = aP[l][j].x;
+                v[10 * j + 5 + 2 * l] = aP[l][j].y;
+            }
+        }
+#pragma unroll
+        for (int e = 10 * NT; e < VP; ++e) v[e] = (R)0;
+        warp_sum_store<R, VP>(v, lane, red);
+        __syncwarp();
+        if (lane == 0) {
+            for (int j = 0; j < NT; ++j) {
+                const int c = n0 + j;
+                if (c >= ns) break;
+                const zd zh = zmk((double)red[10 * j], (double)red[10 * j + 1]);
+                const zd zs = zmk((double)red[10 * j + 2], (double)red[10 * j + 3]);
+                const zd q0 = zmk((double)red[10 * j + 4], (double)red[10 * j + 5]);
+                const zd q1 = zmk((double)red[10 * j + 6], (double)red[10 * j + 7]);
+                const zd q2 = zmk((double)red[10 * j + 8], (double)red[10 * j + 9]);
                 zd xi;
                 const double f = a.occ[c];
                 if (i < na) {
@@ -405,9 +489,8 @@ __global__ void __launch_bounds__(32) k_local(StepArgs a) {
                 jc[2] += f * (xi.x * q2.x + xi.y * q2.y);
             }
         }
+        __syncwarp();
     }
-#pragma unroll
-    for (int q = 0; q < 5; ++q) jc[q] = warp_sum(jc[q]);
     if (lane == 0) {
         double* pj = a.part_jmt + ((size_t)k * at.lrows + row) * 5;
 #pragma unroll
@@ -427,13 +510,13 @@ __global__ void __launch_bounds__(32) k_local(StepArgs a) {
 //    one chunk of the matching rows, A^H read coalesced over the block's rows.
 // Each slot writes [H part | S part] for columns n0 .. n0+NT-1 into part_t.
 template <typename TA, typename TT, typename TC, int NT>
-__global__ void __launch_bounds__(BT) k_toep_seg(StepArgs a, int n0) {
+__global__ void __launch_bounds__(BT) k_toep_seg(StepArgs a, int n0, int slot0) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int k = blockIdx.z;
     const KDev& K = a.kd[k];
     const int ng = K.ng;
     const int g0 = blockIdx.x * BT;
-    const int slot = blockIdx.y;
+    const int slot = blockIdx.y + slot0;
     const int tid = threadIdx.x;
     const int g = g0 + tid;
     const bool act = g < ng;
@@ -553,8 +636,12 @@ __global__ void __launch_bounds__(BT) k_back(StepArgs a, int n0) {
         for (int c = 0; c < NT; ++c) {
             if (c >= nc) break;
             zd th = zmk(0.0, 0.0), ts = zmk(0.0, 0.0);
-            for (int sg = 0; sg < nsg; ++sg)
-                th = zadd(th, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + c) * a.maxng + g]);
+            if (a.prec == 2) {
+                th = K.th[g + (size_t)(n0 + c) * ng];
+            } else {
+                for (int sg = 0; sg < nsg; ++sg)
+                    th = zadd(th, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + c) * a.maxng + g]);
+            }
             for (int sg = a.nseg; sg < a.nseg + nas; ++sg) {
                 th = zadd(th, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + c) * a.maxng + g]);
                 ts = zadd(ts, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + NT + c) * a.maxng + g]);
@@ -1008,7 +1095,7 @@ void launch_phase_fix(const KDev* kd, int nk, int naux, zd* const* extra, const 
 static cudaError_t launch_cheb_coop_raw(const StepArgs& a, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.coop_grid);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(CHEB_THREADS);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -1032,14 +1119,15 @@ int prepare_cheb_coop(const StepArgs& a0, cudaStream_t s) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (!coop || nsm <= 0) return 0;
     cudaError_t e;
-    if (a0.ns <= 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_coop<2>, 256, 0);
-    else if (a0.ns <= 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_coop<4>, 256, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_coop<8>, 256, 0);
+    if (a0.ns <= 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_coop<2>, CHEB_THREADS, 0);
+    else if (a0.ns <= 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_coop<4>, CHEB_THREADS, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_coop<8>, CHEB_THREADS, 0);
     if (e != cudaSuccess || per_sm <= 0) {
         cudaGetLastError();
         return 0;
     }
     // one block per row while the rows last, at most four blocks per SM
+    // (more blocks would lengthen the barrier's arrival chain)
     const int nrow = a0.nk * a0.naux;
     int grid = nrow < 4 * nsm ? nrow : 4 * nsm;
     if (grid > per_sm * nsm) grid = per_sm * nsm;
@@ -1093,11 +1181,16 @@ static size_t toep_smem(const StepArgs& a, size_t tc, size_t tt) {
 template <typename TA, typename TT, typename TC, int NT>
 static void back_launch(const StepArgs& a, int maxng, cudaStream_t s, TraceHook* tr) {
     const size_t sm = toep_smem<NT>(a, sizeof(TC), sizeof(TT));
-    dim3 gt((maxng + BT - 1) / BT, a.nslot, a.nk);
+    // in the tensor-core form the interstitial slots are done already: only
+    // the back-projection slots run here
+    const int slot0 = (a.prec == 2) ? a.nseg : 0;
+    dim3 gt((maxng + BT - 1) / BT, a.nslot - slot0, a.nk);
     dim3 gb((maxng + BT - 1) / BT, 1, a.nk);
     for (int n0 = 0; n0 < a.ns; n0 += NT) {
-        k_toep_seg<TA, TT, TC, NT><<<gt, BT, sm, s>>>(a, n0);
-        mark(tr, "toeplitz_and_backprojection", s);
+        if (gt.y > 0) {
+            k_toep_seg<TA, TT, TC, NT><<<gt, BT, sm, s>>>(a, n0, slot0);
+            mark(tr, slot0 ? "backprojection" : "toeplitz_and_backprojection", s);
+        }
         k_back<NT><<<gb, BT, 0, s>>>(a, n0);
         mark(tr, "back_finish", s);
     }
@@ -1128,12 +1221,22 @@ int prepare_back_kernels(const StepArgs& a) {
 }
 
 void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr) {
-    const bool f32 = a.prec == 1;
-    // Q = A C_G = (A^H)^H C_G: one warp per matching row; split-K in FP64
-    launch_gemm_cn(p.gd_fwd, a.nk, a.ma, p.maxng, a.ns, p.kc_fwd, p.part, 0, f32, nullptr, s);
-    mark(tr, "gemm_forward", s);
-    launch_split_reduce(p.gd_fwd, a.nk, a.ma, a.ns, p.kc_fwd, p.part, 0, s);
-    mark(tr, "split_reduce_forward", s);
+    const bool f32 = a.prec >= 1;
+    if (a.prec == 2) {
+        // tensor cores: V~ * C_G and Q = A C_G in one split-BF16 launch
+        launch_tc_pack(p.tc, a, s);
+        mark(tr, "tc_pack_c", s);
+        launch_tc_operator(p.tc, a, s);
+        mark(tr, "tc_interstitial_and_forward", s);
+        launch_tc_reduce(p.tc, a, s);
+        mark(tr, "tc_reduce", s);
+    } else {
+        // Q = A C_G = (A^H)^H C_G: one warp per matching row; split-K in FP64
+        launch_gemm_cn(p.gd_fwd, a.nk, a.ma, p.maxng, a.ns, p.kc_fwd, p.part, 0, f32, nullptr, s);
+        mark(tr, "gemm_forward", s);
+        launch_split_reduce(p.gd_fwd, a.nk, a.ma, a.ns, p.kc_fwd, p.part, 0, s);
+        mark(tr, "split_reduce_forward", s);
+    }
     if (a.lrows > 0) {
         dim3 g(a.lrows, 1, a.nk);
         if (f32) {
@@ -1158,7 +1261,7 @@ void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, 
 
 void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlaunch, TraceHook* tr) {
     int nl = 0;
-    const bool f32 = a.prec == 1;
+    const bool f32 = a.prec >= 1;
     const int nn = a.naux * a.naux;
     if (a.dv_on) {
         k_set_cur<<<1, 1, 0, s>>>(a);
@@ -1216,7 +1319,10 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
         ++nl;
     }
     launch_operator_pass(a, p, s, tr);
-    nl += 3 + 2 * ((a.ns + 7) / 8);
+    {
+        const int ntb = a.ns <= 2 ? 2 : (a.ns <= 4 ? 4 : 8);
+        nl += (a.prec == 2 ? 3 : 2) + (a.lrows > 0 ? 1 : 0) + 2 * ((a.ns + ntb - 1) / ntb);
+    }
     // theta~ = CC^H (S C): split-K partials, finished per row in k_post
     launch_gemm_cn(p.gd_proj, a.nk, a.naux, p.maxnb, a.ns, p.kc_proj, p.part, 0, f32, nullptr, s);
     mark(tr, "gemm_project", s);

@@ -15,6 +15,8 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
+#include <string>
 
 #include "rtd.h"
 #include "rttddft.h"
@@ -379,4 +381,543 @@ int tc_zgemm(int opA, int M, int N, int K, const zd* A, int lda, const zd* X, in
     cudaFree(D);
     cudaFree(flag);
     return rc;
+}
+
+// ============================================================================
+// Interstitial convolution and matching-coefficient products of the operator
+// apply on the tensor cores (Eq. v_interstitial and the first factor of
+// Eq. v_MT), in the split-BF16 form:
+//   row tiles 0 .. ttiles-1:  T[G, n] = sum_G' V~_{G-G'} C[G', n]
+//   row tiles ttiles ..:      Q[r, n] = sum_G' A[r, G'] C[G', n]
+// Both contract over G' with the same right operand, so one launch covers
+// them.  K is cut into blocks of 32 G' (64 reals: 32 Re then 32 Im); the
+// left operand of a block is [Re | Im] of 32 entries per row, the right one
+// holds, per column n, [Re C | -Im C] (real output rows) and [Im C | Re C]
+// (imaginary output rows).  The V~ rows are generated on the SM: the table
+// window of the (row tile, K slice) pair is staged in shared memory (G is
+// listed in lexicographic order, so the offsets glin(G) - glin(G') + centre
+// of the pair form one contiguous range) and 256 threads write the hi/lo
+// bf16 tile in the 128-byte swizzled K-major layout the tensor core reads.
+// The A rows and the right operand arrive by TMA (3-D maps over k).  One
+// thread issues the products; waits are bounded and abort together.
+// ============================================================================
+#define TCO_GEN 256          // generator threads (8 warps); warp 8 issues
+#define TCO_THREADS 288
+#define TCO_MAXS 4
+
+__device__ bool mbar_wait_ab(uint64_t* b, uint32_t phase, volatile int* ab) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(b, phase)) {
+        if (*ab) return false;
+        if (clock64() - t0 > (1ll << 31)) {
+            *ab = 1;
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
+
+struct TcOpParams {
+    int nk, ns, ma, Dn, kbps, splits, ttiles, atiles, wcap, vt_center, R, S;
+    int kofs;  // k-point of blockIdx.z = 0 in the matching-row operand (single-k calls)
+    const KDev* kd;
+    const zf* tab;
+    float* D;  // [nk][splits][R][Dn]
+    int* flag;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(TCO_THREADS, 1)
+    k_tc_opfwd(const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+               const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl, TcOpParams p) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr int A_BYTES = TC_BM * TC_BK * 2;
+    constexpr int B_BYTES = NT * TC_BK * 2;
+    constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    constexpr uint32_t NCOLS = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
+    __shared__ __align__(8) uint64_t full[TCO_MAXS], empty[TCO_MAXS], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    const int S = p.S;
+    const int k = blockIdx.z, tile = blockIdx.x, split = blockIdx.y;
+    const KDev& K = p.kd[k];
+    const int ng = K.ng;
+    const bool is_t = tile < p.ttiles;
+    const int row0 = (is_t ? tile : tile - p.ttiles) * TC_BM;
+    const int nkb = (ng + 31) >> 5;
+    const int kb0 = split * p.kbps;
+    const int nk = min(nkb, kb0 + p.kbps) - kb0;
+    if (nk <= 0 || (is_t && row0 >= ng)) return;  // the reduction skips these pairs
+    int* gl_s = (int*)(smem + (size_t)S * STAGE);
+    zf* win = (zf*)(gl_s + p.kbps * 32);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], is_t ? 1 + TCO_GEN / 32 : 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(NCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // table window and the G' offsets of this K slice
+    const int gp_lo = kb0 * 32, gp_hi = min(ng, (kb0 + nk) * 32);
+    int wlo = 0;
+    if (is_t && tid < TCO_GEN) {
+        const int* __restrict__ glin = K.glin;
+        const int g1 = min(row0 + TC_BM, ng) - 1;
+        wlo = glin[row0] - glin[gp_hi - 1] + p.vt_center;
+        const int wn = glin[g1] - glin[gp_lo] + p.vt_center - wlo + 1;
+        if (wn > p.wcap) {
+            // the host sizes the slices so that this cannot happen
+            abort_flag = 1;
+            if (tid == 0) atomicOr(p.flag, 8);
+        } else {
+            for (int e = tid; e < wn; e += TCO_GEN) win[e] = p.tab[wlo + e];
+        }
+        for (int i = tid; i < gp_hi - gp_lo; i += TCO_GEN) gl_s[i] = glin[gp_lo + i];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    volatile int* ab = &abort_flag;
+    if (warp == 8) {
+        if (lane == 0 && *ab) {
+            umma_commit(&done);  // nothing in flight: completes at once
+        } else if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                                   ((uint32_t)(TC_BM >> 4) << 24);
+            int issued = 0, consumed = 0;
+            auto load = [&](int j) {
+                const int s = j % S, kx = (kb0 + j) * TC_BK;
+                unsigned char* st = smem + (size_t)s * STAGE;
+                mbar_expect_tx(&full[s], is_t ? 2 * B_BYTES : STAGE);
+                tma_load_3d(st + 2 * A_BYTES, &tmBh, kx, 0, k, &full[s]);
+                tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tmBl, kx, 0, k, &full[s]);
+                if (!is_t) {
+                    tma_load_3d(st, &tmAh, kx, row0, k + p.kofs, &full[s]);
+                    tma_load_3d(st + A_BYTES, &tmAl, kx, row0, k + p.kofs, &full[s]);
+                }
+                issued = j + 1;
+            };
+            for (int j = 0; j < min(nk, S); ++j) load(j);
+            for (int j = 0; j < nk; ++j) {
+                const int s = j % S;
+                if (!mbar_wait_ab(&full[s], (uint32_t)((j / S) & 1), ab)) break;
+                consumed = j + 1;
+                tc_fence_after();
+                const uint32_t ah = smem_u32(smem + (size_t)s * STAGE), al = ah + A_BYTES;
+                const uint32_t bh = ah + 2 * A_BYTES, bl = bh + B_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                    const uint32_t o = kk * 32;
+                    umma_bf16(tmem, umma_desc(ah + o), umma_desc(bh + o), idesc, (j > 0 || kk > 0) ? 1u : 0u);
+                    umma_bf16(tmem, umma_desc(ah + o), umma_desc(bl + o), idesc, 1u);
+                    umma_bf16(tmem, umma_desc(al + o), umma_desc(bh + o), idesc, 1u);
+                }
+                umma_commit(&empty[s]);
+                const int jp = j - 1;
+                if (jp >= 0 && jp + S < nk) {
+                    if (!mbar_wait_ab(&empty[jp % S], (uint32_t)((jp / S) & 1), ab)) break;
+                    load(jp + S);
+                }
+            }
+            umma_commit(&done);
+            if (*ab) {
+                atomicOr(p.flag, 8);
+                // the copies already issued land before the block's shared memory goes away
+                for (int j = consumed; j < issued; ++j) mbar_wait(&full[j % S], (uint32_t)((j / S) & 1));
+            }
+        }
+        __syncwarp();
+    } else if (is_t && !*ab) {
+        // generators: thread (r, h) writes row r, G' 16h .. 16h+15 of every K block
+        const int r = tid & (TC_BM - 1), h = tid >> 7;
+        const int g = row0 + r;
+        const bool valid = g < ng;
+        const int lb = (valid ? K.glin[g] : 0) + p.vt_center - wlo;
+        const uint32_t sw = (uint32_t)(r & 7);
+        for (int j = 0; j < nk; ++j) {
+            const int s = j % S;
+            if (j >= S && !mbar_wait_ab(&empty[s], (uint32_t)(((j / S) - 1) & 1), ab)) break;
+            const int gq = (kb0 + j) * 32 + 16 * h;
+            float re[16], im[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int gp = gq + i;
+                zf v = {0.f, 0.f};
+                if (valid && gp < gp_hi) v = win[lb - gl_s[gp - gp_lo]];
+                re[i] = v.x;
+                im[i] = v.y;
+            }
+            uint32_t hr[8], lr[8], hi_[8], li[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const __nv_bfloat162 a = __floats2bfloat162_rn(re[2 * i], re[2 * i + 1]);
+                const float2 af = __bfloat1622float2(a);
+                hr[i] = bf2_bits(a);
+                lr[i] = bf2_bits(__floats2bfloat162_rn(re[2 * i] - af.x, re[2 * i + 1] - af.y));
+                const __nv_bfloat162 b = __floats2bfloat162_rn(im[2 * i], im[2 * i + 1]);
+                const float2 bf = __bfloat1622float2(b);
+                hi_[i] = bf2_bits(b);
+                li[i] = bf2_bits(__floats2bfloat162_rn(im[2 * i] - bf.x, im[2 * i + 1] - bf.y));
+            }
+            unsigned char* rowp = smem + (size_t)s * STAGE + r * 128;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const uint32_t cre = (uint32_t)(2 * h + q), cim = cre + 4;
+                uint4* p0 = (uint4*)(rowp + ((cre ^ sw) << 4));
+                uint4* p1 = (uint4*)(rowp + ((cim ^ sw) << 4));
+                *p0 = make_uint4(hr[4 * q], hr[4 * q + 1], hr[4 * q + 2], hr[4 * q + 3]);
+                *p1 = make_uint4(hi_[4 * q], hi_[4 * q + 1], hi_[4 * q + 2], hi_[4 * q + 3]);
+                *(uint4*)((unsigned char*)p0 + A_BYTES) = make_uint4(lr[4 * q], lr[4 * q + 1], lr[4 * q + 2], lr[4 * q + 3]);
+                *(uint4*)((unsigned char*)p1 + A_BYTES) = make_uint4(li[4 * q], li[4 * q + 1], li[4 * q + 2], li[4 * q + 3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full[s]);
+        }
+    }
+    __syncthreads();
+    const bool okd = mbar_wait(&done, 0);
+    tc_fence_after();
+    if (warp < 8 && okd && !*ab) {
+        const int q = warp & 3, half = warp >> 2;
+        const int lrow = row0 + q * 32 + lane;
+        const bool valid = is_t ? (lrow < ng) : (lrow < p.ma);
+        float* drow = p.D + (((size_t)k * p.splits + split) * p.R + (size_t)tile * TC_BM + q * 32 + lane) * p.Dn;
+#pragma unroll 1
+        for (int c = half * (NT / 2); c < (half + 1) * (NT / 2); c += 8) {
+            uint32_t v[8];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (valid) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (c + u < p.Dn) drow[c + u] = __uint_as_float(v[u]);
+            }
+        }
+    } else if (tid == 0 && !okd) {
+        atomicOr(p.flag, 8);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
+}
+
+// Right operand of a step: B^[k][row][K-block layout] from C_G (FP64, the
+// first ng rows of K.C).  Rows 2 ns .. and G' >= ng stay zero from set-up.
+__global__ void k_tc_pack_c(const KDev* __restrict__ kd, int ns, int Kp, int Rp, __nv_bfloat16* __restrict__ bh,
+                            __nv_bfloat16* __restrict__ bl) {
+    const int k = blockIdx.z;
+    const KDev& K = kd[k];
+    const int ng = K.ng;
+    const int e = blockIdx.x * 256 + threadIdx.x;  // (n, G') pair
+    if (e >= ns * ng) return;
+    const int n = e / ng, gp = e % ng;
+    const zd c = K.C[gp + (size_t)n * K.nb];
+    const int kb = gp >> 5, o = gp & 31;
+    const size_t re_row = ((size_t)k * Rp + n) * Kp + (size_t)kb * 64;
+    const size_t im_row = ((size_t)k * Rp + ns + n) * Kp + (size_t)kb * 64;
+    __nv_bfloat16 h, l;
+    split_bf16(c.x, h, l);
+    bh[re_row + o] = h;
+    bl[re_row + o] = l;
+    bh[im_row + 32 + o] = h;
+    bl[im_row + 32 + o] = l;
+    split_bf16(c.y, h, l);
+    bh[im_row + o] = h;
+    bl[im_row + o] = l;
+    split_bf16(-c.y, h, l);
+    bh[re_row + 32 + o] = h;
+    bl[re_row + 32 + o] = l;
+}
+
+// Left operand of the matching rows (set-up): A^[k][r][K-block layout] with
+// A[r, G'] = conj(AT[G' + r ng]).
+__global__ void k_tc_pack_at(const zd* __restrict__ at, int ng, int ma, int Kp, int Mp, int k,
+                             __nv_bfloat16* __restrict__ ah, __nv_bfloat16* __restrict__ al) {
+    const size_t e = (size_t)blockIdx.x * 256 + threadIdx.x;
+    if (e >= (size_t)ma * ng) return;
+    const int gp = (int)(e % ng), r = (int)(e / ng);
+    const zd a = at[gp + (size_t)r * ng];
+    const size_t row = ((size_t)k * Mp + r) * Kp + (size_t)(gp >> 5) * 64 + (gp & 31);
+    __nv_bfloat16 h, l;
+    split_bf16(a.x, h, l);
+    ah[row] = h;
+    al[row] = l;
+    split_bf16(-a.y, h, l);
+    ah[row + 32] = h;
+    al[row + 32] = l;
+}
+
+// Sum of the K slices in FP64: T rows into K.th (ng x ns), matching rows into
+// K.Q (ma x ns).
+__global__ void k_tc_opred(TcOpParams p) {
+    const int k = blockIdx.z;
+    const KDev& K = p.kd[k];
+    const int ng = K.ng, ns = p.ns;
+    const int nsp = min(p.splits, (((ng + 31) >> 5) + p.kbps - 1) / p.kbps);
+    const int e = blockIdx.x * 256 + threadIdx.x;
+    const int nrow = ng + p.ma;
+    if (e >= nrow * ns) return;
+    const int row = e % nrow, c = e / nrow;
+    const int drow = row < ng ? row : p.ttiles * TC_BM + (row - ng);
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < nsp; ++s) {
+        const float* d = p.D + (((size_t)k * p.splits + s) * p.R + drow) * p.Dn;
+        re += (double)d[c];
+        im += (double)d[ns + c];
+    }
+    if (row < ng) K.th[row + (size_t)c * ng] = zmk(re, im);
+    else K.Q[(row - ng) + (size_t)c * p.ma] = zmk(re, im);
+}
+
+// ------------------------------------------------------------ operator plan
+struct TcPlan {
+    int nk = 0, ns = 0, ma = 0, Dn = 0, NT = 0, S = 0, kbps = 0, splits = 0, ttiles = 0, atiles = 0;
+    int wcap = 0, R = 0, Kp = 0, Mp = 0, Rp = 0, maxng = 0, vt_center = 0;
+    size_t smem = 0;
+    CUtensorMap tbh, tbl, tah, tal;
+    __nv_bfloat16 *bh = nullptr, *bl = nullptr, *ah = nullptr, *al = nullptr;
+    float* D = nullptr;
+};
+
+static const int TCO_NTS[] = {16, 32, 48, 64, 96, 128, 160, 192, 224, 256};
+
+static size_t tco_smem(int NT, int S, int kbps, int wcap) {
+    return 1024 + (size_t)S * (4 * TC_BM * TC_BK + 4 * (size_t)NT * TC_BK) + (size_t)kbps * 128 + (size_t)wcap * 8;
+}
+
+// largest table window over every (k, row tile, K slice of kbps blocks)
+static int tco_max_window(int nk, const int* ng, const int* const* glin, int kbps) {
+    int w = 0;
+    for (int k = 0; k < nk; ++k) {
+        const int n = ng[k], nkb = (n + 31) / 32;
+        const int* gl = glin[k];
+        for (int t0 = 0; t0 < n; t0 += TC_BM) {
+            const int g1 = std::min(t0 + TC_BM, n) - 1;
+            for (int kb0 = 0; kb0 < nkb; kb0 += kbps) {
+                const int lo = kb0 * 32, hi = std::min(n, (kb0 + kbps) * 32);
+                w = std::max(w, gl[g1] - gl[lo] - (gl[t0] - gl[hi - 1]) + 1);
+            }
+        }
+    }
+    return w;
+}
+
+static int tc_tmap3(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t rows, uint64_t depth,
+                    uint32_t box_rows) {
+    encode_fn_t enc = get_encode();
+    if (!enc) return -1;
+    if ((uintptr_t)base & 15) return -2;
+    cuuint64_t dims[3] = {inner, rows, depth};
+    cuuint64_t strides[2] = {inner * 2, inner * rows * 2};
+    cuuint32_t box[3] = {TC_BK, box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -3;
+}
+
+template <int NT>
+static cudaError_t tco_set_smem(int bytes) {
+    return cudaFuncSetAttribute(k_tc_opfwd<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+void tc_plan_destroy(TcPlan* tp) {
+    if (!tp) return;
+    cudaFree(tp->bh);
+    cudaFree(tp->bl);
+    cudaFree(tp->ah);
+    cudaFree(tp->al);
+    cudaFree(tp->D);
+    delete tp;
+}
+
+int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const int* const* glin_host,
+                   const zd* const* at_dev, int vt_center, cudaStream_t s, std::string* why) {
+    *out = nullptr;
+    if (!get_encode()) {
+        *why = "the driver has no tensor-map encoder";
+        return RTTDDFT_ERR_UNSUPPORTED;
+    }
+    TcPlan* tp = new TcPlan();
+    tp->nk = nk;
+    tp->ns = ns;
+    tp->ma = ma;
+    tp->Dn = 2 * ns;
+    tp->vt_center = vt_center;
+    for (int nt : TCO_NTS)
+        if (nt >= tp->Dn) {
+            tp->NT = nt;
+            break;
+        }
+    if (!tp->NT) {
+        delete tp;
+        *why = "the tensor-core form takes at most 128 states";
+        return RTTDDFT_ERR_UNSUPPORTED;
+    }
+    int dev = 0, nsm = 148, smax = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int maxng = 0;
+    for (int k = 0; k < nk; ++k) maxng = std::max(maxng, ng[k]);
+    tp->maxng = maxng;
+    const int nkb = (maxng + 31) / 32;
+    tp->ttiles = (maxng + TC_BM - 1) / TC_BM;
+    tp->atiles = (ma + TC_BM - 1) / TC_BM;
+    const int tiles = tp->ttiles + tp->atiles;
+    // K slices: fewest block-steps per SM (waves x blocks per slice, plus two for fill and drain)
+    int best = 1;
+    double bcost = 1e30;
+    for (int sp = 1; sp <= nkb; ++sp) {
+        const int kb = (nkb + sp - 1) / sp;
+        const double waves = std::ceil((double)tiles * nk * sp / nsm);
+        const double cost = waves * (kb + 2) + 0.02 * sp;
+        if (cost < bcost) {
+            bcost = cost;
+            best = sp;
+        }
+    }
+    const int budget = smax - 256;
+    for (int sp = best; sp <= nkb; ++sp) {
+        const int kbps = (nkb + sp - 1) / sp;
+        const int wn = tco_max_window(nk, ng, glin_host, kbps);
+        for (int S = TCO_MAXS; S >= 2 && !tp->S; --S)
+            if ((int)tco_smem(tp->NT, S, kbps, wn) <= budget) {
+                tp->S = S;
+                tp->kbps = kbps;
+                tp->wcap = wn;
+            }
+        if (tp->S) break;
+    }
+    if (!tp->S) {
+        delete tp;
+        *why = "the interstitial table window of one K block does not fit in shared memory";
+        return RTTDDFT_ERR_UNSUPPORTED;
+    }
+    tp->splits = (nkb + tp->kbps - 1) / tp->kbps;
+    tp->smem = tco_smem(tp->NT, tp->S, tp->kbps, tp->wcap);
+    tp->R = tiles * TC_BM;
+    tp->Kp = nkb * TC_BK;
+    tp->Rp = tp->NT;
+    tp->Mp = std::max(1, tp->atiles) * TC_BM;
+    const size_t nbh = (size_t)nk * tp->Rp * tp->Kp, nah = (size_t)nk * tp->Mp * tp->Kp;
+    const size_t nd = (size_t)nk * tp->splits * tp->R * tp->Dn;
+    if (cudaMalloc(&tp->bh, nbh * 2) != cudaSuccess || cudaMalloc(&tp->bl, nbh * 2) != cudaSuccess ||
+        cudaMalloc(&tp->ah, nah * 2) != cudaSuccess || cudaMalloc(&tp->al, nah * 2) != cudaSuccess ||
+        cudaMalloc(&tp->D, nd * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        tc_plan_destroy(tp);
+        *why = "out of device memory for the tensor-core operands";
+        return RTTDDFT_ERR_OOM;
+    }
+    cudaMemsetAsync(tp->bh, 0, nbh * 2, s);
+    cudaMemsetAsync(tp->bl, 0, nbh * 2, s);
+    cudaMemsetAsync(tp->ah, 0, nah * 2, s);
+    cudaMemsetAsync(tp->al, 0, nah * 2, s);
+    for (int k = 0; k < nk && ma > 0; ++k) {
+        const size_t n = (size_t)ma * ng[k];
+        k_tc_pack_at<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(at_dev[k], ng[k], ma, tp->Kp, tp->Mp, k, tp->ah,
+                                                                 tp->al);
+    }
+    int e = tc_tmap3(&tp->tbh, tp->bh, tp->Kp, tp->Rp, nk, tp->NT) | tc_tmap3(&tp->tbl, tp->bl, tp->Kp, tp->Rp, nk, tp->NT) |
+            tc_tmap3(&tp->tah, tp->ah, tp->Kp, tp->Mp, nk, TC_BM) | tc_tmap3(&tp->tal, tp->al, tp->Kp, tp->Mp, nk, TC_BM);
+    cudaError_t ce = cudaSuccess;
+    switch (tp->NT) {
+#define RTD_TCO(n) \
+    case n: ce = tco_set_smem<n>((int)tp->smem); break;
+        RTD_TCO(16) RTD_TCO(32) RTD_TCO(48) RTD_TCO(64) RTD_TCO(96) RTD_TCO(128) RTD_TCO(160) RTD_TCO(192)
+        RTD_TCO(224) RTD_TCO(256)
+#undef RTD_TCO
+    }
+    if (e || ce != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        tc_plan_destroy(tp);
+        *why = "tensor-core operand set-up failed";
+        return RTTDDFT_ERR_CUDA;
+    }
+    *out = tp;
+    return RTTDDFT_OK;
+}
+
+static TcOpParams tco_params(const TcPlan* tp, const StepArgs& a) {
+    TcOpParams p{};
+    p.nk = a.nk;
+    p.ns = tp->ns;
+    p.ma = tp->ma;
+    p.Dn = tp->Dn;
+    p.kbps = tp->kbps;
+    p.splits = tp->splits;
+    p.ttiles = tp->ttiles;
+    p.atiles = tp->atiles;
+    p.wcap = tp->wcap;
+    p.vt_center = tp->vt_center;
+    p.R = tp->R;
+    p.S = tp->S;
+    p.kofs = a.kofs;
+    p.kd = a.kd;
+    p.tab = a.dv_on ? a.vstep32 : a.vtab32;
+    p.D = tp->D;
+    p.flag = a.flag;
+    return p;
+}
+
+void launch_tc_pack(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
+    dim3 g((tp->ns * tp->maxng + 255) / 256, 1, a.nk);
+    k_tc_pack_c<<<g, 256, 0, s>>>(a.kd, tp->ns, tp->Kp, tp->Rp, tp->bh, tp->bl);
+}
+
+void launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
+    const TcOpParams p = tco_params(tp, a);
+    dim3 g(tp->ttiles + tp->atiles, tp->splits, a.nk);
+    const CUtensorMap& am = tp->ma > 0 ? tp->tah : tp->tbh;
+    const CUtensorMap& al = tp->ma > 0 ? tp->tal : tp->tbl;
+    switch (tp->NT) {
+#define RTD_TCO(n) \
+    case n: k_tc_opfwd<n><<<g, TCO_THREADS, tp->smem, s>>>(tp->tbh, tp->tbl, am, al, p); break;
+        RTD_TCO(16) RTD_TCO(32) RTD_TCO(48) RTD_TCO(64) RTD_TCO(96) RTD_TCO(128) RTD_TCO(160) RTD_TCO(192)
+        RTD_TCO(224) RTD_TCO(256)
+#undef RTD_TCO
+    }
+}
+
+void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
+    const TcOpParams p = tco_params(tp, a);
+    dim3 g(((tp->maxng + tp->ma) * tp->ns + 255) / 256, 1, a.nk);
+    k_tc_opred<<<g, 256, 0, s>>>(p);
+}
+
+void tc_plan_info(const TcPlan* tp, int* v) {
+    v[0] = tp->NT;
+    v[1] = tp->S;
+    v[2] = tp->kbps;
+    v[3] = tp->splits;
+    v[4] = tp->wcap;
+    v[5] = (int)tp->smem;
 }

@@ -1,5 +1,6 @@
 // Internal layout of the rttddft device state and the kernel launchers.
 #pragma once
+#include <string>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -71,6 +72,7 @@ struct KDev {
     zd* Y;        // nb x 2ns  [H C | S C]
     zd* Q;        // ma x ns
     zd* Z;        // ma x 2ns
+    zd* th;       // ng x ns  interstitial convolution V~ * C_G (tensor-core form)
     zd* gram;     // ns x ns x 2   theta^H theta~ and theta~^H theta~
     zd* evec;     // naux x naux (EIG form)
     double* eval; // naux
@@ -109,6 +111,9 @@ struct StepArgs {
     const zd* h;         // atom blocks (boff)
     const zd* o;         // atom blocks (boff)
     const zd* p;         // 3 blocks per atom at 3*boff
+    const zf* h32;       // FP32 copies of h, o, p (FP32 and split-BF16 forms)
+    const zf* o32;
+    const zf* p32;
     const zd* dh;        // potential change blocks (or null)
     const zd* vtab;      // V~
     const zf* vtab32;
@@ -132,6 +137,7 @@ struct StepArgs {
     zd* part_t;               // [nk][nslot][2 NT][maxng] slot partial sums
     int* flag;                // device error flags (bit 0 Jacobi, 1 bounds, 2 barrier)
     int coop_grid;            // blocks of the cooperative Chebyshev launch (0: per-term launches)
+    int kofs;                 // k-point of kd[0] (single-k operator calls), 0 in the step
 };
 #define POST_STRIDE 36        // part_post row: residual, J_sub (3), then theta^H theta~ (ns <= 4)
 
@@ -165,6 +171,7 @@ struct StepPlan {
     int* d_flag;
     zd* const* jac_mats; double* const* jac_vals; zd* const* jac_vecs;
     int max_sweeps;
+    const struct TcPlan* tc;  // tensor-core operator plan (split-BF16 form) or null
 };
 // Optional per-kernel tracing: an event is recorded after every launch of a step.
 struct TraceHook {
@@ -204,6 +211,15 @@ void launch_adj_grad(const StepArgs& a, const zd* Yh, const zd* Yb, int nterm, d
 void launch_adj_jterm(const StepArgs& a, zd* lam, const zd* theta, const double* g, double sm, double cfac,
                       double* nrm, cudaStream_t s);
 
+// ---- tensor-core split-BF16 operator (k_tc.cu)
+struct TcPlan;
+int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const int* const* glin_host,
+                   const zd* const* at_dev, int vt_center, cudaStream_t s, std::string* why);
+void tc_plan_destroy(TcPlan* tp);
+void tc_plan_info(const TcPlan* tp, int* v);  // NT, stages, K blocks per slice, slices, window, smem
+void launch_tc_pack(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
+void launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
+void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
 // ---- tensor-core split-BF16 complex GEMM (k_tc.cu); returns an RTTDDFT_* code
 int tc_zgemm(int opA, int M, int N, int K, const zd* A, int lda, const zd* X, int ldx, zd* C, int ldc,
              int beta_add, cudaStream_t s);

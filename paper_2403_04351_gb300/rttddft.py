@@ -21,7 +21,7 @@ ERRORS = {
     -5: "ERR_NONFINITE", -6: "ERR_OOM", -7: "ERR_CUDA", -8: "ERR_TIMEOUT", -9: "ERR_UNSUPPORTED",
 }
 PROP = {"chebyshev": 0, "eig": 1, "cn": 2}
-PREC = {"fp64": 0, "fp32": 1}
+PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2}
 AUX = {"ritz": 0, "given": 1}
 
 EXPORTED = ["rttddft_default_options", "rttddft_setup", "rttddft_step", "rttddft_observables",
@@ -61,7 +61,10 @@ class rttddft_obs(ctypes.Structure):
 class rttddft_info(ctypes.Structure):
     _fields_ = [("steps_done", ctypes.c_longlong), ("time", ctypes.c_double),
                 ("n_basis_max", ctypes.c_int), ("cheb_terms", ctypes.c_int),
-                ("dt_cr0", ctypes.c_double), ("kernel_launches_per_step", ctypes.c_int)]
+                ("dt_cr0", ctypes.c_double), ("kernel_launches_per_step", ctypes.c_int),
+                ("precision", ctypes.c_int), ("tc_tile_n", ctypes.c_int), ("tc_stages", ctypes.c_int),
+                ("tc_kblocks", ctypes.c_int), ("tc_slices", ctypes.c_int), ("tc_window", ctypes.c_int),
+                ("tc_smem", ctypes.c_int)]
 
 
 class rttddft_trace(ctypes.Structure):
@@ -365,7 +368,9 @@ class Context:
         i = rttddft_get_info(self.ctx)
         return dict(steps_done=i.steps_done, time=i.time, n_basis_max=i.n_basis_max,
                     cheb_terms=i.cheb_terms, dt_cr0=i.dt_cr0,
-                    kernel_launches_per_step=i.kernel_launches_per_step)
+                    kernel_launches_per_step=i.kernel_launches_per_step, precision=i.precision,
+                    tc=dict(tile_n=i.tc_tile_n, stages=i.tc_stages, kblocks=i.tc_kblocks,
+                            slices=i.tc_slices, window=i.tc_window, smem=i.tc_smem))
 
     def set_dv(self, dv):
         self._dh = _cat_f(dv["dh"])

@@ -1,0 +1,120 @@
+"""The split-BF16 precision form (tensor-core interstitial convolution and
+matching-coefficient products) against the FP64 oracle.
+
+Error model: every bf16 hi/lo split product hi.hi + hi.lo + lo.hi carries a
+relative error of a few 2^-16 of sum |a||x| (the dropped lo.lo term and the
+rounding of lo), and the FP32 accumulation of a K slice adds about
+sqrt(n) 2^-24; the other full-basis contractions run in FP32 (~1e-7).  So
+the operator is checked entrywise against 1e-4 (|H||x|) and the full-basis
+observables against 1e-4 (E), 1e-3 (J from the full basis) and 1e-4
+(|C^H S C - I|).  The dipole and the current of record come from the FP64
+subspace state, so they keep the FP64 tolerances (1e-8 and 1e-10).
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle, explicit_dv, explicit_operators, hamiltonian
+from paper_2403_04351_gb300 import Context, build
+from synth import make_dv, make_system, pulse_samples, tiny_config
+from systems import free_electron_system
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    build()
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+
+
+def ragged_cfg():
+    return tiny_config(name="ragged", n_g=0, n_atoms=3, lmax=2, n_lo_per_atom=3, n_s=3, n_aux=20,
+                       n_k=4, kgrid=(2, 2, 1), n_b_range=(130, 181), seed=17, lattice="mos2",
+                       edir=(1.0, 0.0, 0.0))
+
+
+@pytest.mark.parametrize("case", ["tiny400", "ragged", "free", "dv", "wide"])
+def test_operator_within_split_bound(case):
+    rng = np.random.default_rng(3)
+    dv = None
+    if case in ("tiny400", "dv"):
+        s = make_system("tiny400")
+        dv = make_dv(s) if case == "dv" else None
+    elif case == "ragged":
+        s = make_system(ragged_cfg())
+    elif case == "free":
+        s = free_electron_system(n_g=50, n_s=2, n_aux=6)
+    else:  # many states: several column tiles of the tensor-core output
+        s = make_system(tiny_config(n_g=300, n_atoms=2, lmax=2, n_lo_per_atom=2, n_s=40, n_aux=64, seed=5))
+    ctx = Context(s, precision="bf16x3")
+    info = ctx.info()
+    assert info["precision"] == 2 and info["tc"]["tile_n"] >= 2 * int(s["n_s"])
+    if dv is not None:
+        ctx.set_dv(dv)
+    a_vec = np.array([0.3, -0.7, 1.1]) * 20.0
+    sdv = 0.8 if dv is not None else 0.0
+    for k in range(int(s["n_k"])):
+        ops = explicit_operators(s, k)
+        nb = ops["nb"]
+        ncols = int(s["n_s"]) + 1
+        x = rng.standard_normal((nb, ncols)) + 1j * rng.standard_normal((nb, ncols))
+        hx, sx = ctx.apply(k, x, a_vec, sdv)
+        h = hamiltonian(ops, a_vec, s["c_light"], explicit_dv(s, k, dv) if dv else None, sdv)
+        mag_h = np.abs(h) @ np.abs(x)
+        mag_s = np.abs(ops["S"]) @ np.abs(x)
+        eh = np.abs(hx - h @ x) / mag_h
+        es = np.abs(sx - ops["S"] @ x) / mag_s
+        assert np.max(eh) < 1e-4, (k, np.max(eh))
+        assert np.max(es) < 1e-4, (k, np.max(es))
+        # far better than a single bf16 product (2^-8)
+        assert np.median(eh) < 2.0 ** -13
+    ctx.close()
+
+
+def test_step_error_per_observable_tiny400():
+    s = make_system("tiny400")
+    a = pulse_samples(s, a0=5.0)
+    r = Oracle(s).run(a, s["dt"])
+    ctx = Context(s, precision="bf16x3", graph_steps=10)
+    ctx.step(a)
+    obs = ctx.observables()
+    assert rel(obs["dmu"], r["dmu"]) < 1e-8
+    assert rel(obs["j"], r["J"]) < 1e-10
+    assert rel(obs["energy"], r["E"]) < 1e-4
+    assert rel(obs["j_full"], r["J_full"]) < 1e-3
+    assert np.max(obs["norm_dev"]) < 1e-4
+    ctx.close()
+
+
+def test_ragged_multi_k_batch():
+    s = make_system(ragged_cfg())
+    a = pulse_samples(s, n_steps=40, a0=5.0)
+    r = Oracle(s).run(a, s["dt"])
+    ctx = Context(s, precision="bf16x3", graph_steps=10)
+    ctx.step(a)
+    obs = ctx.observables()
+    assert rel(obs["dmu"], r["dmu"]) < 1e-8
+    assert rel(obs["energy"], r["E"]) < 1e-4
+    assert np.max(obs["norm_dev"]) < 1e-4
+    ctx.close()
+
+
+def test_h2_6000_sampled():
+    s = make_system("h2_6000")
+    n = 20
+    a = pulse_samples(s)[:n]
+    r = Oracle(s).run(a, s["dt"])
+    ctx = Context(s, precision="bf16x3", graph_steps=10)
+    ctx.step(a)
+    obs = ctx.observables()
+    assert rel(obs["dmu"], r["dmu"]) < 1e-8
+    assert rel(obs["j"], r["J"]) < 1e-10
+    assert rel(obs["energy"], r["E"]) < 1e-4
+    assert np.max(obs["norm_dev"]) < 1e-4
+    ctx.close()

@@ -331,7 +331,8 @@ def run_ours(args, rank, world, local_rank):
                    "dt": float(s["dt"]), "precision_form": args.precision,
                    "propagator": "chebyshev (exact exponential to FP64 round-off)",
                    "l2": "flushed (256 MiB read) before every timed step",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "tensor_core_plan": info.get("tc") if args.precision == "bf16x3" else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 8,
                 "d2h_bytes_per_step": 16 * 8},
         "gpu_launches": int(info["kernel_launches_per_step"]) * K,

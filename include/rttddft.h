@@ -154,11 +154,14 @@ typedef struct {
     int kernel_launches_per_step; /* kernels launched per step (graph nodes) */
     int precision;         /* RTTDDFT_PREC_* of the context */
     int tc_tile_n;         /* split-BF16 form: real output columns per tensor-core tile (0 otherwise) */
-    int tc_stages;         /*   shared-memory pipeline stages */
+    int tc_stages;         /*   100 x generated-operand stages + copied-operand stages */
     int tc_kblocks;        /*   K blocks (32 G') per slice */
     int tc_slices;         /*   K slices */
     int tc_window;         /*   largest interstitial table window staged (entries) */
     int tc_smem;           /*   dynamic shared memory per block (bytes) */
+    int tc_candidates;     /*   launch shapes timed by the set-up autotuner */
+    int tc_interstitial_ns;/*   tuned time of the interstitial launch (ns) */
+    int tc_matching_ns;    /*   tuned time of the matching-row launch (ns) */
 } rttddft_info;
 
 RTTDDFT_API void rttddft_default_options(rttddft_options* opt);

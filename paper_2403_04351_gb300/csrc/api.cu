@@ -41,6 +41,7 @@ struct rttddft_ctx {
     size_t nblk = 0;
     zd *d_vtab = nullptr, *d_dvtab = nullptr, *d_vstep = nullptr;
     zf *d_vtab32 = nullptr, *d_vstep32 = nullptr;
+    uint2* d_vsteps = nullptr;  // pre-split per-step table (split-BF16 form)
     double *d_occ = nullptr, *d_wk = nullptr, *d_lam = nullptr;
     DevState* d_st = nullptr;
     double* d_rec = nullptr;
@@ -203,6 +204,7 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.dvtab = ctx->d_dvtab;
     a.vstep = ctx->d_vstep;
     a.vstep32 = ctx->d_vstep32;
+    a.vsteps = ctx->d_vsteps;
     a.a = ctx->d_a;
     a.dvs = dv_on ? ctx->d_dvs : nullptr;
     a.st = ctx->d_st;
@@ -916,7 +918,7 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             }
             std::string why;
             const int e = tc_plan_create(&ctx->tc, nk, ns, at.ma, ngv.data(), glp.data(), atp.data(),
-                                         ctx->vt_center, ctx->stream, &why);
+                                         ctx->d_vtab, ctx->nvt, ctx->vt_center, ctx->d_kd, ctx->stream, &why);
             if (e) fail(ctx, e, "split-BF16 form: " + why);
         }
         CK(cudaMemcpy(ctx->d_kd, ctx->hkd.data(), nk * sizeof(KDev), cudaMemcpyHostToDevice));
@@ -925,12 +927,22 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
         std::vector<GemmDesc> ex, fw, pj, g1, g2, eh, en;
         ctx->kc_fwd = kchunk_for((at.ma + cn_rows(ns) - 1) / cn_rows(ns), nk, ctx->maxng);
         ctx->kc_proj = kchunk_for((naux + cn_rows(ns) - 1) / cn_rows(ns), nk, ctx->maxnb);
+        if (f32) {
+            // the FP32 streaming kernels take K slices of at most 256
+            ctx->kc_fwd = std::min(ctx->kc_fwd, 256);
+            ctx->kc_proj = std::min(ctx->kc_proj, 256);
+        }
         {
             // expand: rows are many, K = n_aux is short; split K only in FP64 where the
             // DFMA pipe of every SM is needed
             const int tiles = (ctx->maxnb + 63) / 64;
             ctx->kc_expand = 0;
-            if (tiles * nk < 2 * 152 && naux >= 128) {
+            if (f32) {
+                // FP32 streaming kernel: K slices of at most 256, enough blocks to fill the GPU
+                int splits = std::max((naux + 255) / 256, (2 * 152 + tiles * nk - 1) / (tiles * nk));
+                splits = std::min(splits, std::max(1, naux / 32));
+                if (splits > 1) ctx->kc_expand = (naux + splits - 1) / splits;
+            } else if (tiles * nk < 2 * 152 && naux >= 128) {
                 int splits = std::min((2 * 152 + tiles * nk - 1) / (tiles * nk), naux / 64);
                 if (splits > 1) ctx->kc_expand = ((naux + splits - 1) / splits + 63) / 64 * 64;
             }
@@ -1387,8 +1399,11 @@ int rttddft_get_info(rttddft_ctx* ctx, rttddft_info* info) {
     info->dt_cr0 = ctx->dtcr0;
     info->kernel_launches_per_step = ctx->launches_per_step;
     info->precision = ctx->opt.precision;
-    int v[6] = {0, 0, 0, 0, 0, 0};
+    int v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (ctx->tc) tc_plan_info(ctx->tc, v);
+    info->tc_candidates = v[6];
+    info->tc_interstitial_ns = v[7];
+    info->tc_matching_ns = v[8];
     info->tc_tile_n = v[0];
     info->tc_stages = v[1];
     info->tc_kblocks = v[2];
@@ -1424,6 +1439,7 @@ int rttddft_set_dv(rttddft_ctx* ctx, const double* dh, const double* dvtab) {
             ctx->d_dvtab = dalloc<zd>(ctx, ctx->nvt);
             ctx->d_vstep = dalloc<zd>(ctx, ctx->nvt);
             if (ctx->opt.precision != RTTDDFT_PREC_FP64) ctx->d_vstep32 = dalloc<zf>(ctx, ctx->nvt);
+            if (ctx->opt.precision == RTTDDFT_PREC_BF16X3) ctx->d_vsteps = dalloc<uint2>(ctx, ctx->nvt);
             std::vector<GemmDesc> w, g, gi;
             std::vector<ToepDesc> td;
             for (int k = 0; k < nk; ++k) {
@@ -1927,6 +1943,7 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         StepArgs a = make_args(ctx, dv_on);
         a.kd = (const KDev*)(base + o_kd);
         if (a.prec == 2) a.prec = 1;  // the static scratch holds the FP32-form operands only
+        a.vsteps = nullptr;
         a.nk = 1;
         a.st = (DevState*)(base + o_st);
         a.part_jmt = (double*)(base + o_jmt);

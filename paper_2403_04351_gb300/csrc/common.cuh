@@ -1,6 +1,7 @@
 // Device helpers shared by the rttddft CUDA translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 typedef double2 zd;  // complex FP64 (re, im)
@@ -74,3 +75,51 @@ template <> struct Cx<zf> {
     static __device__ __forceinline__ zd todbl(zf a) { return tod(a); }
 };
 
+// bf16 split v = hi + lo (each rounded to nearest) packed as hi | lo << 16
+__device__ __forceinline__ uint32_t bf16_split_bits(double v) {
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    const __nv_bfloat16 l = __double2bfloat16(v - (double)__bfloat162float(h));
+    return (uint32_t)__bfloat16_as_ushort(h) | ((uint32_t)__bfloat16_as_ushort(l) << 16);
+}
+
+// Sum over the 32 lanes of V values per lane by exchange-halving steps
+// (each lane keeps half of its values and adds its partner's copy of them)
+// followed by plain steps: V - 1 + (5 - log2 V) additions per lane for
+// V <= 32, instead of 5 V (on GB300 each warp-wide FP64 add holds a
+// sub-partition's FP64 pipe for tens of cycles).  Afterwards lane L holds
+// the full sums of values base .. base + max(1, V/32) - 1.
+template <typename T, int V, int OFF>
+struct WarpHalvingSum {
+    static __device__ __forceinline__ void run(T* v, int lane, int& base) {
+        if constexpr (OFF >= 1) {
+            if constexpr (V > 1) {
+                constexpr int H = V / 2;
+                const bool up = (lane & OFF) != 0;
+#pragma unroll
+                for (int u = 0; u < H; ++u) {
+                    const T send = up ? v[u] : v[u + H];
+                    const T keep = up ? v[u + H] : v[u];
+                    v[u] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+                }
+                if (up) base += H;
+                WarpHalvingSum<T, H, OFF / 2>::run(v, lane, base);
+            } else {
+                v[0] += __shfl_xor_sync(0xffffffffu, v[0], OFF);
+                WarpHalvingSum<T, 1, OFF / 2>::run(v, lane, base);
+            }
+        }
+    }
+};
+// Reduce V (a power of two) values per lane over the warp and store the V
+// sums to out[0 .. V-1] (one writer per value).
+template <typename T, int V>
+__device__ __forceinline__ void warp_sum_store(T* v, int lane, T* out) {
+    int base = 0;
+    WarpHalvingSum<T, V, 16>::run(v, lane, base);
+    constexpr int REM = V >= 32 ? V / 32 : 1;
+    constexpr int MASK = V >= 32 ? 0 : (32 / V - 1);
+    if ((lane & MASK) == 0) {
+#pragma unroll
+        for (int r = 0; r < REM; ++r) out[base + r] = v[r];
+    }
+}

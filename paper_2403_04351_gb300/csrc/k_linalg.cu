@@ -158,6 +158,166 @@ __global__ void __launch_bounds__(256) k_gemm_cn(const GemmDesc* __restrict__ de
     }
 }
 
+// ---------------------------------------------------------------- FP32 streaming forms
+// The same products with A in FP32 (FP32 and split-BF16 precision forms),
+// written for streaming A at full memory bandwidth: every thread issues all
+// of its loads of A for the block's K range before it waits on anything,
+// the block's slice of B is staged once in shared memory (as FP32) while
+// those loads are in flight, and there is no synchronisation inside the K
+// loop.  Sums are FP32 within a block, FP64 across split-K slices.
+
+// CN: C[m, n] (+)= sum_k conj(A[k, m]) B[k, n]; warp = RPW rows, lanes over k
+template <int NT, int RPW, int KC>
+__global__ void __launch_bounds__(256) k_gemm_cn32(const GemmDesc* __restrict__ descs, int N, int kchunk,
+                                                   zd* __restrict__ part, int beta_add,
+                                                   const double* __restrict__ dscale) {
+    constexpr int U = KC / 32;  // loads of A per lane and row
+    __shared__ zf bs[KC][NT];
+    __shared__ float red[8][2 * RPW * NT];
+    const GemmDesc d = descs[blockIdx.z];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mb = blockIdx.x * 8 * RPW;
+    const int k0 = blockIdx.y * kchunk;  // kchunk <= KC
+    if (mb >= d.M || k0 >= d.K) return;
+    const int kn = min(kchunk, d.K - k0);
+    const int m0 = mb + warp * RPW;
+    const zf* __restrict__ A = (const zf*)d.A;
+    for (int n0 = 0; n0 < N; n0 += NT) {
+        zf av[RPW][U];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int kk = lane + 32 * u;
+                av[q][u] = (m0 + q < d.M && kk < kn) ? A[(size_t)(m0 + q) * d.lda + k0 + kk] : make_float2(0.f, 0.f);
+            }
+        __syncthreads();
+        for (int e = threadIdx.x; e < KC * NT; e += 256) {
+            const int kk = e / NT, j = e % NT;
+            bs[kk][j] = (kk < kn && n0 + j < N) ? tof(d.B[k0 + kk + (size_t)(n0 + j) * d.ldb]) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        zf acc[RPW][NT];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q)
+#pragma unroll
+            for (int j = 0; j < NT; ++j) acc[q][j] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int kk = lane + 32 * u;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const zf b = bs[kk][j];
+#pragma unroll
+                for (int q = 0; q < RPW; ++q) cfmac(acc[q][j], av[q][u], b);
+            }
+        }
+        float v[2 * RPW * NT];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q)
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                v[2 * (q * NT + j)] = acc[q][j].x;
+                v[2 * (q * NT + j) + 1] = acc[q][j].y;
+            }
+        warp_sum_store<float, 2 * RPW * NT>(v, lane, red[warp]);
+        __syncwarp();
+        const double sc = dscale ? *dscale : 1.0;
+        for (int e = lane; e < RPW * NT; e += 32) {
+            const int q = e / NT, j = e % NT;
+            const int m = m0 + q, n = n0 + j;
+            if (m >= d.M || n >= N) continue;
+            const zd val = zscale(zmk((double)red[warp][2 * e], (double)red[warp][2 * e + 1]), sc);
+            if (part) {
+                part[d.part_off + ((size_t)blockIdx.y * N + n) * d.M + m] = val;
+            } else {
+                zd* c = d.C + m + (size_t)n * d.ldc;
+                *c = beta_add ? zadd(*c, val) : val;
+            }
+        }
+    }
+}
+
+// NN: C[m, n] (+)= sum_k A[m, k] B[k, n]; thread = row, four k-groups per
+// block of 64 rows, the block's K slice (at most KC) of B in shared memory
+template <int NT, int KC>
+__global__ void __launch_bounds__(256) k_gemm_nn32(const GemmDesc* __restrict__ descs, int N, int kchunk,
+                                                   zd* __restrict__ part, int beta_add,
+                                                   const double* __restrict__ dscale) {
+    constexpr int U = 8;
+    __shared__ zf bs[KC][NT];
+    __shared__ zf redc[3][64][NT];
+    const GemmDesc d = descs[blockIdx.z];
+    const int m0 = blockIdx.x * 64;
+    const int k0 = blockIdx.y * kchunk;
+    if (m0 >= d.M || k0 >= d.K) return;
+    const int kn = min(kchunk, d.K - k0);
+    const int r = threadIdx.x & 63, grp = threadIdx.x >> 6;
+    const int m = m0 + r;
+    const bool act = m < d.M;
+    const zf* __restrict__ A = (const zf*)d.A + m;
+    for (int n0 = 0; n0 < N; n0 += NT) {
+        // the first loads of A go out before the slice of B is staged; two
+        // register buffers alternate so that the next chunk is always in flight
+        zf a0[U], a1[U];
+        auto load = [&](zf* dst, int kb) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int kk = kb + 4 * u;
+                dst[u] = (act && kk < kn) ? A[(size_t)(k0 + kk) * d.lda] : make_float2(0.f, 0.f);
+            }
+        };
+        zf acc[NT];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) acc[j] = make_float2(0.f, 0.f);
+        auto fma_chunk = [&](const zf* av, int kb) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int kk = kb + 4 * u;
+                if (kk < kn) {
+#pragma unroll
+                    for (int j = 0; j < NT; ++j) cfma(acc[j], av[u], bs[kk][j]);
+                }
+            }
+        };
+        load(a0, grp);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kn * NT; e += 256) {
+            const int kk = e / NT, j = e % NT;
+            bs[kk][j] = (n0 + j < N) ? tof(d.B[k0 + kk + (size_t)(n0 + j) * d.ldb]) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int kb = grp; kb < kn; kb += 8 * U) {
+            if (kb + 4 * U < kn) load(a1, kb + 4 * U);
+            fma_chunk(a0, kb);
+            if (kb + 4 * U >= kn) break;
+            if (kb + 8 * U < kn) load(a0, kb + 8 * U);
+            fma_chunk(a1, kb + 4 * U);
+        }
+        if (grp > 0) {
+#pragma unroll
+            for (int j = 0; j < NT; ++j) redc[grp - 1][r][j] = acc[j];
+        }
+        __syncthreads();
+        if (grp == 0 && act) {
+            const double sc = dscale ? *dscale : 1.0;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const int n = n0 + j;
+                if (n >= N) break;
+                zd v = zadd(zadd(tod(acc[j]), tod(redc[0][r][j])), zadd(tod(redc[1][r][j]), tod(redc[2][r][j])));
+                v = zscale(v, sc);
+                if (part) {
+                    part[d.part_off + ((size_t)blockIdx.y * N + n) * d.M + m] = v;
+                } else {
+                    zd* c = d.C + m + (size_t)n * d.ldc;
+                    *c = beta_add ? zadd(*c, v) : v;
+                }
+            }
+        }
+    }
+}
+
 __global__ void k_split_reduce(const GemmDesc* __restrict__ descs, int N, int kchunk,
                                const zd* __restrict__ part, int beta_add) {
     const GemmDesc d = descs[blockIdx.z];
@@ -166,7 +326,17 @@ __global__ void k_split_reduce(const GemmDesc* __restrict__ descs, int N, int kc
     const int m = idx % d.M, n = idx / d.M;
     const int nsp = (d.K + kchunk - 1) / kchunk;
     zd s = zmk(0.0, 0.0);
-    for (int sp = 0; sp < nsp; ++sp) s = zadd(s, part[d.part_off + ((size_t)sp * N + n) * d.M + m]);
+    const zd* p = part + d.part_off + (size_t)n * d.M + m;
+    const size_t st = (size_t)N * d.M;
+    int sp = 0;
+    for (; sp + 8 <= nsp; sp += 8) {
+        zd t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = p[(size_t)(sp + u) * st];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s = zadd(s, t[u]);
+    }
+    for (; sp < nsp; ++sp) s = zadd(s, p[(size_t)sp * st]);
     zd* c = d.C + m + (size_t)n * d.ldc;
     *c = beta_add ? zadd(*c, s) : s;
 }
@@ -201,13 +371,37 @@ static void gemm_cn_t(const GemmDesc* d, int nb, int maxM, int maxK, int N, int 
     }
 }
 
+// largest K slice of a block in the FP32 streaming kernels
+#define GEMM32_KC 256
 void launch_gemm_nn(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kchunk, zd* part,
                     int beta_add, bool a_fp32, const double* ds, cudaStream_t s) {
+    if (a_fp32 && nb > 0 && maxM > 0 && maxK > 0 && N > 0 && (kchunk > 0 ? kchunk : maxK) <= GEMM32_KC) {
+        const int kc = kchunk > 0 ? kchunk : maxK;
+        dim3 grid((maxM + 63) / 64, (maxK + kc - 1) / kc, nb);
+        if (N <= 2) k_gemm_nn32<2, GEMM32_KC><<<grid, 256, 0, s>>>(d, N, kc, part, beta_add, ds);
+        else if (N <= 4) k_gemm_nn32<4, GEMM32_KC><<<grid, 256, 0, s>>>(d, N, kc, part, beta_add, ds);
+        else k_gemm_nn32<8, GEMM32_KC><<<grid, 256, 0, s>>>(d, N, kc, part, beta_add, ds);
+        return;
+    }
     if (a_fp32) gemm_nn_t<zf, zf>(d, nb, maxM, maxK, N, kchunk, part, beta_add, ds, s);
     else gemm_nn_t<zd, zd>(d, nb, maxM, maxK, N, kchunk, part, beta_add, ds, s);
 }
 void launch_gemm_cn(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kchunk, zd* part,
                     int beta_add, bool a_fp32, const double* ds, cudaStream_t s) {
+    if (a_fp32 && nb > 0 && maxM > 0 && maxK > 0 && N > 0 && (kchunk > 0 ? kchunk : maxK) <= GEMM32_KC) {
+        const int kc = kchunk > 0 ? kchunk : maxK;
+        if (N <= 2) {
+            dim3 grid((maxM + 31) / 32, (maxK + kc - 1) / kc, nb);
+            k_gemm_cn32<2, 4, GEMM32_KC><<<grid, 256, 0, s>>>(d, N, kc, part, beta_add, ds);
+        } else if (N <= 4) {
+            dim3 grid((maxM + 15) / 16, (maxK + kc - 1) / kc, nb);
+            k_gemm_cn32<4, 2, GEMM32_KC><<<grid, 256, 0, s>>>(d, N, kc, part, beta_add, ds);
+        } else {
+            dim3 grid((maxM + 7) / 8, (maxK + kc - 1) / kc, nb);
+            k_gemm_cn32<8, 1, GEMM32_KC><<<grid, 256, 0, s>>>(d, N, kc, part, beta_add, ds);
+        }
+        return;
+    }
     if (a_fp32) gemm_cn_t<zf, zf>(d, nb, maxM, maxK, N, kchunk, part, beta_add, ds, s);
     else gemm_cn_t<zd, zd>(d, nb, maxM, maxK, N, kchunk, part, beta_add, ds, s);
 }

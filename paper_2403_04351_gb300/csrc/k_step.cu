@@ -35,6 +35,7 @@ __global__ void k_vstep(StepArgs a) {
     const zd v = zadd(a.vtab[i], zscale(a.dvtab[i], s));
     a.vstep[i] = v;
     if (a.vstep32) a.vstep32[i] = tof(v);
+    if (a.vsteps) a.vsteps[i] = make_uint2(bf16_split_bits(v.x), bf16_split_bits(v.y));
 }
 
 // ------------------------------------------------------------ HH(t_k)
@@ -154,8 +155,9 @@ __device__ bool grid_barrier(unsigned* count, unsigned target, int* flag) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(count, 1u);
+        // release: the block's writes (ordered before by the bar.sync above)
+        // become visible to every block that acquires the count
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
         int ok = 1;
         unsigned long long it = 0;
         while (ld_acquire_gpu(count) < target) {
@@ -172,82 +174,101 @@ __device__ bool grid_barrier(unsigned* count, unsigned target, int* flag) {
     return s_ok != 0;
 }
 
-// Sum over the 32 lanes of V values per lane by exchange-halving steps
-// (each lane keeps half of its values and adds its partner's copy of them)
-// followed by plain steps: V - 1 + (5 - log2 V) additions per lane for
-// V <= 32, instead of 5 V (on GB300 each warp-wide FP64 add holds a
-// sub-partition's FP64 pipe for tens of cycles).  Afterwards lane L holds
-// the full sums of values base .. base + max(1, V/32) - 1.
-template <typename T, int V, int OFF>
-struct WarpHalvingSum {
-    static __device__ __forceinline__ void run(T* v, int lane, int& base) {
-        if constexpr (OFF >= 1) {
-            if constexpr (V > 1) {
-                constexpr int H = V / 2;
-                const bool up = (lane & OFF) != 0;
-#pragma unroll
-                for (int u = 0; u < H; ++u) {
-                    const T send = up ? v[u] : v[u + H];
-                    const T keep = up ? v[u + H] : v[u];
-                    v[u] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
-                }
-                if (up) base += H;
-                WarpHalvingSum<T, H, OFF / 2>::run(v, lane, base);
-            } else {
-                v[0] += __shfl_xor_sync(0xffffffffu, v[0], OFF);
-                WarpHalvingSum<T, 1, OFF / 2>::run(v, lane, base);
-            }
-        }
-    }
-};
-// Reduce V (a power of two) values per lane over the warp and store the V
-// sums to out[0 .. V-1] (one writer per value).
-template <typename T, int V>
-__device__ __forceinline__ void warp_sum_store(T* v, int lane, T* out) {
-    int base = 0;
-    WarpHalvingSum<T, V, 16>::run(v, lane, base);
-    constexpr int REM = V >= 32 ? V / 32 : 1;
-    constexpr int MASK = V >= 32 ? 0 : (32 / V - 1);
-    if ((lane & MASK) == 0) {
-#pragma unroll
-        for (int r = 0; r < REM; ++r) out[base + r] = v[r];
-    }
-}
-
 // The whole Chebyshev series in one cooperative launch.  A block of two
-// warps owns rows (k, i) round-robin; its lanes stride the row's dot
-// products and reduce them with WarpHalvingSum (the FP64 pipe, not memory,
-// bounds a term on GB300); a grid barrier separates consecutive terms.
-// Vectors written by other blocks are read through L2 (ld.global.cg).
+// warps owns rows (k, i) = blockIdx.x + r gridDim.x for all terms; its lanes
+// stride a row's dot products and reduce them with WarpHalvingSum (the FP64
+// pipe, not memory, bounds a term on GB300).  Only the newest vector y_{n-1}
+// is exchanged through global memory (two slots, read through L2 with
+// ld.global.cg); each block keeps y_{n-1}, y_{n-2} and the partial sum of
+// its own rows in shared memory.  A grid barrier separates the terms.
 #define CHEB_THREADS 64
+#define CHEB_JU 4  // row entries per thread held at once (n_aux <= 256 in one pass)
 template <int NT>
-__global__ void __launch_bounds__(CHEB_THREADS) k_cheb_coop(StepArgs a) {
+__global__ void __launch_bounds__(CHEB_THREADS) k_cheb_coop(StepArgs a, int direct) {
     constexpr int V = 2 * NT;
     __shared__ double red[CHEB_THREADS / 32][V];
+    extern __shared__ zd cst[];  // [rows of the block][3][ns]: y_{n-1}, y_{n-2}, partial sum
     const int n = a.naux, ns = a.ns;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t vs = (size_t)n * ns;
     const int nrow = a.nk * n;
+    // direct: every block owns one row and n <= CHEB_JU * CHEB_THREADS, so the
+    // block builds its row of HH(t_k) (Eq. auxiliary_hamiltonian_with_parts)
+    // once, in registers, instead of reading a matrix formed by k_hsub
+    zd hrow[CHEB_JU];
+    if (direct && blockIdx.x < nrow) {
+        const int k = blockIdx.x / n, i = blockIdx.x % n;
+        const KDev& K = a.kd[k];
+        DevState* st = a.st;
+        const double* av = a.a + 3 * (size_t)st->cstep;
+        const double ax = av[0], ay = av[1], az = av[2];
+        const double aa = (ax * ax + ay * ay + az * az) * a.half_inv_c2;
+        if (blockIdx.x == 0 && tid == 0 && !a.dv_on) {
+            st->cur_a[0] = ax;
+            st->cur_a[1] = ay;
+            st->cur_a[2] = az;
+            st->cur_s = 0.0;
+            st->cur_aa = aa;
+        }
+        const size_t nn = (size_t)n * n;
+        const double al[3] = {ax * a.inv_c, ay * a.inv_c, az * a.inv_c};
+#pragma unroll
+        for (int u = 0; u < CHEB_JU; ++u) {
+            const int j = tid + u * CHEB_THREADS;
+            zd v = zmk(0.0, 0.0);
+            if (j < n) {
+                const size_t e = (size_t)i * n + j;  // the storage element (row j, column i) of k_hsub
+#pragma unroll
+                for (int l = 0; l < 3; ++l)
+                    if (al[l] != 0.0) v = zadd(v, zscale(K.psub[l * nn + e], al[l]));
+                if (i == j) v.x += K.eps[i] + aa;
+                if (a.dv_on) v = zadd(v, K.dvsub[e]);
+            }
+            hrow[u] = v;
+        }
+    }
     for (int nt = 1; nt < a.nterms; ++nt) {
         const int last = (nt == a.nterms - 1);
-        for (int q = blockIdx.x; q < nrow; q += gridDim.x) {
+        int r = 0;
+        for (int q = blockIdx.x; q < nrow; q += gridDim.x, ++r) {
             const int k = q / n, i = q % n;
             const KDev& K = a.kd[k];
             const zd* __restrict__ H = K.hsub + (size_t)i * n;
-            const zd* yin = (nt == 1) ? K.theta : K.ring + ((nt - 1) % 3) * vs;
-            const zd* yp2 = (nt >= 2) ? K.ring + ((nt - 2) % 3) * vs : nullptr;
-            zd* yout = K.ring + (nt % 3) * vs;
-            const double lc = K.lam[0], ilh = K.lam[2];
-            const zd cn = K.coef[nt];
+            const zd* yin = (nt == 1) ? K.theta : K.ring + ((nt - 1) & 1) * vs;
+            zd* yout = K.ring + (nt & 1) * vs;
+            zd* y1 = cst + (size_t)r * 3 * ns;
+            zd* y2 = y1 + ns;
+            zd* ac = y2 + ns;
             for (int n0 = 0; n0 < ns; n0 += NT) {
+                // operands of the update first, so their latency overlaps the dot products
+                const bool upd = tid < NT && n0 + tid < ns;
+                zd yi = zmk(0.0, 0.0), cn = zmk(0.0, 0.0), c0 = zmk(0.0, 0.0);
+                double lc = 0.0, ilh = 0.0;
+                if (upd) {
+                    yi = (nt == 1) ? K.theta[i + (size_t)(n0 + tid) * n] : y1[n0 + tid];
+                    cn = K.coef[nt];
+                    if (nt == 1) c0 = K.coef[0];
+                    lc = K.lam[0];
+                    ilh = K.lam[2];
+                }
                 zd acc[NT];
 #pragma unroll
                 for (int c = 0; c < NT; ++c) acc[c] = zmk(0.0, 0.0);
-                for (int j = tid; j < n; j += CHEB_THREADS) {
-                    const zd h = H[j];
+                for (int j0 = tid; j0 < n; j0 += CHEB_JU * CHEB_THREADS) {
+                    zd hv[CHEB_JU], yv[CHEB_JU][NT];
 #pragma unroll
-                    for (int c = 0; c < NT; ++c)
-                        if (n0 + c < ns) zfmac(acc[c], h, __ldcg(yin + j + (size_t)(n0 + c) * n));
+                    for (int u = 0; u < CHEB_JU; ++u) {
+                        const int j = j0 + u * CHEB_THREADS;
+                        const bool ok = j < n;
+                        hv[u] = direct ? hrow[u] : (ok ? H[j] : zmk(0.0, 0.0));
+#pragma unroll
+                        for (int c = 0; c < NT; ++c)
+                            yv[u][c] = (ok && n0 + c < ns) ? __ldcg(yin + j + (size_t)(n0 + c) * n) : zmk(0.0, 0.0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < CHEB_JU; ++u)
+#pragma unroll
+                        for (int c = 0; c < NT; ++c) zfmac(acc[c], hv[u], yv[u][c]);
                 }
                 double v[V];
 #pragma unroll
@@ -257,29 +278,28 @@ __global__ void __launch_bounds__(CHEB_THREADS) k_cheb_coop(StepArgs a) {
                 }
                 warp_sum_store<double, V>(v, lane, red[warp]);
                 __syncthreads();
-                if (tid < NT && n0 + tid < ns) {
-                    const int c = tid;
-                    zd r = zmk(red[0][2 * c], red[0][2 * c + 1]);
+                if (upd) {
+                    const int c = n0 + tid;
+                    zd sm = zmk(red[0][2 * tid], red[0][2 * tid + 1]);
 #pragma unroll
-                    for (int w = 1; w < CHEB_THREADS / 32; ++w) r = zadd(r, zmk(red[w][2 * c], red[w][2 * c + 1]));
-                    const size_t e = i + (size_t)(n0 + c) * n;
-                    const zd yi = __ldcg(yin + e);
-                    const zd w = zscale(zsub(r, zscale(yi, lc)), ilh);
-                    zd y, ac;
+                    for (int w = 1; w < CHEB_THREADS / 32; ++w) sm = zadd(sm, zmk(red[w][2 * tid], red[w][2 * tid + 1]));
+                    const zd w = zscale(zsub(sm, zscale(yi, lc)), ilh);
+                    zd y, s;
                     if (nt == 1) {
                         y = w;
-                        K.ring[e] = yi;
-                        ac = zadd(zmul(K.coef[0], yi), zmul(cn, y));
+                        s = zadd(zmul(c0, yi), zmul(cn, y));
                     } else {
-                        y = zsub(zscale(w, 2.0), __ldcg(yp2 + e));
-                        ac = zadd(__ldcg(K.acc + e), zmul(cn, y));
+                        y = zsub(zscale(w, 2.0), y2[c]);
+                        s = zadd(ac[c], zmul(cn, y));
                     }
-                    yout[e] = y;
+                    y2[c] = yi;
+                    y1[c] = y;
                     if (last) {
                         const zd ph = (a.prop == 0) ? zmk(K.lam[3], K.lam[4]) : zmk(1.0, 0.0);
-                        K.theta[e] = zmul(ph, ac);
+                        K.theta[i + (size_t)c * n] = zmul(ph, s);
                     } else {
-                        K.acc[e] = ac;
+                        yout[i + (size_t)c * n] = y;
+                        ac[c] = s;
                     }
                 }
                 __syncthreads();
@@ -776,93 +796,114 @@ __global__ void k_reproj(StepArgs a) {
 // update the dipole by the trapezoid rule (Eq. dipole) and append the
 // record.  One block.
 __global__ void __launch_bounds__(256) k_finalize(StepArgs a, int set_gs) {
-    __shared__ double sh[8][13];
+    // the k-weights enter the per-row shares, so one block reduction covers all
+    // k-points; sums by halving warp sums (each warp-wide FP64 add is costly on
+    // GB300), maxima of non-negative values as integer maxima of their bits
+    __shared__ double sh[8][16];
+    __shared__ unsigned long long shm[8][2];
     DevState* st = a.st;
     const int ns = a.ns, n = a.naux, lrows = a.lrows;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double J[3] = {0, 0, 0}, JF[3] = {0, 0, 0}, E = 0.0, ndev = 0.0, res = 0.0, dtcr = 1e300;
-    const double io = -1.0 / a.omega;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    // 0-2 J_sub, 3 E, 4 c^H S c, 5-7 sum (G+k)|c|^2, 8-10 J_mt; all times w_k
+    double v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = 0.0;
+    double mres = 0.0, mdev = 0.0;
     for (int k = 0; k < a.nk; ++k) {
         const KDev& K = a.kd[k];
+        const double w = a.wk[k];
         const int nback = (K.ng + BT - 1) / BT;
-        // 0-2 J_sub, 3 E, 4 c^H S c, 5-7 sum (G+k)|c|^2, 8-10 J_mt | 11 residual, 12 norm (max)
-        double v[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int i = tid; i < n; i += blockDim.x) {
             const double* p = a.part_post + ((size_t)k * n + i) * POST_STRIDE;
-            v[0] += p[1];
-            v[1] += p[2];
-            v[2] += p[3];
-            v[11] = fmax(v[11], p[0]);
+            v[0] += w * p[1];
+            v[1] += w * p[2];
+            v[2] += w * p[3];
+            mres = fmax(mres, p[0]);
         }
-        if (!set_gs) {
-            for (int c = tid; c < nback; c += blockDim.x) {
-                const double* pf = a.part_full + ((size_t)k * a.max_nback + c) * 5;
-                v[3] += pf[0];
-                v[4] += pf[1];
-                v[5] += pf[2];
-                v[6] += pf[3];
-                v[7] += pf[4];
-            }
-            for (int r = tid; r < lrows; r += blockDim.x) {
-                const double* pj = a.part_jmt + ((size_t)k * lrows + r) * 5;
-                v[8] += pj[0];
-                v[9] += pj[1];
-                v[10] += pj[2];
-                v[3] += pj[3];
-                v[4] += pj[4];
-            }
-            if (ns <= 4) {
-                // sum the rows' shares of theta^H theta~ in a fixed order (one warp per entry)
-                for (int e = warp; e < ns * ns; e += blockDim.x / 32) {
-                    double gx = 0.0, gy = 0.0;
-                    for (int i = lane; i < n; i += 32) {
-                        const double* p = a.part_post + ((size_t)k * n + i) * POST_STRIDE + 4 + 2 * e;
-                        gx += p[0];
-                        gy += p[1];
-                    }
-                    gx = warp_sum(gx);
-                    gy = warp_sum(gy);
-                    if (e % ns == e / ns) gx -= 1.0;
-                    v[12] = fmax(v[12], hypot(gx, gy));
-                }
-            } else {
-                for (int e = tid; e < ns * ns; e += blockDim.x) {
-                    zd g = K.gram[e];
-                    if (e % ns == e / ns) g.x -= 1.0;
-                    v[12] = fmax(v[12], hypot(g.x, g.y));
-                }
-            }
-        }
+        if (set_gs) continue;
+        for (int c = tid; c < nback; c += blockDim.x) {
+            const double* pf = a.part_full + ((size_t)k * a.max_nback + c) * 5;
 #pragma unroll
-        for (int q = 0; q < 13; ++q) {
-            const double r = (q >= 11) ? warp_max(v[q]) : warp_sum(v[q]);
-            if (lane == 0) sh[warp][q] = r;
+            for (int q = 0; q < 5; ++q) v[3 + q] += w * pf[q];
         }
-        __syncthreads();
-        if (tid == 0) {
-            double t[13];
-            for (int q = 0; q < 13; ++q) {
-                t[q] = 0.0;
-                for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w)
-                    t[q] = (q >= 11) ? fmax(t[q], sh[w][q]) : t[q] + sh[w][q];
-            }
-            const double w = a.wk[k];
-            for (int l = 0; l < 3; ++l) {
-                J[l] += w * io * t[l];
-                JF[l] += w * io * (t[5 + l] + t[8 + l] + st->cur_a[l] * a.inv_c * t[4]);
-            }
-            E += w * t[3];
-            res = fmax(res, t[11]);
-            ndev = fmax(ndev, t[12]);
-            const double dk = (a.prop == 1) ? 0.2 / (K.eval[n - 1] - K.eval[0]) : 0.2 / (2.0 * K.lam[1]);
-            dtcr = fmin(dtcr, dk);
+        for (int r = tid; r < lrows; r += blockDim.x) {
+            const double* pj = a.part_jmt + ((size_t)k * lrows + r) * 5;
+            v[8] += w * pj[0];
+            v[9] += w * pj[1];
+            v[10] += w * pj[2];
+            v[3] += w * pj[3];
+            v[4] += w * pj[4];
         }
-        __syncthreads();
+        if (ns <= 4) {
+            // the rows' shares of theta^H theta~ in a fixed order (one warp per entry)
+            for (int e = warp; e < ns * ns; e += nw) {
+                double g[2] = {0.0, 0.0};
+                for (int i = lane; i < n; i += 32) {
+                    const double* p = a.part_post + ((size_t)k * n + i) * POST_STRIDE + 4 + 2 * e;
+                    g[0] += p[0];
+                    g[1] += p[1];
+                }
+                __shared__ double gs[8][2];
+                warp_sum_store<double, 2>(g, lane, gs[warp]);
+                __syncwarp();
+                double gx = gs[warp][0];
+                const double gy = gs[warp][1];
+                if (e % ns == e / ns) gx -= 1.0;
+                mdev = fmax(mdev, hypot(gx, gy));
+                __syncwarp();
+            }
+        } else {
+            for (int e = tid; e < ns * ns; e += blockDim.x) {
+                zd g = K.gram[e];
+                if (e % ns == e / ns) g.x -= 1.0;
+                mdev = fmax(mdev, hypot(g.x, g.y));
+            }
+        }
     }
+    warp_sum_store<double, 16>(v, lane, sh[warp]);
+    unsigned long long br = (unsigned long long)__double_as_longlong(mres);
+    unsigned long long bd = (unsigned long long)__double_as_longlong(mdev);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long xr = __shfl_xor_sync(0xffffffffu, br, o);
+        const unsigned long long xd = __shfl_xor_sync(0xffffffffu, bd, o);
+        br = xr > br ? xr : br;
+        bd = xd > bd ? xd : bd;
+    }
+    if (lane == 0) {
+        shm[warp][0] = br;
+        shm[warp][1] = bd;
+    }
+    __syncthreads();
+    if (tid < 11) {
+        double t = sh[0][tid];
+        for (int w = 1; w < nw; ++w) t += sh[w][tid];
+        sh[0][tid] = t;
+    } else if (tid < 13) {
+        unsigned long long m = shm[0][tid - 11];
+        for (int w = 1; w < nw; ++w) m = shm[w][tid - 11] > m ? shm[w][tid - 11] : m;
+        shm[0][tid - 11] = m;
+    }
+    __syncthreads();
     if (tid != 0) return;
+    const double io = -1.0 / a.omega;
+    double J[3], JF[3];
+    for (int l = 0; l < 3; ++l) {
+        J[l] = io * sh[0][l];
+        JF[l] = io * (sh[0][5 + l] + sh[0][8 + l] + st->cur_a[l] * a.inv_c * sh[0][4]);
+    }
     if (set_gs) {
         for (int l = 0; l < 3; ++l) st->j_gs[l] = J[l];
         return;
+    }
+    const double E = sh[0][3];
+    const double res = __longlong_as_double((long long)shm[0][0]);
+    const double ndev = __longlong_as_double((long long)shm[0][1]);
+    double dtcr = 1e300;
+    for (int k = 0; k < a.nk; ++k) {
+        const KDev& K = a.kd[k];
+        const double dk = (a.prop == 1) ? 0.2 / (K.eval[n - 1] - K.eval[0]) : 0.2 / (2.0 * K.lam[1]);
+        dtcr = fmin(dtcr, dk);
     }
     const double t = st->t + a.dt;
     double* r = a.rec + (size_t)st->rec_count * RTD_REC_STRIDE;
@@ -883,6 +924,7 @@ __global__ void __launch_bounds__(256) k_finalize(StepArgs a, int set_gs) {
     st->rec_count += 1;
     st->gstep += 1;
     st->cstep += 1;
+    st->bar = 0u;  // the next step's cooperative series counts from zero
 }
 
 // ------------------------------------------------------------ Jacobi eigensolver
@@ -1092,20 +1134,32 @@ void launch_phase_fix(const KDev* kd, int nk, int naux, zd* const* extra, const 
 }
 
 // ------------------------------------------------------------ orchestration
+// the cooperative series forms its own rows of HH when each block owns one
+// row and the row fits the registers of the block's threads
+int cheb_direct(const StepArgs& a) {
+    return (a.coop_grid >= a.nk * a.naux && a.naux <= CHEB_JU * CHEB_THREADS && a.ns <= 4) ? 1 : 0;
+}
+// per-row state of the cooperative series: 3 ns complex per row of a block
+static size_t cheb_coop_smem(const StepArgs& a, int grid) {
+    const int nrow = a.nk * a.naux;
+    const int rows = grid > 0 ? (nrow + grid - 1) / grid : 0;
+    return (size_t)rows * 3 * a.ns * sizeof(zd);
+}
 static cudaError_t launch_cheb_coop_raw(const StepArgs& a, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.coop_grid);
     cfg.blockDim = dim3(CHEB_THREADS);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = cheb_coop_smem(a, a.coop_grid);
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    if (a.ns <= 2) return cudaLaunchKernelEx(&cfg, k_cheb_coop<2>, a);
-    if (a.ns <= 4) return cudaLaunchKernelEx(&cfg, k_cheb_coop<4>, a);
-    return cudaLaunchKernelEx(&cfg, k_cheb_coop<8>, a);
+    const int direct = cheb_direct(a);
+    if (a.ns <= 2) return cudaLaunchKernelEx(&cfg, k_cheb_coop<2>, a, direct);
+    if (a.ns <= 4) return cudaLaunchKernelEx(&cfg, k_cheb_coop<4>, a, direct);
+    return cudaLaunchKernelEx(&cfg, k_cheb_coop<8>, a, direct);
 }
 void launch_cheb_coop(const StepArgs& a, cudaStream_t s) { launch_cheb_coop_raw(a, s); }
 
@@ -1118,19 +1172,23 @@ int prepare_cheb_coop(const StepArgs& a0, cudaStream_t s) {
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (!coop || nsm <= 0) return 0;
-    cudaError_t e;
-    if (a0.ns <= 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_coop<2>, CHEB_THREADS, 0);
-    else if (a0.ns <= 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_coop<4>, CHEB_THREADS, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_coop<8>, CHEB_THREADS, 0);
-    if (e != cudaSuccess || per_sm <= 0) {
-        cudaGetLastError();
-        return 0;
-    }
     // one block per row while the rows last, at most four blocks per SM
     // (more blocks would lengthen the barrier's arrival chain)
     const int nrow = a0.nk * a0.naux;
     int grid = nrow < 4 * nsm ? nrow : 4 * nsm;
-    if (grid > per_sm * nsm) grid = per_sm * nsm;
+    const size_t smem = cheb_coop_smem(a0, grid);
+    const void* fn = a0.ns <= 2 ? (const void*)k_cheb_coop<2>
+                                : (a0.ns <= 4 ? (const void*)k_cheb_coop<4> : (const void*)k_cheb_coop<8>);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, CHEB_THREADS, smem);
+    if (e != cudaSuccess || per_sm <= 0 || grid > per_sm * nsm) {
+        cudaGetLastError();
+        return 0;
+    }
     StepArgs a = a0;
     a.coop_grid = grid;
     cudaGraph_t g = nullptr;
@@ -1282,9 +1340,11 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
         mark(tr, "dv_interstitial_project", s);
         nl += 6;
     }
-    k_hsub<<<dim3((nn + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
-    mark(tr, "hsub", s);
-    ++nl;
+    if (!(a.prop != 1 && a.coop_grid > 0 && cheb_direct(a))) {
+        k_hsub<<<dim3((nn + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
+        mark(tr, "hsub", s);
+        ++nl;
+    }
     if (a.prop == 1) {
         launch_jacobi(p.jac_mats, p.jac_vals, p.jac_vecs, a.nk, a.naux, p.max_sweeps, p.d_flag, s);
         mark(tr, "jacobi", s);

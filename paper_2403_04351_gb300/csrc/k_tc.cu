@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <vector>
 
 #include "rtd.h"
 #include "rttddft.h"
@@ -88,7 +89,9 @@ __global__ void __launch_bounds__(128, 1)
               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int nkb2,
               int kb_per_split, float* __restrict__ D, int M, int N, int* flag) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // aligned by offsetting the shared array itself, so that the compiler keeps
+    // shared-memory (not generic) addressing for every access through smem
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     constexpr int A_BYTES = TC_BM * TC_BK * 2;
     constexpr int B_BYTES = NT * TC_BK * 2;
     constexpr int STAGE = A_BYTES + B_BYTES;
@@ -384,24 +387,17 @@ int tc_zgemm(int opA, int M, int N, int K, const zd* A, int lda, const zd* X, in
 }
 
 // ============================================================================
-// Interstitial convolution and matching-coefficient products of the operator
-// apply on the tensor cores (Eq. v_interstitial and the first factor of
-// Eq. v_MT), in the split-BF16 form:
-//   row tiles 0 .. ttiles-1:  T[G, n] = sum_G' V~_{G-G'} C[G', n]
-//   row tiles ttiles ..:      Q[r, n] = sum_G' A[r, G'] C[G', n]
-// Both contract over G' with the same right operand, so one launch covers
-// them.  K is cut into blocks of 32 G' (64 reals: 32 Re then 32 Im); the
-// left operand of a block is [Re | Im] of 32 entries per row, the right one
+// Matching-coefficient products of the operator apply on the tensor cores
+// (the first factor of Eq. v_MT), in the split-BF16 form:
+//   Q[r, n] = sum_G' A[r, G'] C[G', n]
+// K is cut into blocks of 32 G' (64 reals: 32 Re then 32 Im); the left
+// operand of a block is [Re | Im] of 32 entries per row, the right one
 // holds, per column n, [Re C | -Im C] (real output rows) and [Im C | Re C]
-// (imaginary output rows).  The V~ rows are generated on the SM: the table
-// window of the (row tile, K slice) pair is staged in shared memory (G is
-// listed in lexicographic order, so the offsets glin(G) - glin(G') + centre
-// of the pair form one contiguous range) and 256 threads write the hi/lo
-// bf16 tile in the 128-byte swizzled K-major layout the tensor core reads.
-// The A rows and the right operand arrive by TMA (3-D maps over k).  One
-// thread issues the products; waits are bounded and abort together.
+// (imaginary output rows).  Both operands arrive by TMA (3-D maps over k)
+// through one ring of stages; one thread issues the products (hi.hi, hi.lo,
+// lo.hi per block); waits are bounded and abort together.
 // ============================================================================
-#define TCO_GEN 256          // generator threads (8 warps); warp 8 issues
+#define TCO_GEN 256  // threads of the generating / epilogue warps (8 warps); warp 8 issues
 #define TCO_THREADS 288
 #define TCO_MAXS 4
 
@@ -426,13 +422,11 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
         "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
-__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
 
 struct TcOpParams {
-    int nk, ns, ma, Dn, kbps, splits, ttiles, atiles, wcap, vt_center, R, S;
+    int nk, ns, ma, Dn, kbps, splits, atiles, R, S;
     int kofs;  // k-point of blockIdx.z = 0 in the matching-row operand (single-k calls)
     const KDev* kd;
-    const zf* tab;
     float* D;  // [nk][splits][R][Dn]
     int* flag;
 };
@@ -442,7 +436,9 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     k_tc_opfwd(const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl, TcOpParams p) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // aligned by offsetting the shared array itself, so that the compiler keeps
+    // shared-memory (not generic) addressing for every access through smem
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     constexpr int A_BYTES = TC_BM * TC_BK * 2;
     constexpr int B_BYTES = NT * TC_BK * 2;
     constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
@@ -454,18 +450,15 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     const int k = blockIdx.z, tile = blockIdx.x, split = blockIdx.y;
     const KDev& K = p.kd[k];
     const int ng = K.ng;
-    const bool is_t = tile < p.ttiles;
-    const int row0 = (is_t ? tile : tile - p.ttiles) * TC_BM;
+    const int row0 = tile * TC_BM;
     const int nkb = (ng + 31) >> 5;
     const int kb0 = split * p.kbps;
     const int nk = min(nkb, kb0 + p.kbps) - kb0;
-    if (nk <= 0 || (is_t && row0 >= ng)) return;  // the reduction skips these pairs
-    int* gl_s = (int*)(smem + (size_t)S * STAGE);
-    zf* win = (zf*)(gl_s + p.kbps * 32);
+    if (nk <= 0) return;  // the reduction skips these slices
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], is_t ? 1 + TCO_GEN / 32 : 1);
+            mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         mbar_init(&done, 1);
@@ -478,45 +471,24 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // table window and the G' offsets of this K slice
-    const int gp_lo = kb0 * 32, gp_hi = min(ng, (kb0 + nk) * 32);
-    int wlo = 0;
-    if (is_t && tid < TCO_GEN) {
-        const int* __restrict__ glin = K.glin;
-        const int g1 = min(row0 + TC_BM, ng) - 1;
-        wlo = glin[row0] - glin[gp_hi - 1] + p.vt_center;
-        const int wn = glin[g1] - glin[gp_lo] + p.vt_center - wlo + 1;
-        if (wn > p.wcap) {
-            // the host sizes the slices so that this cannot happen
-            abort_flag = 1;
-            if (tid == 0) atomicOr(p.flag, 8);
-        } else {
-            for (int e = tid; e < wn; e += TCO_GEN) win[e] = p.tab[wlo + e];
-        }
-        for (int i = tid; i < gp_hi - gp_lo; i += TCO_GEN) gl_s[i] = glin[gp_lo + i];
-    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     volatile int* ab = &abort_flag;
     if (warp == 8) {
-        if (lane == 0 && *ab) {
-            umma_commit(&done);  // nothing in flight: completes at once
-        } else if (lane == 0) {
+        if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                                    ((uint32_t)(TC_BM >> 4) << 24);
             int issued = 0, consumed = 0;
             auto load = [&](int j) {
                 const int s = j % S, kx = (kb0 + j) * TC_BK;
                 unsigned char* st = smem + (size_t)s * STAGE;
-                mbar_expect_tx(&full[s], is_t ? 2 * B_BYTES : STAGE);
+                mbar_expect_tx(&full[s], STAGE);
                 tma_load_3d(st + 2 * A_BYTES, &tmBh, kx, 0, k, &full[s]);
                 tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tmBl, kx, 0, k, &full[s]);
-                if (!is_t) {
-                    tma_load_3d(st, &tmAh, kx, row0, k + p.kofs, &full[s]);
-                    tma_load_3d(st + A_BYTES, &tmAl, kx, row0, k + p.kofs, &full[s]);
-                }
+                tma_load_3d(st, &tmAh, kx, row0, k + p.kofs, &full[s]);
+                tma_load_3d(st + A_BYTES, &tmAl, kx, row0, k + p.kofs, &full[s]);
                 issued = j + 1;
             };
             for (int j = 0; j < min(nk, S); ++j) load(j);
@@ -549,53 +521,6 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
             }
         }
         __syncwarp();
-    } else if (is_t && !*ab) {
-        // generators: thread (r, h) writes row r, G' 16h .. 16h+15 of every K block
-        const int r = tid & (TC_BM - 1), h = tid >> 7;
-        const int g = row0 + r;
-        const bool valid = g < ng;
-        const int lb = (valid ? K.glin[g] : 0) + p.vt_center - wlo;
-        const uint32_t sw = (uint32_t)(r & 7);
-        for (int j = 0; j < nk; ++j) {
-            const int s = j % S;
-            if (j >= S && !mbar_wait_ab(&empty[s], (uint32_t)(((j / S) - 1) & 1), ab)) break;
-            const int gq = (kb0 + j) * 32 + 16 * h;
-            float re[16], im[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int gp = gq + i;
-                zf v = {0.f, 0.f};
-                if (valid && gp < gp_hi) v = win[lb - gl_s[gp - gp_lo]];
-                re[i] = v.x;
-                im[i] = v.y;
-            }
-            uint32_t hr[8], lr[8], hi_[8], li[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const __nv_bfloat162 a = __floats2bfloat162_rn(re[2 * i], re[2 * i + 1]);
-                const float2 af = __bfloat1622float2(a);
-                hr[i] = bf2_bits(a);
-                lr[i] = bf2_bits(__floats2bfloat162_rn(re[2 * i] - af.x, re[2 * i + 1] - af.y));
-                const __nv_bfloat162 b = __floats2bfloat162_rn(im[2 * i], im[2 * i + 1]);
-                const float2 bf = __bfloat1622float2(b);
-                hi_[i] = bf2_bits(b);
-                li[i] = bf2_bits(__floats2bfloat162_rn(im[2 * i] - bf.x, im[2 * i + 1] - bf.y));
-            }
-            unsigned char* rowp = smem + (size_t)s * STAGE + r * 128;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const uint32_t cre = (uint32_t)(2 * h + q), cim = cre + 4;
-                uint4* p0 = (uint4*)(rowp + ((cre ^ sw) << 4));
-                uint4* p1 = (uint4*)(rowp + ((cim ^ sw) << 4));
-                *p0 = make_uint4(hr[4 * q], hr[4 * q + 1], hr[4 * q + 2], hr[4 * q + 3]);
-                *p1 = make_uint4(hi_[4 * q], hi_[4 * q + 1], hi_[4 * q + 2], hi_[4 * q + 3]);
-                *(uint4*)((unsigned char*)p0 + A_BYTES) = make_uint4(lr[4 * q], lr[4 * q + 1], lr[4 * q + 2], lr[4 * q + 3]);
-                *(uint4*)((unsigned char*)p1 + A_BYTES) = make_uint4(li[4 * q], li[4 * q + 1], li[4 * q + 2], li[4 * q + 3]);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&full[s]);
-        }
     }
     __syncthreads();
     const bool okd = mbar_wait(&done, 0);
@@ -603,8 +528,7 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     if (warp < 8 && okd && !*ab) {
         const int q = warp & 3, half = warp >> 2;
         const int lrow = row0 + q * 32 + lane;
-        const bool valid = is_t ? (lrow < ng) : (lrow < p.ma);
-        float* drow = p.D + (((size_t)k * p.splits + split) * p.R + (size_t)tile * TC_BM + q * 32 + lane) * p.Dn;
+        float* drow = p.D + (((size_t)k * p.splits + split) * p.R + lrow) * p.Dn;
 #pragma unroll 1
         for (int c = half * (NT / 2); c < (half + 1) * (NT / 2); c += 8) {
             uint32_t v[8];
@@ -613,7 +537,7 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
                 : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (valid) {
+            if (lrow < p.ma) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
                     if (c + u < p.Dn) drow[c + u] = __uint_as_float(v[u]);
@@ -626,6 +550,242 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     __syncthreads();
     if (warp == 8)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
+}
+
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
+
+// ============================================================================
+// The interstitial rows alone (T[G, n] = sum_G' V~_{G-G'} C[G', n]) with two
+// rings: SA stages of the generated left operand (256 threads write the
+// hi/lo tiles from the pre-split table window by byte permutes) and SB
+// deeper stages of the small TMA-fed right operand, so that the copy
+// latency of the right operand stays hidden behind several K blocks.
+// ============================================================================
+#define TCT_MAXSA 4
+#define TCT_MAXSB 16
+struct TcToepParams {
+    int nk, Dn, kbps, splits, ttiles, wcap, vt_center, SA, SB;
+    const KDev* kd;
+    const uint2* tab;  // pre-split table
+    float* D;          // [nk][splits][ttiles * 128][Dn]
+    int* flag;
+};
+
+template <int NT, bool GW>
+__global__ void __launch_bounds__(TCO_THREADS, 1)
+    k_tc_toep(const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, TcToepParams p) {
+    // GW: gather the table from global memory (L1/L2) instead of a shared window
+    extern __shared__ unsigned char smem_raw[];
+    // aligned by offsetting the shared array itself, so that the compiler keeps
+    // shared-memory (not generic) addressing for every access through smem
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    constexpr int A_BYTES = TC_BM * TC_BK * 2;
+    constexpr int B_BYTES = NT * TC_BK * 2;
+    constexpr uint32_t NCOLS = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
+    __shared__ __align__(8) uint64_t fullA[TCT_MAXSA], emptyA[TCT_MAXSA], fullB[TCT_MAXSB], emptyB[TCT_MAXSB], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    const int SA = p.SA, SB = p.SB;
+    const int k = blockIdx.z, tile = blockIdx.x, split = blockIdx.y;
+    const KDev& K = p.kd[k];
+    const int ng = K.ng;
+    const int row0 = tile * TC_BM;
+    const int nkb = (ng + 31) >> 5;
+    const int kb0 = split * p.kbps;
+    const int nk = min(nkb, kb0 + p.kbps) - kb0;
+    if (nk <= 0 || row0 >= ng) return;  // the reduction skips these pairs
+    unsigned char* ringA = smem;
+    unsigned char* ringB = smem + (size_t)SA * 2 * A_BYTES;
+    int* gl_s = (int*)(ringB + (size_t)SB * 2 * B_BYTES);
+    uint2* win = (uint2*)(gl_s + p.kbps * 32);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < SA; ++s) {
+            mbar_init(&fullA[s], TCO_GEN / 32);
+            mbar_init(&emptyA[s], 1);
+        }
+        for (int s = 0; s < SB; ++s) {
+            mbar_init(&fullB[s], 1);
+            mbar_init(&emptyB[s], 1);
+        }
+        mbar_init(&done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(NCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    const int gp_lo = kb0 * 32, gp_hi = min(ng, (kb0 + nk) * 32);
+    int wlo = 0;
+    if (tid < TCO_GEN) {
+        const int* __restrict__ glin = K.glin;
+        const int g1 = min(row0 + TC_BM, ng) - 1;
+        wlo = glin[row0] - glin[gp_hi - 1] + p.vt_center;
+        if constexpr (!GW) {
+            const int wn = glin[g1] - glin[gp_lo] + p.vt_center - wlo + 1;
+            if (wn > p.wcap) {
+                // the host sizes the slices so that this cannot happen
+                abort_flag = 1;
+                if (tid == 0) atomicOr(p.flag, 8);
+            } else {
+                for (int e = tid; e < wn; e += TCO_GEN) win[e] = p.tab[wlo + e];
+            }
+        }
+        for (int i = tid; i < gp_hi - gp_lo; i += TCO_GEN) gl_s[i] = glin[gp_lo + i];
+    }
+    const uint2* __restrict__ gtab = p.tab + wlo;  // GW: the same offsets into the table
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    volatile int* ab = &abort_flag;
+    if (warp == 8) {
+        if (lane == 0 && *ab) {
+            umma_commit(&done);
+        } else if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                                   ((uint32_t)(TC_BM >> 4) << 24);
+            int issued = 0, consumed = 0;
+            auto loadB = [&](int j) {
+                const int s = j % SB, kx = (kb0 + j) * TC_BK;
+                unsigned char* st = ringB + (size_t)s * 2 * B_BYTES;
+                mbar_expect_tx(&fullB[s], 2 * B_BYTES);
+                tma_load_3d(st, &tmBh, kx, 0, k, &fullB[s]);
+                tma_load_3d(st + B_BYTES, &tmBl, kx, 0, k, &fullB[s]);
+                issued = j + 1;
+            };
+            for (int j = 0; j < min(nk, SB); ++j) loadB(j);
+            for (int j = 0; j < nk; ++j) {
+                const int sa = j % SA, sb = j % SB;
+                if (!mbar_wait_ab(&fullB[sb], (uint32_t)((j / SB) & 1), ab)) break;
+                consumed = j + 1;
+                if (!mbar_wait_ab(&fullA[sa], (uint32_t)((j / SA) & 1), ab)) break;
+                tc_fence_after();
+                const uint32_t ah = smem_u32(ringA + (size_t)sa * 2 * A_BYTES), al = ah + A_BYTES;
+                const uint32_t bh = smem_u32(ringB + (size_t)sb * 2 * B_BYTES), bl = bh + B_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                    const uint32_t o = kk * 32;
+                    umma_bf16(tmem, umma_desc(ah + o), umma_desc(bh + o), idesc, (j > 0 || kk > 0) ? 1u : 0u);
+                    umma_bf16(tmem, umma_desc(ah + o), umma_desc(bl + o), idesc, 1u);
+                    umma_bf16(tmem, umma_desc(al + o), umma_desc(bh + o), idesc, 1u);
+                }
+                umma_commit(&emptyA[sa]);
+                umma_commit(&emptyB[sb]);
+                const int jp = j - 1;
+                if (jp >= 0 && jp + SB < nk) {
+                    if (!mbar_wait_ab(&emptyB[jp % SB], (uint32_t)((jp / SB) & 1), ab)) break;
+                    loadB(jp + SB);
+                }
+            }
+            umma_commit(&done);
+            if (*ab) {
+                atomicOr(p.flag, 8);
+                for (int j = consumed; j < issued; ++j) mbar_wait(&fullB[j % SB], (uint32_t)((j / SB) & 1));
+            }
+        }
+        __syncwarp();
+    } else if (!*ab) {
+        // generators: thread (r, h) writes row r, G' 16h .. 16h+15 of every K block
+        const int r = tid & (TC_BM - 1), h = tid >> 7;
+        const int g = row0 + r;
+        const bool valid = g < ng;
+        const int lb = (valid ? K.glin[g] : 0) + p.vt_center - wlo;
+        const uint32_t sw = (uint32_t)(r & 7);
+        for (int j = 0; j < nk; ++j) {
+            const int sa = j % SA;
+            if (j >= SA && !mbar_wait_ab(&emptyA[sa], (uint32_t)(((j / SA) - 1) & 1), ab)) break;
+            const int gq = (kb0 + j) * 32 + 16 * h;
+            uint2 u[16];
+            if (valid && gq + 16 <= gp_hi) {
+                const int4* g4 = (const int4*)(gl_s + (gq - gp_lo));
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int4 t = g4[q];
+                    if constexpr (GW) {
+                        u[4 * q + 0] = __ldg(gtab + (lb - t.x));
+                        u[4 * q + 1] = __ldg(gtab + (lb - t.y));
+                        u[4 * q + 2] = __ldg(gtab + (lb - t.z));
+                        u[4 * q + 3] = __ldg(gtab + (lb - t.w));
+                    } else {
+                        u[4 * q + 0] = win[lb - t.x];
+                        u[4 * q + 1] = win[lb - t.y];
+                        u[4 * q + 2] = win[lb - t.z];
+                        u[4 * q + 3] = win[lb - t.w];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int gp = gq + i;
+                    if (valid && gp < gp_hi) {
+                        const int x = lb - gl_s[gp - gp_lo];
+                        u[i] = GW ? __ldg(gtab + x) : win[x];
+                    } else {
+                        u[i] = make_uint2(0u, 0u);
+                    }
+                }
+            }
+            unsigned char* rowp = ringA + (size_t)sa * 2 * A_BYTES + r * 128;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const uint2* w = u + 8 * q;
+                const uint32_t cre = (uint32_t)(2 * h + q), cim = cre + 4;
+                uint4* p0 = (uint4*)(rowp + ((cre ^ sw) << 4));
+                uint4* p1 = (uint4*)(rowp + ((cim ^ sw) << 4));
+                *p0 = make_uint4(__byte_perm(w[0].x, w[1].x, 0x5410), __byte_perm(w[2].x, w[3].x, 0x5410),
+                                 __byte_perm(w[4].x, w[5].x, 0x5410), __byte_perm(w[6].x, w[7].x, 0x5410));
+                *p1 = make_uint4(__byte_perm(w[0].y, w[1].y, 0x5410), __byte_perm(w[2].y, w[3].y, 0x5410),
+                                 __byte_perm(w[4].y, w[5].y, 0x5410), __byte_perm(w[6].y, w[7].y, 0x5410));
+                *(uint4*)((unsigned char*)p0 + A_BYTES) =
+                    make_uint4(__byte_perm(w[0].x, w[1].x, 0x7632), __byte_perm(w[2].x, w[3].x, 0x7632),
+                               __byte_perm(w[4].x, w[5].x, 0x7632), __byte_perm(w[6].x, w[7].x, 0x7632));
+                *(uint4*)((unsigned char*)p1 + A_BYTES) =
+                    make_uint4(__byte_perm(w[0].y, w[1].y, 0x7632), __byte_perm(w[2].y, w[3].y, 0x7632),
+                               __byte_perm(w[4].y, w[5].y, 0x7632), __byte_perm(w[6].y, w[7].y, 0x7632));
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&fullA[sa]);
+        }
+    }
+    __syncthreads();
+    const bool okd = mbar_wait(&done, 0);
+    tc_fence_after();
+    if (warp < 8 && okd && !*ab) {
+        const int q = warp & 3, half = warp >> 2;
+        const int lrow = row0 + q * 32 + lane;
+        float* drow = p.D + (((size_t)k * p.splits + split) * ((size_t)p.ttiles * TC_BM) + lrow) * p.Dn;
+#pragma unroll 1
+        for (int c = half * (NT / 2); c < (half + 1) * (NT / 2); c += 8) {
+            uint32_t v[8];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (lrow < ng) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (c + u < p.Dn) drow[c + u] = __uint_as_float(v[u]);
+            }
+        }
+    } else if (tid == 0 && !okd) {
+        atomicOr(p.flag, 8);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
+}
+
+// the pre-split table of the tensor-core form (set-up)
+__global__ void k_tc_split_table(const zd* __restrict__ t, uint2* __restrict__ out, int n) {
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i < n) out[i] = make_uint2(bf16_split_bits(t[i].x), bf16_split_bits(t[i].y));
 }
 
 // Right operand of a step: B^[k][row][K-block layout] from C_G (FP64, the
@@ -674,43 +834,81 @@ __global__ void k_tc_pack_at(const zd* __restrict__ at, int ng, int ma, int Kp, 
     al[row + 32] = l;
 }
 
-// Sum of the K slices in FP64: T rows into K.th (ng x ns), matching rows into
-// K.Q (ma x ns).
-__global__ void k_tc_opred(TcOpParams p) {
+// Sum of the K slices in FP64: interstitial rows into K.th (ng x ns),
+// matching rows into K.Q (ma x ns).
+struct TcRedParams {
+    int ns, ma, Dn, kbps_t, splits_t, kbps_a, splits_a, Rt, Ra;
+    int part;  // 0: all rows, 1: interstitial rows only, 2: matching rows only
+    const KDev* kd;
+    const float* Dt;
+    const float* Da;
+};
+// sum of nsp slices of one output pair, eight loads in flight
+__device__ __forceinline__ void tc_sum_slices(const float* d, size_t stride, int nsp, int c, int ns, double& re,
+                                              double& im) {
+    int s = 0;
+    for (; s + 8 <= nsp; s += 8) {
+        float a[8], b[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            a[u] = d[(size_t)(s + u) * stride + c];
+            b[u] = d[(size_t)(s + u) * stride + ns + c];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            re += (double)a[u];
+            im += (double)b[u];
+        }
+    }
+    for (; s < nsp; ++s) {
+        re += (double)d[(size_t)s * stride + c];
+        im += (double)d[(size_t)s * stride + ns + c];
+    }
+}
+__global__ void k_tc_opred(TcRedParams p) {
     const int k = blockIdx.z;
     const KDev& K = p.kd[k];
     const int ng = K.ng, ns = p.ns;
-    const int nsp = min(p.splits, (((ng + 31) >> 5) + p.kbps - 1) / p.kbps);
+    const int nkb = (ng + 31) >> 5;
+    const int r0 = (p.part == 2) ? ng : 0;
+    const int r1 = (p.part == 1) ? ng : ng + p.ma;
+    const int nrow = r1 - r0;
     const int e = blockIdx.x * 256 + threadIdx.x;
-    const int nrow = ng + p.ma;
     if (e >= nrow * ns) return;
-    const int row = e % nrow, c = e / nrow;
-    const int drow = row < ng ? row : p.ttiles * TC_BM + (row - ng);
+    const int row = r0 + e % nrow, c = e / nrow;
     double re = 0.0, im = 0.0;
-    for (int s = 0; s < nsp; ++s) {
-        const float* d = p.D + (((size_t)k * p.splits + s) * p.R + drow) * p.Dn;
-        re += (double)d[c];
-        im += (double)d[ns + c];
+    if (row < ng) {
+        const int nsp = min(p.splits_t, (nkb + p.kbps_t - 1) / p.kbps_t);
+        tc_sum_slices(p.Dt + ((size_t)k * p.splits_t * p.Rt + row) * p.Dn, (size_t)p.Rt * p.Dn, nsp, c, ns, re, im);
+        K.th[row + (size_t)c * ng] = zmk(re, im);
+    } else {
+        const int r = row - ng;
+        const int nsp = min(p.splits_a, (nkb + p.kbps_a - 1) / p.kbps_a);
+        tc_sum_slices(p.Da + ((size_t)k * p.splits_a * p.Ra + r) * p.Dn, (size_t)p.Ra * p.Dn, nsp, c, ns, re, im);
+        K.Q[r + (size_t)c * p.ma] = zmk(re, im);
     }
-    if (row < ng) K.th[row + (size_t)c * ng] = zmk(re, im);
-    else K.Q[(row - ng) + (size_t)c * p.ma] = zmk(re, im);
 }
 
 // ------------------------------------------------------------ operator plan
 struct TcPlan {
-    int nk = 0, ns = 0, ma = 0, Dn = 0, NT = 0, S = 0, kbps = 0, splits = 0, ttiles = 0, atiles = 0;
-    int wcap = 0, R = 0, Kp = 0, Mp = 0, Rp = 0, maxng = 0, vt_center = 0;
-    size_t smem = 0;
+    int nk = 0, ns = 0, ma = 0, Dn = 0, NT = 0, ttiles = 0, atiles = 0, Kp = 0, Mp = 0, Rp = 0;
+    int maxng = 0, vt_center = 0;
+    // interstitial rows
+    int SA = 0, SB = 0, kbps_t = 0, splits_t = 0, wcap = 0;
+    size_t smem_t = 0;
+    // matching rows
+    int S_a = 0, kbps_a = 0, splits_a = 0;
+    size_t smem_a = 0;
     CUtensorMap tbh, tbl, tah, tal;
     __nv_bfloat16 *bh = nullptr, *bl = nullptr, *ah = nullptr, *al = nullptr;
-    float* D = nullptr;
+    float *Dt = nullptr, *Da = nullptr;
+    uint2* tabs = nullptr;  // the pre-split static table
+    int* tflag = nullptr;   // error flag of the tuning launches
+    float ms_t = 0.f, ms_a = 0.f;  // tuned launch times
+    int ncand = 0;
 };
 
 static const int TCO_NTS[] = {16, 32, 48, 64, 96, 128, 160, 192, 224, 256};
-
-static size_t tco_smem(int NT, int S, int kbps, int wcap) {
-    return 1024 + (size_t)S * (4 * TC_BM * TC_BK + 4 * (size_t)NT * TC_BK) + (size_t)kbps * 128 + (size_t)wcap * 8;
-}
 
 // largest table window over every (k, row tile, K slice of kbps blocks)
 static int tco_max_window(int nk, const int* ng, const int* const* glin, int kbps) {
@@ -745,8 +943,12 @@ static int tc_tmap3(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t 
 }
 
 template <int NT>
-static cudaError_t tco_set_smem(int bytes) {
-    return cudaFuncSetAttribute(k_tc_opfwd<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+static cudaError_t tco_set_smem(int bytes_opfwd, int bytes_toep) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_opfwd<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_opfwd);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_toep<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_toep);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tc_toep<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_toep);
 }
 
 void tc_plan_destroy(TcPlan* tp) {
@@ -755,12 +957,165 @@ void tc_plan_destroy(TcPlan* tp) {
     cudaFree(tp->bl);
     cudaFree(tp->ah);
     cudaFree(tp->al);
-    cudaFree(tp->D);
+    cudaFree(tp->Dt);
+    cudaFree(tp->Da);
+    cudaFree(tp->tabs);
+    cudaFree(tp->tflag);
     delete tp;
 }
 
+// waves x (K blocks per slice + 2 for fill and drain), a small charge per slice
+static int tco_best_splits(int tiles, int nk, int nkb, int nsm, int per_sm) {
+    int best = 1;
+    double bcost = 1e30;
+    for (int sp = 1; sp <= nkb; ++sp) {
+        const int kb = (nkb + sp - 1) / sp;
+        const double waves = std::ceil((double)tiles * nk * sp / ((double)nsm * per_sm));
+        const double cost = waves * (kb + 2) + 0.02 * sp;
+        if (cost < bcost) {
+            bcost = cost;
+            best = sp;
+        }
+    }
+    return best;
+}
+
+struct TcToepCand {
+    int kbps, splits, SA, SB, wn;  // wn = 0: table gathered from global memory
+    size_t smem;
+    float ms;
+};
+struct TcRowsCand {
+    int kbps, splits, S;
+    size_t smem;
+    float ms;
+};
+
+template <int NT>
+static void tco_launch_toep(const TcPlan* tp, const TcToepCand& c, const KDev* kd, int nk, cudaStream_t s) {
+    TcToepParams p{};
+    p.nk = nk;
+    p.Dn = tp->Dn;
+    p.kbps = c.kbps;
+    p.splits = c.splits;
+    p.ttiles = tp->ttiles;
+    p.wcap = c.wn;
+    p.vt_center = tp->vt_center;
+    p.SA = c.SA;
+    p.SB = c.SB;
+    p.kd = kd;
+    p.tab = tp->tabs;
+    p.D = tp->Dt;
+    p.flag = tp->tflag;
+    if (c.wn > 0) k_tc_toep<NT, false><<<dim3(tp->ttiles, c.splits, nk), TCO_THREADS, c.smem, s>>>(tp->tbh, tp->tbl, p);
+    else k_tc_toep<NT, true><<<dim3(tp->ttiles, c.splits, nk), TCO_THREADS, c.smem, s>>>(tp->tbh, tp->tbl, p);
+    // with the sum of its slices, so that many slices pay for their reduction
+    TcRedParams r{};
+    r.ns = tp->ns;
+    r.ma = tp->ma;
+    r.Dn = tp->Dn;
+    r.kbps_t = c.kbps;
+    r.splits_t = c.splits;
+    r.Rt = tp->ttiles * TC_BM;
+    r.part = 1;
+    r.kd = kd;
+    r.Dt = tp->Dt;
+    k_tc_opred<<<dim3((tp->maxng * tp->ns + 255) / 256, 1, nk), 256, 0, s>>>(r);
+}
+template <int NT>
+static void tco_launch_rows(const TcPlan* tp, const TcRowsCand& c, const KDev* kd, int nk, cudaStream_t s) {
+    TcOpParams p{};
+    p.nk = nk;
+    p.ns = tp->ns;
+    p.ma = tp->ma;
+    p.Dn = tp->Dn;
+    p.kbps = c.kbps;
+    p.splits = c.splits;
+    p.atiles = tp->atiles;
+    p.R = tp->Mp;
+    p.S = c.S;
+    p.kd = kd;
+    p.D = tp->Da;
+    p.flag = tp->tflag;
+    k_tc_opfwd<NT><<<dim3(tp->atiles, c.splits, nk), TCO_THREADS, c.smem, s>>>(tp->tbh, tp->tbl, tp->tah, tp->tal, p);
+    TcRedParams r{};
+    r.ns = tp->ns;
+    r.ma = tp->ma;
+    r.Dn = tp->Dn;
+    r.kbps_a = c.kbps;
+    r.splits_a = c.splits;
+    r.Ra = tp->Mp;
+    r.part = 2;
+    r.kd = kd;
+    r.Da = tp->Da;
+    k_tc_opred<<<dim3((tp->ma * tp->ns + 255) / 256, 1, nk), 256, 0, s>>>(r);
+}
+
+template <int NT>
+static int tco_tune_t(TcPlan* tp, std::vector<TcToepCand>& tc, std::vector<TcRowsCand>& ta, const KDev* kd, int nk,
+                      cudaStream_t s) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1;
+    auto time_it = [&](auto&& launch) -> float {
+        launch();
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) launch();
+        cudaEventRecord(e1, s);
+        float ms = 1e30f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ms = 1e30f;
+        return ms;
+    };
+    int bt = 0;
+    for (size_t i = 0; i < tc.size(); ++i) {
+        tc[i].ms = time_it([&] { tco_launch_toep<NT>(tp, tc[i], kd, nk, s); });
+        if (tc[i].ms < tc[bt].ms) bt = (int)i;
+    }
+    int ba = 0;
+    for (size_t i = 0; i < ta.size(); ++i) {
+        ta[i].ms = time_it([&] { tco_launch_rows<NT>(tp, ta[i], kd, nk, s); });
+        if (ta[i].ms < ta[ba].ms) ba = (int)i;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int flag = 0;
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess ||
+        cudaMemcpy(&flag, tp->tflag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || flag)
+        return -1;
+    const TcToepCand& c = tc[bt];
+    tp->kbps_t = c.kbps;
+    tp->splits_t = c.splits;
+    tp->SA = c.SA;
+    tp->SB = c.SB;
+    tp->wcap = c.wn;
+    tp->smem_t = c.smem;
+    tp->ms_t = c.ms / 3;
+    if (!ta.empty()) {
+        const TcRowsCand& r = ta[ba];
+        tp->kbps_a = r.kbps;
+        tp->splits_a = r.splits;
+        tp->S_a = r.S;
+        tp->smem_a = r.smem;
+        tp->ms_a = r.ms / 3;
+    }
+    tp->ncand = (int)(tc.size() + ta.size());
+    return 0;
+}
+
+static int tco_tune(TcPlan* tp, std::vector<TcToepCand>& tc, std::vector<TcRowsCand>& ta, const KDev* kd, int nk,
+                    cudaStream_t s) {
+    switch (tp->NT) {
+#define RTD_TCO(n) \
+    case n: return tco_tune_t<n>(tp, tc, ta, kd, nk, s);
+        RTD_TCO(16) RTD_TCO(32) RTD_TCO(48) RTD_TCO(64) RTD_TCO(96) RTD_TCO(128) RTD_TCO(160) RTD_TCO(192)
+        RTD_TCO(224) RTD_TCO(256)
+#undef RTD_TCO
+    }
+    return -1;
+}
+
 int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const int* const* glin_host,
-                   const zd* const* at_dev, int vt_center, cudaStream_t s, std::string* why) {
+                   const zd* const* at_dev, const zd* vtab, int nvt, int vt_center, const KDev* d_kd,
+                   cudaStream_t s, std::string* why) {
     *out = nullptr;
     if (!get_encode()) {
         *why = "the driver has no tensor-map encoder";
@@ -786,53 +1141,99 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int budget = smax - 512;
     int maxng = 0;
     for (int k = 0; k < nk; ++k) maxng = std::max(maxng, ng[k]);
     tp->maxng = maxng;
     const int nkb = (maxng + 31) / 32;
     tp->ttiles = (maxng + TC_BM - 1) / TC_BM;
     tp->atiles = (ma + TC_BM - 1) / TC_BM;
-    const int tiles = tp->ttiles + tp->atiles;
-    // K slices: fewest block-steps per SM (waves x blocks per slice, plus two for fill and drain)
-    int best = 1;
-    double bcost = 1e30;
-    for (int sp = 1; sp <= nkb; ++sp) {
-        const int kb = (nkb + sp - 1) / sp;
-        const double waves = std::ceil((double)tiles * nk * sp / nsm);
-        const double cost = waves * (kb + 2) + 0.02 * sp;
-        if (cost < bcost) {
-            bcost = cost;
-            best = sp;
+    const int A2 = 4 * TC_BM * TC_BK, B2 = 4 * tp->NT * TC_BK;  // hi + lo bytes of a stage
+    // candidate shapes of the interstitial launch: K slices, generated stages SA,
+    // copied stages SB, all that fit
+    std::vector<TcToepCand> tc_c;
+    {
+        const int s0 = tco_best_splits(tp->ttiles, nk, nkb, nsm, 1);
+        int last_kbps = -1;
+        // K slices: from the cost model's choice, halving the blocks per slice down to
+        // one; at most 8 slice sizes that fit, and partial outputs of at most 4 GB
+        int tried = 0;
+        for (int kbps = (nkb + s0 - 1) / s0; kbps >= 1 && tried < 8; kbps = (kbps == 1 ? 0 : (kbps + 1) / 2)) {
+            if (kbps == last_kbps) break;
+            last_kbps = kbps;
+            const int sp = (nkb + kbps - 1) / kbps;
+            if ((double)nk * sp * tp->ttiles * TC_BM * tp->Dn * 4.0 > 4.0e9) break;
+            const int wn = tco_max_window(nk, ng, glin_host, kbps);
+            bool any = false;
+            for (int SA = 2; SA <= TCT_MAXSA; ++SA)
+                for (int SB : {2, 4, 8, 16}) {
+                    if (SB > TCT_MAXSB) continue;
+                    const size_t need = 1024 + (size_t)SA * A2 + (size_t)SB * B2 + (size_t)kbps * 128 + (size_t)wn * 8;
+                    if ((int)need <= budget) {
+                        tc_c.push_back({kbps, sp, SA, SB, wn, need, 0.f});
+                        any = true;
+                    }
+                }
+            if (any) ++tried;
+        }
+        // table gathered through L1/L2: no window, so any K slice fits
+        last_kbps = -1;
+        for (int kbps = (nkb + s0 - 1) / s0, n = 0; kbps >= 1 && n < 3; kbps = (kbps + 1) / 2, ++n) {
+            if (kbps == last_kbps) break;
+            last_kbps = kbps;
+            const int sp = (nkb + kbps - 1) / kbps;
+            if ((double)nk * sp * tp->ttiles * TC_BM * tp->Dn * 4.0 > 4.0e9) break;
+            for (int SA = 2; SA <= TCT_MAXSA; ++SA)
+                for (int SB : {2, 4, 8}) {
+                    const size_t need = 1024 + (size_t)SA * A2 + (size_t)SB * B2 + (size_t)kbps * 128;
+                    if ((int)need <= budget) tc_c.push_back({kbps, sp, SA, SB, 0, need, 0.f});
+                }
+            if (kbps == 1) break;
         }
     }
-    const int budget = smax - 256;
-    for (int sp = best; sp <= nkb; ++sp) {
-        const int kbps = (nkb + sp - 1) / sp;
-        const int wn = tco_max_window(nk, ng, glin_host, kbps);
-        for (int S = TCO_MAXS; S >= 2 && !tp->S; --S)
-            if ((int)tco_smem(tp->NT, S, kbps, wn) <= budget) {
-                tp->S = S;
-                tp->kbps = kbps;
-                tp->wcap = wn;
-            }
-        if (tp->S) break;
-    }
-    if (!tp->S) {
+    if (tc_c.empty()) {
         delete tp;
         *why = "the interstitial table window of one K block does not fit in shared memory";
         return RTTDDFT_ERR_UNSUPPORTED;
     }
-    tp->splits = (nkb + tp->kbps - 1) / tp->kbps;
-    tp->smem = tco_smem(tp->NT, tp->S, tp->kbps, tp->wcap);
-    tp->R = tiles * TC_BM;
+    // matching rows: K slices and stages
+    std::vector<TcRowsCand> ta_c;
+    if (tp->atiles > 0) {
+        const int s0 = tco_best_splits(tp->atiles, nk, nkb, nsm, 1);
+        int last_kbps = -1;
+        for (int mult = 1; mult <= 8; mult *= 2) {
+            const int sp = std::min(nkb, s0 * mult);
+            const int kbps = (nkb + sp - 1) / sp;
+            if (kbps == last_kbps) continue;
+            last_kbps = kbps;
+            for (int S = 2; S <= TCO_MAXS; ++S) {
+                const size_t need = 1024 + (size_t)S * (A2 + B2) + (size_t)kbps * 128;
+                if ((int)need <= budget) ta_c.push_back({kbps, (nkb + kbps - 1) / kbps, S, need, 0.f});
+            }
+        }
+    }
+    int max_sp_t = 0, max_sp_a = 1;
+    size_t max_sm_t = 0, max_sm_a = 0;
+    for (auto& c : tc_c) {
+        max_sp_t = std::max(max_sp_t, c.splits);
+        max_sm_t = std::max(max_sm_t, c.smem);
+    }
+    for (auto& c : ta_c) {
+        max_sp_a = std::max(max_sp_a, c.splits);
+        max_sm_a = std::max(max_sm_a, c.smem);
+    }
     tp->Kp = nkb * TC_BK;
     tp->Rp = tp->NT;
     tp->Mp = std::max(1, tp->atiles) * TC_BM;
     const size_t nbh = (size_t)nk * tp->Rp * tp->Kp, nah = (size_t)nk * tp->Mp * tp->Kp;
-    const size_t nd = (size_t)nk * tp->splits * tp->R * tp->Dn;
+    const size_t ndt = (size_t)nk * max_sp_t * tp->ttiles * TC_BM * tp->Dn;
+    const size_t nda = (size_t)nk * max_sp_a * tp->Mp * tp->Dn;
     if (cudaMalloc(&tp->bh, nbh * 2) != cudaSuccess || cudaMalloc(&tp->bl, nbh * 2) != cudaSuccess ||
         cudaMalloc(&tp->ah, nah * 2) != cudaSuccess || cudaMalloc(&tp->al, nah * 2) != cudaSuccess ||
-        cudaMalloc(&tp->D, nd * sizeof(float)) != cudaSuccess) {
+        cudaMalloc(&tp->Dt, ndt * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&tp->Da, nda * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&tp->tabs, (size_t)std::max(1, nvt) * sizeof(uint2)) != cudaSuccess ||
+        cudaMalloc(&tp->tflag, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         tc_plan_destroy(tp);
         *why = "out of device memory for the tensor-core operands";
@@ -842,6 +1243,8 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
     cudaMemsetAsync(tp->bl, 0, nbh * 2, s);
     cudaMemsetAsync(tp->ah, 0, nah * 2, s);
     cudaMemsetAsync(tp->al, 0, nah * 2, s);
+    cudaMemsetAsync(tp->tflag, 0, sizeof(int), s);
+    if (nvt > 0) k_tc_split_table<<<(nvt + 255) / 256, 256, 0, s>>>(vtab, tp->tabs, nvt);
     for (int k = 0; k < nk && ma > 0; ++k) {
         const size_t n = (size_t)ma * ng[k];
         k_tc_pack_at<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(at_dev[k], ng[k], ma, tp->Kp, tp->Mp, k, tp->ah,
@@ -852,7 +1255,7 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
     cudaError_t ce = cudaSuccess;
     switch (tp->NT) {
 #define RTD_TCO(n) \
-    case n: ce = tco_set_smem<n>((int)tp->smem); break;
+    case n: ce = tco_set_smem<n>((int)std::max(max_sm_a, (size_t)1024), (int)max_sm_t); break;
         RTD_TCO(16) RTD_TCO(32) RTD_TCO(48) RTD_TCO(64) RTD_TCO(96) RTD_TCO(128) RTD_TCO(160) RTD_TCO(192)
         RTD_TCO(224) RTD_TCO(256)
 #undef RTD_TCO
@@ -862,28 +1265,50 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
         *why = "tensor-core operand set-up failed";
         return RTTDDFT_ERR_CUDA;
     }
+    // autotune: time every candidate on these operands (3 launches after one
+    // warm-up) and keep the fastest
+    const int ti = tco_tune(tp, tc_c, ta_c, d_kd, nk, s);
+    if (ti) {
+        tc_plan_destroy(tp);
+        *why = "tensor-core autotuning failed";
+        return RTTDDFT_ERR_CUDA;
+    }
     *out = tp;
     return RTTDDFT_OK;
 }
 
-static TcOpParams tco_params(const TcPlan* tp, const StepArgs& a) {
+static TcOpParams tco_rows_params(const TcPlan* tp, const StepArgs& a) {
     TcOpParams p{};
     p.nk = a.nk;
     p.ns = tp->ns;
     p.ma = tp->ma;
     p.Dn = tp->Dn;
-    p.kbps = tp->kbps;
-    p.splits = tp->splits;
-    p.ttiles = tp->ttiles;
+    p.kbps = tp->kbps_a;
+    p.splits = tp->splits_a;
     p.atiles = tp->atiles;
-    p.wcap = tp->wcap;
-    p.vt_center = tp->vt_center;
-    p.R = tp->R;
-    p.S = tp->S;
+    p.R = tp->Mp;
+    p.S = tp->S_a;
     p.kofs = a.kofs;
     p.kd = a.kd;
-    p.tab = a.dv_on ? a.vstep32 : a.vtab32;
-    p.D = tp->D;
+    p.D = tp->Da;
+    p.flag = a.flag;
+    return p;
+}
+
+static TcToepParams tco_toep_params(const TcPlan* tp, const StepArgs& a) {
+    TcToepParams p{};
+    p.nk = a.nk;
+    p.Dn = tp->Dn;
+    p.kbps = tp->kbps_t;
+    p.splits = tp->splits_t;
+    p.ttiles = tp->ttiles;
+    p.wcap = tp->wcap;
+    p.vt_center = tp->vt_center;
+    p.SA = tp->SA;
+    p.SB = tp->SB;
+    p.kd = a.kd;
+    p.tab = a.dv_on ? a.vsteps : tp->tabs;
+    p.D = tp->Dt;
     p.flag = a.flag;
     return p;
 }
@@ -894,13 +1319,17 @@ void launch_tc_pack(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
 }
 
 void launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
-    const TcOpParams p = tco_params(tp, a);
-    dim3 g(tp->ttiles + tp->atiles, tp->splits, a.nk);
-    const CUtensorMap& am = tp->ma > 0 ? tp->tah : tp->tbh;
-    const CUtensorMap& al = tp->ma > 0 ? tp->tal : tp->tbl;
+    const TcToepParams pt = tco_toep_params(tp, a);
+    const TcOpParams pa = tco_rows_params(tp, a);
+    dim3 gt(tp->ttiles, tp->splits_t, a.nk);
+    dim3 ga(tp->atiles, tp->splits_a, a.nk);
     switch (tp->NT) {
-#define RTD_TCO(n) \
-    case n: k_tc_opfwd<n><<<g, TCO_THREADS, tp->smem, s>>>(tp->tbh, tp->tbl, am, al, p); break;
+#define RTD_TCO(n)                                                                                    \
+    case n:                                                                                           \
+        if (tp->wcap > 0) k_tc_toep<n, false><<<gt, TCO_THREADS, tp->smem_t, s>>>(tp->tbh, tp->tbl, pt); \
+        else k_tc_toep<n, true><<<gt, TCO_THREADS, tp->smem_t, s>>>(tp->tbh, tp->tbl, pt);             \
+        if (tp->atiles > 0) k_tc_opfwd<n><<<ga, TCO_THREADS, tp->smem_a, s>>>(tp->tbh, tp->tbl, tp->tah, tp->tal, pa); \
+        break;
         RTD_TCO(16) RTD_TCO(32) RTD_TCO(48) RTD_TCO(64) RTD_TCO(96) RTD_TCO(128) RTD_TCO(160) RTD_TCO(192)
         RTD_TCO(224) RTD_TCO(256)
 #undef RTD_TCO
@@ -908,16 +1337,32 @@ void launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
 }
 
 void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
-    const TcOpParams p = tco_params(tp, a);
+    TcRedParams p{};
+    p.ns = tp->ns;
+    p.ma = tp->ma;
+    p.Dn = tp->Dn;
+    p.kbps_t = tp->kbps_t;
+    p.splits_t = tp->splits_t;
+    p.kbps_a = tp->kbps_a;
+    p.splits_a = tp->splits_a;
+    p.Rt = tp->ttiles * TC_BM;
+    p.Ra = tp->Mp;
+    p.part = 0;
+    p.kd = a.kd;
+    p.Dt = tp->Dt;
+    p.Da = tp->Da;
     dim3 g(((tp->maxng + tp->ma) * tp->ns + 255) / 256, 1, a.nk);
     k_tc_opred<<<g, 256, 0, s>>>(p);
 }
 
 void tc_plan_info(const TcPlan* tp, int* v) {
     v[0] = tp->NT;
-    v[1] = tp->S;
-    v[2] = tp->kbps;
-    v[3] = tp->splits;
+    v[1] = tp->SA * 100 + tp->SB;
+    v[2] = tp->kbps_t;
+    v[3] = tp->splits_t;
     v[4] = tp->wcap;
-    v[5] = (int)tp->smem;
+    v[5] = (int)tp->smem_t;
+    v[6] = tp->ncand;
+    v[7] = (int)(tp->ms_t * 1e6f);  // ns
+    v[8] = (int)(tp->ms_a * 1e6f);
 }

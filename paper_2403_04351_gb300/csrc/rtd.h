@@ -120,6 +120,8 @@ struct StepArgs {
     const zd* dvtab;     // dV~ (or null)
     zd* vstep;           // per-step combined table V~ + s dV~
     zf* vstep32;
+    const uint2* vtabs;  // V~ split for the tensor cores: (Re hi | Re lo << 16, Im hi | Im lo << 16)
+    uint2* vsteps;       // the same for the per-step table
     const double* a;     // call samples [cstep][3]
     const double* dvs;   // call dv scales (or null)
     DevState* st;
@@ -214,9 +216,12 @@ void launch_adj_jterm(const StepArgs& a, zd* lam, const zd* theta, const double*
 // ---- tensor-core split-BF16 operator (k_tc.cu)
 struct TcPlan;
 int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const int* const* glin_host,
-                   const zd* const* at_dev, int vt_center, cudaStream_t s, std::string* why);
+                   const zd* const* at_dev, const zd* vtab, int nvt, int vt_center, const KDev* d_kd,
+                   cudaStream_t s, std::string* why);
 void tc_plan_destroy(TcPlan* tp);
-void tc_plan_info(const TcPlan* tp, int* v);  // NT, stages, K blocks per slice, slices, window, smem
+// NT, 100 x generated stages + copied stages, K blocks per slice, slices, window, smem of the
+// interstitial launch, candidates tuned, tuned interstitial and matching-row times (ns)
+void tc_plan_info(const TcPlan* tp, int* v);
 void launch_tc_pack(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
 void launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
 void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s);

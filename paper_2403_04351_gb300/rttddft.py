@@ -64,7 +64,8 @@ class rttddft_info(ctypes.Structure):
                 ("dt_cr0", ctypes.c_double), ("kernel_launches_per_step", ctypes.c_int),
                 ("precision", ctypes.c_int), ("tc_tile_n", ctypes.c_int), ("tc_stages", ctypes.c_int),
                 ("tc_kblocks", ctypes.c_int), ("tc_slices", ctypes.c_int), ("tc_window", ctypes.c_int),
-                ("tc_smem", ctypes.c_int)]
+                ("tc_smem", ctypes.c_int), ("tc_candidates", ctypes.c_int),
+                ("tc_interstitial_ns", ctypes.c_int), ("tc_matching_ns", ctypes.c_int)]
 
 
 class rttddft_trace(ctypes.Structure):
@@ -370,7 +371,9 @@ class Context:
                     cheb_terms=i.cheb_terms, dt_cr0=i.dt_cr0,
                     kernel_launches_per_step=i.kernel_launches_per_step, precision=i.precision,
                     tc=dict(tile_n=i.tc_tile_n, stages=i.tc_stages, kblocks=i.tc_kblocks,
-                            slices=i.tc_slices, window=i.tc_window, smem=i.tc_smem))
+                            slices=i.tc_slices, window=i.tc_window, smem=i.tc_smem,
+                            candidates=i.tc_candidates, interstitial_ns=i.tc_interstitial_ns,
+                            matching_ns=i.tc_matching_ns))
 
     def set_dv(self, dv):
         self._dh = _cat_f(dv["dh"])

@@ -305,12 +305,33 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
 
     # the plain FP64 GPU step, for the ratio the target is stated against
-    fp64 = None
-    if args.precision != "fp64" and args.fp64_steps > 0:
-        c64, d64, _, _ = timed_form("fp64", args.fp64_steps, 3)
-        c64.close()
-        fp64 = {"value": n_states * args.fp64_steps / d64, "ms_per_step": d64 / args.fp64_steps * 1e3,
-                "steps": args.fp64_steps}
+    # the other precision forms over the same samples (same warm-up), for the
+    # throughput of each and its error per observable against the plain FP64 form
+    forms = {args.precision: {"value": value, "ms_per_step": dev_max / K * 1e3, "steps": K}}
+    form_obs = {args.precision: obs}
+    if args.fp64_steps > 0:
+        for prec in ("fp64", "fp32", "bf16x3"):
+            if prec == args.precision:
+                continue
+            c2, d2, _, o2 = timed_form(prec, args.fp64_steps, W)
+            c2.close()
+            forms[prec] = {"value": n_states * args.fp64_steps / d2, "ms_per_step": d2 / args.fp64_steps * 1e3,
+                           "steps": args.fp64_steps}
+            form_obs[prec] = o2
+    if "fp64" in form_obs:
+        ref = form_obs["fp64"]
+        for prec, o in form_obs.items():
+            n = min(len(o["t"]), len(ref["t"]))
+            if n == 0:
+                continue
+
+            def relerr(key):
+                a_, b_ = np.asarray(o[key][:n]), np.asarray(ref[key][:n])
+                return float(np.max(np.abs(a_ - b_)) / max(float(np.max(np.abs(b_))), 1e-300))
+            forms[prec]["error_vs_fp64"] = {"dmu": relerr("dmu"), "j": relerr("j"), "energy": relerr("energy"),
+                                            "j_full": relerr("j_full"),
+                                            "norm_dev_max": float(np.max(o["norm_dev"][:n])), "steps": n}
+    fp64 = forms.get("fp64") if args.precision != "fp64" else None
 
     # roofline of the dominant kernel slot (and of the tensor-core kernel, if any)
     dom = max(tr.items(), key=lambda kv: kv[1][0])[0] if tr else None
@@ -341,6 +362,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline_tc": roof_tc,
         "kernel_share": share,
         "fp64": fp64,
+        "forms": forms,
         "wall_s": wall,
         "observables_last": {"dmu": obs["dmu"][-1].tolist() if len(obs["t"]) else None,
                              "norm_dev_max": float(np.max(obs["norm_dev"])) if len(obs["t"]) else None},
@@ -406,7 +428,7 @@ def main():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", choices=["fp32", "fp64", "bf16x3"], default="fp32")
     p.add_argument("--workload", default="h2_6000")
-    p.add_argument("--fp64-steps", type=int, default=50)
+    p.add_argument("--fp64-steps", type=int, default=50, help="steps timed for each other precision form")
     p.add_argument("--trace-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--ref-steps", type=int, default=40)

@@ -226,6 +226,7 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.part_t = ctx->d_part_t;
     a.flag = ctx->d_flag;
     a.coop_grid = ctx->coop_grid;
+    a.tcback = (ctx->opt.precision == RTTDDFT_PREC_BF16X3 && tc_has_back(ctx->tc)) ? 1 : 0;
     return a;
 }
 
@@ -737,6 +738,8 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             K.Q = dalloc<zd>(ctx, (size_t)std::max(at.ma, 1) * ns);
             K.Z = dalloc<zd>(ctx, (size_t)std::max(at.ma, 1) * 2 * ns);
             K.th = (o->precision == RTTDDFT_PREC_BF16X3) ? dalloc<zd>(ctx, (size_t)K.ng * ns) : nullptr;
+            K.tb = (o->precision == RTTDDFT_PREC_BF16X3 && at.ma > 0) ? dalloc<zd>(ctx, (size_t)K.ng * 2 * ns)
+                                                                       : nullptr;
             K.gram = dalloc<zd>(ctx, 2 * (size_t)ns * ns);
             K.evec = dalloc<zd>(ctx, nn);
             K.eval = dalloc<double>(ctx, naux);
@@ -1944,6 +1947,7 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         a.kd = (const KDev*)(base + o_kd);
         if (a.prec == 2) a.prec = 1;  // the static scratch holds the FP32-form operands only
         a.vsteps = nullptr;
+        a.tcback = 0;
         a.nk = 1;
         a.st = (DevState*)(base + o_st);
         a.part_jmt = (double*)(base + o_jmt);

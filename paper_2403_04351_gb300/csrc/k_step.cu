@@ -662,9 +662,14 @@ __global__ void __launch_bounds__(BT) k_back(StepArgs a, int n0) {
                 for (int sg = 0; sg < nsg; ++sg)
                     th = zadd(th, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + c) * a.maxng + g]);
             }
-            for (int sg = a.nseg; sg < a.nseg + nas; ++sg) {
-                th = zadd(th, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + c) * a.maxng + g]);
-                ts = zadd(ts, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + NT + c) * a.maxng + g]);
+            if (a.tcback) {
+                th = zadd(th, K.tb[g + (size_t)(n0 + c) * ng]);
+                ts = K.tb[g + (size_t)(ns + n0 + c) * ng];
+            } else {
+                for (int sg = a.nseg; sg < a.nseg + nas; ++sg) {
+                    th = zadd(th, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + c) * a.maxng + g]);
+                    ts = zadd(ts, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + NT + c) * a.maxng + g]);
+                }
             }
             const zd x = X[g + (size_t)(n0 + c) * nb];
             const zd hv = zadd(th, zscale(x, dg));
@@ -1242,7 +1247,8 @@ static void back_launch(const StepArgs& a, int maxng, cudaStream_t s, TraceHook*
     // in the tensor-core form the interstitial slots are done already: only
     // the back-projection slots run here
     const int slot0 = (a.prec == 2) ? a.nseg : 0;
-    dim3 gt((maxng + BT - 1) / BT, a.nslot - slot0, a.nk);
+    // with the back-projection on the tensor cores too, no slot kernel runs
+    dim3 gt((maxng + BT - 1) / BT, a.tcback ? 0 : a.nslot - slot0, a.nk);
     dim3 gb((maxng + BT - 1) / BT, 1, a.nk);
     for (int n0 = 0; n0 < a.ns; n0 += NT) {
         if (gt.y > 0) {
@@ -1305,6 +1311,11 @@ void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, 
             else k_local<zd, 4><<<g, 32, 0, s>>>(a);
         }
         mark(tr, "local_mt", s);
+    }
+    if (a.tcback) {
+        // A^H [hQ | oQ] on the tensor cores
+        launch_tc_back(p.tc, a, s);
+        mark(tr, "tc_backprojection", s);
     }
     if (f32) {
         if (a.ns <= 2) back_launch<zf, zf, zf, 2>(a, p.maxng, s, tr);
@@ -1381,7 +1392,8 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
     launch_operator_pass(a, p, s, tr);
     {
         const int ntb = a.ns <= 2 ? 2 : (a.ns <= 4 ? 4 : 8);
-        nl += (a.prec == 2 ? 3 : 2) + (a.lrows > 0 ? 1 : 0) + 2 * ((a.ns + ntb - 1) / ntb);
+        const int chunks = (a.ns + ntb - 1) / ntb;
+        nl += (a.prec == 2 ? 3 : 2) + (a.lrows > 0 ? 1 : 0) + (a.tcback ? 3 + chunks : 2 * chunks);
     }
     // theta~ = CC^H (S C): split-K partials, finished per row in k_post
     launch_gemm_cn(p.gd_proj, a.nk, a.naux, p.maxnb, a.ns, p.kc_proj, p.part, 0, f32, nullptr, s);

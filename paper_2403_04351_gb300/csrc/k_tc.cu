@@ -387,9 +387,9 @@ int tc_zgemm(int opA, int M, int N, int K, const zd* A, int lda, const zd* X, in
 }
 
 // ============================================================================
-// Matching-coefficient products of the operator apply on the tensor cores
-// (the first factor of Eq. v_MT), in the split-BF16 form:
-//   Q[r, n] = sum_G' A[r, G'] C[G', n]
+// TMA-fed split-BF16 products of the operator apply on the tensor cores:
+//   Q[r, n] = sum_G' A[r, G'] C[G', n]          (first factor of Eq. v_MT)
+//   Y[G, c] = sum_r conj(A[r, G]) Z[r, c]        (back-projection A^H [hQ | oQ])
 // K is cut into blocks of 32 G' (64 reals: 32 Re then 32 Im); the left
 // operand of a block is [Re | Im] of 32 entries per row, the right one
 // holds, per column n, [Re C | -Im C] (real output rows) and [Im C | Re C]
@@ -425,6 +425,8 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
 
 struct TcOpParams {
     int nk, ns, ma, Dn, kbps, splits, atiles, R, S;
+    int nkb_fixed;  // K blocks of every k-point (0: ceil(N_G(k) / 32))
+    int rows_ng;    // valid output rows: N_G(k) (1) or ma (0)
     int kofs;  // k-point of blockIdx.z = 0 in the matching-row operand (single-k calls)
     const KDev* kd;
     float* D;  // [nk][splits][R][Dn]
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     const KDev& K = p.kd[k];
     const int ng = K.ng;
     const int row0 = tile * TC_BM;
-    const int nkb = (ng + 31) >> 5;
+    const int nkb = p.nkb_fixed > 0 ? p.nkb_fixed : (ng + 31) >> 5;
     const int kb0 = split * p.kbps;
     const int nk = min(nkb, kb0 + p.kbps) - kb0;
     if (nk <= 0) return;  // the reduction skips these slices
@@ -537,7 +539,7 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
                 : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (lrow < p.ma) {
+            if (lrow < (p.rows_ng ? ng : p.ma)) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
                     if (c + u < p.Dn) drow[c + u] = __uint_as_float(v[u]);
@@ -834,14 +836,63 @@ __global__ void k_tc_pack_at(const zd* __restrict__ at, int ng, int ma, int Kp, 
     al[row + 32] = l;
 }
 
+// Left operand of the back-projection (set-up): A^[k][G][K-block layout over
+// the matching rows r], the entry A^H[G, r] = AT[G + r ng].
+__global__ void k_tc_pack_atb(const zd* __restrict__ at, int ng, int ma, int Kp, int Mp, int k,
+                              __nv_bfloat16* __restrict__ ah, __nv_bfloat16* __restrict__ al) {
+    const size_t e = (size_t)blockIdx.x * 256 + threadIdx.x;
+    if (e >= (size_t)ma * ng) return;
+    const int g = (int)(e % ng), r = (int)(e / ng);
+    const zd a = at[g + (size_t)r * ng];
+    const size_t row = ((size_t)k * Mp + g) * Kp + (size_t)(r >> 5) * 64 + (r & 31);
+    __nv_bfloat16 h, l;
+    split_bf16(a.x, h, l);
+    ah[row] = h;
+    al[row] = l;
+    split_bf16(a.y, h, l);
+    ah[row + 32] = h;
+    al[row + 32] = l;
+}
+
+// Right operand of the back-projection (per step) from Z = [hQ | oQ]
+// (ma x 2 ns, FP64): rows c < 2 ns hold [Re Z | -Im Z], rows 2 ns + c hold
+// [Im Z | Re Z] over the matching rows.
+__global__ void k_tc_pack_z(const KDev* __restrict__ kd, int ns, int ma, int Kp, int Rp,
+                            __nv_bfloat16* __restrict__ bh, __nv_bfloat16* __restrict__ bl) {
+    const int k = blockIdx.z;
+    const KDev& K = kd[k];
+    const int nc = 2 * ns;
+    const int e = blockIdx.x * 256 + threadIdx.x;  // (c, r) pair
+    if (e >= nc * ma) return;
+    const int c = e / ma, r = e % ma;
+    const zd z = K.Z[r + (size_t)c * ma];
+    const int kb = r >> 5, o = r & 31;
+    const size_t re_row = ((size_t)k * Rp + c) * Kp + (size_t)kb * 64;
+    const size_t im_row = ((size_t)k * Rp + nc + c) * Kp + (size_t)kb * 64;
+    __nv_bfloat16 h, l;
+    split_bf16(z.x, h, l);
+    bh[re_row + o] = h;
+    bl[re_row + o] = l;
+    bh[im_row + 32 + o] = h;
+    bl[im_row + 32 + o] = l;
+    split_bf16(z.y, h, l);
+    bh[im_row + o] = h;
+    bl[im_row + o] = l;
+    split_bf16(-z.y, h, l);
+    bh[re_row + 32 + o] = h;
+    bl[re_row + 32 + o] = l;
+}
+
 // Sum of the K slices in FP64: interstitial rows into K.th (ng x ns),
 // matching rows into K.Q (ma x ns).
 struct TcRedParams {
     int ns, ma, Dn, kbps_t, splits_t, kbps_a, splits_a, Rt, Ra;
-    int part;  // 0: all rows, 1: interstitial rows only, 2: matching rows only
+    int part;  // 0: interstitial and matching rows, 1: interstitial only, 2: matching only, 3: back-projection
+    int Dnb, kbps_b, splits_b, nkb_b, Rb;
     const KDev* kd;
     const float* Dt;
     const float* Da;
+    const float* Db;
 };
 // sum of nsp slices of one output pair, eight loads in flight
 __device__ __forceinline__ void tc_sum_slices(const float* d, size_t stride, int nsp, int c, int ns, double& re,
@@ -870,6 +921,18 @@ __global__ void k_tc_opred(TcRedParams p) {
     const KDev& K = p.kd[k];
     const int ng = K.ng, ns = p.ns;
     const int nkb = (ng + 31) >> 5;
+    if (p.part == 3) {
+        // back-projection: K.tb[g + c ng] for c < 2 ns (H part, then S part)
+        const int nc = 2 * ns;
+        const int e = blockIdx.x * 256 + threadIdx.x;
+        if (e >= ng * nc) return;
+        const int g = e % ng, c = e / ng;
+        const int nsp = min(p.splits_b, (p.nkb_b + p.kbps_b - 1) / p.kbps_b);
+        double re = 0.0, im = 0.0;
+        tc_sum_slices(p.Db + ((size_t)k * p.splits_b * p.Rb + g) * p.Dnb, (size_t)p.Rb * p.Dnb, nsp, c, nc, re, im);
+        K.tb[g + (size_t)c * ng] = zmk(re, im);
+        return;
+    }
     const int r0 = (p.part == 2) ? ng : 0;
     const int r1 = (p.part == 1) ? ng : ng + p.ma;
     const int nrow = r1 - r0;
@@ -906,6 +969,13 @@ struct TcPlan {
     int* tflag = nullptr;   // error flag of the tuning launches
     float ms_t = 0.f, ms_a = 0.f;  // tuned launch times
     int ncand = 0;
+    // back-projection Y_G = A^H [hQ | oQ]: rows G, K over the matching rows
+    int NTb = 0, Dnb = 0, nkb_b = 0, Kpb = 0, Rpb = 0, S_b = 0, kbps_b = 0, splits_b = 0;
+    size_t smem_b = 0;
+    float ms_b = 0.f;
+    CUtensorMap tzh, tzl, tabh, tabl;
+    __nv_bfloat16 *zh = nullptr, *zl = nullptr, *abh = nullptr, *abl = nullptr;
+    float* Db = nullptr;
 };
 
 static const int TCO_NTS[] = {16, 32, 48, 64, 96, 128, 160, 192, 224, 256};
@@ -961,6 +1031,11 @@ void tc_plan_destroy(TcPlan* tp) {
     cudaFree(tp->Da);
     cudaFree(tp->tabs);
     cudaFree(tp->tflag);
+    cudaFree(tp->zh);
+    cudaFree(tp->zl);
+    cudaFree(tp->abh);
+    cudaFree(tp->abl);
+    cudaFree(tp->Db);
     delete tp;
 }
 
@@ -1049,6 +1124,82 @@ static void tco_launch_rows(const TcPlan* tp, const TcRowsCand& c, const KDev* k
     r.kd = kd;
     r.Da = tp->Da;
     k_tc_opred<<<dim3((tp->ma * tp->ns + 255) / 256, 1, nk), 256, 0, s>>>(r);
+}
+
+template <int NT>
+static void tco_launch_back(const TcPlan* tp, const TcRowsCand& c, const KDev* kd, int nk, cudaStream_t s,
+                            int kofs = 0) {
+    TcOpParams p{};
+    p.kofs = kofs;
+    p.nk = nk;
+    p.ns = tp->ns;
+    p.ma = tp->ma;
+    p.Dn = tp->Dnb;
+    p.kbps = c.kbps;
+    p.splits = c.splits;
+    p.atiles = tp->ttiles;
+    p.R = tp->ttiles * TC_BM;
+    p.S = c.S;
+    p.nkb_fixed = tp->nkb_b;
+    p.rows_ng = 1;
+    p.kd = kd;
+    p.D = tp->Db;
+    p.flag = tp->tflag;
+    k_tc_opfwd<NT><<<dim3(tp->ttiles, c.splits, nk), TCO_THREADS, c.smem, s>>>(tp->tzh, tp->tzl, tp->tabh, tp->tabl, p);
+    TcRedParams r{};
+    r.ns = tp->ns;
+    r.ma = tp->ma;
+    r.part = 3;
+    r.Dnb = tp->Dnb;
+    r.kbps_b = c.kbps;
+    r.splits_b = c.splits;
+    r.nkb_b = tp->nkb_b;
+    r.Rb = tp->ttiles * TC_BM;
+    r.kd = kd;
+    r.Db = tp->Db;
+    k_tc_opred<<<dim3((tp->maxng * 2 * tp->ns + 255) / 256, 1, nk), 256, 0, s>>>(r);
+}
+
+static void tco_launch_back_any(const TcPlan* tp, const TcRowsCand& c, const KDev* kd, int nk, cudaStream_t s,
+                                int kofs = 0) {
+    switch (tp->NTb) {
+#define RTD_TCO(n) \
+    case n: tco_launch_back<n>(tp, c, kd, nk, s, kofs); break;
+        RTD_TCO(16) RTD_TCO(32) RTD_TCO(48) RTD_TCO(64) RTD_TCO(96) RTD_TCO(128) RTD_TCO(160) RTD_TCO(192)
+        RTD_TCO(224) RTD_TCO(256)
+#undef RTD_TCO
+    }
+}
+
+// time the back-projection candidates and keep the fastest
+static int tco_tune_back(TcPlan* tp, std::vector<TcRowsCand>& tb, const KDev* kd, int nk, cudaStream_t s) {
+    if (tb.empty()) return 0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1;
+    int best = 0;
+    for (size_t i = 0; i < tb.size(); ++i) {
+        tco_launch_back_any(tp, tb[i], kd, nk, s);
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) tco_launch_back_any(tp, tb[i], kd, nk, s);
+        cudaEventRecord(e1, s);
+        float ms = 1e30f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ms = 1e30f;
+        tb[i].ms = ms;
+        if (ms < tb[best].ms) best = (int)i;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int flag = 0;
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess ||
+        cudaMemcpy(&flag, tp->tflag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || flag)
+        return -1;
+    tp->S_b = tb[best].S;
+    tp->kbps_b = tb[best].kbps;
+    tp->splits_b = tb[best].splits;
+    tp->smem_b = tb[best].smem;
+    tp->ms_b = tb[best].ms / 3;
+    tp->ncand += (int)tb.size();
+    return 0;
 }
 
 template <int NT>
@@ -1252,6 +1403,72 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
     }
     int e = tc_tmap3(&tp->tbh, tp->bh, tp->Kp, tp->Rp, nk, tp->NT) | tc_tmap3(&tp->tbl, tp->bl, tp->Kp, tp->Rp, nk, tp->NT) |
             tc_tmap3(&tp->tah, tp->ah, tp->Kp, tp->Mp, nk, TC_BM) | tc_tmap3(&tp->tal, tp->al, tp->Kp, tp->Mp, nk, TC_BM);
+    // back-projection Y_G += A^H [hQ | oQ] (4 ns real output columns, K = matching rows)
+    std::vector<TcRowsCand> tb_c;
+    if (ma > 0 && 4 * ns <= 256) {
+        tp->Dnb = 4 * ns;
+        for (int nt : TCO_NTS)
+            if (nt >= tp->Dnb) {
+                tp->NTb = nt;
+                break;
+            }
+        tp->nkb_b = (ma + 31) / 32;
+        tp->Kpb = tp->nkb_b * TC_BK;
+        tp->Rpb = tp->NTb;
+        const int Bb2 = 4 * tp->NTb * TC_BK;
+        const int s0 = tco_best_splits(tp->ttiles, nk, tp->nkb_b, nsm, 1);
+        int last_kbps = -1;
+        for (int mult = 1; mult <= 8; mult *= 2) {
+            const int sp = std::min(tp->nkb_b, s0 * mult);
+            const int kbps = (tp->nkb_b + sp - 1) / sp;
+            if (kbps == last_kbps) continue;
+            last_kbps = kbps;
+            const int spl = (tp->nkb_b + kbps - 1) / kbps;
+            if ((double)nk * spl * tp->ttiles * TC_BM * tp->Dnb * 4.0 > 4.0e9) break;
+            for (int S = 2; S <= TCO_MAXS; ++S) {
+                const size_t need = 1024 + (size_t)S * (A2 + Bb2);
+                if ((int)need <= budget) tb_c.push_back({kbps, spl, S, need, 0.f});
+            }
+        }
+        int max_sp_b = 1;
+        size_t max_sm_b = 1024;
+        for (auto& c : tb_c) {
+            max_sp_b = std::max(max_sp_b, c.splits);
+            max_sm_b = std::max(max_sm_b, c.smem);
+        }
+        const size_t nzb = (size_t)nk * tp->Rpb * tp->Kpb, nab = (size_t)nk * tp->ttiles * TC_BM * tp->Kpb;
+        const size_t ndb = (size_t)nk * max_sp_b * tp->ttiles * TC_BM * tp->Dnb;
+        if (tb_c.empty() || cudaMalloc(&tp->zh, nzb * 2) != cudaSuccess || cudaMalloc(&tp->zl, nzb * 2) != cudaSuccess ||
+            cudaMalloc(&tp->abh, nab * 2) != cudaSuccess || cudaMalloc(&tp->abl, nab * 2) != cudaSuccess ||
+            cudaMalloc(&tp->Db, ndb * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            tc_plan_destroy(tp);
+            *why = "out of device memory for the back-projection operands";
+            return RTTDDFT_ERR_OOM;
+        }
+        cudaMemsetAsync(tp->zh, 0, nzb * 2, s);
+        cudaMemsetAsync(tp->zl, 0, nzb * 2, s);
+        cudaMemsetAsync(tp->abh, 0, nab * 2, s);
+        cudaMemsetAsync(tp->abl, 0, nab * 2, s);
+        for (int k = 0; k < nk; ++k) {
+            const size_t n = (size_t)ma * ng[k];
+            k_tc_pack_atb<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(at_dev[k], ng[k], ma, tp->Kpb, tp->ttiles * TC_BM,
+                                                                       k, tp->abh, tp->abl);
+        }
+        e |= tc_tmap3(&tp->tzh, tp->zh, tp->Kpb, tp->Rpb, nk, tp->NTb) |
+             tc_tmap3(&tp->tzl, tp->zl, tp->Kpb, tp->Rpb, nk, tp->NTb) |
+             tc_tmap3(&tp->tabh, tp->abh, tp->Kpb, (uint64_t)tp->ttiles * TC_BM, nk, TC_BM) |
+             tc_tmap3(&tp->tabl, tp->abl, tp->Kpb, (uint64_t)tp->ttiles * TC_BM, nk, TC_BM);
+        cudaError_t cb = cudaSuccess;
+        switch (tp->NTb) {
+#define RTD_TCO(n) \
+    case n: cb = cudaFuncSetAttribute(k_tc_opfwd<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(max_sm_b, std::max(max_sm_a, (size_t)1024))); break;
+            RTD_TCO(16) RTD_TCO(32) RTD_TCO(48) RTD_TCO(64) RTD_TCO(96) RTD_TCO(128) RTD_TCO(160) RTD_TCO(192)
+            RTD_TCO(224) RTD_TCO(256)
+#undef RTD_TCO
+        }
+        if (cb != cudaSuccess) e |= 1;
+    }
     cudaError_t ce = cudaSuccess;
     switch (tp->NT) {
 #define RTD_TCO(n) \
@@ -1267,7 +1484,8 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
     }
     // autotune: time every candidate on these operands (3 launches after one
     // warm-up) and keep the fastest
-    const int ti = tco_tune(tp, tc_c, ta_c, d_kd, nk, s);
+    int ti = tco_tune(tp, tc_c, ta_c, d_kd, nk, s);
+    if (!ti) ti = tco_tune_back(tp, tb_c, d_kd, nk, s);
     if (ti) {
         tc_plan_destroy(tp);
         *why = "tensor-core autotuning failed";
@@ -1334,6 +1552,15 @@ void launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
         RTD_TCO(224) RTD_TCO(256)
 #undef RTD_TCO
     }
+}
+
+bool tc_has_back(const TcPlan* tp) { return tp && tp->NTb > 0; }
+
+void launch_tc_back(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
+    dim3 gz((2 * tp->ns * tp->ma + 255) / 256, 1, a.nk);
+    k_tc_pack_z<<<gz, 256, 0, s>>>(a.kd, tp->ns, tp->ma, tp->Kpb, tp->Rpb, tp->zh, tp->zl);
+    TcRowsCand c{tp->kbps_b, tp->splits_b, tp->S_b, tp->smem_b, 0.f};
+    tco_launch_back_any(tp, c, a.kd, a.nk, s, a.kofs);  // single-k calls: left operand of k-point kofs
 }
 
 void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {

@@ -73,6 +73,7 @@ struct KDev {
     zd* Q;        // ma x ns
     zd* Z;        // ma x 2ns
     zd* th;       // ng x ns  interstitial convolution V~ * C_G (tensor-core form)
+    zd* tb;       // ng x 2ns back-projection A^H [hQ | oQ] (tensor-core form)
     zd* gram;     // ns x ns x 2   theta^H theta~ and theta~^H theta~
     zd* evec;     // naux x naux (EIG form)
     double* eval; // naux
@@ -140,6 +141,7 @@ struct StepArgs {
     int* flag;                // device error flags (bit 0 Jacobi, 1 bounds, 2 barrier)
     int coop_grid;            // blocks of the cooperative Chebyshev launch (0: per-term launches)
     int kofs;                 // k-point of kd[0] (single-k operator calls), 0 in the step
+    int tcback;               // the back-projection runs on the tensor cores (split-BF16 form)
 };
 #define POST_STRIDE 36        // part_post row: residual, J_sub (3), then theta^H theta~ (ns <= 4)
 
@@ -225,6 +227,8 @@ void tc_plan_info(const TcPlan* tp, int* v);
 void launch_tc_pack(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
 void launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
 void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
+bool tc_has_back(const TcPlan* tp);  // the back-projection runs on the tensor cores (4 N_s <= 256)
+void launch_tc_back(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
 // ---- tensor-core split-BF16 complex GEMM (k_tc.cu); returns an RTTDDFT_* code
 int tc_zgemm(int opA, int M, int N, int K, const zd* A, int lda, const zd* X, int ldx, zd* C, int ldc,
              int beta_add, cudaStream_t s);

@@ -227,6 +227,8 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.flag = ctx->d_flag;
     a.coop_grid = ctx->coop_grid;
     a.tcback = (ctx->opt.precision == RTTDDFT_PREC_BF16X3 && tc_has_back(ctx->tc)) ? 1 : 0;
+    a.at_n = ctx->at.n;
+    a.at_maxm = ctx->maxm;
     return a;
 }
 

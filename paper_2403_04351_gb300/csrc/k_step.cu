@@ -518,6 +518,109 @@ __global__ void __launch_bounds__(32) k_local(StepArgs a) {
     }
 }
 
+// The muffin-tin products for many states (FP32 forms, N_s > 4): one block of
+// four warps per (atom, chunk of its rows, k); X = [Q_a; C_lo,a] (m x N_s) is
+// staged once in shared memory as FP32, lanes own columns (CPL per lane) and
+// a warp walks one local row at a time, reading the row of h, o, p (FP32
+// copies, broadcast) once for all columns.  Outputs as k_local.
+#define LOCW_ROWCHUNKS 4
+template <int CPL>
+__global__ void __launch_bounds__(128) k_local_wide(StepArgs a) {
+    extern __shared__ zf xs[];  // [m][ns]
+    const int k = blockIdx.z;
+    const KDev& K = a.kd[k];
+    const AtomTab& at = *a.at;
+    const int al = blockIdx.x / LOCW_ROWCHUNKS, chunk = blockIdx.x % LOCW_ROWCHUNKS;
+    if (al >= at.n) return;
+    const int m = at.m[al], na = at.na[al];
+    const int ns = a.ns, nb = K.nb, ma = at.ma, ng = K.ng;
+    const int aoff = at.aoff[al], lo0 = ng + at.looff[al];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < m * ns; e += blockDim.x) {
+        const int j = e / ns, c = e % ns;
+        const zd x = (j < na) ? K.Q[aoff + j + (size_t)c * ma] : K.C[lo0 + (j - na) + (size_t)c * nb];
+        xs[e] = tof(x);
+    }
+    __syncthreads();
+    const DevState* st = a.st;
+    const float fx = (float)(st->cur_a[0] * a.inv_c), fy = (float)(st->cur_a[1] * a.inv_c),
+                fz = (float)(st->cur_a[2] * a.inv_c), fa = (float)st->cur_aa;
+    const double sdv = st->cur_s;
+    const size_t mm = (size_t)m * m;
+    const int r0 = chunk * ((m + LOCW_ROWCHUNKS - 1) / LOCW_ROWCHUNKS);
+    const int r1 = min(m, r0 + (m + LOCW_ROWCHUNKS - 1) / LOCW_ROWCHUNKS);
+    for (int i = r0 + warp; i < r1; i += 4) {
+        const size_t bo = at.boff[al] + (size_t)i * m;
+        const zf* __restrict__ hr = a.h32 + bo;
+        const zf* __restrict__ orow = a.o32 + bo;
+        const zf* __restrict__ pr = a.p32 + 3 * at.boff[al] + (size_t)i * m;
+        const zd* __restrict__ dh = a.dh ? a.dh + bo : nullptr;
+        zf aH[CPL], aS[CPL], aP[3][CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            aH[q] = aS[q] = make_float2(0.f, 0.f);
+            aP[0][q] = aP[1][q] = aP[2][q] = make_float2(0.f, 0.f);
+        }
+        for (int j = 0; j < m; ++j) {
+            const zf hj = hr[j], oj = orow[j];
+            const zf px = pr[j], py = pr[mm + j], pz = pr[2 * mm + j];
+            zf he;
+            he.x = hj.x + fx * px.x + fy * py.x + fz * pz.x + fa * oj.x;
+            he.y = hj.y + fx * px.y + fy * py.y + fz * pz.y + fa * oj.y;
+            if (dh && sdv != 0.0) {
+                const zd d = dh[j];
+                he.x += (float)(sdv * d.x);
+                he.y += (float)(sdv * d.y);
+            }
+            const zf* xr = xs + (size_t)j * ns;
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                const int c = lane + 32 * q;
+                if (c < ns) {
+                    const zf x = xr[c];
+                    cfmac(aH[q], he, x);
+                    cfmac(aS[q], oj, x);
+                    cfmac(aP[0][q], px, x);
+                    cfmac(aP[1][q], py, x);
+                    cfmac(aP[2][q], pz, x);
+                }
+            }
+        }
+        // outputs and the row's occupation-weighted shares
+        float jc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            const int c = lane + 32 * q;
+            if (c >= ns) continue;
+            const zd zh = tod(aH[q]), zs = tod(aS[q]);
+            const zf xi = xs[(size_t)i * ns + c];
+            const float f = (float)a.occ[c];
+            if (i < na) {
+                K.Z[aoff + i + (size_t)c * ma] = zh;
+                K.Z[aoff + i + (size_t)(ns + c) * ma] = zs;
+            } else {
+                const int r = lo0 + (i - na);
+                K.Y[r + (size_t)c * nb] = zh;
+                K.Y[r + (size_t)(ns + c) * nb] = zs;
+                jc[3] += f * (xi.x * aH[q].x + xi.y * aH[q].y);
+                jc[4] += f * (xi.x * aS[q].x + xi.y * aS[q].y);
+            }
+#pragma unroll
+            for (int l = 0; l < 3; ++l) jc[l] += f * (xi.x * aP[l][q].x + xi.y * aP[l][q].y);
+        }
+        float v[8] = {jc[0], jc[1], jc[2], jc[3], jc[4], 0.f, 0.f, 0.f};
+        __shared__ float red[4][8];
+        warp_sum_store<float, 8>(v, lane, red[warp]);
+        __syncwarp();
+        if (lane == 0) {
+            double* pj = a.part_jmt + ((size_t)k * at.lrows + at.loff[al] + i) * 5;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) pj[q] = (double)red[warp][q];
+        }
+        __syncwarp();
+    }
+}
+
 // Plane-wave rows of H C and S C in independent partial sums, one block per
 // (row tile of BT rows G, slot):
 //  - slots 0 .. nseg-1: the interstitial sum of Eq. v_interstitial over one
@@ -1264,8 +1367,20 @@ static void back_launch(const StepArgs& a, int maxng, cudaStream_t s, TraceHook*
 // The attribute is global per kernel, so it only ever grows (a context with
 // a smaller window must not lower another context's limit).
 static size_t g_toep_smem[6];
+static size_t g_locw_smem[2];
 int prepare_back_kernels(const StepArgs& a) {
     cudaError_t e = cudaSuccess;
+    if (a.prec >= 1 && a.ns > 4 && a.at_n > 0) {
+        // the wide muffin-tin kernel stages [Q; C_lo] of one atom (FP32)
+        const size_t need = (size_t)a.at_maxm * a.ns * sizeof(zf);
+        const int w = a.ns <= 64 ? 0 : 1;
+        if (need > g_locw_smem[w]) {
+            e = w == 0 ? cudaFuncSetAttribute(k_local_wide<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need)
+                       : cudaFuncSetAttribute(k_local_wide<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+            if (e != cudaSuccess) return 1;
+            g_locw_smem[w] = need;
+        }
+    }
     int slot = 0;
 #define RTD_SET(TA, TT, TC, NT)                                                                      \
     {                                                                                                \
@@ -1303,7 +1418,12 @@ void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, 
     }
     if (a.lrows > 0) {
         dim3 g(a.lrows, 1, a.nk);
-        if (f32) {
+        if (f32 && a.ns > 4) {
+            const size_t sm = (size_t)a.at_maxm * a.ns * sizeof(zf);
+            dim3 gw(a.at_n * LOCW_ROWCHUNKS, 1, a.nk);
+            if (a.ns <= 64) k_local_wide<2><<<gw, 128, sm, s>>>(a);
+            else k_local_wide<4><<<gw, 128, sm, s>>>(a);
+        } else if (f32) {
             if (a.ns <= 2) k_local<zf, 2><<<g, 32, 0, s>>>(a);
             else k_local<zf, 4><<<g, 32, 0, s>>>(a);
         } else {

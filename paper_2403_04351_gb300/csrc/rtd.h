@@ -142,6 +142,7 @@ struct StepArgs {
     int coop_grid;            // blocks of the cooperative Chebyshev launch (0: per-term launches)
     int kofs;                 // k-point of kd[0] (single-k operator calls), 0 in the step
     int tcback;               // the back-projection runs on the tensor cores (split-BF16 form)
+    int at_n, at_maxm;        // atoms, and the largest local block m = N_A + n_lo
 };
 #define POST_STRIDE 36        // part_post row: residual, J_sub (3), then theta^H theta~ (ns <= 4)
 

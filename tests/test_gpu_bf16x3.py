@@ -118,3 +118,35 @@ def test_h2_6000_sampled():
     assert rel(obs["energy"], r["E"]) < 1e-4
     assert np.max(obs["norm_dev"]) < 1e-4
     ctx.close()
+
+
+def test_fp32_form_many_states_operator():
+    """The FP32 form's operator with 40 states (the columns-per-lane
+    muffin-tin kernel), entrywise within 1e-5 (|H||x|)."""
+    rng = np.random.default_rng(9)
+    s = make_system(tiny_config(n_g=300, n_atoms=2, lmax=2, n_lo_per_atom=2, n_s=40, n_aux=64, seed=5))
+    ctx = Context(s, precision="fp32")
+    a_vec = np.array([0.3, -0.7, 1.1]) * 20.0
+    ops = explicit_operators(s, 0)
+    nb = ops["nb"]
+    x = rng.standard_normal((nb, 40)) + 1j * rng.standard_normal((nb, 40))
+    hx, sx = ctx.apply(0, x, a_vec, 0.0)
+    h = hamiltonian(ops, a_vec, s["c_light"], None, 0.0)
+    assert np.max(np.abs(hx - h @ x) / (np.abs(h) @ np.abs(x))) < 1e-5
+    assert np.max(np.abs(sx - ops["S"] @ x) / (np.abs(ops["S"]) @ np.abs(x))) < 1e-5
+    ctx.close()
+
+
+def test_many_states_step_matches_oracle():
+    """40 states over 30 steps in the split-BF16 and FP32 forms: the dipole
+    from the FP64 subspace state, the full-basis energy within each form's bound."""
+    s = make_system(tiny_config(n_g=300, n_atoms=2, lmax=2, n_lo_per_atom=2, n_s=40, n_aux=64, seed=5))
+    a = pulse_samples(s, n_steps=30, a0=5.0)
+    r = Oracle(s).run(a, s["dt"])
+    for prec, etol in (("bf16x3", 1e-4), ("fp32", 1e-5)):
+        ctx = Context(s, precision=prec, graph_steps=10)
+        ctx.step(a)
+        obs = ctx.observables()
+        assert rel(obs["dmu"], r["dmu"]) < 1e-8, prec
+        assert rel(obs["energy"], r["E"]) < etol, prec
+        ctx.close()

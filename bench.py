@@ -310,7 +310,7 @@ def run_ours(args, rank, world, local_rank):
     forms = {args.precision: {"value": value, "ms_per_step": dev_max / K * 1e3, "steps": K}}
     form_obs = {args.precision: obs}
     if args.fp64_steps > 0:
-        for prec in ("fp64", "fp32", "bf16x3"):
+        for prec in ("fp64", "fp32", "bf16x3", "fp16x3"):
             if prec == args.precision:
                 continue
             c2, d2, _, o2 = timed_form(prec, args.fp64_steps, W)
@@ -345,7 +345,8 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": dev_max / K * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp32": "f32+f64", "bf16x3": "bf16x3+f32+f64"}[args.precision],
+        "dtype": {"fp64": "f64", "fp32": "f32+f64", "bf16x3": "bf16x3+f32+f64",
+                  "fp16x3": "fp16x3+f32+f64"}[args.precision],
         "data": "synthetic (seeded generator shaped like the paper's H2 cell)",
         "config": {"workload": args.workload, "n_k": int(s["n_k"]), "n_basis": int(s["n_g"][0]) +
                    int(np.sum(s["n_lo"])), "n_states": int(s["n_s"]), "n_aux": int(s["n_aux"]),
@@ -353,7 +354,7 @@ def run_ours(args, rank, world, local_rank):
                    "propagator": "chebyshev (exact exponential to FP64 round-off)",
                    "l2": "flushed (256 MiB read) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "tensor_core_plan": info.get("tc") if args.precision == "bf16x3" else None},
+                   "tensor_core_plan": info.get("tc") if args.precision in ("bf16x3", "fp16x3") else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 8,
                 "d2h_bytes_per_step": 16 * 8},
         "gpu_launches": int(info["kernel_launches_per_step"]) * K,
@@ -426,7 +427,7 @@ def main():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--precision", choices=["fp32", "fp64", "bf16x3"], default="fp32")
+    p.add_argument("--precision", choices=["fp32", "fp64", "bf16x3", "fp16x3"], default="fp32")
     p.add_argument("--workload", default="h2_6000")
     p.add_argument("--fp64-steps", type=int, default=50, help="steps timed for each other precision form")
     p.add_argument("--trace-steps", type=int, default=5)

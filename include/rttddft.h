@@ -77,6 +77,13 @@ extern "C" {
  * the K slices, relative error a few 2^-16); the other full-basis
  * contractions as in RTTDDFT_PREC_FP32.  At most 128 states. */
 #define RTTDDFT_PREC_BF16X3 2
+/* split-FP16: the same products with fp16 hi/lo splits (22 significant bits,
+ * relative error a few 2^-22): the matching coefficients and the V~ table are
+ * scaled by powers of two so that their largest entry sits near 2^14 (the
+ * per-step table V~ + s dV~ may reach 4 times the largest |V~|), C by 2^12
+ * (|c| <= 16) and [hQ | oQ] by 2^10 (<= 64); a scaled value outside the fp16
+ * range makes the step fail with ERR_NONFINITE.  At most 128 states. */
+#define RTTDDFT_PREC_FP16X3 3
 
 /* how the auxiliary basis CC(0) is obtained at set-up */
 #define RTTDDFT_AUX_RITZ 0  /* Ritz vectors of H0 in span(caux): S-orthonormal, H0-diagonal */

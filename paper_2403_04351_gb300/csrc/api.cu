@@ -41,7 +41,8 @@ struct rttddft_ctx {
     size_t nblk = 0;
     zd *d_vtab = nullptr, *d_dvtab = nullptr, *d_vstep = nullptr;
     zf *d_vtab32 = nullptr, *d_vstep32 = nullptr;
-    uint2* d_vsteps = nullptr;  // pre-split per-step table (split-BF16 form)
+    uint2* d_vsteps = nullptr;  // pre-split per-step table (tensor-core forms)
+    double tc_st = 1.0;         // its fp16 scale
     double *d_occ = nullptr, *d_wk = nullptr, *d_lam = nullptr;
     DevState* d_st = nullptr;
     double* d_rec = nullptr;
@@ -226,7 +227,9 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.part_t = ctx->d_part_t;
     a.flag = ctx->d_flag;
     a.coop_grid = ctx->coop_grid;
-    a.tcback = (ctx->opt.precision == RTTDDFT_PREC_BF16X3 && tc_has_back(ctx->tc)) ? 1 : 0;
+    a.tcback = (ctx->opt.precision >= RTTDDFT_PREC_BF16X3 && tc_has_back(ctx->tc)) ? 1 : 0;
+    a.tc_fmt = tc_format(ctx->tc);
+    a.tc_st = tc_table_scale(ctx->tc);
     a.at_n = ctx->at.n;
     a.at_maxm = ctx->maxm;
     return a;
@@ -494,7 +497,7 @@ static void validate(const rttddft_system* s, const rttddft_options* o) {
     if (!o) fail(ctx, RTTDDFT_ERR_ARG, "options are NULL");
     if (!(o->dt > 0)) fail(ctx, RTTDDFT_ERR_ARG, "dt must be > 0");
     if (o->propagator < 0 || o->propagator > 2) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown propagator");
-    if (o->precision < 0 || o->precision > 2) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown precision form");
+    if (o->precision < 0 || o->precision > 3) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown precision form");
     if (o->aux_mode < 0 || o->aux_mode > 1) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown aux_mode");
     if (o->aux_mode == RTTDDFT_AUX_GIVEN && !s->eps) fail(ctx, RTTDDFT_ERR_ARG, "GIVEN mode needs eps");
     if (o->max_record < 1 || o->graph_steps < 0 || o->max_sweeps < 1) fail(ctx, RTTDDFT_ERR_ARG, "bad option value");
@@ -739,9 +742,9 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             K.Y = dalloc<zd>(ctx, (size_t)K.nb * 2 * ns);
             K.Q = dalloc<zd>(ctx, (size_t)std::max(at.ma, 1) * ns);
             K.Z = dalloc<zd>(ctx, (size_t)std::max(at.ma, 1) * 2 * ns);
-            K.th = (o->precision == RTTDDFT_PREC_BF16X3) ? dalloc<zd>(ctx, (size_t)K.ng * ns) : nullptr;
-            K.tb = (o->precision == RTTDDFT_PREC_BF16X3 && at.ma > 0) ? dalloc<zd>(ctx, (size_t)K.ng * 2 * ns)
-                                                                       : nullptr;
+            const bool tcf = o->precision >= RTTDDFT_PREC_BF16X3;
+            K.th = tcf ? dalloc<zd>(ctx, (size_t)K.ng * ns) : nullptr;
+            K.tb = (tcf && at.ma > 0) ? dalloc<zd>(ctx, (size_t)K.ng * 2 * ns) : nullptr;
             K.gram = dalloc<zd>(ctx, 2 * (size_t)ns * ns);
             K.evec = dalloc<zd>(ctx, nn);
             K.eval = dalloc<double>(ctx, naux);
@@ -911,8 +914,8 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             KCHECK();
             CK(cudaStreamSynchronize(ctx->stream));
         }
-        // ---- tensor-core operands of the split-BF16 form
-        if (o->precision == RTTDDFT_PREC_BF16X3) {
+        // ---- tensor-core operands of the split-BF16 and split-FP16 forms
+        if (o->precision >= RTTDDFT_PREC_BF16X3) {
             std::vector<int> ngv(nk);
             std::vector<const int*> glp(nk);
             std::vector<const zd*> atp(nk);
@@ -921,10 +924,23 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
                 glp[k] = ctx->h_glin[k].data();
                 atp[k] = ctx->hkd[k].at;
             }
+            // fp16 operand scales: the largest |A| and |V~| to 2^14 (powers of two)
+            double amax = 0.0, vmax = 0.0;
+            if (at.n > 0) {
+                size_t na = 0;
+                for (int k = 0; k < nk; ++k) na += (size_t)at.ma * ctx->hkd[k].ng;
+                for (size_t i = 0; i < 2 * na; ++i) amax = std::max(amax, std::fabs(s->amat[i]));
+            }
+            for (int i = 0; i < 2 * ctx->nvt; ++i) vmax = std::max(vmax, std::fabs(s->vtab[i]));
+            auto pow2_scale = [](double m) { return m > 0.0 ? std::ldexp(1.0, 14 - (int)std::ceil(std::log2(m))) : 1.0; };
+            // the per-step table V~ + s dV~ keeps a factor 4 of headroom
+            ctx->tc_st = pow2_scale(vmax) * 0.25;
             std::string why;
+            const int fmt = (o->precision == RTTDDFT_PREC_BF16X3) ? 1 : 0;
             const int e = tc_plan_create(&ctx->tc, nk, ns, at.ma, ngv.data(), glp.data(), atp.data(),
-                                         ctx->d_vtab, ctx->nvt, ctx->vt_center, ctx->d_kd, ctx->stream, &why);
-            if (e) fail(ctx, e, "split-BF16 form: " + why);
+                                         ctx->d_vtab, ctx->nvt, ctx->vt_center, ctx->d_kd, fmt, pow2_scale(amax),
+                                         ctx->tc_st, ctx->stream, &why);
+            if (e) fail(ctx, e, std::string(fmt ? "split-BF16" : "split-FP16") + " form: " + why);
         }
         CK(cudaMemcpy(ctx->d_kd, ctx->hkd.data(), nk * sizeof(KDev), cudaMemcpyHostToDevice));
         // ---- step descriptors
@@ -943,8 +959,10 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             const int tiles = (ctx->maxnb + 63) / 64;
             ctx->kc_expand = 0;
             if (f32) {
-                // FP32 streaming kernel: K slices of at most 256, enough blocks to fill the GPU
-                int splits = std::max((naux + 255) / 256, (2 * 152 + tiles * nk - 1) / (tiles * nk));
+                // FP32 streaming kernel: K slices of at most 256; split only while the
+                // row tiles alone leave most SMs idle (a split costs a reduction launch)
+                int splits = (naux + 255) / 256;
+                if (tiles * nk < 64) splits = std::max(splits, (2 * 152 + tiles * nk - 1) / (tiles * nk));
                 splits = std::min(splits, std::max(1, naux / 32));
                 if (splits > 1) ctx->kc_expand = (naux + splits - 1) / splits;
             } else if (tiles * nk < 2 * 152 && naux >= 128) {
@@ -1213,6 +1231,8 @@ static void sync_and_check(rttddft_ctx* ctx) {
         if (flag & 1) fail(ctx, RTTDDFT_ERR_TIMEOUT, "Jacobi eigensolver reached its sweep limit");
         if (flag & 4) fail(ctx, RTTDDFT_ERR_TIMEOUT, "the grid barrier of the Chebyshev series timed out");
         if (flag & 8) fail(ctx, RTTDDFT_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
+        if (flag & 32)
+            fail(ctx, RTTDDFT_ERR_NONFINITE, "a scaled operand of the split-FP16 form left the fp16 range");
         fail(ctx, RTTDDFT_ERR_ARG, "a pulse sample or dv scale exceeded a_max / s_max");
     }
 }
@@ -1444,7 +1464,7 @@ int rttddft_set_dv(rttddft_ctx* ctx, const double* dh, const double* dvtab) {
             ctx->d_dvtab = dalloc<zd>(ctx, ctx->nvt);
             ctx->d_vstep = dalloc<zd>(ctx, ctx->nvt);
             if (ctx->opt.precision != RTTDDFT_PREC_FP64) ctx->d_vstep32 = dalloc<zf>(ctx, ctx->nvt);
-            if (ctx->opt.precision == RTTDDFT_PREC_BF16X3) ctx->d_vsteps = dalloc<uint2>(ctx, ctx->nvt);
+            if (ctx->opt.precision >= RTTDDFT_PREC_BF16X3) ctx->d_vsteps = dalloc<uint2>(ctx, ctx->nvt);
             std::vector<GemmDesc> w, g, gi;
             std::vector<ToepDesc> td;
             for (int k = 0; k < nk; ++k) {
@@ -1947,7 +1967,7 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         KCHECK();
         StepArgs a = make_args(ctx, dv_on);
         a.kd = (const KDev*)(base + o_kd);
-        if (a.prec == 2) a.prec = 1;  // the static scratch holds the FP32-form operands only
+        if (a.prec >= 2) a.prec = 1;  // the static scratch holds the FP32-form operands only
         a.vsteps = nullptr;
         a.tcback = 0;
         a.nk = 1;

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 typedef double2 zd;  // complex FP64 (re, im)
@@ -75,11 +76,28 @@ template <> struct Cx<zf> {
     static __device__ __forceinline__ zd todbl(zf a) { return tod(a); }
 };
 
-// bf16 split v = hi + lo (each rounded to nearest) packed as hi | lo << 16
-__device__ __forceinline__ uint32_t bf16_split_bits(double v) {
-    const __nv_bfloat16 h = __double2bfloat16(v);
-    const __nv_bfloat16 l = __double2bfloat16(v - (double)__bfloat162float(h));
-    return (uint32_t)__bfloat16_as_ushort(h) | ((uint32_t)__bfloat16_as_ushort(l) << 16);
+// 16-bit split w = v * scale = hi + lo (each rounded to nearest): fmt 1 bf16,
+// fmt 0 fp16 (scale keeps w inside the fp16 range); returns false when |w|
+// exceeds the fp16 range
+#define TC_FP16_MAX 65000.0
+__device__ __forceinline__ bool split16(double v, int fmt, double scale, unsigned short& hi, unsigned short& lo) {
+    const double w = v * scale;
+    if (fmt) {
+        const __nv_bfloat16 h = __double2bfloat16(w);
+        hi = __bfloat16_as_ushort(h);
+        lo = __bfloat16_as_ushort(__double2bfloat16(w - (double)__bfloat162float(h)));
+        return true;
+    }
+    const __half h = __double2half(w);
+    hi = __half_as_ushort(h);
+    lo = __half_as_ushort(__double2half(w - (double)__half2float(h)));
+    return fabs(w) <= TC_FP16_MAX;
+}
+// the split packed as hi | lo << 16
+__device__ __forceinline__ uint32_t split16_bits(double v, int fmt, double scale, bool& ok) {
+    unsigned short h, l;
+    ok = split16(v, fmt, scale, h, l);
+    return (uint32_t)h | ((uint32_t)l << 16);
 }
 
 // Sum over the 32 lanes of V values per lane by exchange-halving steps

@@ -35,7 +35,11 @@ __global__ void k_vstep(StepArgs a) {
     const zd v = zadd(a.vtab[i], zscale(a.dvtab[i], s));
     a.vstep[i] = v;
     if (a.vstep32) a.vstep32[i] = tof(v);
-    if (a.vsteps) a.vsteps[i] = make_uint2(bf16_split_bits(v.x), bf16_split_bits(v.y));
+    if (a.vsteps) {
+        bool o1, o2;
+        a.vsteps[i] = make_uint2(split16_bits(v.x, a.tc_fmt, a.tc_st, o1), split16_bits(v.y, a.tc_fmt, a.tc_st, o2));
+        if (!(o1 && o2)) atomicOr(a.flag, 32);
+    }
 }
 
 // ------------------------------------------------------------ HH(t_k)
@@ -523,14 +527,14 @@ __global__ void __launch_bounds__(32) k_local(StepArgs a) {
 // staged once in shared memory as FP32, lanes own columns (CPL per lane) and
 // a warp walks one local row at a time, reading the row of h, o, p (FP32
 // copies, broadcast) once for all columns.  Outputs as k_local.
-#define LOCW_ROWCHUNKS 4
+#define LOCW_MIN_NS 16  // above this many states the columns-per-lane kernel wins
 template <int CPL>
-__global__ void __launch_bounds__(128) k_local_wide(StepArgs a) {
+__global__ void __launch_bounds__(128) k_local_wide(StepArgs a, int rowchunks) {
     extern __shared__ zf xs[];  // [m][ns]
     const int k = blockIdx.z;
     const KDev& K = a.kd[k];
     const AtomTab& at = *a.at;
-    const int al = blockIdx.x / LOCW_ROWCHUNKS, chunk = blockIdx.x % LOCW_ROWCHUNKS;
+    const int al = blockIdx.x / rowchunks, chunk = blockIdx.x % rowchunks;
     if (al >= at.n) return;
     const int m = at.m[al], na = at.na[al];
     const int ns = a.ns, nb = K.nb, ma = at.ma, ng = K.ng;
@@ -547,8 +551,8 @@ __global__ void __launch_bounds__(128) k_local_wide(StepArgs a) {
                 fz = (float)(st->cur_a[2] * a.inv_c), fa = (float)st->cur_aa;
     const double sdv = st->cur_s;
     const size_t mm = (size_t)m * m;
-    const int r0 = chunk * ((m + LOCW_ROWCHUNKS - 1) / LOCW_ROWCHUNKS);
-    const int r1 = min(m, r0 + (m + LOCW_ROWCHUNKS - 1) / LOCW_ROWCHUNKS);
+    const int r0 = chunk * ((m + rowchunks - 1) / rowchunks);
+    const int r1 = min(m, r0 + (m + rowchunks - 1) / rowchunks);
     for (int i = r0 + warp; i < r1; i += 4) {
         const size_t bo = at.boff[al] + (size_t)i * m;
         const zf* __restrict__ hr = a.h32 + bo;
@@ -759,20 +763,29 @@ __global__ void __launch_bounds__(BT) k_back(StepArgs a, int n0) {
         for (int c = 0; c < NT; ++c) {
             if (c >= nc) break;
             zd th = zmk(0.0, 0.0), ts = zmk(0.0, 0.0);
-            if (a.prec == 2) {
-                th = K.th[g + (size_t)(n0 + c) * ng];
-            } else {
-                for (int sg = 0; sg < nsg; ++sg)
-                    th = zadd(th, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + c) * a.maxng + g]);
-            }
+            // slot partials, loads issued four slots at a time (in slot order)
+            const zd* pt = a.part_t + (((size_t)k * a.nslot) * 2 * NT + c) * a.maxng + g;
+            const size_t sst = (size_t)2 * NT * a.maxng;
+            auto sum4 = [&](int s0, int s1, size_t off) {
+                zd t = zmk(0.0, 0.0);
+                for (int sg = s0; sg < s1; sg += 4) {
+                    zd v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        v[u] = (sg + u < s1) ? pt[(size_t)(sg + u) * sst + off] : zmk(0.0, 0.0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) t = zadd(t, v[u]);
+                }
+                return t;
+            };
+            if (a.prec >= 2) th = K.th[g + (size_t)(n0 + c) * ng];
+            else th = sum4(0, nsg, 0);
             if (a.tcback) {
                 th = zadd(th, K.tb[g + (size_t)(n0 + c) * ng]);
                 ts = K.tb[g + (size_t)(ns + n0 + c) * ng];
             } else {
-                for (int sg = a.nseg; sg < a.nseg + nas; ++sg) {
-                    th = zadd(th, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + c) * a.maxng + g]);
-                    ts = zadd(ts, a.part_t[(((size_t)k * a.nslot + sg) * 2 * NT + NT + c) * a.maxng + g]);
-                }
+                th = zadd(th, sum4(a.nseg, a.nseg + nas, 0));
+                ts = sum4(a.nseg, a.nseg + nas, (size_t)NT * a.maxng);
             }
             const zd x = X[g + (size_t)(n0 + c) * nb];
             const zd hv = zadd(th, zscale(x, dg));
@@ -829,7 +842,28 @@ __device__ double block_max(double v, double* sh) {
 // theta~ = CC^H S C from the split-K partials (l == 0: its deviation from
 // theta and, for N_s <= 4, the row's share of theta^H theta~), and the
 // row's share of J_sub,l = sum_n f_n Re theta_in^* ((PP_l + A_l/c) theta)_in.
-__global__ void __launch_bounds__(128) k_post(StepArgs a, int do_theta, int do_j) {
+__device__ void post_body(const StepArgs& a, int do_theta, int do_j);
+__device__ void finalize_body(const StepArgs& a, int set_gs);
+// fin: the last block to finish also runs the step's finalize (one launch
+// fewer per step); blocks count themselves in st->post_done
+__global__ void __launch_bounds__(128) k_post(StepArgs a, int do_theta, int do_j, int fin) {
+    post_body(a, do_theta, do_j);
+    if (!fin) return;
+    __shared__ int last;
+    // every writing thread publishes its rows before the block counts itself
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+        last = (atomicAdd(&a.st->post_done, 1u) == total - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    finalize_body(a, 0);  // reads the other blocks' rows through L2 (ld.global.cg)
+    if (threadIdx.x == 0) a.st->post_done = 0u;
+}
+__device__ void post_body(const StepArgs& a, int do_theta, int do_j) {
     const int k = blockIdx.z;
     const KDev& K = a.kd[k];
     const int n = a.naux, ns = a.ns;
@@ -903,7 +937,7 @@ __global__ void k_reproj(StepArgs a) {
 // Sum the step's partials over k-points (weights w_k) in a fixed order,
 // update the dipole by the trapezoid rule (Eq. dipole) and append the
 // record.  One block.
-__global__ void __launch_bounds__(256) k_finalize(StepArgs a, int set_gs) {
+__device__ void finalize_body(const StepArgs& a, int set_gs) {
     // the k-weights enter the per-row shares, so one block reduction covers all
     // k-points; sums by halving warp sums (each warp-wide FP64 add is costly on
     // GB300), maxima of non-negative values as integer maxima of their bits
@@ -923,10 +957,10 @@ __global__ void __launch_bounds__(256) k_finalize(StepArgs a, int set_gs) {
         const int nback = (K.ng + BT - 1) / BT;
         for (int i = tid; i < n; i += blockDim.x) {
             const double* p = a.part_post + ((size_t)k * n + i) * POST_STRIDE;
-            v[0] += w * p[1];
-            v[1] += w * p[2];
-            v[2] += w * p[3];
-            mres = fmax(mres, p[0]);
+            v[0] += w * __ldcg(p + 1);
+            v[1] += w * __ldcg(p + 2);
+            v[2] += w * __ldcg(p + 3);
+            mres = fmax(mres, __ldcg(p));
         }
         if (set_gs) continue;
         for (int c = tid; c < nback; c += blockDim.x) {
@@ -948,8 +982,8 @@ __global__ void __launch_bounds__(256) k_finalize(StepArgs a, int set_gs) {
                 double g[2] = {0.0, 0.0};
                 for (int i = lane; i < n; i += 32) {
                     const double* p = a.part_post + ((size_t)k * n + i) * POST_STRIDE + 4 + 2 * e;
-                    g[0] += p[0];
-                    g[1] += p[1];
+                    g[0] += __ldcg(p);
+                    g[1] += __ldcg(p + 1);
                 }
                 __shared__ double gs[8][2];
                 warp_sum_store<double, 2>(g, lane, gs[warp]);
@@ -1034,6 +1068,8 @@ __global__ void __launch_bounds__(256) k_finalize(StepArgs a, int set_gs) {
     st->cstep += 1;
     st->bar = 0u;  // the next step's cooperative series counts from zero
 }
+
+__global__ void __launch_bounds__(256) k_finalize(StepArgs a, int set_gs) { finalize_body(a, set_gs); }
 
 // ------------------------------------------------------------ Jacobi eigensolver
 // Cyclic two-sided Jacobi for a complex Hermitian matrix (one block per
@@ -1326,7 +1362,7 @@ void launch_prep_coef(const StepArgs& a, cudaStream_t s) {
 
 void launch_subspace_current(const StepArgs& a, int set_gs, cudaStream_t s) {
     dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
-    k_post<<<g, 128, 0, s>>>(a, 0, 1);
+    k_post<<<g, 128, 0, s>>>(a, 0, 1, 0);
     k_finalize<<<1, 256, 0, s>>>(a, set_gs);
 }
 
@@ -1349,7 +1385,7 @@ static void back_launch(const StepArgs& a, int maxng, cudaStream_t s, TraceHook*
     const size_t sm = toep_smem<NT>(a, sizeof(TC), sizeof(TT));
     // in the tensor-core form the interstitial slots are done already: only
     // the back-projection slots run here
-    const int slot0 = (a.prec == 2) ? a.nseg : 0;
+    const int slot0 = (a.prec >= 2) ? a.nseg : 0;
     // with the back-projection on the tensor cores too, no slot kernel runs
     dim3 gt((maxng + BT - 1) / BT, a.tcback ? 0 : a.nslot - slot0, a.nk);
     dim3 gb((maxng + BT - 1) / BT, 1, a.nk);
@@ -1367,16 +1403,17 @@ static void back_launch(const StepArgs& a, int maxng, cudaStream_t s, TraceHook*
 // The attribute is global per kernel, so it only ever grows (a context with
 // a smaller window must not lower another context's limit).
 static size_t g_toep_smem[6];
-static size_t g_locw_smem[2];
+static size_t g_locw_smem[3];
 int prepare_back_kernels(const StepArgs& a) {
     cudaError_t e = cudaSuccess;
-    if (a.prec >= 1 && a.ns > 4 && a.at_n > 0) {
+    if (a.prec >= 1 && a.ns > LOCW_MIN_NS && a.at_n > 0) {
         // the wide muffin-tin kernel stages [Q; C_lo] of one atom (FP32)
         const size_t need = (size_t)a.at_maxm * a.ns * sizeof(zf);
-        const int w = a.ns <= 64 ? 0 : 1;
+        const int w = a.ns <= 32 ? 0 : (a.ns <= 64 ? 1 : 2);
         if (need > g_locw_smem[w]) {
-            e = w == 0 ? cudaFuncSetAttribute(k_local_wide<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need)
-                       : cudaFuncSetAttribute(k_local_wide<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+            e = w == 0 ? cudaFuncSetAttribute(k_local_wide<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need)
+                : w == 1 ? cudaFuncSetAttribute(k_local_wide<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need)
+                         : cudaFuncSetAttribute(k_local_wide<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
             if (e != cudaSuccess) return 1;
             g_locw_smem[w] = need;
         }
@@ -1401,7 +1438,7 @@ int prepare_back_kernels(const StepArgs& a) {
 
 void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr) {
     const bool f32 = a.prec >= 1;
-    if (a.prec == 2) {
+    if (a.prec >= 2) {
         // tensor cores: V~ * C_G and Q = A C_G in one split-BF16 launch
         launch_tc_pack(p.tc, a, s);
         mark(tr, "tc_pack_c", s);
@@ -1418,11 +1455,15 @@ void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, 
     }
     if (a.lrows > 0) {
         dim3 g(a.lrows, 1, a.nk);
-        if (f32 && a.ns > 4) {
+        if (f32 && a.ns > LOCW_MIN_NS) {
+            // lanes own columns; row chunks per atom so that about two blocks per SM work
             const size_t sm = (size_t)a.at_maxm * a.ns * sizeof(zf);
-            dim3 gw(a.at_n * LOCW_ROWCHUNKS, 1, a.nk);
-            if (a.ns <= 64) k_local_wide<2><<<gw, 128, sm, s>>>(a);
-            else k_local_wide<4><<<gw, 128, sm, s>>>(a);
+            int rc = std::max(4, (2 * 152 + a.at_n * a.nk - 1) / (a.at_n * a.nk));
+            rc = std::min(rc, std::max(1, a.at_maxm / 4));
+            dim3 gw(a.at_n * rc, 1, a.nk);
+            if (a.ns <= 32) k_local_wide<1><<<gw, 128, sm, s>>>(a, rc);
+            else if (a.ns <= 64) k_local_wide<2><<<gw, 128, sm, s>>>(a, rc);
+            else k_local_wide<4><<<gw, 128, sm, s>>>(a, rc);
         } else if (f32) {
             if (a.ns <= 2) k_local<zf, 2><<<g, 32, 0, s>>>(a);
             else k_local<zf, 4><<<g, 32, 0, s>>>(a);
@@ -1513,15 +1554,18 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
     {
         const int ntb = a.ns <= 2 ? 2 : (a.ns <= 4 ? 4 : 8);
         const int chunks = (a.ns + ntb - 1) / ntb;
-        nl += (a.prec == 2 ? 3 : 2) + (a.lrows > 0 ? 1 : 0) + (a.tcback ? 3 + chunks : 2 * chunks);
+        nl += (a.prec >= 2 ? 3 : 2) + (a.lrows > 0 ? 1 : 0) + (a.tcback ? 3 + chunks : 2 * chunks);
     }
     // theta~ = CC^H (S C): split-K partials, finished per row in k_post
     launch_gemm_cn(p.gd_proj, a.nk, a.naux, p.maxnb, a.ns, p.kc_proj, p.part, 0, f32, nullptr, s);
     mark(tr, "gemm_project", s);
+    // without reprojection, and with theta^H theta~ summed from the post rows
+    // (N_s <= 4), the last post block also finalises the step
+    const bool merged = !a.reproject && a.ns <= 4;
     {
         dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
-        k_post<<<g, 128, 0, s>>>(a, 1, a.reproject ? 0 : 1);
-        mark(tr, "project_finish_current", s);
+        k_post<<<g, 128, 0, s>>>(a, 1, a.reproject ? 0 : 1, merged ? 1 : 0);
+        mark(tr, merged ? "project_current_finalize" : "project_finish_current", s);
     }
     if (a.ns > 4) {
         launch_gemm_cn(p.gd_g1, a.nk, a.ns, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
@@ -1533,13 +1577,15 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
         launch_gemm_cn(p.gd_g2, a.nk, a.ns, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
         k_reproj<<<dim3((a.naux * a.ns + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
         dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
-        k_post<<<g, 128, 0, s>>>(a, 0, 1);
+        k_post<<<g, 128, 0, s>>>(a, 0, 1, 0);
         mark(tr, "reproject", s);
         nl += 3;
     }
-    k_finalize<<<1, 256, 0, s>>>(a, 0);
-    mark(tr, "finalize", s);
-    ++nl;
+    if (!merged) {
+        k_finalize<<<1, 256, 0, s>>>(a, 0);
+        mark(tr, "finalize", s);
+        ++nl;
+    }
     if (nlaunch) *nlaunch = nl;
 }
 
@@ -1604,5 +1650,5 @@ void launch_hsub_only(const StepArgs& a, const StepPlan& p, int cstep, cudaStrea
 // J contributions of the current theta (rows into part_post[.][1..3])
 void launch_subspace_j(const StepArgs& a, cudaStream_t s) {
     dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
-    k_post<<<g, 128, 0, s>>>(a, 0, 1);
+    k_post<<<g, 128, 0, s>>>(a, 0, 1, 0);
 }

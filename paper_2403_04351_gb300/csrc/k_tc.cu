@@ -427,6 +427,7 @@ struct TcOpParams {
     int nk, ns, ma, Dn, kbps, splits, atiles, R, S;
     int nkb_fixed;  // K blocks of every k-point (0: ceil(N_G(k) / 32))
     int rows_ng;    // valid output rows: N_G(k) (1) or ma (0)
+    int fmt;        // operand format: 1 bf16, 0 fp16
     int kofs;  // k-point of blockIdx.z = 0 in the matching-row operand (single-k calls)
     const KDev* kd;
     float* D;  // [nk][splits][R][Dn]
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     volatile int* ab = &abort_flag;
     if (warp == 8) {
         if (lane == 0) {
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+            const uint32_t idesc = (1u << 4) | ((uint32_t)p.fmt << 7) | ((uint32_t)p.fmt << 10) | ((uint32_t)(NT >> 3) << 17) |
                                    ((uint32_t)(TC_BM >> 4) << 24);
             int issued = 0, consumed = 0;
             auto load = [&](int j) {
@@ -567,6 +568,7 @@ __device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinter
 #define TCT_MAXSB 16
 struct TcToepParams {
     int nk, Dn, kbps, splits, ttiles, wcap, vt_center, SA, SB;
+    int fmt;  // operand format: 1 bf16, 0 fp16
     const KDev* kd;
     const uint2* tab;  // pre-split table
     float* D;          // [nk][splits][ttiles * 128][Dn]
@@ -648,7 +650,7 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
         if (lane == 0 && *ab) {
             umma_commit(&done);
         } else if (lane == 0) {
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+            const uint32_t idesc = (1u << 4) | ((uint32_t)p.fmt << 7) | ((uint32_t)p.fmt << 10) | ((uint32_t)(NT >> 3) << 17) |
                                    ((uint32_t)(TC_BM >> 4) << 24);
             int issued = 0, consumed = 0;
             auto loadB = [&](int j) {
@@ -785,15 +787,28 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
 }
 
 // the pre-split table of the tensor-core form (set-up)
-__global__ void k_tc_split_table(const zd* __restrict__ t, uint2* __restrict__ out, int n) {
+__global__ void k_tc_split_table(const zd* __restrict__ t, uint2* __restrict__ out, int n, int fmt, double scale,
+                                 int* flag) {
     const int i = blockIdx.x * 256 + threadIdx.x;
-    if (i < n) out[i] = make_uint2(bf16_split_bits(t[i].x), bf16_split_bits(t[i].y));
+    if (i >= n) return;
+    bool o1, o2;
+    out[i] = make_uint2(split16_bits(t[i].x, fmt, scale, o1), split16_bits(t[i].y, fmt, scale, o2));
+    if (!(o1 && o2)) atomicOr(flag, 32);
+}
+
+// store the scaled split of v at hi[i], lo[i]; flag bit 5 when out of the fp16 range
+__device__ __forceinline__ void put16(double v, int fmt, double scale, unsigned short* hi, unsigned short* lo,
+                                      size_t i, int* flag) {
+    unsigned short h, l;
+    if (!split16(v, fmt, scale, h, l)) atomicOr(flag, 32);
+    hi[i] = h;
+    lo[i] = l;
 }
 
 // Right operand of a step: B^[k][row][K-block layout] from C_G (FP64, the
-// first ng rows of K.C).  Rows 2 ns .. and G' >= ng stay zero from set-up.
-__global__ void k_tc_pack_c(const KDev* __restrict__ kd, int ns, int Kp, int Rp, __nv_bfloat16* __restrict__ bh,
-                            __nv_bfloat16* __restrict__ bl) {
+// first ng rows of K.C), scaled by sc.  Rows 2 ns .. and G' >= ng stay zero.
+__global__ void k_tc_pack_c(const KDev* __restrict__ kd, int ns, int Kp, int Rp, unsigned short* __restrict__ bh,
+                            unsigned short* __restrict__ bl, int fmt, double sc, int* flag) {
     const int k = blockIdx.z;
     const KDev& K = kd[k];
     const int ng = K.ng;
@@ -804,61 +819,46 @@ __global__ void k_tc_pack_c(const KDev* __restrict__ kd, int ns, int Kp, int Rp,
     const int kb = gp >> 5, o = gp & 31;
     const size_t re_row = ((size_t)k * Rp + n) * Kp + (size_t)kb * 64;
     const size_t im_row = ((size_t)k * Rp + ns + n) * Kp + (size_t)kb * 64;
-    __nv_bfloat16 h, l;
-    split_bf16(c.x, h, l);
-    bh[re_row + o] = h;
-    bl[re_row + o] = l;
-    bh[im_row + 32 + o] = h;
-    bl[im_row + 32 + o] = l;
-    split_bf16(c.y, h, l);
-    bh[im_row + o] = h;
-    bl[im_row + o] = l;
-    split_bf16(-c.y, h, l);
-    bh[re_row + 32 + o] = h;
-    bl[re_row + 32 + o] = l;
+    put16(c.x, fmt, sc, bh, bl, re_row + o, flag);
+    put16(c.x, fmt, sc, bh, bl, im_row + 32 + o, flag);
+    put16(c.y, fmt, sc, bh, bl, im_row + o, flag);
+    put16(-c.y, fmt, sc, bh, bl, re_row + 32 + o, flag);
 }
 
 // Left operand of the matching rows (set-up): A^[k][r][K-block layout] with
-// A[r, G'] = conj(AT[G' + r ng]).
+// A[r, G'] = conj(AT[G' + r ng]), scaled by sa.
 __global__ void k_tc_pack_at(const zd* __restrict__ at, int ng, int ma, int Kp, int Mp, int k,
-                             __nv_bfloat16* __restrict__ ah, __nv_bfloat16* __restrict__ al) {
+                             unsigned short* __restrict__ ah, unsigned short* __restrict__ al, int fmt, double sa,
+                             int* flag) {
     const size_t e = (size_t)blockIdx.x * 256 + threadIdx.x;
     if (e >= (size_t)ma * ng) return;
     const int gp = (int)(e % ng), r = (int)(e / ng);
     const zd a = at[gp + (size_t)r * ng];
     const size_t row = ((size_t)k * Mp + r) * Kp + (size_t)(gp >> 5) * 64 + (gp & 31);
-    __nv_bfloat16 h, l;
-    split_bf16(a.x, h, l);
-    ah[row] = h;
-    al[row] = l;
-    split_bf16(-a.y, h, l);
-    ah[row + 32] = h;
-    al[row + 32] = l;
+    put16(a.x, fmt, sa, ah, al, row, flag);
+    put16(-a.y, fmt, sa, ah, al, row + 32, flag);
 }
 
 // Left operand of the back-projection (set-up): A^[k][G][K-block layout over
-// the matching rows r], the entry A^H[G, r] = AT[G + r ng].
+// the matching rows r], the entry A^H[G, r] = AT[G + r ng], scaled by sa.
 __global__ void k_tc_pack_atb(const zd* __restrict__ at, int ng, int ma, int Kp, int Mp, int k,
-                              __nv_bfloat16* __restrict__ ah, __nv_bfloat16* __restrict__ al) {
+                              unsigned short* __restrict__ ah, unsigned short* __restrict__ al, int fmt, double sa,
+                              int* flag) {
     const size_t e = (size_t)blockIdx.x * 256 + threadIdx.x;
     if (e >= (size_t)ma * ng) return;
     const int g = (int)(e % ng), r = (int)(e / ng);
     const zd a = at[g + (size_t)r * ng];
     const size_t row = ((size_t)k * Mp + g) * Kp + (size_t)(r >> 5) * 64 + (r & 31);
-    __nv_bfloat16 h, l;
-    split_bf16(a.x, h, l);
-    ah[row] = h;
-    al[row] = l;
-    split_bf16(a.y, h, l);
-    ah[row + 32] = h;
-    al[row + 32] = l;
+    put16(a.x, fmt, sa, ah, al, row, flag);
+    put16(a.y, fmt, sa, ah, al, row + 32, flag);
 }
 
 // Right operand of the back-projection (per step) from Z = [hQ | oQ]
-// (ma x 2 ns, FP64): rows c < 2 ns hold [Re Z | -Im Z], rows 2 ns + c hold
-// [Im Z | Re Z] over the matching rows.
+// (ma x 2 ns, FP64), scaled by sz: rows c < 2 ns hold [Re Z | -Im Z], rows
+// 2 ns + c hold [Im Z | Re Z] over the matching rows.
 __global__ void k_tc_pack_z(const KDev* __restrict__ kd, int ns, int ma, int Kp, int Rp,
-                            __nv_bfloat16* __restrict__ bh, __nv_bfloat16* __restrict__ bl) {
+                            unsigned short* __restrict__ bh, unsigned short* __restrict__ bl, int fmt, double sz,
+                            int* flag) {
     const int k = blockIdx.z;
     const KDev& K = kd[k];
     const int nc = 2 * ns;
@@ -869,18 +869,10 @@ __global__ void k_tc_pack_z(const KDev* __restrict__ kd, int ns, int ma, int Kp,
     const int kb = r >> 5, o = r & 31;
     const size_t re_row = ((size_t)k * Rp + c) * Kp + (size_t)kb * 64;
     const size_t im_row = ((size_t)k * Rp + nc + c) * Kp + (size_t)kb * 64;
-    __nv_bfloat16 h, l;
-    split_bf16(z.x, h, l);
-    bh[re_row + o] = h;
-    bl[re_row + o] = l;
-    bh[im_row + 32 + o] = h;
-    bl[im_row + 32 + o] = l;
-    split_bf16(z.y, h, l);
-    bh[im_row + o] = h;
-    bl[im_row + o] = l;
-    split_bf16(-z.y, h, l);
-    bh[re_row + 32 + o] = h;
-    bl[re_row + 32 + o] = l;
+    put16(z.x, fmt, sz, bh, bl, re_row + o, flag);
+    put16(z.x, fmt, sz, bh, bl, im_row + 32 + o, flag);
+    put16(z.y, fmt, sz, bh, bl, im_row + o, flag);
+    put16(-z.y, fmt, sz, bh, bl, re_row + 32 + o, flag);
 }
 
 // Sum of the K slices in FP64: interstitial rows into K.th (ng x ns),
@@ -889,31 +881,29 @@ struct TcRedParams {
     int ns, ma, Dn, kbps_t, splits_t, kbps_a, splits_a, Rt, Ra;
     int part;  // 0: interstitial and matching rows, 1: interstitial only, 2: matching only, 3: back-projection
     int Dnb, kbps_b, splits_b, nkb_b, Rb;
+    double inv_t, inv_a, inv_b;  // undo the operand scales of the split-FP16 form
     const KDev* kd;
     const float* Dt;
     const float* Da;
     const float* Db;
 };
-// sum of nsp slices of one output pair, eight loads in flight
+// sum of nsp slices of one output pair, loads issued four slices at a time
+// (predicated, so short sums do not serialise on a scalar tail)
 __device__ __forceinline__ void tc_sum_slices(const float* d, size_t stride, int nsp, int c, int ns, double& re,
                                               double& im) {
-    int s = 0;
-    for (; s + 8 <= nsp; s += 8) {
-        float a[8], b[8];
+    for (int s = 0; s < nsp; s += 4) {
+        float a[4], b[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            a[u] = d[(size_t)(s + u) * stride + c];
-            b[u] = d[(size_t)(s + u) * stride + ns + c];
+        for (int u = 0; u < 4; ++u) {
+            const bool ok = s + u < nsp;
+            a[u] = ok ? d[(size_t)(s + u) * stride + c] : 0.f;
+            b[u] = ok ? d[(size_t)(s + u) * stride + ns + c] : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 4; ++u) {
             re += (double)a[u];
             im += (double)b[u];
         }
-    }
-    for (; s < nsp; ++s) {
-        re += (double)d[(size_t)s * stride + c];
-        im += (double)d[(size_t)s * stride + ns + c];
     }
 }
 __global__ void k_tc_opred(TcRedParams p) {
@@ -930,7 +920,7 @@ __global__ void k_tc_opred(TcRedParams p) {
         const int nsp = min(p.splits_b, (p.nkb_b + p.kbps_b - 1) / p.kbps_b);
         double re = 0.0, im = 0.0;
         tc_sum_slices(p.Db + ((size_t)k * p.splits_b * p.Rb + g) * p.Dnb, (size_t)p.Rb * p.Dnb, nsp, c, nc, re, im);
-        K.tb[g + (size_t)c * ng] = zmk(re, im);
+        K.tb[g + (size_t)c * ng] = zmk(re * p.inv_b, im * p.inv_b);
         return;
     }
     const int r0 = (p.part == 2) ? ng : 0;
@@ -943,12 +933,12 @@ __global__ void k_tc_opred(TcRedParams p) {
     if (row < ng) {
         const int nsp = min(p.splits_t, (nkb + p.kbps_t - 1) / p.kbps_t);
         tc_sum_slices(p.Dt + ((size_t)k * p.splits_t * p.Rt + row) * p.Dn, (size_t)p.Rt * p.Dn, nsp, c, ns, re, im);
-        K.th[row + (size_t)c * ng] = zmk(re, im);
+        K.th[row + (size_t)c * ng] = zmk(re * p.inv_t, im * p.inv_t);
     } else {
         const int r = row - ng;
         const int nsp = min(p.splits_a, (nkb + p.kbps_a - 1) / p.kbps_a);
         tc_sum_slices(p.Da + ((size_t)k * p.splits_a * p.Ra + r) * p.Dn, (size_t)p.Ra * p.Dn, nsp, c, ns, re, im);
-        K.Q[r + (size_t)c * p.ma] = zmk(re, im);
+        K.Q[r + (size_t)c * p.ma] = zmk(re * p.inv_a, im * p.inv_a);
     }
 }
 
@@ -963,8 +953,10 @@ struct TcPlan {
     int S_a = 0, kbps_a = 0, splits_a = 0;
     size_t smem_a = 0;
     CUtensorMap tbh, tbl, tah, tal;
-    __nv_bfloat16 *bh = nullptr, *bl = nullptr, *ah = nullptr, *al = nullptr;
+    unsigned short *bh = nullptr, *bl = nullptr, *ah = nullptr, *al = nullptr;  // 16-bit operand splits
     float *Dt = nullptr, *Da = nullptr;
+    int fmt = 1;                                    // 1 bf16, 0 fp16
+    double sA = 1.0, sT = 1.0, sC = 1.0, sZ = 1.0;  // operand scales (powers of two)
     uint2* tabs = nullptr;  // the pre-split static table
     int* tflag = nullptr;   // error flag of the tuning launches
     float ms_t = 0.f, ms_a = 0.f;  // tuned launch times
@@ -974,7 +966,7 @@ struct TcPlan {
     size_t smem_b = 0;
     float ms_b = 0.f;
     CUtensorMap tzh, tzl, tabh, tabl;
-    __nv_bfloat16 *zh = nullptr, *zl = nullptr, *abh = nullptr, *abl = nullptr;
+    unsigned short *zh = nullptr, *zl = nullptr, *abh = nullptr, *abl = nullptr;
     float* Db = nullptr;
 };
 
@@ -1078,6 +1070,7 @@ static void tco_launch_toep(const TcPlan* tp, const TcToepCand& c, const KDev* k
     p.vt_center = tp->vt_center;
     p.SA = c.SA;
     p.SB = c.SB;
+    p.fmt = tp->fmt;
     p.kd = kd;
     p.tab = tp->tabs;
     p.D = tp->Dt;
@@ -1093,6 +1086,7 @@ static void tco_launch_toep(const TcPlan* tp, const TcToepCand& c, const KDev* k
     r.splits_t = c.splits;
     r.Rt = tp->ttiles * TC_BM;
     r.part = 1;
+    r.inv_t = 1.0 / (tp->sT * tp->sC);
     r.kd = kd;
     r.Dt = tp->Dt;
     k_tc_opred<<<dim3((tp->maxng * tp->ns + 255) / 256, 1, nk), 256, 0, s>>>(r);
@@ -1109,6 +1103,7 @@ static void tco_launch_rows(const TcPlan* tp, const TcRowsCand& c, const KDev* k
     p.atiles = tp->atiles;
     p.R = tp->Mp;
     p.S = c.S;
+    p.fmt = tp->fmt;
     p.kd = kd;
     p.D = tp->Da;
     p.flag = tp->tflag;
@@ -1121,6 +1116,7 @@ static void tco_launch_rows(const TcPlan* tp, const TcRowsCand& c, const KDev* k
     r.splits_a = c.splits;
     r.Ra = tp->Mp;
     r.part = 2;
+    r.inv_a = 1.0 / (tp->sA * tp->sC);
     r.kd = kd;
     r.Da = tp->Da;
     k_tc_opred<<<dim3((tp->ma * tp->ns + 255) / 256, 1, nk), 256, 0, s>>>(r);
@@ -1128,7 +1124,7 @@ static void tco_launch_rows(const TcPlan* tp, const TcRowsCand& c, const KDev* k
 
 template <int NT>
 static void tco_launch_back(const TcPlan* tp, const TcRowsCand& c, const KDev* kd, int nk, cudaStream_t s,
-                            int kofs = 0) {
+                            int kofs = 0, int* flag = nullptr) {
     TcOpParams p{};
     p.kofs = kofs;
     p.nk = nk;
@@ -1142,9 +1138,10 @@ static void tco_launch_back(const TcPlan* tp, const TcRowsCand& c, const KDev* k
     p.S = c.S;
     p.nkb_fixed = tp->nkb_b;
     p.rows_ng = 1;
+    p.fmt = tp->fmt;
     p.kd = kd;
     p.D = tp->Db;
-    p.flag = tp->tflag;
+    p.flag = flag ? flag : tp->tflag;
     k_tc_opfwd<NT><<<dim3(tp->ttiles, c.splits, nk), TCO_THREADS, c.smem, s>>>(tp->tzh, tp->tzl, tp->tabh, tp->tabl, p);
     TcRedParams r{};
     r.ns = tp->ns;
@@ -1155,16 +1152,17 @@ static void tco_launch_back(const TcPlan* tp, const TcRowsCand& c, const KDev* k
     r.splits_b = c.splits;
     r.nkb_b = tp->nkb_b;
     r.Rb = tp->ttiles * TC_BM;
+    r.inv_b = 1.0 / (tp->sA * tp->sZ);
     r.kd = kd;
     r.Db = tp->Db;
     k_tc_opred<<<dim3((tp->maxng * 2 * tp->ns + 255) / 256, 1, nk), 256, 0, s>>>(r);
 }
 
 static void tco_launch_back_any(const TcPlan* tp, const TcRowsCand& c, const KDev* kd, int nk, cudaStream_t s,
-                                int kofs = 0) {
+                                int kofs = 0, int* flag = nullptr) {
     switch (tp->NTb) {
 #define RTD_TCO(n) \
-    case n: tco_launch_back<n>(tp, c, kd, nk, s, kofs); break;
+    case n: tco_launch_back<n>(tp, c, kd, nk, s, kofs, flag); break;
         RTD_TCO(16) RTD_TCO(32) RTD_TCO(48) RTD_TCO(64) RTD_TCO(96) RTD_TCO(128) RTD_TCO(160) RTD_TCO(192)
         RTD_TCO(224) RTD_TCO(256)
 #undef RTD_TCO
@@ -1266,7 +1264,7 @@ static int tco_tune(TcPlan* tp, std::vector<TcToepCand>& tc, std::vector<TcRowsC
 
 int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const int* const* glin_host,
                    const zd* const* at_dev, const zd* vtab, int nvt, int vt_center, const KDev* d_kd,
-                   cudaStream_t s, std::string* why) {
+                   int fmt, double sa, double st, cudaStream_t s, std::string* why) {
     *out = nullptr;
     if (!get_encode()) {
         *why = "the driver has no tensor-map encoder";
@@ -1278,6 +1276,15 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
     tp->ma = ma;
     tp->Dn = 2 * ns;
     tp->vt_center = vt_center;
+    tp->fmt = fmt;
+    if (!fmt) {
+        // fp16: the matching coefficients and the table scaled to ~2^14 at their
+        // largest entry, C (|c| <= 16) by 2^12 and Z (|z| <= 64) by 2^10
+        tp->sA = sa;
+        tp->sT = st;
+        tp->sC = 4096.0;
+        tp->sZ = 1024.0;
+    }
     for (int nt : TCO_NTS)
         if (nt >= tp->Dn) {
             tp->NT = nt;
@@ -1395,11 +1402,11 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
     cudaMemsetAsync(tp->ah, 0, nah * 2, s);
     cudaMemsetAsync(tp->al, 0, nah * 2, s);
     cudaMemsetAsync(tp->tflag, 0, sizeof(int), s);
-    if (nvt > 0) k_tc_split_table<<<(nvt + 255) / 256, 256, 0, s>>>(vtab, tp->tabs, nvt);
+    if (nvt > 0) k_tc_split_table<<<(nvt + 255) / 256, 256, 0, s>>>(vtab, tp->tabs, nvt, tp->fmt, tp->sT, tp->tflag);
     for (int k = 0; k < nk && ma > 0; ++k) {
         const size_t n = (size_t)ma * ng[k];
         k_tc_pack_at<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(at_dev[k], ng[k], ma, tp->Kp, tp->Mp, k, tp->ah,
-                                                                 tp->al);
+                                                                 tp->al, tp->fmt, tp->sA, tp->tflag);
     }
     int e = tc_tmap3(&tp->tbh, tp->bh, tp->Kp, tp->Rp, nk, tp->NT) | tc_tmap3(&tp->tbl, tp->bl, tp->Kp, tp->Rp, nk, tp->NT) |
             tc_tmap3(&tp->tah, tp->ah, tp->Kp, tp->Mp, nk, TC_BM) | tc_tmap3(&tp->tal, tp->al, tp->Kp, tp->Mp, nk, TC_BM);
@@ -1453,7 +1460,7 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
         for (int k = 0; k < nk; ++k) {
             const size_t n = (size_t)ma * ng[k];
             k_tc_pack_atb<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(at_dev[k], ng[k], ma, tp->Kpb, tp->ttiles * TC_BM,
-                                                                       k, tp->abh, tp->abl);
+                                                                       k, tp->abh, tp->abl, tp->fmt, tp->sA, tp->tflag);
         }
         e |= tc_tmap3(&tp->tzh, tp->zh, tp->Kpb, tp->Rpb, nk, tp->NTb) |
              tc_tmap3(&tp->tzl, tp->zl, tp->Kpb, tp->Rpb, nk, tp->NTb) |
@@ -1507,6 +1514,7 @@ static TcOpParams tco_rows_params(const TcPlan* tp, const StepArgs& a) {
     p.R = tp->Mp;
     p.S = tp->S_a;
     p.kofs = a.kofs;
+    p.fmt = tp->fmt;
     p.kd = a.kd;
     p.D = tp->Da;
     p.flag = a.flag;
@@ -1524,6 +1532,7 @@ static TcToepParams tco_toep_params(const TcPlan* tp, const StepArgs& a) {
     p.vt_center = tp->vt_center;
     p.SA = tp->SA;
     p.SB = tp->SB;
+    p.fmt = tp->fmt;
     p.kd = a.kd;
     p.tab = a.dv_on ? a.vsteps : tp->tabs;
     p.D = tp->Dt;
@@ -1533,7 +1542,7 @@ static TcToepParams tco_toep_params(const TcPlan* tp, const StepArgs& a) {
 
 void launch_tc_pack(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
     dim3 g((tp->ns * tp->maxng + 255) / 256, 1, a.nk);
-    k_tc_pack_c<<<g, 256, 0, s>>>(a.kd, tp->ns, tp->Kp, tp->Rp, tp->bh, tp->bl);
+    k_tc_pack_c<<<g, 256, 0, s>>>(a.kd, tp->ns, tp->Kp, tp->Rp, tp->bh, tp->bl, tp->fmt, tp->sC, a.flag);
 }
 
 void launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
@@ -1558,9 +1567,9 @@ bool tc_has_back(const TcPlan* tp) { return tp && tp->NTb > 0; }
 
 void launch_tc_back(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
     dim3 gz((2 * tp->ns * tp->ma + 255) / 256, 1, a.nk);
-    k_tc_pack_z<<<gz, 256, 0, s>>>(a.kd, tp->ns, tp->ma, tp->Kpb, tp->Rpb, tp->zh, tp->zl);
+    k_tc_pack_z<<<gz, 256, 0, s>>>(a.kd, tp->ns, tp->ma, tp->Kpb, tp->Rpb, tp->zh, tp->zl, tp->fmt, tp->sZ, a.flag);
     TcRowsCand c{tp->kbps_b, tp->splits_b, tp->S_b, tp->smem_b, 0.f};
-    tco_launch_back_any(tp, c, a.kd, a.nk, s, a.kofs);  // single-k calls: left operand of k-point kofs
+    tco_launch_back_any(tp, c, a.kd, a.nk, s, a.kofs, a.flag);  // single-k calls: left operand of k-point kofs
 }
 
 void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
@@ -1575,6 +1584,8 @@ void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
     p.Rt = tp->ttiles * TC_BM;
     p.Ra = tp->Mp;
     p.part = 0;
+    p.inv_t = 1.0 / (tp->sT * tp->sC);
+    p.inv_a = 1.0 / (tp->sA * tp->sC);
     p.kd = a.kd;
     p.Dt = tp->Dt;
     p.Da = tp->Da;
@@ -1593,3 +1604,6 @@ void tc_plan_info(const TcPlan* tp, int* v) {
     v[7] = (int)(tp->ms_t * 1e6f);  // ns
     v[8] = (int)(tp->ms_a * 1e6f);
 }
+
+double tc_table_scale(const TcPlan* tp) { return tp ? tp->sT : 1.0; }
+int tc_format(const TcPlan* tp) { return tp ? tp->fmt : 1; }

@@ -97,7 +97,8 @@ struct DevState {
     double cur_s;       // potential-change scale of the current step
     double cur_aa;      // |A|^2 / (2 c^2)
     int err;            // nonzero: a device iteration limit ran out
-    unsigned bar;       // arrival counter of the grid barrier (zeroed by k_hsub)
+    unsigned bar;       // arrival counter of the grid barrier (zeroed by k_hsub and k_finalize)
+    unsigned post_done; // blocks of k_post finished in this step (the last one finalises)
 };
 
 // Everything the step kernels need, passed by value
@@ -143,6 +144,8 @@ struct StepArgs {
     int kofs;                 // k-point of kd[0] (single-k operator calls), 0 in the step
     int tcback;               // the back-projection runs on the tensor cores (split-BF16 form)
     int at_n, at_maxm;        // atoms, and the largest local block m = N_A + n_lo
+    int tc_fmt;               // tensor-core operand format: 1 bf16, 0 fp16
+    double tc_st;             // scale of the split table (fp16 range)
 };
 #define POST_STRIDE 36        // part_post row: residual, J_sub (3), then theta^H theta~ (ns <= 4)
 
@@ -218,9 +221,13 @@ void launch_adj_jterm(const StepArgs& a, zd* lam, const zd* theta, const double*
 
 // ---- tensor-core split-BF16 operator (k_tc.cu)
 struct TcPlan;
+// fmt: 1 split-BF16, 0 split-FP16 (operands scaled by powers of two: sa for the
+// matching coefficients, st for the table, fixed scales for C and Z)
 int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const int* const* glin_host,
                    const zd* const* at_dev, const zd* vtab, int nvt, int vt_center, const KDev* d_kd,
-                   cudaStream_t s, std::string* why);
+                   int fmt, double sa, double st, cudaStream_t s, std::string* why);
+double tc_table_scale(const TcPlan* tp);
+int tc_format(const TcPlan* tp);
 void tc_plan_destroy(TcPlan* tp);
 // NT, 100 x generated stages + copied stages, K blocks per slice, slices, window, smem of the
 // interstitial launch, candidates tuned, tuned interstitial and matching-row times (ns)

@@ -21,7 +21,7 @@ ERRORS = {
     -5: "ERR_NONFINITE", -6: "ERR_OOM", -7: "ERR_CUDA", -8: "ERR_TIMEOUT", -9: "ERR_UNSUPPORTED",
 }
 PROP = {"chebyshev": 0, "eig": 1, "cn": 2}
-PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2}
+PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2, "fp16x3": 3}
 AUX = {"ritz": 0, "given": 1}
 
 EXPORTED = ["rttddft_default_options", "rttddft_setup", "rttddft_step", "rttddft_observables",

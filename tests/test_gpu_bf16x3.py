@@ -1,5 +1,6 @@
-"""The split-BF16 precision form (tensor-core interstitial convolution and
-matching-coefficient products) against the FP64 oracle.
+"""The split-BF16 and split-FP16 precision forms (tensor-core interstitial
+convolution, matching-coefficient products and back-projection) against the
+FP64 oracle.
 
 Error model: every bf16 hi/lo split product hi.hi + hi.lo + lo.hi carries a
 relative error of a few 2^-16 of sum |a||x| (the dropped lo.lo term and the
@@ -39,8 +40,14 @@ def ragged_cfg():
                        edir=(1.0, 0.0, 0.0))
 
 
+# (form, entrywise bound in units of (|H||x|), median bound): split-BF16 keeps
+# ~16 significant bits, split-FP16 ~22
+FORMS = [("bf16x3", 1e-4, 2.0 ** -13), ("fp16x3", 1e-5, 2.0 ** -19)]
+
+
+@pytest.mark.parametrize("form,tol,med", FORMS)
 @pytest.mark.parametrize("case", ["tiny400", "ragged", "free", "dv", "wide"])
-def test_operator_within_split_bound(case):
+def test_operator_within_split_bound(case, form, tol, med):
     rng = np.random.default_rng(3)
     dv = None
     if case in ("tiny400", "dv"):
@@ -52,9 +59,9 @@ def test_operator_within_split_bound(case):
         s = free_electron_system(n_g=50, n_s=2, n_aux=6)
     else:  # many states: several column tiles of the tensor-core output
         s = make_system(tiny_config(n_g=300, n_atoms=2, lmax=2, n_lo_per_atom=2, n_s=40, n_aux=64, seed=5))
-    ctx = Context(s, precision="bf16x3")
+    ctx = Context(s, precision=form)
     info = ctx.info()
-    assert info["precision"] == 2 and info["tc"]["tile_n"] >= 2 * int(s["n_s"])
+    assert info["precision"] == {"bf16x3": 2, "fp16x3": 3}[form] and info["tc"]["tile_n"] >= 2 * int(s["n_s"])
     if dv is not None:
         ctx.set_dv(dv)
     a_vec = np.array([0.3, -0.7, 1.1]) * 20.0
@@ -70,25 +77,42 @@ def test_operator_within_split_bound(case):
         mag_s = np.abs(ops["S"]) @ np.abs(x)
         eh = np.abs(hx - h @ x) / mag_h
         es = np.abs(sx - ops["S"] @ x) / mag_s
-        assert np.max(eh) < 1e-4, (k, np.max(eh))
-        assert np.max(es) < 1e-4, (k, np.max(es))
-        # far better than a single bf16 product (2^-8)
-        assert np.median(eh) < 2.0 ** -13
+        assert np.max(eh) < tol, (k, np.max(eh))
+        assert np.max(es) < tol, (k, np.max(es))
+        # far better than a single 16-bit product
+        assert np.median(eh) < med
     ctx.close()
 
 
-def test_step_error_per_observable_tiny400():
+@pytest.mark.parametrize("form,etol,jtol,ntol", [("bf16x3", 1e-4, 1e-3, 1e-4), ("fp16x3", 1e-5, 1e-4, 1e-5)])
+def test_step_error_per_observable_tiny400(form, etol, jtol, ntol):
     s = make_system("tiny400")
     a = pulse_samples(s, a0=5.0)
     r = Oracle(s).run(a, s["dt"])
-    ctx = Context(s, precision="bf16x3", graph_steps=10)
+    ctx = Context(s, precision=form, graph_steps=10)
     ctx.step(a)
     obs = ctx.observables()
     assert rel(obs["dmu"], r["dmu"]) < 1e-8
     assert rel(obs["j"], r["J"]) < 1e-10
-    assert rel(obs["energy"], r["E"]) < 1e-4
-    assert rel(obs["j_full"], r["J_full"]) < 1e-3
-    assert np.max(obs["norm_dev"]) < 1e-4
+    assert rel(obs["energy"], r["E"]) < etol
+    assert rel(obs["j_full"], r["J_full"]) < jtol
+    assert np.max(obs["norm_dev"]) < ntol
+    ctx.close()
+
+
+def test_fp16_range_violation_is_reported():
+    """C scaled by 2^12 must stay inside the fp16 range: a state with an
+    entry of 100 makes the step fail with ERR_NONFINITE, nothing silent."""
+    from paper_2403_04351_gb300 import RttddftError
+    s = make_system("tiny400")
+    ctx = Context(s, precision="fp16x3")
+    th = ctx.get_state(0) * 0.0
+    th[0, 0] = 1e3  # C = CC theta has entries far above 16
+    ctx.set_state(0, th)
+    with pytest.raises(RttddftError) as e:
+        ctx.step(pulse_samples(s, n_steps=2))
+        ctx.observables()
+    assert e.value.code == -5
     ctx.close()
 
 

@@ -55,7 +55,9 @@ struct rttddft_ctx {
     int* d_flag = nullptr;
     GemmDesc *gd_expand = nullptr, *gd_fwd = nullptr, *gd_proj = nullptr, *gd_g1 = nullptr,
              *gd_g2 = nullptr, *gd_evh = nullptr, *gd_evn = nullptr;
-    GemmDesc *gd_dvw = nullptr, *gd_dvg = nullptr, *gd_dvi = nullptr;
+    GemmDesc *gd_dvw = nullptr, *gd_dvg = nullptr, *gd_dvi = nullptr, *gd_dvi32 = nullptr;
+    zd* d_part_dv = nullptr;
+    int kc_dvi = 0;
     ToepDesc* td_dv = nullptr;
     zd** d_jac_mats = nullptr;
     double** d_jac_vals = nullptr;
@@ -254,6 +256,9 @@ static StepPlan make_plan(rttddft_ctx* ctx) {
     p.gd_dvw = ctx->gd_dvw;
     p.gd_dvg = ctx->gd_dvg;
     p.gd_dvi = ctx->gd_dvi;
+    p.gd_dvi32 = ctx->gd_dvi32;
+    p.part_dv = ctx->d_part_dv;
+    p.kc_dvi = ctx->kc_dvi;
     p.td_dv = ctx->td_dv;
     p.n_dvw = ctx->nk * ctx->at.n;
     p.maxm = ctx->maxm;
@@ -1510,10 +1515,36 @@ int rttddft_set_dv(rttddft_ctx* ctx, const double* dh, const double* dvtab) {
             ctx->gd_dvg = upload_descs(ctx, g);
             ctx->gd_dvi = upload_descs(ctx, gi);
             ctx->td_dv = dupload(ctx, td.data(), td.size());
+            if (ctx->tc) {
+                // tensor-core forms: the interstitial convolution on tcgen05, its
+                // projection CC_G^H T from the FP32 copy of CC in K slices of 256
+                std::vector<const zd*> cp(nk);
+                std::vector<int> nbv(nk), ngv(nk);
+                for (int k = 0; k < nk; ++k) {
+                    cp[k] = ctx->hkd[k].caux;
+                    nbv[k] = ctx->hkd[k].nb;
+                    ngv[k] = ctx->hkd[k].ng;
+                }
+                std::string why;
+                const int e = tc_dv_prepare(ctx->tc, cp.data(), nbv.data(), ngv.data(), naux, ctx->nvt,
+                                            ctx->stream, &why);
+                if (e) fail(ctx, e, why);
+                ctx->kc_dvi = 256;
+                size_t off = 0;
+                std::vector<GemmDesc> g32 = gi;
+                for (int k = 0; k < nk; ++k) {
+                    g32[k].A = ctx->hkd[k].caux32;
+                    g32[k].part_off = off;
+                    off += (size_t)((ctx->hkd[k].ng + 255) / 256) * naux * naux;
+                }
+                ctx->gd_dvi32 = upload_descs(ctx, g32);
+                ctx->d_part_dv = dalloc<zd>(ctx, off);
+            }
             CK(cudaMemcpy(ctx->d_kd, ctx->hkd.data(), nk * sizeof(KDev), cudaMemcpyHostToDevice));
         }
         if (at.n > 0) CK(cudaMemcpy(ctx->d_dh, dh, nblk * sizeof(zd), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->d_dvtab, dvtab, ctx->nvt * sizeof(zd), cudaMemcpyHostToDevice));
+        if (ctx->tc) tc_dv_set_table(ctx->tc, ctx->d_dvtab, ctx->nvt, ctx->stream);
         ctx->dv_set = true;
         // bound || CC^H dV_1 CC ||_F for the Chebyshev scaling (one evaluation with s = 1)
         {

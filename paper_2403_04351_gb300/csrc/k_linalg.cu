@@ -5,6 +5,8 @@
 // right-hand columns; these kernels keep every DFMA useful and spread the
 // work over all SMs (split-K where the output is small).  The FP32-storage
 // variants stream half the bytes and run on the FFMA pipe.
+#include <algorithm>
+
 #include "rtd.h"
 
 // ---------------------------------------------------------------- NN
@@ -15,9 +17,13 @@
 template <typename TA, typename TC, int NT>
 __global__ void __launch_bounds__(256) k_gemm_nn(const GemmDesc* __restrict__ descs, int N,
                                                  int kchunk, zd* __restrict__ part, int beta_add,
-                                                 const double* __restrict__ dscale) {
+                                                 const double* __restrict__ dscale, int ncg) {
     const GemmDesc d = descs[blockIdx.z];
-    const int m0 = blockIdx.x * 64;
+    // blockIdx.x = row tile + mtiles x column group: the column chunks of NT are
+    // spread over ncg groups of blocks
+    const int mtiles = (gridDim.x + ncg - 1) / ncg;
+    const int mt = blockIdx.x % mtiles, cg = blockIdx.x / mtiles;
+    const int m0 = mt * 64;
     const int k0 = blockIdx.y * kchunk;
     if (m0 >= d.M || k0 >= d.K) return;
     const int k1 = min(d.K, k0 + kchunk);
@@ -27,7 +33,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const GemmDesc* __restrict__ de
     const TA* __restrict__ A = (const TA*)d.A;
     __shared__ TC bs[64][NT];
     __shared__ TC red[3][64][NT];
-    for (int n0 = 0; n0 < N; n0 += NT) {
+    for (int n0 = cg * NT; n0 < N; n0 += NT * ncg) {
         TC acc[NT];
 #pragma unroll
         for (int j = 0; j < NT; ++j) acc[j] = Cx<TC>::zero();
@@ -82,16 +88,18 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const GemmDesc* __restrict__ de
 template <typename TA, typename TC, int NT, int RPW>
 __global__ void __launch_bounds__(256) k_gemm_cn(const GemmDesc* __restrict__ descs, int N,
                                                  int kchunk, zd* __restrict__ part, int beta_add,
-                                                 const double* __restrict__ dscale) {
+                                                 const double* __restrict__ dscale, int ncg) {
     const GemmDesc d = descs[blockIdx.z];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mb = blockIdx.x * 8 * RPW;
+    const int mtiles = (gridDim.x + ncg - 1) / ncg;
+    const int cg = blockIdx.x / mtiles;
+    const int mb = (blockIdx.x % mtiles) * 8 * RPW;
     const int k0 = blockIdx.y * kchunk;
     if (mb >= d.M || k0 >= d.K) return;
     const int k1 = min(d.K, k0 + kchunk);
     const int m0 = mb + warp * RPW;
     __shared__ TC bs[128][NT];
-    for (int n0 = 0; n0 < N; n0 += NT) {
+    for (int n0 = cg * NT; n0 < N; n0 += NT * ncg) {
         TC acc[RPW][NT];
 #pragma unroll
         for (int q = 0; q < RPW; ++q)
@@ -341,33 +349,46 @@ __global__ void k_split_reduce(const GemmDesc* __restrict__ descs, int N, int kc
     *c = beta_add ? zadd(*c, s) : s;
 }
 
+// column groups for the generic kernels: enough blocks to cover about two per
+// SM, at most one group per column chunk
+static int column_groups(int blocks, int chunks) {
+    int g = (2 * 152 + blocks - 1) / std::max(blocks, 1);
+    return std::max(1, std::min(g, chunks));
+}
+
 template <typename TA, typename TC>
 static void gemm_nn_t(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kchunk, zd* part,
                       int beta_add, const double* ds, cudaStream_t s) {
     if (nb <= 0 || maxM <= 0 || maxK <= 0 || N <= 0) return;
     if (kchunk <= 0) kchunk = maxK;
-    dim3 grid((maxM + 63) / 64, (maxK + kchunk - 1) / kchunk, nb);
+    const int NTb = N <= 2 ? 2 : (N <= 4 ? 4 : 8);
+    const int mt = (maxM + 63) / 64, ks = (maxK + kchunk - 1) / kchunk;
+    const int ncg = column_groups(mt * ks * nb, (N + NTb - 1) / NTb);
+    dim3 grid(mt * ncg, ks, nb);
     if (N <= 2)
-        k_gemm_nn<TA, TC, 2><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+        k_gemm_nn<TA, TC, 2><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds, ncg);
     else if (N <= 4)
-        k_gemm_nn<TA, TC, 4><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+        k_gemm_nn<TA, TC, 4><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds, ncg);
     else
-        k_gemm_nn<TA, TC, 8><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+        k_gemm_nn<TA, TC, 8><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds, ncg);
 }
 template <typename TA, typename TC>
 static void gemm_cn_t(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kchunk, zd* part,
                       int beta_add, const double* ds, cudaStream_t s) {
     if (nb <= 0 || maxM <= 0 || maxK <= 0 || N <= 0) return;
     if (kchunk <= 0) kchunk = maxK;
+    const int ks = (maxK + kchunk - 1) / kchunk;
     if (N <= 2) {
-        dim3 grid((maxM + 31) / 32, (maxK + kchunk - 1) / kchunk, nb);
-        k_gemm_cn<TA, TC, 2, 4><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+        dim3 grid((maxM + 31) / 32, ks, nb);
+        k_gemm_cn<TA, TC, 2, 4><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds, 1);
     } else if (N <= 4) {
-        dim3 grid((maxM + 15) / 16, (maxK + kchunk - 1) / kchunk, nb);
-        k_gemm_cn<TA, TC, 4, 2><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+        dim3 grid((maxM + 15) / 16, ks, nb);
+        k_gemm_cn<TA, TC, 4, 2><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds, 1);
     } else {
-        dim3 grid((maxM + 7) / 8, (maxK + kchunk - 1) / kchunk, nb);
-        k_gemm_cn<TA, TC, 8, 1><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds);
+        const int mt = (maxM + 7) / 8;
+        const int ncg = column_groups(mt * ks * nb, (N + 7) / 8);
+        dim3 grid(mt * ncg, ks, nb);
+        k_gemm_cn<TA, TC, 8, 1><<<grid, 256, 0, s>>>(d, N, kchunk, part, beta_add, ds, ncg);
     }
 }
 

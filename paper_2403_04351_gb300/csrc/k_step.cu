@@ -1489,6 +1489,30 @@ void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, 
     }
 }
 
+// Eq. v_MT and Eq. v_interstitial rebuilt from the scaled blocks:
+// dVV = L^H (s dh) L + CC_G^H (s dV~ * CC_G).  In the tensor-core forms the
+// interstitial convolution runs on tcgen05 (split-BF16) and its projection in
+// FP32; otherwise both in FP64.  Returns the launches.
+static int launch_dv_rebuild(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr) {
+    launch_gemm_nn(p.gd_dvw, p.n_dvw, p.maxm, p.maxm, a.naux, 0, nullptr, 0, false, &a.st->cur_s, s);
+    mark(tr, "dv_mt_blocks", s);
+    launch_gemm_cn(p.gd_dvg, a.nk, a.naux, a.lrows, a.naux, 0, nullptr, 0, false, nullptr, s);
+    mark(tr, "dv_mt_project", s);
+    if (a.prec >= 2 && p.tc && tc_dv_ready(p.tc) && p.gd_dvi32) {
+        launch_tc_dv_toeplitz(p.tc, a, p.td_dv, s);
+        mark(tr, "tc_dv_interstitial", s);
+        launch_gemm_cn(p.gd_dvi32, a.nk, a.naux, p.maxng, a.naux, p.kc_dvi, p.part_dv, 0, true, nullptr, s);
+        launch_split_reduce(p.gd_dvi32, a.nk, a.naux, a.naux, p.kc_dvi, p.part_dv, 1, s);
+        mark(tr, "dv_interstitial_project", s);
+        return 4 + 2 * tc_dv_tiles(p.tc);
+    }
+    launch_toeplitz(a.kd, p.td_dv, a.nk, p.maxng, a.naux, a.dvtab, a.vt_center, 0, 0, &a.st->cur_s, s);
+    mark(tr, "dv_interstitial_toeplitz", s);
+    launch_gemm_cn(p.gd_dvi, a.nk, a.naux, p.maxng, a.naux, 0, nullptr, 1, false, nullptr, s);
+    mark(tr, "dv_interstitial_project", s);
+    return 4;
+}
+
 void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlaunch, TraceHook* tr) {
     int nl = 0;
     const bool f32 = a.prec >= 1;
@@ -1500,17 +1524,7 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
         // dVV = L^H (s dh) L + CC_G^H (s dV~ * CC_G)
         k_vstep<<<(a.nvt + 255) / 256, 256, 0, s>>>(a);
         mark(tr, "dv_table", s);
-        launch_gemm_nn(p.gd_dvw, p.n_dvw, p.maxm, p.maxm, a.naux, 0, nullptr, 0, false,
-                       &a.st->cur_s, s);
-        mark(tr, "dv_mt_blocks", s);
-        launch_gemm_cn(p.gd_dvg, a.nk, a.naux, a.lrows, a.naux, 0, nullptr, 0, false, nullptr, s);
-        mark(tr, "dv_mt_project", s);
-        launch_toeplitz(a.kd, p.td_dv, a.nk, p.maxng, a.naux, a.dvtab, a.vt_center, 0, 0,
-                        &a.st->cur_s, s);
-        mark(tr, "dv_interstitial_toeplitz", s);
-        launch_gemm_cn(p.gd_dvi, a.nk, a.naux, p.maxng, a.naux, 0, nullptr, 1, false, nullptr, s);
-        mark(tr, "dv_interstitial_project", s);
-        nl += 6;
+        nl += 2 + launch_dv_rebuild(a, p, s, tr);
     }
     if (!(a.prop != 1 && a.coop_grid > 0 && cheb_direct(a))) {
         k_hsub<<<dim3((nn + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
@@ -1619,10 +1633,7 @@ void launch_propagate_only(const StepArgs& a, const StepPlan& p, int cstep, cuda
     if (a.dv_on) {
         k_set_cur<<<1, 1, 0, s>>>(a);
         k_vstep<<<(a.nvt + 255) / 256, 256, 0, s>>>(a);
-        launch_gemm_nn(p.gd_dvw, p.n_dvw, p.maxm, p.maxm, a.naux, 0, nullptr, 0, false, &a.st->cur_s, s);
-        launch_gemm_cn(p.gd_dvg, a.nk, a.naux, a.lrows, a.naux, 0, nullptr, 0, false, nullptr, s);
-        launch_toeplitz(a.kd, p.td_dv, a.nk, p.maxng, a.naux, a.dvtab, a.vt_center, 0, 0, &a.st->cur_s, s);
-        launch_gemm_cn(p.gd_dvi, a.nk, a.naux, p.maxng, a.naux, 0, nullptr, 1, false, nullptr, s);
+        launch_dv_rebuild(a, p, s, nullptr);
     }
     k_hsub<<<dim3((a.naux * a.naux + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
     dim3 g(a.naux, 1, a.nk);
@@ -1639,10 +1650,7 @@ void launch_hsub_only(const StepArgs& a, const StepPlan& p, int cstep, cudaStrea
     k_set_cstep<<<1, 1, 0, s>>>(a.st, cstep);
     if (a.dv_on) {
         k_set_cur<<<1, 1, 0, s>>>(a);
-        launch_gemm_nn(p.gd_dvw, p.n_dvw, p.maxm, p.maxm, a.naux, 0, nullptr, 0, false, &a.st->cur_s, s);
-        launch_gemm_cn(p.gd_dvg, a.nk, a.naux, a.lrows, a.naux, 0, nullptr, 0, false, nullptr, s);
-        launch_toeplitz(a.kd, p.td_dv, a.nk, p.maxng, a.naux, a.dvtab, a.vt_center, 0, 0, &a.st->cur_s, s);
-        launch_gemm_cn(p.gd_dvi, a.nk, a.naux, p.maxng, a.naux, 0, nullptr, 1, false, nullptr, s);
+        launch_dv_rebuild(a, p, s, nullptr);
     }
     k_hsub<<<dim3((a.naux * a.naux + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
 }

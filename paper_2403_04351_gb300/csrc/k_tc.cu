@@ -568,7 +568,8 @@ __device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinter
 #define TCT_MAXSB 16
 struct TcToepParams {
     int nk, Dn, kbps, splits, ttiles, wcap, vt_center, SA, SB;
-    int fmt;  // operand format: 1 bf16, 0 fp16
+    int fmt;    // operand format: 1 bf16, 0 fp16
+    int brow0;  // first row of the right operand's tile (column tiles of wide products)
     const KDev* kd;
     const uint2* tab;  // pre-split table
     float* D;          // [nk][splits][ttiles * 128][Dn]
@@ -657,8 +658,8 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
                 const int s = j % SB, kx = (kb0 + j) * TC_BK;
                 unsigned char* st = ringB + (size_t)s * 2 * B_BYTES;
                 mbar_expect_tx(&fullB[s], 2 * B_BYTES);
-                tma_load_3d(st, &tmBh, kx, 0, k, &fullB[s]);
-                tma_load_3d(st + B_BYTES, &tmBl, kx, 0, k, &fullB[s]);
+                tma_load_3d(st, &tmBh, kx, p.brow0, k, &fullB[s]);
+                tma_load_3d(st + B_BYTES, &tmBl, kx, p.brow0, k, &fullB[s]);
                 issued = j + 1;
             };
             for (int j = 0; j < min(nk, SB); ++j) loadB(j);
@@ -961,6 +962,14 @@ struct TcPlan {
     int* tflag = nullptr;   // error flag of the tuning launches
     float ms_t = 0.f, ms_a = 0.f;  // tuned launch times
     int ncand = 0;
+    // potential-change rebuild T = dV~ * CC_G (Eq. v_interstitial), N_aux columns in
+    // tiles of 128 complex columns, split-BF16, table gathered through L2
+    int dv_ready = 0, naux = 0, dv_tiles = 0, dv_kbps = 0, dv_splits = 0;
+    size_t dv_smem = 0;
+    CUtensorMap tch, tcl;
+    unsigned short *cch = nullptr, *ccl = nullptr;
+    uint2* dvtabs = nullptr;
+    float* Dd = nullptr;
     // back-projection Y_G = A^H [hQ | oQ]: rows G, K over the matching rows
     int NTb = 0, Dnb = 0, nkb_b = 0, Kpb = 0, Rpb = 0, S_b = 0, kbps_b = 0, splits_b = 0;
     size_t smem_b = 0;
@@ -1023,6 +1032,10 @@ void tc_plan_destroy(TcPlan* tp) {
     cudaFree(tp->Da);
     cudaFree(tp->tabs);
     cudaFree(tp->tflag);
+    cudaFree(tp->cch);
+    cudaFree(tp->ccl);
+    cudaFree(tp->dvtabs);
+    cudaFree(tp->Dd);
     cudaFree(tp->zh);
     cudaFree(tp->zl);
     cudaFree(tp->abh);
@@ -1607,3 +1620,134 @@ void tc_plan_info(const TcPlan* tp, int* v) {
 
 double tc_table_scale(const TcPlan* tp) { return tp ? tp->sT : 1.0; }
 int tc_format(const TcPlan* tp) { return tp ? tp->fmt : 1; }
+
+// ------------------------------------------------------------ potential-change rebuild
+// CC_G packed per column tile: rows [j NTV, j NTV + h_j) hold [Re CC | -Im CC] of the
+// tile's h_j columns, rows [j NTV + h_j, j NTV + 2 h_j) hold [Im CC | Re CC].
+#define TC_DV_NT 256
+__global__ void k_tc_pack_cc(const zd* __restrict__ caux, int nb, int ng, int naux, int Kp, int rows, int k,
+                             unsigned short* __restrict__ bh, unsigned short* __restrict__ bl, int* flag) {
+    const size_t e = (size_t)blockIdx.x * 256 + threadIdx.x;
+    if (e >= (size_t)naux * ng) return;
+    const int gp = (int)(e % ng), col = (int)(e / ng);
+    const int j = col / (TC_DV_NT / 2), cl = col % (TC_DV_NT / 2);
+    const int h = min(TC_DV_NT / 2, naux - j * (TC_DV_NT / 2));
+    const zd c = caux[gp + (size_t)col * nb];
+    const int kb = gp >> 5, o = gp & 31;
+    const size_t re_row = ((size_t)k * rows + (size_t)j * TC_DV_NT + cl) * Kp + (size_t)kb * 64;
+    const size_t im_row = ((size_t)k * rows + (size_t)j * TC_DV_NT + h + cl) * Kp + (size_t)kb * 64;
+    put16(c.x, 1, 1.0, bh, bl, re_row + o, flag);
+    put16(c.x, 1, 1.0, bh, bl, im_row + 32 + o, flag);
+    put16(c.y, 1, 1.0, bh, bl, im_row + o, flag);
+    put16(-c.y, 1, 1.0, bh, bl, re_row + 32 + o, flag);
+}
+
+// T[G + (c0 + c) ng] = s sum over slices (tile of h columns); T is the per-k
+// buffer of the descriptor's B operand (dv[k].X of the Toeplitz descriptor)
+struct TcDvRedParams {
+    int splits, kbps, Rt, h, c0;
+    const KDev* kd;
+    const ToepDesc* td;
+    const float* D;
+    const DevState* st;
+};
+__global__ void k_tc_dvred(TcDvRedParams p) {
+    const int k = blockIdx.z;
+    const KDev& K = p.kd[k];
+    const int ng = K.ng, nkb = (ng + 31) >> 5;
+    const int e = blockIdx.x * 256 + threadIdx.x;
+    if (e >= ng * p.h) return;
+    const int g = e % ng, c = e / ng;
+    const int nsp = min(p.splits, (nkb + p.kbps - 1) / p.kbps);
+    double re = 0.0, im = 0.0;
+    tc_sum_slices(p.D + ((size_t)k * p.splits * p.Rt + g) * TC_DV_NT, (size_t)p.Rt * TC_DV_NT, nsp, c, p.h, re, im);
+    const double sc = p.st->cur_s;
+    p.td[k].Y[g + (size_t)(p.c0 + c) * ng] = zmk(re * sc, im * sc);
+}
+
+// Set-up of the rebuild operands (at the first rttddft_set_dv): CC_G packed,
+// the dV~ table pre-split, the partial-output buffer.
+int tc_dv_prepare(TcPlan* tp, const zd* const* caux_dev, const int* nb, const int* ng, int naux, int nvt,
+                  cudaStream_t s, std::string* why) {
+    if (tp->dv_ready) return RTTDDFT_OK;
+    tp->naux = naux;
+    tp->dv_tiles = (naux + TC_DV_NT / 2 - 1) / (TC_DV_NT / 2);
+    const int nkb = tp->Kp / TC_BK;
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int sp = std::max(1, std::min(nkb, (2 * nsm + tp->ttiles * tp->nk - 1) / (tp->ttiles * tp->nk)));
+    tp->dv_kbps = (nkb + sp - 1) / sp;
+    tp->dv_splits = (nkb + tp->dv_kbps - 1) / tp->dv_kbps;
+    tp->dv_smem = 1024 + (size_t)2 * 4 * TC_BM * TC_BK + (size_t)2 * 4 * TC_DV_NT * TC_BK + (size_t)tp->dv_kbps * 128;
+    const int rows = tp->dv_tiles * TC_DV_NT;
+    const size_t ncc = (size_t)tp->nk * rows * tp->Kp;
+    const size_t nd = (size_t)tp->nk * tp->dv_splits * tp->ttiles * TC_BM * TC_DV_NT;
+    if (cudaMalloc(&tp->cch, ncc * 2) != cudaSuccess || cudaMalloc(&tp->ccl, ncc * 2) != cudaSuccess ||
+        cudaMalloc(&tp->dvtabs, (size_t)std::max(1, nvt) * sizeof(uint2)) != cudaSuccess ||
+        cudaMalloc(&tp->Dd, nd * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        *why = "out of device memory for the potential-change operands";
+        return RTTDDFT_ERR_OOM;
+    }
+    cudaMemsetAsync(tp->cch, 0, ncc * 2, s);
+    cudaMemsetAsync(tp->ccl, 0, ncc * 2, s);
+    for (int k = 0; k < tp->nk; ++k) {
+        const size_t n = (size_t)naux * ng[k];
+        k_tc_pack_cc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(caux_dev[k], nb[k], ng[k], naux, tp->Kp, rows, k,
+                                                                 tp->cch, tp->ccl, tp->tflag);
+    }
+    int e = tc_tmap3(&tp->tch, tp->cch, tp->Kp, rows, tp->nk, TC_DV_NT) |
+            tc_tmap3(&tp->tcl, tp->ccl, tp->Kp, rows, tp->nk, TC_DV_NT);
+    const cudaError_t ce = cudaFuncSetAttribute(k_tc_toep<TC_DV_NT, true>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp->dv_smem);
+    if (e || ce != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        *why = "potential-change operand set-up failed";
+        return RTTDDFT_ERR_CUDA;
+    }
+    tp->dv_ready = 1;
+    return RTTDDFT_OK;
+}
+
+// the pre-split dV~ table (every rttddft_set_dv)
+void tc_dv_set_table(TcPlan* tp, const zd* dvtab, int nvt, cudaStream_t s) {
+    if (nvt > 0) k_tc_split_table<<<(nvt + 255) / 256, 256, 0, s>>>(dvtab, tp->dvtabs, nvt, 1, 1.0, tp->tflag);
+}
+
+bool tc_dv_ready(const TcPlan* tp) { return tp && tp->dv_ready; }
+int tc_dv_tiles(const TcPlan* tp) { return tp ? tp->dv_tiles : 0; }
+
+// T = s dV~ * CC_G for every column tile (into the Toeplitz descriptors' Y)
+void launch_tc_dv_toeplitz(const TcPlan* tp, const StepArgs& a, const ToepDesc* td, cudaStream_t s) {
+    TcToepParams p{};
+    p.nk = a.nk;
+    p.Dn = TC_DV_NT;
+    p.kbps = tp->dv_kbps;
+    p.splits = tp->dv_splits;
+    p.ttiles = tp->ttiles;
+    p.wcap = 0;
+    p.vt_center = tp->vt_center;
+    p.SA = 2;
+    p.SB = 2;
+    p.fmt = 1;
+    p.kd = a.kd;
+    p.tab = tp->dvtabs;
+    p.D = tp->Dd;
+    p.flag = a.flag;
+    for (int j = 0; j < tp->dv_tiles; ++j) {
+        p.brow0 = j * TC_DV_NT;
+        k_tc_toep<TC_DV_NT, true><<<dim3(tp->ttiles, tp->dv_splits, a.nk), TCO_THREADS, tp->dv_smem, s>>>(tp->tch,
+                                                                                                         tp->tcl, p);
+        TcDvRedParams r{};
+        r.splits = tp->dv_splits;
+        r.kbps = tp->dv_kbps;
+        r.Rt = tp->ttiles * TC_BM;
+        r.c0 = j * (TC_DV_NT / 2);
+        r.h = std::min(TC_DV_NT / 2, tp->naux - r.c0);
+        r.kd = a.kd;
+        r.td = td;
+        r.D = tp->Dd;
+        r.st = a.st;
+        k_tc_dvred<<<dim3((tp->maxng * r.h + 255) / 256, 1, a.nk), 256, 0, s>>>(r);
+    }
+}

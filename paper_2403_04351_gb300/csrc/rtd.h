@@ -173,6 +173,9 @@ struct StepPlan {
     int kc_fwd, kc_proj, kc_expand;
     // potential change (a2)
     const GemmDesc *gd_dvw, *gd_dvg, *gd_dvi;   // W = dh L, dV = L^H W, dV += C_G^H T
+    const GemmDesc* gd_dvi32;                    // dV += C_G^H T with FP32 C_G (tensor-core forms)
+    zd* part_dv;                                 // its split-K partials
+    int kc_dvi;
     const ToepDesc* td_dv;                       // T = dV~ C_G
     int n_dvw;                                   // entries of gd_dvw (nk * atoms)
     int maxm;
@@ -236,6 +239,12 @@ void launch_tc_pack(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
 void launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
 void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
 bool tc_has_back(const TcPlan* tp);  // the back-projection runs on the tensor cores (4 N_s <= 256)
+int tc_dv_prepare(TcPlan* tp, const zd* const* caux_dev, const int* nb, const int* ng, int naux, int nvt,
+                  cudaStream_t s, std::string* why);
+void tc_dv_set_table(TcPlan* tp, const zd* dvtab, int nvt, cudaStream_t s);
+bool tc_dv_ready(const TcPlan* tp);
+int tc_dv_tiles(const TcPlan* tp);
+void launch_tc_dv_toeplitz(const TcPlan* tp, const StepArgs& a, const ToepDesc* td, cudaStream_t s);
 void launch_tc_back(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
 // ---- tensor-core split-BF16 complex GEMM (k_tc.cu); returns an RTTDDFT_* code
 int tc_zgemm(int opA, int M, int N, int K, const zd* A, int lda, const zd* X, int ldx, zd* C, int ldc,

@@ -686,10 +686,10 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
         ctx->d_flag = dalloc<int>(ctx, 1);
         ctx->d_rec = dalloc<double>(ctx, (size_t)o->max_record * RTD_REC_STRIDE);
         ctx->d_lam = dalloc<double>(ctx, LAM_N * (size_t)nk);
-        ctx->max_nback = (ctx->maxng + BT - 1) / BT;
+        ctx->max_nback = (ctx->maxng + BKB - 1) / BKB;
         {
             // split the G' sum of the interstitial term so that ~4 blocks per SM work
-            const int tiles = ctx->max_nback;
+            const int tiles = (ctx->maxng + BT - 1) / BT;
             int nseg = (4 * 152 + tiles * nk - 1) / (tiles * nk);
             nseg = std::max(1, std::min(nseg, tiles));
             ctx->segw = ((tiles + nseg - 1) / nseg) * BT;

@@ -739,12 +739,12 @@ __global__ void __launch_bounds__(BT) k_toep_seg(StepArgs a, int n0, int slot0) 
 // summed in a fixed slot order.  The block adds its rows' f-weighted shares of
 // Re c^H HC, Re c^H SC and sum (G+k)|c|^2 into its slot of part_full.
 template <int NT>
-__global__ void __launch_bounds__(BT) k_back(StepArgs a, int n0) {
-    __shared__ double rs[BT / 32][5];
+__global__ void __launch_bounds__(BKB) k_back(StepArgs a, int n0) {
+    __shared__ double rs[8];
     const int k = blockIdx.z;
     const KDev& K = a.kd[k];
     const int ng = K.ng;
-    const int g0 = blockIdx.x * BT;
+    const int g0 = blockIdx.x * BKB;
     if (g0 >= ng) return;
     const int tid = threadIdx.x;
     const int g = g0 + tid;
@@ -801,18 +801,14 @@ __global__ void __launch_bounds__(BT) k_back(StepArgs a, int n0) {
             red[4] += q[2] * w;
         }
     }
-    const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        const double v = warp_sum(red[q]);
-        if (lane == 0) rs[warp][q] = v;
-    }
-    __syncthreads();
+    // one warp: halving sum of the five shares
+    const int lane = tid & 31;
+    double v[8] = {red[0], red[1], red[2], red[3], red[4], 0.0, 0.0, 0.0};
+    warp_sum_store<double, 8>(v, lane, rs);
+    __syncwarp();
     if (tid < 5) {
-        double v = 0.0;
-        for (int w = 0; w < BT / 32; ++w) v += rs[w][tid];
         double* pf = a.part_full + ((size_t)k * a.max_nback + blockIdx.x) * 5 + tid;
-        *pf = (n0 == 0) ? v : *pf + v;
+        *pf = (n0 == 0) ? rs[tid] : *pf + rs[tid];
     }
 }
 
@@ -864,6 +860,9 @@ __global__ void __launch_bounds__(128) k_post(StepArgs a, int do_theta, int do_j
     if (threadIdx.x == 0) a.st->post_done = 0u;
 }
 __device__ void post_body(const StepArgs& a, int do_theta, int do_j) {
+    // halving warp sums over up to 4 columns at a time (each warp-wide FP64 add
+    // is costly on GB300); per-warp scratch for the sums
+    __shared__ double ws[4][8];
     const int k = blockIdx.z;
     const KDev& K = a.kd[k];
     const int n = a.naux, ns = a.ns;
@@ -877,14 +876,28 @@ __device__ void post_body(const StepArgs& a, int do_theta, int do_j) {
         const int nsp = (d.K + a.kc_proj - 1) / a.kc_proj;
         double res = 0.0;
         zd mine = zmk(0.0, 0.0);
-        for (int c = 0; c < ns; ++c) {
-            zd t = zmk(0.0, 0.0);
-            for (int sp = lane; sp < nsp; sp += 32) t = zadd(t, a.part_proj[d.part_off + ((size_t)sp * ns + c) * n + i]);
-            t = warp_zsum(t);
-            if (lane == 0) K.theta_t[i + (size_t)c * n] = t;
-            const zd dd = zsub(t, K.theta[i + (size_t)c * n]);
-            res = fmax(res, dd.x * dd.x + dd.y * dd.y);
-            if (lane == c) mine = t;
+        for (int c0 = 0; c0 < ns; c0 += 4) {
+            double v[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                zd t = zmk(0.0, 0.0);
+                if (c0 + q < ns)
+                    for (int sp = lane; sp < nsp; sp += 32)
+                        t = zadd(t, a.part_proj[d.part_off + ((size_t)sp * ns + c0 + q) * n + i]);
+                v[2 * q] = t.x;
+                v[2 * q + 1] = t.y;
+            }
+            warp_sum_store<double, 8>(v, lane, ws[warp]);
+            __syncwarp();
+            for (int q = 0; q < 4 && c0 + q < ns; ++q) {
+                const int c = c0 + q;
+                const zd t = zmk(ws[warp][2 * q], ws[warp][2 * q + 1]);
+                if (lane == 0) K.theta_t[i + (size_t)c * n] = t;
+                const zd dd = zsub(t, K.theta[i + (size_t)c * n]);
+                res = fmax(res, dd.x * dd.x + dd.y * dd.y);
+                if (lane == c) mine = t;
+            }
+            __syncwarp();
         }
         res = sqrt(res);
         if (ns <= 4) {
@@ -904,13 +917,28 @@ __device__ void post_body(const StepArgs& a, int do_theta, int do_j) {
         const zd* __restrict__ P = K.psub + (size_t)l * n * n + (size_t)i * n;
         const double al = a.st->cur_a[l] * a.inv_c;
         double jl = 0.0;
-        for (int c = 0; c < ns; ++c) {
-            const zd* th = K.theta + (size_t)c * n;
-            zd v = zmk(0.0, 0.0);
-            for (int j = lane; j < n; j += 32) zfmac(v, P[j], th[j]);
-            v = warp_zsum(v);
-            const zd ti = th[i];
-            jl += a.occ[c] * (ti.x * (v.x + al * ti.x) + ti.y * (v.y + al * ti.y));
+        for (int c0 = 0; c0 < ns; c0 += 4) {
+            double v[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                zd t = zmk(0.0, 0.0);
+                if (c0 + q < ns) {
+                    const zd* th = K.theta + (size_t)(c0 + q) * n;
+                    for (int j = lane; j < n; j += 32) zfmac(t, P[j], th[j]);
+                }
+                v[2 * q] = t.x;
+                v[2 * q + 1] = t.y;
+            }
+            warp_sum_store<double, 8>(v, lane, ws[warp]);
+            __syncwarp();
+            if (lane == 0) {
+                for (int q = 0; q < 4 && c0 + q < ns; ++q) {
+                    const int c = c0 + q;
+                    const zd ti = K.theta[i + (size_t)c * n];
+                    jl += a.occ[c] * (ti.x * (ws[warp][2 * q] + al * ti.x) + ti.y * (ws[warp][2 * q + 1] + al * ti.y));
+                }
+            }
+            __syncwarp();
         }
         if (lane == 0) prow[1 + l] = jl;
     }
@@ -954,7 +982,7 @@ __device__ void finalize_body(const StepArgs& a, int set_gs) {
     for (int k = 0; k < a.nk; ++k) {
         const KDev& K = a.kd[k];
         const double w = a.wk[k];
-        const int nback = (K.ng + BT - 1) / BT;
+        const int nback = (K.ng + BKB - 1) / BKB;
         for (int i = tid; i < n; i += blockDim.x) {
             const double* p = a.part_post + ((size_t)k * n + i) * POST_STRIDE;
             v[0] += w * __ldcg(p + 1);
@@ -1388,13 +1416,13 @@ static void back_launch(const StepArgs& a, int maxng, cudaStream_t s, TraceHook*
     const int slot0 = (a.prec >= 2) ? a.nseg : 0;
     // with the back-projection on the tensor cores too, no slot kernel runs
     dim3 gt((maxng + BT - 1) / BT, a.tcback ? 0 : a.nslot - slot0, a.nk);
-    dim3 gb((maxng + BT - 1) / BT, 1, a.nk);
+    dim3 gb((maxng + BKB - 1) / BKB, 1, a.nk);
     for (int n0 = 0; n0 < a.ns; n0 += NT) {
         if (gt.y > 0) {
             k_toep_seg<TA, TT, TC, NT><<<gt, BT, sm, s>>>(a, n0, slot0);
             mark(tr, slot0 ? "backprojection" : "toeplitz_and_backprojection", s);
         }
-        k_back<NT><<<gb, BT, 0, s>>>(a, n0);
+        k_back<NT><<<gb, BKB, 0, s>>>(a, n0);
         mark(tr, "back_finish", s);
     }
 }
@@ -1573,9 +1601,9 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
     // theta~ = CC^H (S C): split-K partials, finished per row in k_post
     launch_gemm_cn(p.gd_proj, a.nk, a.naux, p.maxnb, a.ns, p.kc_proj, p.part, 0, f32, nullptr, s);
     mark(tr, "gemm_project", s);
-    // without reprojection, and with theta^H theta~ summed from the post rows
-    // (N_s <= 4), the last post block also finalises the step
-    const bool merged = !a.reproject && a.ns <= 4;
+    // the finalize stays a separate launch (merging it into the last post block
+    // measured slower: the last block runs it with fewer threads)
+    const bool merged = false;
     {
         dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
         k_post<<<g, 128, 0, s>>>(a, 1, a.reproject ? 0 : 1, merged ? 1 : 0);

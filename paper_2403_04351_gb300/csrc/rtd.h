@@ -10,7 +10,8 @@
 #define RTD_MAX_ATOMS 64
 #define RTD_MAX_TERMS 512
 #define RTD_REC_STRIDE 16  // doubles per step record
-#define BT 128            // plane-wave rows (and G' columns) per tile of the back kernel
+#define BT 128            // plane-wave rows (and G' columns) per tile of the slot kernels
+#define BKB 32            // plane-wave rows per block of the [HC | SC] row kernel k_back
 #define LAM_N 8           // doubles per k-point of the Chebyshev scaling record
 
 // Record fields (offsets within one record)

@@ -34,6 +34,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# precision forms timed beside the headline one ("+fft": FFT route of the interstitial sum)
+FORMS = ("fp64", "fp32", "bf16x3", "fp16x3", "fp64+fft", "fp32+fft")
 METRIC = "state*steps/sec per GB300, plain FP64 vs split-precision/batched at stated error"
 UNIT = "state*steps/s"
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; the profiling recipe's table)
@@ -65,7 +67,7 @@ def _bf16_peak():
 
 def _src_hash():
     h = hashlib.sha256()
-    for f in ("k_linalg.cu", "k_step.cu", "k_tc.cu", "common.cuh", "rtd.h"):
+    for f in ("k_linalg.cu", "k_step.cu", "k_tc.cu", "k_fft.cu", "common.cuh", "rtd.h"):
         with open(os.path.join(ROOT, "paper_2403_04351_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -141,6 +143,9 @@ def algorithmic_work(name, sysd, prec, nterms=1):
         if name == "toeplitz_and_backprojection":
             fl += 8 * ns * (ng * ng + 2 * ng * ma)
             by += ma * ng * cb + ng * ns * 16 * 2
+        elif name == "backprojection":
+            fl += 8 * ns * 2 * ng * ma
+            by += ma * ng * cb + ng * ns * 16 * 2
         elif name == "tc_interstitial_and_forward":
             # split-BF16: three bf16 products per complex multiply-add
             fl += 3 * 8 * ns * (ng * ng + ng * ma)
@@ -158,10 +163,47 @@ def algorithmic_work(name, sysd, prec, nterms=1):
             terms = 1 if name == "chebyshev_term" else max(1, nterms - 1)
             fl += terms * 8 * naux * naux * ns
             by += terms * naux * naux * 16
+        elif name == "fft_interstitial":
+            pass  # counted once over all k below
         elif name == "local_mt":
             m = (ma + nlo)
             fl += 8 * 5 * ns * m * m / max(1, int(sysd["n_atoms"]))
             by += 5 * m * m * 16 / max(1, int(sysd["n_atoms"]))
+    if name == "fft_interstitial":
+        fl, by = fft_work(sysd)
+    return fl, by
+
+
+def _smooth(n):
+    m = n
+    while True:
+        r = m
+        for p in (2, 3, 5):
+            while r % p == 0:
+                r //= p
+        if r == 1:
+            return m
+        m += 1
+
+
+def fft_work(sysd):
+    """(flops, bytes) of the pruned FFT convolution of all k-points and
+    states: 5 L log2 L flops per 1-D transform of L points (the usual count),
+    6 per grid point for the product with v(r); bytes: the grid buffers read
+    and written once per pass (they stay in L2 at these sizes)."""
+    import math
+    ns = int(sysd["n_s"])
+    F = [_smooth(int(v)) for v in sysd["vt_dim"]]
+    f1 = lambda L: 5.0 * L * math.log2(L)
+    fl = by = 0.0
+    for gi in sysd["g_int"]:
+        gi = np.asarray(gi)
+        nline = len({(int(a), int(b)) for a, b in gi[:, :2]})
+        nplane = len(set(int(a) for a in gi[:, 0]))
+        per = (2 * nline * f1(F[2]) + 2 * nplane * F[2] * f1(F[1]) + F[1] * F[2] * (2 * f1(F[0]) + 6 * F[0]))
+        pts = 2 * nline * F[2] + 4 * nplane * F[1] * F[2] + 2 * F[0] * F[1] * F[2]
+        fl += ns * per
+        by += ns * pts * 2 * 16
     return fl, by
 
 
@@ -193,6 +235,8 @@ def roofline_of(name, tr, s, prec, nterms):
     """Roofline entry of one traced kernel slot: algorithmic work per launch
     over its mean event-timed duration, against the peak of its bound."""
     dur = tr[name][0] / tr[name][1] * 1e-3  # seconds per launch
+    form = prec
+    prec = prec.partition("+")[0]
     fl, by = algorithmic_work(name, s, prec, nterms)
     hbm, src = _peaks()
     if name in ("gemm_expand", "gemm_project", "gemm_forward") and prec != "fp64":
@@ -216,7 +260,7 @@ def roofline_of(name, tr, s, prec, nterms):
                 "frac": ach / peak, "peak_source": src}
     roof["kernel"] = name
     roof["ms_per_launch"] = dur * 1e3
-    roof["traffic"] = TRAFFIC.get((name, prec, s["name"], _src_hash()))
+    roof["traffic"] = TRAFFIC.get((name, form, s["name"], _src_hash()))
     return roof
 
 
@@ -247,9 +291,11 @@ def run_ours(args, rank, world, local_rank):
     flush = _Flush()
     n_states = int(s["n_s"]) * int(s["n_k"])
 
-    def timed_form(prec, nsteps, nwarm):
+    def timed_form(form, nsteps, nwarm):
+        # a form is a precision form, with "+fft" for the FFT route of the interstitial sum
+        prec, _, route = form.partition("+")
         ctx = Context(s, precision=prec, graph_steps=1, a_max=a0, max_record=nsteps + nwarm + 8,
-                      stream=stream.cuda_stream)
+                      stream=stream.cuda_stream, interstitial="fft" if route == "fft" else "toeplitz")
         assert ctx.stream_handle() == stream.cuda_stream
         d_a = torch.from_numpy(a_all[:nsteps + nwarm]).to(dev)
         for i in range(nwarm):
@@ -310,7 +356,7 @@ def run_ours(args, rank, world, local_rank):
     forms = {args.precision: {"value": value, "ms_per_step": dev_max / K * 1e3, "steps": K}}
     form_obs = {args.precision: obs}
     if args.fp64_steps > 0:
-        for prec in ("fp64", "fp32", "bf16x3", "fp16x3"):
+        for prec in FORMS:
             if prec == args.precision:
                 continue
             c2, d2, _, o2 = timed_form(prec, args.fp64_steps, W)
@@ -346,11 +392,12 @@ def run_ours(args, rank, world, local_rank):
         "ms_per_step": dev_max / K * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32+f64", "bf16x3": "bf16x3+f32+f64",
-                  "fp16x3": "fp16x3+f32+f64"}[args.precision],
+                  "fp16x3": "fp16x3+f32+f64"}[args.precision.partition("+")[0]],
         "data": "synthetic (seeded generator shaped like the paper's H2 cell)",
         "config": {"workload": args.workload, "n_k": int(s["n_k"]), "n_basis": int(s["n_g"][0]) +
                    int(np.sum(s["n_lo"])), "n_states": int(s["n_s"]), "n_aux": int(s["n_aux"]),
-                   "dt": float(s["dt"]), "precision_form": args.precision,
+                   "dt": float(s["dt"]), "precision_form": args.precision.partition("+")[0],
+                   "interstitial": "fft" if args.precision.endswith("+fft") else "toeplitz (direct sum)",
                    "propagator": "chebyshev (exact exponential to FP64 round-off)",
                    "l2": "flushed (256 MiB read) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU",
@@ -427,7 +474,8 @@ def main():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--precision", choices=["fp32", "fp64", "bf16x3", "fp16x3"], default="fp32")
+    p.add_argument("--precision", choices=list(FORMS), default="fp32",
+                   help="precision form; '+fft' selects the FFT route of the interstitial sum")
     p.add_argument("--workload", default="h2_6000")
     p.add_argument("--fp64-steps", type=int, default=50, help="steps timed for each other precision form")
     p.add_argument("--trace-steps", type=int, default=5)

@@ -85,6 +85,16 @@ extern "C" {
  * range makes the step fail with ERR_NONFINITE.  At most 128 states. */
 #define RTTDDFT_PREC_FP16X3 3
 
+/* how the interstitial sum of Eq. v_interstitial, sum_G' V~_{G-G'} C_G', is
+ * evaluated (Sec. 3: matrix products against FFTs) */
+#define RTTDDFT_INTERSTITIAL_TOEPLITZ 0 /* direct sum over G' with V~_{G-G'} generated from the table */
+/* circular convolution on a grid of F_i >= vt_dim[i] points per axis (the
+ * smallest products of 2, 3 and 5, at most 128): pruned inverse and forward
+ * 3-D FFTs around a product with the table's real-space image; FP64 and FP32
+ * forms only (ERR_UNSUPPORTED otherwise or when an axis needs more than 128
+ * points).  Equal to the direct sum up to rounding. */
+#define RTTDDFT_INTERSTITIAL_FFT 1
+
 /* how the auxiliary basis CC(0) is obtained at set-up */
 #define RTTDDFT_AUX_RITZ 0  /* Ritz vectors of H0 in span(caux): S-orthonormal, H0-diagonal */
 #define RTTDDFT_AUX_GIVEN 1 /* caux and eps used as given; S-orthonormality is checked */
@@ -134,6 +144,7 @@ typedef struct {
     double a_max;       /* bound on |A(t)| used for the Chebyshev spectral interval; 0: taken
                            from the samples of each call (device samples are then read back) */
     double s_max;       /* bound on |s_k| of the potential change; 0: from the samples */
+    int interstitial;   /* RTTDDFT_INTERSTITIAL_* (default TOEPLITZ) */
 } rttddft_options;
 
 /* Per-step records (all k-points summed with their weights), caller-allocated
@@ -169,6 +180,9 @@ typedef struct {
     int tc_candidates;     /*   launch shapes timed by the set-up autotuner */
     int tc_interstitial_ns;/*   tuned time of the interstitial launch (ns) */
     int tc_matching_ns;    /*   tuned time of the matching-row launch (ns) */
+    int interstitial;      /* RTTDDFT_INTERSTITIAL_* of the context */
+    int fft_grid[3];       /* FFT route: grid points per axis (0 otherwise) */
+    int fft_fused;         /*   1: a plane's two in-plane axes in one launch (chosen at set-up by timing) */
 } rttddft_info;
 
 RTTDDFT_API void rttddft_default_options(rttddft_options* opt);

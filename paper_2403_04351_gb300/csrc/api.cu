@@ -66,6 +66,8 @@ struct rttddft_ctx {
     std::vector<double> eps_min, eps_max, pnorm, dvnorm;
     std::vector<std::vector<int>> h_glin;       // host copy of the table offsets of G per k
     TcPlan* tc = nullptr;                       // tensor-core operator (split-BF16 form)
+    FftPlan* fft = nullptr;                     // FFT route of the interstitial convolution
+    ToepDesc* td_op = nullptr;                  // per k {C, th}: the operator's convolution
     double dtcr0 = 0;
     int nterms = 0, launches_per_step = 0;
     bool dv_set = false;
@@ -234,6 +236,7 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.tc_st = tc_table_scale(ctx->tc);
     a.at_n = ctx->at.n;
     a.at_maxm = ctx->maxm;
+    a.ith = (ctx->opt.precision >= RTTDDFT_PREC_BF16X3 || ctx->fft) ? 1 : 0;
     return a;
 }
 
@@ -268,6 +271,8 @@ static StepPlan make_plan(rttddft_ctx* ctx) {
     p.jac_vecs = ctx->d_jac_vecs;
     p.max_sweeps = ctx->opt.max_sweeps;
     p.tc = ctx->tc;
+    p.fft = ctx->fft;
+    p.td_op = ctx->td_op;
     return p;
 }
 
@@ -503,6 +508,10 @@ static void validate(const rttddft_system* s, const rttddft_options* o) {
     if (!(o->dt > 0)) fail(ctx, RTTDDFT_ERR_ARG, "dt must be > 0");
     if (o->propagator < 0 || o->propagator > 2) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown propagator");
     if (o->precision < 0 || o->precision > 3) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown precision form");
+    if (o->interstitial != RTTDDFT_INTERSTITIAL_TOEPLITZ && o->interstitial != RTTDDFT_INTERSTITIAL_FFT)
+        fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown interstitial route");
+    if (o->interstitial == RTTDDFT_INTERSTITIAL_FFT && o->precision > RTTDDFT_PREC_FP32)
+        fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "the FFT interstitial route runs in the FP64 and FP32 forms");
     if (o->aux_mode < 0 || o->aux_mode > 1) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown aux_mode");
     if (o->aux_mode == RTTDDFT_AUX_GIVEN && !s->eps) fail(ctx, RTTDDFT_ERR_ARG, "GIVEN mode needs eps");
     if (o->max_record < 1 || o->graph_steps < 0 || o->max_sweeps < 1) fail(ctx, RTTDDFT_ERR_ARG, "bad option value");
@@ -527,6 +536,7 @@ void rttddft_default_options(rttddft_options* opt) {
     opt->max_sweeps = 30;
     opt->a_max = 0.0;
     opt->s_max = 0.0;
+    opt->interstitial = RTTDDFT_INTERSTITIAL_TOEPLITZ;
 }
 
 const char* rttddft_version(void) { return "rttddft-gb300 0.1 (sm_103a)"; }
@@ -541,6 +551,7 @@ void rttddft_destroy(rttddft_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     tc_plan_destroy(ctx->tc);
+    fft_plan_destroy(ctx->fft);
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
@@ -748,7 +759,8 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             K.Q = dalloc<zd>(ctx, (size_t)std::max(at.ma, 1) * ns);
             K.Z = dalloc<zd>(ctx, (size_t)std::max(at.ma, 1) * 2 * ns);
             const bool tcf = o->precision >= RTTDDFT_PREC_BF16X3;
-            K.th = tcf ? dalloc<zd>(ctx, (size_t)K.ng * ns) : nullptr;
+            const bool fftr = o->interstitial == RTTDDFT_INTERSTITIAL_FFT;
+            K.th = (tcf || fftr) ? dalloc<zd>(ctx, (size_t)K.ng * ns) : nullptr;
             K.tb = (tcf && at.ma > 0) ? dalloc<zd>(ctx, (size_t)K.ng * 2 * ns) : nullptr;
             K.gram = dalloc<zd>(ctx, 2 * (size_t)ns * ns);
             K.evec = dalloc<zd>(ctx, nn);
@@ -946,6 +958,26 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
                                          ctx->d_vtab, ctx->nvt, ctx->vt_center, ctx->d_kd, fmt, pow2_scale(amax),
                                          ctx->tc_st, ctx->stream, &why);
             if (e) fail(ctx, e, std::string(fmt ? "split-BF16" : "split-FP16") + " form: " + why);
+        }
+        // ---- FFT route of the interstitial convolution
+        if (o->interstitial == RTTDDFT_INTERSTITIAL_FFT) {
+            std::vector<int> ngv(nk);
+            std::vector<const int*> gp(nk);
+            std::vector<ToepDesc> td(nk);
+            for (int k = 0; k < nk; ++k) {
+                const KDev& K = ctx->hkd[k];
+                ngv[k] = K.ng;
+                gp[k] = s->g_int + 3 * g_off[k];
+                td[k] = ToepDesc{K.C, K.th, K.nb, K.ng};
+            }
+            std::string why;
+            const int e = fft_plan_create(&ctx->fft, nk, ngv.data(), gp.data(), ctx->vt_dim, ctx->d_vtab, ns,
+                                          o->precision == RTTDDFT_PREC_FP64 ? 0 : 1, ctx->stream, &why);
+            if (e) fail(ctx, e, why);
+            ctx->td_op = dupload(ctx, td.data(), td.size());
+            if (fft_tune(ctx->fft, ctx->td_op, ns, ctx->stream)) fail(ctx, RTTDDFT_ERR_CUDA, "FFT route: set-up timing failed");
+            KCHECK();
+            CK(cudaStreamSynchronize(ctx->stream));
         }
         CK(cudaMemcpy(ctx->d_kd, ctx->hkd.data(), nk * sizeof(KDev), cudaMemcpyHostToDevice));
         // ---- step descriptors
@@ -1440,6 +1472,8 @@ int rttddft_get_info(rttddft_ctx* ctx, rttddft_info* info) {
     info->tc_slices = v[3];
     info->tc_window = v[4];
     info->tc_smem = v[5];
+    info->interstitial = ctx->opt.interstitial;
+    fft_plan_info(ctx->fft, info->fft_grid, &info->fft_fused);
     return RTTDDFT_OK;
 }
 
@@ -1545,6 +1579,12 @@ int rttddft_set_dv(rttddft_ctx* ctx, const double* dh, const double* dvtab) {
         if (at.n > 0) CK(cudaMemcpy(ctx->d_dh, dh, nblk * sizeof(zd), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->d_dvtab, dvtab, ctx->nvt * sizeof(zd), cudaMemcpyHostToDevice));
         if (ctx->tc) tc_dv_set_table(ctx->tc, ctx->d_dvtab, ctx->nvt, ctx->stream);
+        if (ctx->fft) {
+            std::string why;
+            const int e = fft_set_dv(ctx->fft, ctx->d_dvtab, ctx->vt_dim, naux, ctx->stream, &why);
+            if (e) fail(ctx, e, why);
+            KCHECK();
+        }
         ctx->dv_set = true;
         // bound || CC^H dV_1 CC ||_F for the Chebyshev scaling (one evaluation with s = 1)
         {
@@ -2001,6 +2041,7 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         if (a.prec >= 2) a.prec = 1;  // the static scratch holds the FP32-form operands only
         a.vsteps = nullptr;
         a.tcback = 0;
+        a.ith = 0;  // the interstitial sum from the table (the FFT buffers belong to the context)
         a.nk = 1;
         a.st = (DevState*)(base + o_st);
         a.part_jmt = (double*)(base + o_jmt);
@@ -2011,6 +2052,7 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
             a.vstep32 = f32 ? (zf*)(base + o_vs32) : nullptr;
         }
         StepPlan p = make_plan(ctx);
+        p.fft = nullptr;
         p.gd_fwd = (const GemmDesc*)(base + o_gd);
         p.maxng = ng;
         p.part = (zd*)(base + o_part);

@@ -778,7 +778,7 @@ __global__ void __launch_bounds__(BKB) k_back(StepArgs a, int n0) {
                 }
                 return t;
             };
-            if (a.prec >= 2) th = K.th[g + (size_t)(n0 + c) * ng];
+            if (a.ith) th = K.th[g + (size_t)(n0 + c) * ng];
             else th = sum4(0, nsg, 0);
             if (a.tcback) {
                 th = zadd(th, K.tb[g + (size_t)(n0 + c) * ng]);
@@ -1409,22 +1409,26 @@ static size_t toep_smem(const StepArgs& a, size_t tc, size_t tt) {
 }
 
 template <typename TA, typename TT, typename TC, int NT>
-static void back_launch(const StepArgs& a, int maxng, cudaStream_t s, TraceHook* tr) {
+static int back_launch(const StepArgs& a, int maxng, cudaStream_t s, TraceHook* tr) {
     const size_t sm = toep_smem<NT>(a, sizeof(TC), sizeof(TT));
     // in the tensor-core form the interstitial slots are done already: only
     // the back-projection slots run here
-    const int slot0 = (a.prec >= 2) ? a.nseg : 0;
+    const int slot0 = a.ith ? a.nseg : 0;
     // with the back-projection on the tensor cores too, no slot kernel runs
     dim3 gt((maxng + BT - 1) / BT, a.tcback ? 0 : a.nslot - slot0, a.nk);
     dim3 gb((maxng + BKB - 1) / BKB, 1, a.nk);
+    int nl = 0;
     for (int n0 = 0; n0 < a.ns; n0 += NT) {
         if (gt.y > 0) {
+            ++nl;
             k_toep_seg<TA, TT, TC, NT><<<gt, BT, sm, s>>>(a, n0, slot0);
             mark(tr, slot0 ? "backprojection" : "toeplitz_and_backprojection", s);
         }
         k_back<NT><<<gb, BKB, 0, s>>>(a, n0);
         mark(tr, "back_finish", s);
+        ++nl;
     }
+    return nl;
 }
 
 // Opt the slot kernels in to the shared memory their table window needs.
@@ -1464,24 +1468,35 @@ int prepare_back_kernels(const StepArgs& a) {
     return 0;
 }
 
-void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr) {
+int launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr) {
     const bool f32 = a.prec >= 1;
+    int nl = 0;
     if (a.prec >= 2) {
         // tensor cores: V~ * C_G and Q = A C_G in one split-BF16 launch
         launch_tc_pack(p.tc, a, s);
         mark(tr, "tc_pack_c", s);
-        launch_tc_operator(p.tc, a, s);
+        nl += launch_tc_operator(p.tc, a, s);
         mark(tr, "tc_interstitial_and_forward", s);
         launch_tc_reduce(p.tc, a, s);
         mark(tr, "tc_reduce", s);
+        nl += 2;
     } else {
-        // Q = A C_G = (A^H)^H C_G: one warp per matching row; split-K in FP64
-        launch_gemm_cn(p.gd_fwd, a.nk, a.ma, p.maxng, a.ns, p.kc_fwd, p.part, 0, f32, nullptr, s);
-        mark(tr, "gemm_forward", s);
-        launch_split_reduce(p.gd_fwd, a.nk, a.ma, a.ns, p.kc_fwd, p.part, 0, s);
-        mark(tr, "split_reduce_forward", s);
+        if (p.fft) {
+            // V~ * C_G by FFT (th), the current table V~ + s dV~ when the change is on
+            nl += launch_fft_conv(p.fft, p.td_op, a.kofs, a.nk, a.ns, 0, a.dv_on, &a.st->cur_s, s);
+            mark(tr, "fft_interstitial", s);
+        }
+        if (a.ma > 0) {
+            // Q = A C_G = (A^H)^H C_G: one warp per matching row; split-K in FP64
+            launch_gemm_cn(p.gd_fwd, a.nk, a.ma, p.maxng, a.ns, p.kc_fwd, p.part, 0, f32, nullptr, s);
+            mark(tr, "gemm_forward", s);
+            launch_split_reduce(p.gd_fwd, a.nk, a.ma, a.ns, p.kc_fwd, p.part, 0, s);
+            mark(tr, "split_reduce_forward", s);
+            nl += 2;
+        }
     }
     if (a.lrows > 0) {
+        ++nl;
         dim3 g(a.lrows, 1, a.nk);
         if (f32 && a.ns > LOCW_MIN_NS) {
             // lanes own columns; row chunks per atom so that about two blocks per SM work
@@ -1503,18 +1518,19 @@ void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, 
     }
     if (a.tcback) {
         // A^H [hQ | oQ] on the tensor cores
-        launch_tc_back(p.tc, a, s);
+        nl += launch_tc_back(p.tc, a, s);
         mark(tr, "tc_backprojection", s);
     }
     if (f32) {
-        if (a.ns <= 2) back_launch<zf, zf, zf, 2>(a, p.maxng, s, tr);
-        else if (a.ns <= 4) back_launch<zf, zf, zf, 4>(a, p.maxng, s, tr);
-        else back_launch<zf, zf, zf, 8>(a, p.maxng, s, tr);
+        if (a.ns <= 2) nl += back_launch<zf, zf, zf, 2>(a, p.maxng, s, tr);
+        else if (a.ns <= 4) nl += back_launch<zf, zf, zf, 4>(a, p.maxng, s, tr);
+        else nl += back_launch<zf, zf, zf, 8>(a, p.maxng, s, tr);
     } else {
-        if (a.ns <= 2) back_launch<zd, zd, zd, 2>(a, p.maxng, s, tr);
-        else if (a.ns <= 4) back_launch<zd, zd, zd, 4>(a, p.maxng, s, tr);
-        else back_launch<zd, zd, zd, 8>(a, p.maxng, s, tr);
+        if (a.ns <= 2) nl += back_launch<zd, zd, zd, 2>(a, p.maxng, s, tr);
+        else if (a.ns <= 4) nl += back_launch<zd, zd, zd, 4>(a, p.maxng, s, tr);
+        else nl += back_launch<zd, zd, zd, 8>(a, p.maxng, s, tr);
     }
+    return nl;
 }
 
 // Eq. v_MT and Eq. v_interstitial rebuilt from the scaled blocks:
@@ -1534,11 +1550,19 @@ static int launch_dv_rebuild(const StepArgs& a, const StepPlan& p, cudaStream_t 
         mark(tr, "dv_interstitial_project", s);
         return 4 + 2 * tc_dv_tiles(p.tc);
     }
-    launch_toeplitz(a.kd, p.td_dv, a.nk, p.maxng, a.naux, a.dvtab, a.vt_center, 0, 0, &a.st->cur_s, s);
-    mark(tr, "dv_interstitial_toeplitz", s);
+    int nl = 3;
+    if (p.fft) {
+        // T = s (dV~ * CC_G) by FFT over the N_aux columns
+        nl += launch_fft_conv(p.fft, p.td_dv, a.kofs, a.nk, a.naux, 1, 1, &a.st->cur_s, s);
+        mark(tr, "dv_interstitial_fft", s);
+    } else {
+        launch_toeplitz(a.kd, p.td_dv, a.nk, p.maxng, a.naux, a.dvtab, a.vt_center, 0, 0, &a.st->cur_s, s);
+        mark(tr, "dv_interstitial_toeplitz", s);
+        ++nl;
+    }
     launch_gemm_cn(p.gd_dvi, a.nk, a.naux, p.maxng, a.naux, 0, nullptr, 1, false, nullptr, s);
     mark(tr, "dv_interstitial_project", s);
-    return 4;
+    return nl;
 }
 
 void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlaunch, TraceHook* tr) {
@@ -1592,12 +1616,7 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
         mark(tr, "split_reduce_expand", s);
         ++nl;
     }
-    launch_operator_pass(a, p, s, tr);
-    {
-        const int ntb = a.ns <= 2 ? 2 : (a.ns <= 4 ? 4 : 8);
-        const int chunks = (a.ns + ntb - 1) / ntb;
-        nl += (a.prec >= 2 ? 3 : 2) + (a.lrows > 0 ? 1 : 0) + (a.tcback ? 3 + chunks : 2 * chunks);
-    }
+    nl += launch_operator_pass(a, p, s, tr);
     // theta~ = CC^H (S C): split-K partials, finished per row in k_post
     launch_gemm_cn(p.gd_proj, a.nk, a.naux, p.maxnb, a.ns, p.kc_proj, p.part, 0, f32, nullptr, s);
     mark(tr, "gemm_project", s);

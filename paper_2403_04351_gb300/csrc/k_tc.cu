@@ -1558,7 +1558,7 @@ void launch_tc_pack(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
     k_tc_pack_c<<<g, 256, 0, s>>>(a.kd, tp->ns, tp->Kp, tp->Rp, tp->bh, tp->bl, tp->fmt, tp->sC, a.flag);
 }
 
-void launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
+int launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
     const TcToepParams pt = tco_toep_params(tp, a);
     const TcOpParams pa = tco_rows_params(tp, a);
     dim3 gt(tp->ttiles, tp->splits_t, a.nk);
@@ -1574,15 +1574,17 @@ void launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
         RTD_TCO(224) RTD_TCO(256)
 #undef RTD_TCO
     }
+    return tp->atiles > 0 ? 2 : 1;
 }
 
 bool tc_has_back(const TcPlan* tp) { return tp && tp->NTb > 0; }
 
-void launch_tc_back(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
+int launch_tc_back(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
     dim3 gz((2 * tp->ns * tp->ma + 255) / 256, 1, a.nk);
     k_tc_pack_z<<<gz, 256, 0, s>>>(a.kd, tp->ns, tp->ma, tp->Kpb, tp->Rpb, tp->zh, tp->zl, tp->fmt, tp->sZ, a.flag);
     TcRowsCand c{tp->kbps_b, tp->splits_b, tp->S_b, tp->smem_b, 0.f};
     tco_launch_back_any(tp, c, a.kd, a.nk, s, a.kofs, a.flag);  // single-k calls: left operand of k-point kofs
+    return 3;
 }
 
 void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {

@@ -146,6 +146,7 @@ struct StepArgs {
     int tcback;               // the back-projection runs on the tensor cores (split-BF16 form)
     int at_n, at_maxm;        // atoms, and the largest local block m = N_A + n_lo
     int tc_fmt;               // tensor-core operand format: 1 bf16, 0 fp16
+    int ith;                  // the interstitial sum arrives in K.th (tensor cores or FFT)
     double tc_st;             // scale of the split table (fp16 range)
 };
 #define POST_STRIDE 36        // part_post row: residual, J_sub (3), then theta^H theta~ (ns <= 4)
@@ -184,6 +185,8 @@ struct StepPlan {
     zd* const* jac_mats; double* const* jac_vals; zd* const* jac_vecs;
     int max_sweeps;
     const struct TcPlan* tc;  // tensor-core operator plan (split-BF16 form) or null
+    const struct FftPlan* fft;  // FFT route of the interstitial convolution or null
+    const ToepDesc* td_op;      // per k: {C, th}: the operator's convolution source and destination
 };
 // Optional per-kernel tracing: an event is recorded after every launch of a step.
 struct TraceHook {
@@ -193,7 +196,7 @@ struct TraceHook {
 };
 void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlaunch,
                  TraceHook* tr = nullptr);
-void launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr = nullptr);
+int launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr = nullptr);
 int prepare_back_kernels(const StepArgs& a);
 // blocks for the cooperative Chebyshev launch if it can be captured in a graph, else 0
 int prepare_cheb_coop(const StepArgs& a, cudaStream_t s);
@@ -227,6 +230,18 @@ void launch_adj_jterm(const StepArgs& a, zd* lam, const zd* theta, const double*
 struct TcPlan;
 // fmt: 1 split-BF16, 0 split-FP16 (operands scaled by powers of two: sa for the
 // matching coefficients, st for the table, fixed scales for C and Z)
+// interstitial convolution by FFT (k_fft.cu)
+struct FftPlan;
+int fft_grid_for(const int vt_dim[3], int F[3]);
+int fft_plan_create(FftPlan** out, int nk, const int* ng, const int* const* gint, const int vt_dim[3],
+                    const zd* vtab_dev, int ncol, int prec, cudaStream_t st, std::string* why);
+int fft_set_dv(FftPlan* pl, const zd* dvtab_dev, const int vt_dim[3], int ncol, cudaStream_t st, std::string* why);
+void fft_plan_destroy(FftPlan* pl);
+void fft_plan_info(const FftPlan* pl, int F[3], int* fused);
+int fft_tune(FftPlan* pl, const ToepDesc* td, int ncol, cudaStream_t st);
+int launch_fft_conv(const FftPlan* pl, const ToepDesc* td, int kofs, int nk, int ncol, int vmode, int use_vd,
+                    const double* s, cudaStream_t st);
+
 int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const int* const* glin_host,
                    const zd* const* at_dev, const zd* vtab, int nvt, int vt_center, const KDev* d_kd,
                    int fmt, double sa, double st, cudaStream_t s, std::string* why);
@@ -237,7 +252,7 @@ void tc_plan_destroy(TcPlan* tp);
 // interstitial launch, candidates tuned, tuned interstitial and matching-row times (ns)
 void tc_plan_info(const TcPlan* tp, int* v);
 void launch_tc_pack(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
-void launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
+int launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
 void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
 bool tc_has_back(const TcPlan* tp);  // the back-projection runs on the tensor cores (4 N_s <= 256)
 int tc_dv_prepare(TcPlan* tp, const zd* const* caux_dev, const int* nb, const int* ng, int naux, int nvt,
@@ -246,7 +261,7 @@ void tc_dv_set_table(TcPlan* tp, const zd* dvtab, int nvt, cudaStream_t s);
 bool tc_dv_ready(const TcPlan* tp);
 int tc_dv_tiles(const TcPlan* tp);
 void launch_tc_dv_toeplitz(const TcPlan* tp, const StepArgs& a, const ToepDesc* td, cudaStream_t s);
-void launch_tc_back(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
+int launch_tc_back(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
 // ---- tensor-core split-BF16 complex GEMM (k_tc.cu); returns an RTTDDFT_* code
 int tc_zgemm(int opA, int M, int N, int K, const zd* A, int lda, const zd* X, int ldx, zd* C, int ldc,
              int beta_add, cudaStream_t s);

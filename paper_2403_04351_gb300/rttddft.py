@@ -23,6 +23,7 @@ ERRORS = {
 PROP = {"chebyshev": 0, "eig": 1, "cn": 2}
 PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2, "fp16x3": 3}
 AUX = {"ritz": 0, "given": 1}
+INTERSTITIAL = {"toeplitz": 0, "fft": 1}
 
 EXPORTED = ["rttddft_default_options", "rttddft_setup", "rttddft_step", "rttddft_observables",
             "rttddft_set_dv", "rttddft_apply", "rttddft_get_state", "rttddft_set_state",
@@ -49,7 +50,7 @@ class rttddft_options(ctypes.Structure):
                 ("max_record", ctypes.c_int), ("graph_steps", ctypes.c_int),
                 ("cheb_tol", ctypes.c_double), ("ortho_tol", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int), ("a_max", ctypes.c_double),
-                ("s_max", ctypes.c_double)]
+                ("s_max", ctypes.c_double), ("interstitial", ctypes.c_int)]
 
 
 class rttddft_obs(ctypes.Structure):
@@ -65,7 +66,8 @@ class rttddft_info(ctypes.Structure):
                 ("precision", ctypes.c_int), ("tc_tile_n", ctypes.c_int), ("tc_stages", ctypes.c_int),
                 ("tc_kblocks", ctypes.c_int), ("tc_slices", ctypes.c_int), ("tc_window", ctypes.c_int),
                 ("tc_smem", ctypes.c_int), ("tc_candidates", ctypes.c_int),
-                ("tc_interstitial_ns", ctypes.c_int), ("tc_matching_ns", ctypes.c_int)]
+                ("tc_interstitial_ns", ctypes.c_int), ("tc_matching_ns", ctypes.c_int),
+                ("interstitial", ctypes.c_int), ("fft_grid", ctypes.c_int * 3), ("fft_fused", ctypes.c_int)]
 
 
 class rttddft_trace(ctypes.Structure):
@@ -254,7 +256,8 @@ class Context:
 
     def __init__(self, sys, dt=None, propagator="chebyshev", precision="fp64", reproject=False,
                  aux_mode="ritz", caux=None, eps=None, c0=None, max_record=4096, graph_steps=1,
-                 cheb_tol=1e-16, stream=None, max_sweeps=30, a_max=0.0, s_max=0.0):
+                 cheb_tol=1e-16, stream=None, max_sweeps=30, a_max=0.0, s_max=0.0,
+                 interstitial="toeplitz"):
         self.n_k = int(sys["n_k"])
         self.n_s = int(sys["n_s"])
         self.n_aux = int(sys["n_aux"]) if caux is None else int(np.asarray(caux[0]).shape[1])
@@ -298,6 +301,7 @@ class Context:
         o.max_sweeps = int(max_sweeps)
         o.a_max = float(a_max)
         o.s_max = float(s_max)
+        o.interstitial = INTERSTITIAL[interstitial]
         self.options = o
         self.max_record = int(max_record)
         self._stream = stream
@@ -373,7 +377,9 @@ class Context:
                     tc=dict(tile_n=i.tc_tile_n, stages=i.tc_stages, kblocks=i.tc_kblocks,
                             slices=i.tc_slices, window=i.tc_window, smem=i.tc_smem,
                             candidates=i.tc_candidates, interstitial_ns=i.tc_interstitial_ns,
-                            matching_ns=i.tc_matching_ns))
+                            matching_ns=i.tc_matching_ns),
+                    interstitial=i.interstitial, fft_grid=tuple(int(x) for x in i.fft_grid),
+                    fft_fused=i.fft_fused)
 
     def set_dv(self, dv):
         self._dh = _cat_f(dv["dh"])

@@ -474,7 +474,7 @@ def main():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--precision", choices=list(FORMS), default="fp32",
+    p.add_argument("--precision", choices=list(FORMS), default="fp32+fft",
                    help="precision form; '+fft' selects the FFT route of the interstitial sum")
     p.add_argument("--workload", default="h2_6000")
     p.add_argument("--fp64-steps", type=int, default=50, help="steps timed for each other precision form")

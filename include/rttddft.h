@@ -161,6 +161,9 @@ typedef struct {
     double* resid;      /* [capacity] max |CC^H S C - theta| over k */
     double* dt_cr;      /* [capacity] f/(lambda_max - lambda_min) of HH (Eq. critical_timestep, f = 0.2);
                            spectral bounds for the Chebyshev forms, eigenvalues for EIG */
+    double* n_exc;      /* [capacity] or NULL: excited electrons N_e - sum w f sum_{i < N_s} |theta_ij|^2,
+                           the charge that left the N_s lowest auxiliary vectors (the occupied
+                           ground state when C(0) is the default) */
 } rttddft_obs;
 
 typedef struct {
@@ -294,6 +297,25 @@ typedef struct {
 } rttddft_trace;
 RTTDDFT_API int rttddft_trace_steps(rttddft_ctx* ctx, int nsteps, const double* a_samples,
                                     const double* dv_scale, rttddft_trace* out);
+
+/* Dynamical polarizability (Eq. polarizability) from a recorded time series:
+ *   alpha_{l l'}(w) = (i Omega / w) J_l(w) / E_l'(w),
+ *   F(w) = dt sum_{n < n_t} f(t_n) e^{(i w - eta) t_n},  t_n = t0 + n dt,
+ * for f = the induced current J_ind = J - J(t0) (e.g. the record's j minus its
+ * field-free value) and f = the electric field E = -(1/c) dA/dt at the same
+ * times; eta >= 0 damps the finite window.  One GPU block per frequency, FP64
+ * sums in a fixed order.
+ *   j_ind, e_field  [n_t][3] (host or device);  w [n_w] frequencies > 0 (host or
+ *                   device; host values are checked);  omega_cell = Omega > 0;
+ *   out_j, out_e    [n_w][3] complex J(w), E(w), or NULL;
+ *   alpha           [n_w][3][3] complex, row l, column l' (l' fastest), or NULL;
+ *                   an entry with E_l'(w) exactly zero is written as 0.
+ * Outputs on the host or the device like the inputs; the call returns after the
+ * results are written.  Errors: ERR_ARG (sizes, dt <= 0, a host w <= 0, NULL
+ * inputs), ERR_CUDA. */
+RTTDDFT_API int rttddft_polarizability(int n_t, double t0, double dt, const double* j_ind, const double* e_field,
+                                       double eta, int n_w, const double* w, double omega_cell, double* out_j,
+                                       double* out_e, double* alpha, void* cuda_stream);
 
 /* Split-BF16 complex GEMM on the tensor cores, the contraction form of the
  * precision option RTTDDFT_PREC_BF16X3 (the bulk contractions of Sec. 2:

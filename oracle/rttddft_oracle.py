@@ -262,7 +262,7 @@ class Oracle:
         th = [kp["theta0"].copy() for kp in self.kp] if thetas is None else \
             [t.copy() for t in thetas]
         rec = {key: [] for key in ("t", "J", "J_full", "dmu", "E", "norm_dev", "resid",
-                                   "dtcr")}
+                                   "dtcr", "n_exc")}
         states = []
         dmu = np.zeros(3)
         jind_prev = np.zeros(3)
@@ -310,6 +310,7 @@ class Oracle:
             rec["norm_dev"].append(ndev)
             rec["resid"].append(res)
             rec["dtcr"].append(F_CRIT / max(lam_rng))
+            rec["n_exc"].append(self.excited_electrons(th))
             if keep_states:
                 states.append([t.copy() for t in th])
         out = {key: np.asarray(v) for key, v in rec.items()}
@@ -318,6 +319,18 @@ class Oracle:
         if keep_states:
             out["states"] = states
         return out
+
+    def excited_electrons(self, thetas):
+        """N_exc = N_e - sum_k w_k sum_j f_j sum_{i < N_s} |theta_ij|^2: the
+        charge outside the N_s lowest auxiliary vectors, i.e. the occupied
+        ground state (the quantity the paper plots for CO and pyridine@MoS2
+        without a formula; this is the reading used here)."""
+        ne = float(np.sum(self.wk) * np.sum(self.occ))
+        kept = 0.0
+        for ik, th in enumerate(thetas):
+            occ_block = th[:self.n_s, :]
+            kept += self.wk[ik] * float(np.sum(self.occ[None, :] * np.abs(occ_block) ** 2))
+        return ne - kept
 
     def energy(self, thetas, a_vec, dv_scale=0.0):
         """E = sum_k w_k sum_j f_j Re c_j^H H(A) c_j with c = CC theta."""
@@ -408,3 +421,23 @@ def full_basis_propagator(ops, a_vec, c_light, dt):
     s_h = (u * w ** 0.5) @ u.conj().T
     ht = s_mh @ h @ s_mh
     return s_mh @ sla.expm(-1j * dt * 0.5 * (ht + ht.conj().T)) @ s_h
+
+
+def polarizability(t0, dt, j_ind, e_field, w, omega_cell, eta=0.0):
+    """Eq. polarizability: alpha_{l l'}(w) = (i Omega / w) J_l(w) / E_l'(w), the
+    time series taken to the frequency domain by the damped discrete transform
+    F(w) = dt sum_n f(t_n) e^{(i w - eta) t_n}, t_n = t0 + n dt (the paper does
+    not give its transform; this is the reading used here).  Entries whose
+    E_l'(w) is exactly zero are 0.  Returns (alpha [n_w, 3, 3], J(w), E(w))."""
+    j_ind = np.asarray(j_ind, dtype=np.float64).reshape(-1, 3)
+    e_field = np.asarray(e_field, dtype=np.float64).reshape(-1, 3)
+    w = np.asarray(w, dtype=np.float64).ravel()
+    t = t0 + dt * np.arange(j_ind.shape[0])
+    kern = np.exp((1j * w[:, None] - eta) * t[None, :])  # [n_w, n_t]
+    jw = dt * kern @ j_ind
+    ew = dt * kern @ e_field
+    alpha = np.zeros((w.size, 3, 3), dtype=np.complex128)
+    for lp in range(3):
+        nz = ew[:, lp] != 0
+        alpha[nz, :, lp] = (1j * omega_cell / w[nz, None]) * jw[nz, :] / ew[nz, lp, None]
+    return alpha, jw, ew

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "librttddft.so")
-SOURCES = ["k_linalg.cu", "k_step.cu", "k_adjoint.cu", "k_tc.cu", "k_fft.cu", "api.cu"]
+SOURCES = ["k_linalg.cu", "k_step.cu", "k_adjoint.cu", "k_tc.cu", "k_fft.cu", "k_spectrum.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
          "-fvisibility=hidden", "-I" + INCLUDE, "-I" + CSRC]

@@ -68,6 +68,9 @@ struct rttddft_ctx {
     TcPlan* tc = nullptr;                       // tensor-core operator (split-BF16 form)
     FftPlan* fft = nullptr;                     // FFT route of the interstitial convolution
     ToepDesc* td_op = nullptr;                  // per k {C, th}: the operator's convolution
+    unsigned* d_tile_cnt = nullptr;             // row-tile counters of the fused split-K sums
+    cudaStream_t side = nullptr;                // the FFT route's interstitial rows overlap the matching rows
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double dtcr0 = 0;
     int nterms = 0, launches_per_step = 0;
     bool dv_set = false;
@@ -273,6 +276,10 @@ static StepPlan make_plan(rttddft_ctx* ctx) {
     p.tc = ctx->tc;
     p.fft = ctx->fft;
     p.td_op = ctx->td_op;
+    p.tile_cnt = ctx->d_tile_cnt;
+    p.side = ctx->side;
+    p.ev_fork = ctx->ev_fork;
+    p.ev_join = ctx->ev_join;
     return p;
 }
 
@@ -555,6 +562,9 @@ void rttddft_destroy(rttddft_ctx* ctx) {
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -711,6 +721,9 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             ctx->d_part_t = dalloc<zd>(ctx, (size_t)nk * ctx->nslot * 2 * ctx->ntsel * ctx->maxng);
         }
         ctx->d_part_jmt = dalloc<double>(ctx, (size_t)nk * std::max(at.lrows, 1) * 5);
+        // one counter per 8-row tile and k-point (the smallest row tile of the FP32 kernels)
+        ctx->d_tile_cnt = dalloc<unsigned>(ctx, (size_t)nk * ((std::max(at.ma, 1) + 7) / 8));
+        CK(cudaMemset(ctx->d_tile_cnt, 0, sizeof(unsigned) * nk * ((std::max(at.ma, 1) + 7) / 8)));
         ctx->d_part_full = dalloc<double>(ctx, (size_t)nk * ctx->max_nback * 5);
         ctx->d_part_post = dalloc<double>(ctx, (size_t)nk * naux * POST_STRIDE);
         CK(cudaMemset(ctx->d_part_jmt, 0, sizeof(double) * nk * std::max(at.lrows, 1) * 5));
@@ -976,6 +989,9 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             if (e) fail(ctx, e, why);
             ctx->td_op = dupload(ctx, td.data(), td.size());
             if (fft_tune(ctx->fft, ctx->td_op, ns, ctx->stream)) fail(ctx, RTTDDFT_ERR_CUDA, "FFT route: set-up timing failed");
+            CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
             KCHECK();
             CK(cudaStreamSynchronize(ctx->stream));
         }
@@ -1389,6 +1405,7 @@ int rttddft_observables(rttddft_ctx* ctx, rttddft_obs* out, int clear) {
             if (out->norm_dev) out->norm_dev[i] = q[REC_NDEV];
             if (out->resid) out->resid[i] = q[REC_RES];
             if (out->dt_cr) out->dt_cr[i] = q[REC_DTCR];
+            if (out->n_exc) out->n_exc[i] = q[REC_NEXC];
         }
         out->count = n;
         if (clear) {
@@ -2053,6 +2070,8 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         }
         StepPlan p = make_plan(ctx);
         p.fft = nullptr;
+        p.side = nullptr;
+        p.tile_cnt = nullptr;  // the context's counters may be in use on another stream
         p.gd_fwd = (const GemmDesc*)(base + o_gd);
         p.maxng = ng;
         p.part = (zd*)(base + o_part);

@@ -132,6 +132,7 @@ struct WarpHalvingSum {
 // sums to out[0 .. V-1] (one writer per value).
 template <typename T, int V>
 __device__ __forceinline__ void warp_sum_store(T* v, int lane, T* out) {
+    static_assert(V > 0 && (V & (V - 1)) == 0, "warp_sum_store reduces a power of two of values");
     int base = 0;
     WarpHalvingSum<T, V, 16>::run(v, lane, base);
     constexpr int REM = V >= 32 ? V / 32 : 1;

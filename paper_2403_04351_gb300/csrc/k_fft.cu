@@ -294,28 +294,43 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_c(FftArgs f) {
         const int p = K.plane_of[r1];
         x[l * F1 + r1] = (p >= 0) ? b2[(size_t)p * pst + off + l] : cmk<C>(0, 0);
     }
-    __syncthreads();
-    C* r = fft_lines(x, y, nl, F1, f.rad[0], f.nst[0], W, true);
+    // the potential of this block's points, loaded (coalesced along r3) before
+    // the inverse transform so that the loads overlap it
+    constexpr int PV = FFT_MAX_N * FFT_LPB / FFT_THREADS;
+    C pv[PV];
     {
         const C* v = (const C*)f.v;
         const C* vd = (const C*)f.vd;
         typedef typename Rt<C>::R R_;
         const R_ sc = f.use_vd ? (R_)(*f.s) : R_(0);
-        for (int i = threadIdx.x; i < F1 * nl; i += blockDim.x) {
-            const int l = i / F1, r1 = i - l * F1;
-            const size_t gi = (size_t)r1 * pst + off + l;
-            C pv;
-            if (f.vmode == 0) {
-                pv = v[gi];
-                if (f.use_vd) {
+#pragma unroll
+        for (int u = 0; u < PV; ++u) {
+            const int i = threadIdx.x + u * FFT_THREADS;
+            pv[u] = cmk<C>(0, 0);
+            if (i < F1 * nl) {
+                const int r1 = i / nl, l = i - r1 * nl;
+                const size_t gi = (size_t)r1 * pst + off + l;
+                if (f.vmode == 0) {
+                    pv[u] = v[gi];
+                    if (f.use_vd) {
+                        const C d = vd[gi];
+                        pv[u] = cmk<C>(pv[u].x + sc * d.x, pv[u].y + sc * d.y);
+                    }
+                } else {
                     const C d = vd[gi];
-                    pv = cmk<C>(pv.x + sc * d.x, pv.y + sc * d.y);
+                    pv[u] = cmk<C>(sc * d.x, sc * d.y);
                 }
-            } else {
-                const C d = vd[gi];
-                pv = cmk<C>(sc * d.x, sc * d.y);
             }
-            r[i] = cml(r[i], pv);
+        }
+    }
+    __syncthreads();
+    C* r = fft_lines(x, y, nl, F1, f.rad[0], f.nst[0], W, true);
+#pragma unroll
+    for (int u = 0; u < PV; ++u) {
+        const int i = threadIdx.x + u * FFT_THREADS;
+        if (i < F1 * nl) {
+            const int r1 = i / nl, l = i - r1 * nl;
+            r[l * F1 + r1] = cml(r[l * F1 + r1], pv[u]);
         }
     }
     __syncthreads();

@@ -178,7 +178,8 @@ __global__ void __launch_bounds__(256) k_gemm_cn(const GemmDesc* __restrict__ de
 template <int NT, int RPW, int KC>
 __global__ void __launch_bounds__(256) k_gemm_cn32(const GemmDesc* __restrict__ descs, int N, int kchunk,
                                                    zd* __restrict__ part, int beta_add,
-                                                   const double* __restrict__ dscale) {
+                                                   const double* __restrict__ dscale,
+                                                   unsigned* __restrict__ tile_cnt) {
     constexpr int U = KC / 32;  // loads of A per lane and row
     __shared__ zf bs[KC][NT];
     __shared__ float red[8][2 * RPW * NT];
@@ -243,6 +244,40 @@ __global__ void __launch_bounds__(256) k_gemm_cn32(const GemmDesc* __restrict__ 
                 *c = beta_add ? zadd(*c, val) : val;
             }
         }
+    }
+    if (!part || !tile_cnt) return;
+    // the last K slice of this row tile to finish sums the slices in slice
+    // order (the same sums as k_split_reduce, whichever block is last)
+    __shared__ unsigned last;
+    __threadfence();
+    __syncthreads();
+    const int nsp = (d.K + kchunk - 1) / kchunk;
+    if (threadIdx.x == 0) {
+        unsigned* c = tile_cnt + (size_t)blockIdx.z * gridDim.x + blockIdx.x;
+        last = (atomicAdd(c, 1u) == (unsigned)(nsp - 1)) ? 1u : 0u;
+        if (last) *c = 0u;  // ready for the next launch
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int rows = 8 * RPW;
+    const size_t st = (size_t)N * d.M;
+    for (int e = threadIdx.x; e < rows * N; e += 256) {
+        const int m = mb + e % rows, n = e / rows;
+        if (m >= d.M) continue;
+        const zd* p = part + d.part_off + (size_t)n * d.M + m;
+        zd sum = zmk(0.0, 0.0);
+        int sp = 0;
+        for (; sp + 8 <= nsp; sp += 8) {
+            zd t[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t[u] = __ldcg(p + (size_t)(sp + u) * st);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sum = zadd(sum, t[u]);
+        }
+        for (; sp < nsp; ++sp) sum = zadd(sum, __ldcg(p + (size_t)sp * st));
+        zd* c = d.C + m + (size_t)n * d.ldc;
+        *c = beta_add ? zadd(*c, sum) : sum;
     }
 }
 
@@ -407,24 +442,26 @@ void launch_gemm_nn(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kc
     if (a_fp32) gemm_nn_t<zf, zf>(d, nb, maxM, maxK, N, kchunk, part, beta_add, ds, s);
     else gemm_nn_t<zd, zd>(d, nb, maxM, maxK, N, kchunk, part, beta_add, ds, s);
 }
-void launch_gemm_cn(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kchunk, zd* part,
-                    int beta_add, bool a_fp32, const double* ds, cudaStream_t s) {
+bool launch_gemm_cn(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kchunk, zd* part,
+                    int beta_add, bool a_fp32, const double* ds, cudaStream_t s, unsigned* tile_cnt) {
     if (a_fp32 && nb > 0 && maxM > 0 && maxK > 0 && N > 0 && (kchunk > 0 ? kchunk : maxK) <= GEMM32_KC) {
         const int kc = kchunk > 0 ? kchunk : maxK;
+        unsigned* tc = part ? tile_cnt : nullptr;
         if (N <= 2) {
             dim3 grid((maxM + 31) / 32, (maxK + kc - 1) / kc, nb);
-            k_gemm_cn32<2, 4, GEMM32_KC><<<grid, 256, 0, s>>>(d, N, kc, part, beta_add, ds);
+            k_gemm_cn32<2, 4, GEMM32_KC><<<grid, 256, 0, s>>>(d, N, kc, part, beta_add, ds, tc);
         } else if (N <= 4) {
             dim3 grid((maxM + 15) / 16, (maxK + kc - 1) / kc, nb);
-            k_gemm_cn32<4, 2, GEMM32_KC><<<grid, 256, 0, s>>>(d, N, kc, part, beta_add, ds);
+            k_gemm_cn32<4, 2, GEMM32_KC><<<grid, 256, 0, s>>>(d, N, kc, part, beta_add, ds, tc);
         } else {
             dim3 grid((maxM + 7) / 8, (maxK + kc - 1) / kc, nb);
-            k_gemm_cn32<8, 1, GEMM32_KC><<<grid, 256, 0, s>>>(d, N, kc, part, beta_add, ds);
+            k_gemm_cn32<8, 1, GEMM32_KC><<<grid, 256, 0, s>>>(d, N, kc, part, beta_add, ds, tc);
         }
-        return;
+        return tc != nullptr;
     }
     if (a_fp32) gemm_cn_t<zf, zf>(d, nb, maxM, maxK, N, kchunk, part, beta_add, ds, s);
     else gemm_cn_t<zd, zd>(d, nb, maxM, maxK, N, kchunk, part, beta_add, ds, s);
+    return false;
 }
 void launch_split_reduce(const GemmDesc* d, int nb, int maxM, int N, int kchunk, const zd* part,
                          int beta_add, cudaStream_t s) {

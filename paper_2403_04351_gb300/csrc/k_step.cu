@@ -968,13 +968,47 @@ __global__ void k_reproj(StepArgs a) {
 __device__ void finalize_body(const StepArgs& a, int set_gs) {
     // the k-weights enter the per-row shares, so one block reduction covers all
     // k-points; sums by halving warp sums (each warp-wide FP64 add is costly on
-    // GB300), maxima of non-negative values as integer maxima of their bits
+    // GB300), maxima of non-negative values as integer maxima of their bits.
+    // The kernel is latency-bound: every row's loads are issued before its adds,
+    // and the scalars of the serial tail are fetched by the last warp meanwhile.
     __shared__ double sh[8][16];
     __shared__ unsigned long long shm[8][2];
+    __shared__ double pre[16];  // 0 t, 1-3 A, 4-6 J(t0), 7-9 J_ind prev, 10-12 dmu, 13 dt_cr, 14 N_e
+    __shared__ int pre_rec;
     DevState* st = a.st;
     const int ns = a.ns, n = a.naux, lrows = a.lrows;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    // 0-2 J_sub, 3 E, 4 c^H S c, 5-7 sum (G+k)|c|^2, 8-10 J_mt; all times w_k
+    if (warp == nw - 1) {
+        if (lane == 0) pre[0] = st->t;
+        if (lane >= 1 && lane <= 3) pre[lane] = st->cur_a[lane - 1];
+        if (lane >= 4 && lane <= 6) pre[lane] = st->j_gs[lane - 4];
+        if (lane >= 7 && lane <= 9) pre[lane] = st->jind_prev[lane - 7];
+        if (lane >= 10 && lane <= 12) pre[lane] = st->dmu[lane - 10];
+        if (lane == 13) pre_rec = st->rec_count;
+        if (!set_gs) {
+            // dt_cr and N_e over the k-points, one lane per k
+            double dtc = 1e300, ne = 0.0;
+            for (int k = lane; k < a.nk; k += 32) {
+                const KDev& K = a.kd[k];
+                const double dk = (a.prop == 1) ? 0.2 / (K.eval[n - 1] - K.eval[0]) : 0.2 / (2.0 * K.lam[1]);
+                dtc = fmin(dtc, dk);
+                double f = 0.0;
+                for (int j = 0; j < ns; ++j) f += a.occ[j];
+                ne += a.wk[k] * f;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
+                ne += __shfl_xor_sync(0xffffffffu, ne, o);
+            }
+            if (lane == 0) {
+                pre[13] = dtc;
+                pre[14] = ne;
+            }
+        }
+    }
+    // 0-2 J_sub, 3 E, 4 c^H S c, 5-7 sum (G+k)|c|^2, 8-10 J_mt, 11 the occupied
+    // ground-state share sum_j f_j sum_{i < N_s} |theta_ij|^2; all times w_k
     double v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = 0.0;
@@ -982,27 +1016,44 @@ __device__ void finalize_body(const StepArgs& a, int set_gs) {
     for (int k = 0; k < a.nk; ++k) {
         const KDev& K = a.kd[k];
         const double w = a.wk[k];
-        const int nback = (K.ng + BKB - 1) / BKB;
-        for (int i = tid; i < n; i += blockDim.x) {
-            const double* p = a.part_post + ((size_t)k * n + i) * POST_STRIDE;
-            v[0] += w * __ldcg(p + 1);
-            v[1] += w * __ldcg(p + 2);
-            v[2] += w * __ldcg(p + 3);
-            mres = fmax(mres, __ldcg(p));
-        }
-        if (set_gs) continue;
-        for (int c = tid; c < nback; c += blockDim.x) {
-            const double* pf = a.part_full + ((size_t)k * a.max_nback + c) * 5;
+        const int nback = set_gs ? 0 : (K.ng + BKB - 1) / BKB;
+        const int lr = set_gs ? 0 : lrows;
+        const int cnt = max(n, max(nback, lr));
+        for (int i0 = 0; i0 < cnt; i0 += blockDim.x) {
+            const int i = i0 + tid;
+            double pp[4] = {0.0, 0.0, 0.0, 0.0}, pf[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, pj[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            if (i < n) {
+                const double* p = a.part_post + ((size_t)k * n + i) * POST_STRIDE;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pp[q] = __ldcg(p + q);
+            }
+            if (i < nback) {
+                const double* p = a.part_full + ((size_t)k * a.max_nback + i) * 5;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) pf[q] = p[q];
+            }
+            if (i < lr) {
+                const double* p = a.part_jmt + ((size_t)k * lrows + i) * 5;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) pj[q] = p[q];
+            }
+            mres = fmax(mres, pp[0]);
+            v[0] += w * pp[1];
+            v[1] += w * pp[2];
+            v[2] += w * pp[3];
 #pragma unroll
             for (int q = 0; q < 5; ++q) v[3 + q] += w * pf[q];
-        }
-        for (int r = tid; r < lrows; r += blockDim.x) {
-            const double* pj = a.part_jmt + ((size_t)k * lrows + r) * 5;
             v[8] += w * pj[0];
             v[9] += w * pj[1];
             v[10] += w * pj[2];
             v[3] += w * pj[3];
             v[4] += w * pj[4];
+        }
+        if (set_gs) continue;
+        for (int e = tid; e < ns * ns; e += blockDim.x) {
+            const int i = e % ns, j = e / ns;
+            const zd t = K.theta[i + (size_t)j * n];
+            v[11] += w * a.occ[j] * (t.x * t.x + t.y * t.y);
         }
         if (ns <= 4) {
             // the rows' shares of theta^H theta~ in a fixed order (one warp per entry)
@@ -1045,14 +1096,14 @@ __device__ void finalize_body(const StepArgs& a, int set_gs) {
         shm[warp][1] = bd;
     }
     __syncthreads();
-    if (tid < 11) {
+    if (tid < 12) {
         double t = sh[0][tid];
         for (int w = 1; w < nw; ++w) t += sh[w][tid];
         sh[0][tid] = t;
-    } else if (tid < 13) {
-        unsigned long long m = shm[0][tid - 11];
-        for (int w = 1; w < nw; ++w) m = shm[w][tid - 11] > m ? shm[w][tid - 11] : m;
-        shm[0][tid - 11] = m;
+    } else if (tid < 14) {
+        unsigned long long m = shm[0][tid - 12];
+        for (int w = 1; w < nw; ++w) m = shm[w][tid - 12] > m ? shm[w][tid - 12] : m;
+        shm[0][tid - 12] = m;
     }
     __syncthreads();
     if (tid != 0) return;
@@ -1060,7 +1111,7 @@ __device__ void finalize_body(const StepArgs& a, int set_gs) {
     double J[3], JF[3];
     for (int l = 0; l < 3; ++l) {
         J[l] = io * sh[0][l];
-        JF[l] = io * (sh[0][5 + l] + sh[0][8 + l] + st->cur_a[l] * a.inv_c * sh[0][4]);
+        JF[l] = io * (sh[0][5 + l] + sh[0][8 + l] + pre[1 + l] * a.inv_c * sh[0][4]);
     }
     if (set_gs) {
         for (int l = 0; l < 3; ++l) st->j_gs[l] = J[l];
@@ -1069,29 +1120,26 @@ __device__ void finalize_body(const StepArgs& a, int set_gs) {
     const double E = sh[0][3];
     const double res = __longlong_as_double((long long)shm[0][0]);
     const double ndev = __longlong_as_double((long long)shm[0][1]);
-    double dtcr = 1e300;
-    for (int k = 0; k < a.nk; ++k) {
-        const KDev& K = a.kd[k];
-        const double dk = (a.prop == 1) ? 0.2 / (K.eval[n - 1] - K.eval[0]) : 0.2 / (2.0 * K.lam[1]);
-        dtcr = fmin(dtcr, dk);
-    }
-    const double t = st->t + a.dt;
-    double* r = a.rec + (size_t)st->rec_count * RTD_REC_STRIDE;
+    const double t = pre[0] + a.dt;
+    double* r = a.rec + (size_t)pre_rec * RTD_REC_STRIDE;
     r[REC_T] = t;
     for (int l = 0; l < 3; ++l) {
-        const double jind = J[l] - st->j_gs[l];
-        st->dmu[l] += a.omega * a.dt * 0.5 * (st->jind_prev[l] + jind);
+        const double jind = J[l] - pre[4 + l];
+        const double dmu = pre[10 + l] + a.omega * a.dt * 0.5 * (pre[7 + l] + jind);
+        st->dmu[l] = dmu;
         st->jind_prev[l] = jind;
         r[REC_J + l] = J[l];
         r[REC_JF + l] = JF[l];
-        r[REC_DMU + l] = st->dmu[l];
+        r[REC_DMU + l] = dmu;
     }
     r[REC_E] = E;
+    // number of excited electrons: N_e minus the occupied ground-state share
+    r[REC_NEXC] = pre[14] - sh[0][11];
     r[REC_NDEV] = ndev;
     r[REC_RES] = res;
-    r[REC_DTCR] = dtcr;
+    r[REC_DTCR] = pre[13];
     st->t = t;
-    st->rec_count += 1;
+    st->rec_count = pre_rec + 1;
     st->gstep += 1;
     st->cstep += 1;
     st->bar = 0u;  // the next step's cooperative series counts from zero
@@ -1409,7 +1457,7 @@ static size_t toep_smem(const StepArgs& a, size_t tc, size_t tt) {
 }
 
 template <typename TA, typename TT, typename TC, int NT>
-static int back_launch(const StepArgs& a, int maxng, cudaStream_t s, TraceHook* tr) {
+static int back_launch(const StepArgs& a, int maxng, cudaStream_t s, TraceHook* tr, cudaEvent_t join) {
     const size_t sm = toep_smem<NT>(a, sizeof(TC), sizeof(TT));
     // in the tensor-core form the interstitial slots are done already: only
     // the back-projection slots run here
@@ -1424,6 +1472,7 @@ static int back_launch(const StepArgs& a, int maxng, cudaStream_t s, TraceHook* 
             k_toep_seg<TA, TT, TC, NT><<<gt, BT, sm, s>>>(a, n0, slot0);
             mark(tr, slot0 ? "backprojection" : "toeplitz_and_backprojection", s);
         }
+        if (join && n0 == 0) cudaStreamWaitEvent(s, join, 0);  // the interstitial rows of the side stream
         k_back<NT><<<gb, BKB, 0, s>>>(a, n0);
         mark(tr, "back_finish", s);
         ++nl;
@@ -1471,6 +1520,9 @@ int prepare_back_kernels(const StepArgs& a) {
 int launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr) {
     const bool f32 = a.prec >= 1;
     int nl = 0;
+    // trace mode keeps one stream so that its events time every launch in turn
+    const bool fork = p.fft && p.side && a.prec < 2 && !tr;
+    const cudaEvent_t join = fork ? p.ev_join : nullptr;
     if (a.prec >= 2) {
         // tensor cores: V~ * C_G and Q = A C_G in one split-BF16 launch
         launch_tc_pack(p.tc, a, s);
@@ -1482,17 +1534,30 @@ int launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, T
         nl += 2;
     } else {
         if (p.fft) {
-            // V~ * C_G by FFT (th), the current table V~ + s dV~ when the change is on
-            nl += launch_fft_conv(p.fft, p.td_op, a.kofs, a.nk, a.ns, 0, a.dv_on, &a.st->cur_s, s);
-            mark(tr, "fft_interstitial", s);
+            // V~ * C_G by FFT (th), the current table V~ + s dV~ when the change is on.
+            // It needs only C, so it runs on the side stream beside the matching
+            // rows, the muffin-tin blocks and the back-projection, and k_back waits for it.
+            cudaStream_t fs = s;
+            if (fork) {
+                cudaEventRecord(p.ev_fork, s);
+                cudaStreamWaitEvent(p.side, p.ev_fork, 0);
+                fs = p.side;
+            }
+            nl += launch_fft_conv(p.fft, p.td_op, a.kofs, a.nk, a.ns, 0, a.dv_on, &a.st->cur_s, fs);
+            if (fork) cudaEventRecord(p.ev_join, p.side);
+            mark(tr, "fft_interstitial", fs);
         }
         if (a.ma > 0) {
             // Q = A C_G = (A^H)^H C_G: one warp per matching row; split-K in FP64
-            launch_gemm_cn(p.gd_fwd, a.nk, a.ma, p.maxng, a.ns, p.kc_fwd, p.part, 0, f32, nullptr, s);
+            const bool summed = launch_gemm_cn(p.gd_fwd, a.nk, a.ma, p.maxng, a.ns, p.kc_fwd, p.part, 0, f32,
+                                               nullptr, s, p.tile_cnt);
             mark(tr, "gemm_forward", s);
-            launch_split_reduce(p.gd_fwd, a.nk, a.ma, a.ns, p.kc_fwd, p.part, 0, s);
-            mark(tr, "split_reduce_forward", s);
-            nl += 2;
+            ++nl;
+            if (!summed) {
+                launch_split_reduce(p.gd_fwd, a.nk, a.ma, a.ns, p.kc_fwd, p.part, 0, s);
+                mark(tr, "split_reduce_forward", s);
+                ++nl;
+            }
         }
     }
     if (a.lrows > 0) {
@@ -1522,13 +1587,13 @@ int launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, T
         mark(tr, "tc_backprojection", s);
     }
     if (f32) {
-        if (a.ns <= 2) nl += back_launch<zf, zf, zf, 2>(a, p.maxng, s, tr);
-        else if (a.ns <= 4) nl += back_launch<zf, zf, zf, 4>(a, p.maxng, s, tr);
-        else nl += back_launch<zf, zf, zf, 8>(a, p.maxng, s, tr);
+        if (a.ns <= 2) nl += back_launch<zf, zf, zf, 2>(a, p.maxng, s, tr, join);
+        else if (a.ns <= 4) nl += back_launch<zf, zf, zf, 4>(a, p.maxng, s, tr, join);
+        else nl += back_launch<zf, zf, zf, 8>(a, p.maxng, s, tr, join);
     } else {
-        if (a.ns <= 2) nl += back_launch<zd, zd, zd, 2>(a, p.maxng, s, tr);
-        else if (a.ns <= 4) nl += back_launch<zd, zd, zd, 4>(a, p.maxng, s, tr);
-        else nl += back_launch<zd, zd, zd, 8>(a, p.maxng, s, tr);
+        if (a.ns <= 2) nl += back_launch<zd, zd, zd, 2>(a, p.maxng, s, tr, join);
+        else if (a.ns <= 4) nl += back_launch<zd, zd, zd, 4>(a, p.maxng, s, tr, join);
+        else nl += back_launch<zd, zd, zd, 8>(a, p.maxng, s, tr, join);
     }
     return nl;
 }

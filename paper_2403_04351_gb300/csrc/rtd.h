@@ -16,7 +16,7 @@
 
 // Record fields (offsets within one record)
 enum { REC_T = 0, REC_J = 1, REC_JF = 4, REC_DMU = 7, REC_E = 10, REC_NDEV = 11,
-       REC_RES = 12, REC_DTCR = 13 };
+       REC_RES = 12, REC_DTCR = 13, REC_NEXC = 14 };
 
 // One entry of a batched GEMM; batched kernels index an array of these
 // with blockIdx.z.  Matrices are complex column-major.
@@ -154,8 +154,13 @@ struct StepArgs {
 // ---- k_linalg.cu
 void launch_gemm_nn(const GemmDesc* d, int nbatch, int maxM, int maxK, int N, int kchunk,
                     zd* part, int beta_add, bool a_fp32, const double* dscale, cudaStream_t s);
-void launch_gemm_cn(const GemmDesc* d, int nbatch, int maxM, int maxK, int N, int kchunk,
-                    zd* part, int beta_add, bool a_fp32, const double* dscale, cudaStream_t s);
+// returns true when the split-K slices were also summed into C by the launch
+// itself (FP32 streaming kernel with tile counters: the last slice of a row
+// tile sums them in slice order); otherwise a split launch needs
+// launch_split_reduce.  tile_cnt: zeroed, one counter per (row tile, batch).
+bool launch_gemm_cn(const GemmDesc* d, int nbatch, int maxM, int maxK, int N, int kchunk,
+                    zd* part, int beta_add, bool a_fp32, const double* dscale, cudaStream_t s,
+                    unsigned* tile_cnt = nullptr);
 void launch_split_reduce(const GemmDesc* d, int nbatch, int maxM, int N, int kchunk, const zd* part,
                          int beta_add, cudaStream_t s);
 // dmode: 0 none, 1 kinetic |G+k|^2/2, 2..4 (G+k)_{x,y,z}, 5 unit
@@ -186,6 +191,9 @@ struct StepPlan {
     int max_sweeps;
     const struct TcPlan* tc;  // tensor-core operator plan (split-BF16 form) or null
     const struct FftPlan* fft;  // FFT route of the interstitial convolution or null
+    unsigned* tile_cnt;         // zeroed row-tile counters of the fused split-K sums (or null)
+    cudaStream_t side;          // second stream for work that overlaps the main chain (or null)
+    cudaEvent_t ev_fork, ev_join;
     const ToepDesc* td_op;      // per k: {C, th}: the operator's convolution source and destination
 };
 // Optional per-kernel tracing: an event is recorded after every launch of a step.

@@ -28,7 +28,7 @@ INTERSTITIAL = {"toeplitz": 0, "fft": 1}
 EXPORTED = ["rttddft_default_options", "rttddft_setup", "rttddft_step", "rttddft_observables",
             "rttddft_set_dv", "rttddft_apply", "rttddft_get_state", "rttddft_set_state",
             "rttddft_get_aux", "rttddft_get_info", "rttddft_adjoint", "rttddft_trace_steps",
-            "rttddft_apply_noalloc", "rttddft_zgemm_bf16x3",
+            "rttddft_apply_noalloc", "rttddft_zgemm_bf16x3", "rttddft_polarizability",
             "rttddft_destroy", "rttddft_last_error", "rttddft_version"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -56,7 +56,7 @@ class rttddft_options(ctypes.Structure):
 class rttddft_obs(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_int), ("count", ctypes.c_int), ("t", _dp), ("j", _dp),
                 ("j_full", _dp), ("dmu", _dp), ("energy", _dp), ("norm_dev", _dp),
-                ("resid", _dp), ("dt_cr", _dp)]
+                ("resid", _dp), ("dt_cr", _dp), ("n_exc", _dp)]
 
 
 class rttddft_info(ctypes.Structure):
@@ -125,6 +125,9 @@ def load_library(path=None):
     lib.rttddft_zgemm_bf16x3.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
                                          ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp]
     lib.rttddft_zgemm_bf16x3.restype = ctypes.c_int
+    d = ctypes.c_double
+    lib.rttddft_polarizability.argtypes = [ctypes.c_int, d, d, vp, vp, d, ctypes.c_int, vp, d, vp, vp, vp, vp]
+    lib.rttddft_polarizability.restype = ctypes.c_int
     lib.rttddft_destroy.argtypes = [vp]
     lib.rttddft_destroy.restype = None
     lib.rttddft_last_error.argtypes = [vp]
@@ -190,6 +193,24 @@ def rttddft_apply_noalloc(ctx, k, ncols, x, a_vec, dv_scale, hx, sx):
     """Operator apply with the library's static scratch (device pointers only)."""
     _check(ctx, load_library().rttddft_apply_noalloc(ctx, int(k), int(ncols), _ptr(x), _ptr(a_vec),
                                                      float(dv_scale), _ptr(hx), _ptr(sx)))
+
+
+def rttddft_polarizability(t0, dt, j_ind, e_field, w, omega_cell, eta=0.0, stream=None):
+    """alpha(w) of Eq. polarizability with J(w) and E(w) (numpy in, numpy out)."""
+    j = np.ascontiguousarray(j_ind, dtype=np.float64).reshape(-1, 3)
+    e = np.ascontiguousarray(e_field, dtype=np.float64).reshape(-1, 3)
+    if j.shape != e.shape:
+        raise ValueError("j_ind and e_field need the same [n_t][3] shape")
+    wv = np.ascontiguousarray(w, dtype=np.float64).ravel()
+    oj = np.zeros((wv.size, 3), dtype=np.complex128)
+    oe = np.zeros((wv.size, 3), dtype=np.complex128)
+    al = np.zeros((wv.size, 3, 3), dtype=np.complex128)
+    lib = load_library()
+    code = lib.rttddft_polarizability(int(j.shape[0]), float(t0), float(dt), _ptr(j), _ptr(e), float(eta),
+                                      int(wv.size), _ptr(wv), float(omega_cell), _ptr(oj), _ptr(oe), _ptr(al),
+                                      _ptr(stream))
+    _check(None, code)
+    return al, oj, oe
 
 
 def rttddft_zgemm_bf16x3(trans, m, n, k, a, lda, x, ldx, c, ldc, beta_add=0, stream=None):
@@ -323,7 +344,7 @@ class Context:
 
     def observables(self, clear=True):
         cap = self.max_record
-        out = {k: np.zeros(cap) for k in ("t", "energy", "norm_dev", "resid", "dt_cr")}
+        out = {k: np.zeros(cap) for k in ("t", "energy", "norm_dev", "resid", "dt_cr", "n_exc")}
         for k in ("j", "j_full", "dmu"):
             out[k] = np.zeros((cap, 3))
         obs = rttddft_obs()

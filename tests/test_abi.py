@@ -119,3 +119,16 @@ def test_fft_route_options_are_checked_on_the_host(lib, small):
         _expect("ERR_UNSUPPORTED", small, interstitial="bogus")
     finally:
         rttddft.INTERSTITIAL = o
+
+
+def test_polarizability_arguments_checked_on_the_host(lib):
+    j = np.zeros((10, 3))
+    w = np.array([0.5, 1.0])
+    f = lib.rttddft_polarizability
+    P = rttddft._ptr
+    assert f(0, 0.0, 0.1, P(j), P(j), 0.0, 2, P(w), 1.0, None, None, None, None) == -1
+    assert f(10, 0.0, 0.0, P(j), P(j), 0.0, 2, P(w), 1.0, None, None, None, None) == -1
+    assert f(10, 0.0, 0.1, P(j), P(j), -1.0, 2, P(w), 1.0, None, None, None, None) == -1
+    wb = np.array([0.5, 0.0])
+    assert f(10, 0.0, 0.1, P(j), P(j), 0.0, 2, P(wb), 1.0, None, None, None, None) == -1
+    assert f(10, 0.0, 0.1, P(j), P(j), 0.0, 2, P(w), 0.0, None, None, None, None) == -1

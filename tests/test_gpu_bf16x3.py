@@ -94,6 +94,7 @@ def test_step_error_per_observable_tiny400(form, etol, jtol, ntol):
     obs = ctx.observables()
     assert rel(obs["dmu"], r["dmu"]) < 1e-8
     assert rel(obs["j"], r["J"]) < 1e-10
+    assert np.max(np.abs(obs["n_exc"] - r["n_exc"])) < 1e-10
     assert rel(obs["energy"], r["E"]) < etol
     assert rel(obs["j_full"], r["J_full"]) < jtol
     assert np.max(obs["norm_dev"]) < ntol

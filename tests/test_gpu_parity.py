@@ -114,6 +114,16 @@ def compare_run(obs, r, dmu_tol=1e-8, j_tol=1e-10, e_tol=1e-10):
     assert rel(obs["energy"], r["E"]) < e_tol
     assert np.max(obs["norm_dev"]) < 1e-10
     assert np.max(obs["resid"]) < 1e-10
+    # excited electrons from the FP64 state: absolute, N_e times a few 1e-12
+    assert np.max(np.abs(obs["n_exc"] - r["n_exc"])) < 1e-10
+
+
+def test_excited_electrons_stay_zero_without_field(tiny):
+    ctx = Context(tiny, graph_steps=10)
+    ctx.step(np.zeros((40, 3)))
+    obs = ctx.observables()
+    assert np.max(np.abs(obs["n_exc"])) < 1e-12
+    ctx.close()
 
 
 def test_chebyshev_step_matches_oracle_over_200_steps(tiny, tiny_oracle):
@@ -187,6 +197,7 @@ def test_fp32_form_error_per_observable(tiny, tiny_oracle):
     # the state of record (theta) and the current J stay FP64
     assert rel(obs["dmu"], r["dmu"]) < 1e-8
     assert rel(obs["j"], r["J"]) < 1e-10
+    assert np.max(np.abs(obs["n_exc"] - r["n_exc"])) < 1e-10
     # observables of the FP32 full-basis pass
     assert rel(obs["energy"], r["E"]) < 1e-5
     assert rel(obs["j_full"], r["J_full"]) < 1e-4

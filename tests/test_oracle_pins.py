@@ -13,7 +13,7 @@ import scipy.linalg as sla
 
 from oracle import (Oracle, critical_timestep, explicit_dv, explicit_operators,
                     full_basis_propagator, hamiltonian, interstitial_potential,
-                    overall_speedup, propagate_cn, propagate_exact, ritz_basis)
+                    overall_speedup, polarizability, propagate_cn, propagate_exact, ritz_basis)
 from synth import make_dv, make_system, pulse_samples, tiny_config
 from systems import free_electron_system, permutation_mt_system, plane_wave_basis
 
@@ -152,6 +152,39 @@ def test_complete_subspace_equals_full_basis_propagation():
     for k in range(6):
         c = full_basis_propagator(ops, a[k], s["c_light"], 0.3) @ c
     assert _rel(r["C"][0], c) < 1e-11
+
+
+def test_excited_electrons_match_full_basis_projection():
+    """N_exc = N_e - sum_j f_j sum_{i < N_s} |<phi_i(0)| S |psi_j(t)>|^2 from an
+    independent route: brute-force full-basis propagation and the occupied
+    generalized eigenvectors of (H0, S) from LAPACK, in a complete subspace;
+    zero when no field acts."""
+    s = make_system(tiny_config(n_g=24, n_atoms=2, lmax=1, n_lo_per_atom=2, n_s=3,
+                                seed=21))
+    orc = Oracle(s)
+    ops = explicit_operators(s, 0)
+    still = orc.run(np.zeros((8, 3)), 0.3)
+    assert np.max(np.abs(still["n_exc"])) < 1e-13
+    a = pulse_samples(s, n_steps=6, dt=0.3, a0=20.0, omega=0.5, edir=(0.2, 0.5, 0.8))
+    r = orc.run(a, 0.3)
+    h0 = hamiltonian(ops, np.zeros(3), s["c_light"])
+    w, phi = sla.eigh(h0, ops["S"])
+    occ = np.asarray(s["occ"])
+    ns = int(s["n_s"])
+    c = orc.kp[0]["caux"] @ orc.kp[0]["theta0"]
+    assert r["n_exc"].min() > 0.0
+    for k in range(6):
+        c = full_basis_propagator(ops, a[k], s["c_light"], 0.3) @ c
+        ov = phi[:, :ns].conj().T @ ops["S"] @ c
+        brute = float(np.sum(occ)) - float(np.sum(occ[None, :] * np.abs(ov) ** 2))
+        assert abs(r["n_exc"][k] - brute) < 1e-11
+
+
+def test_excited_electrons_are_second_order_in_a_weak_field(tiny_oracle, tiny):
+    n1 = tiny_oracle.run(pulse_samples(tiny, n_steps=100, a0=5e-3), 0.1)["n_exc"][-1]
+    n2 = tiny_oracle.run(pulse_samples(tiny, n_steps=100, a0=1e-2), 0.1)["n_exc"][-1]
+    assert n1 > 0.0
+    assert abs(n2 / n1 - 4.0) < 1e-3
 
 
 # -------------------------------------------------------------- propagators
@@ -344,3 +377,42 @@ def test_overall_speedups_of_table_h2():
             assert abs(got - s) <= tol * s + 0.5
             # the inverse reading (time x step length) is far off
             assert abs(139.0 * 0.0012 / (t * dtcr) - s) > 0.5 * s
+
+
+# --------------------------------------------------------------- spectrum
+
+def test_damped_transform_of_a_cosine_is_a_geometric_series():
+    """F(w) = dt sum_n cos(w0 t_n) e^{(i w - eta) t_n} in closed form:
+    (dt/2) sum_pm e^{z t0} (1 - e^{z N dt}) / (1 - e^{z dt}), z = i(w pm w0) - eta."""
+    t0, dt, n, w0, eta = 0.2, 0.05, 3000, 0.7, 0.01
+    t = t0 + dt * np.arange(n)
+    f = np.stack([np.cos(w0 * t), 2.0 * np.cos(w0 * t), np.zeros(n)], axis=1)
+    e = np.ones((n, 3))
+    w = np.array([0.3, 0.69, 1.4])
+    _, jw, _ = polarizability(t0, dt, f, e, w, 1.0, eta=eta)
+    expect = np.zeros(w.size, dtype=complex)
+    for sgn in (1.0, -1.0):
+        z = 1j * (w + sgn * w0) - eta
+        expect += 0.5 * dt * np.exp(z * t0) * (1 - np.exp(z * n * dt)) / (1 - np.exp(z * dt))
+    assert np.max(np.abs(jw[:, 0] - expect)) < 1e-12 * np.max(np.abs(expect))
+    assert np.max(np.abs(jw[:, 1] - 2 * expect)) < 1e-12 * np.max(np.abs(expect))
+    assert np.all(jw[:, 2] == 0)
+
+
+def test_polarizability_of_a_proportional_response():
+    """J_l(t) = kappa_l E_l(t) gives alpha_ll = i Omega kappa_l / w and
+    alpha_{l l'} = (i Omega / w) kappa_l E_l(w) / E_l'(w); a zero field
+    component leaves its column at 0."""
+    rng = np.random.default_rng(2)
+    n = 500
+    e = rng.standard_normal((n, 3))
+    e[:, 2] = 0.0
+    kappa = np.array([0.3, -1.2, 0.5])
+    j = e * kappa[None, :]
+    w = np.array([0.1, 0.5, 2.0])
+    om = 123.0
+    al, jw, ew = polarizability(0.0, 0.1, j, e, w, om, eta=0.02)
+    for l in range(2):
+        assert np.max(np.abs(al[:, l, l] - 1j * om * kappa[l] / w)) < 1e-12 * om / w.min()
+    assert np.max(np.abs(al[:, 0, 1] - 1j * om / w * kappa[0] * ew[:, 0] / ew[:, 1])) < 1e-9
+    assert np.all(al[:, :, 2] == 0)

@@ -6,9 +6,11 @@ this package.  The CUDA library never imports, links or calls it.
 from .rttddft_oracle import (Oracle, explicit_operators, explicit_dv, hamiltonian,
                              interstitial_potential, embedding, ritz_basis, fix_phases,
                              propagate_exact, propagate_cn, critical_timestep,
-                             overall_speedup, full_basis_propagator, polarizability, F_CRIT)
+                             overall_speedup, full_basis_propagator, polarizability, F_CRIT,
+                             interstitial_density, hartree_table)
 
 __all__ = ["Oracle", "explicit_operators", "explicit_dv", "hamiltonian",
            "interstitial_potential", "embedding", "ritz_basis", "fix_phases",
            "propagate_exact", "propagate_cn", "critical_timestep", "overall_speedup",
-           "full_basis_propagator", "polarizability", "F_CRIT"]
+           "full_basis_propagator", "polarizability", "F_CRIT",
+           "interstitial_density", "hartree_table"]

@@ -37,7 +37,12 @@ Readings where the paper is silent (each listed in the design notes):
 * the dipole integral is the trapezoid rule on the step grid, dmu(t0) = 0;
 * the auxiliary basis is the set of Ritz vectors of H0 in the span of the
   given trial vectors (S-orthonormal, H0 diagonal on them), each scaled so
-  that the sum of its coefficients is real and positive.
+  that the sum of its coefficients is real and positive;
+* the per-step potential from the evolving density (Sec. 2: VV(t) is what
+  changes from step to step) is modelled by its Hartree part in the
+  interstitial only: n_g = (1/Omega) sum_k w_k sum_j f_j sum_G C_G conj(C_{G-g})
+  over the plane-wave rows, dV_g = 4 pi (n_g(t) - n_g(0)) / |g|^2 (g != 0,
+  cartesian g), on the table box; the potential of step k comes from C_k.
 """
 from __future__ import annotations
 
@@ -111,6 +116,40 @@ def explicit_dv(sys, ik, dv):
         e = embedding(sys, ik, a)
         m += e.conj().T @ dv["dh"][a] @ e
     return m
+
+
+def interstitial_density(sys, cs, occ, wk, omega):
+    """Fourier coefficients n_g of the interstitial density on the table box
+    (shape vt_dim, g_i from -e_i to e_i): n_g = (1/Omega) sum_k w_k sum_j f_j
+    sum_{G, G - g in the set} C_Gj conj(C_{G-g, j}), from the plane-wave rows
+    of the coefficient matrices cs[k] (n_b x n_s); the e^{ik.r} phase of a
+    Bloch state drops out of |psi|^2."""
+    dim = np.asarray(sys["vt_dim"])
+    e = (dim - 1) // 2
+    box = np.zeros(tuple(int(x) for x in dim), dtype=np.complex128)
+    for ik, c in enumerate(cs):
+        gi = np.asarray(sys["g_int"][ik])
+        cg = np.asarray(c)[:gi.shape[0], :]
+        for g in range(gi.shape[0]):
+            d = gi[g][None, :] - gi + e[None, :]
+            val = wk[ik] * ((cg[g][None, :] * np.conj(cg)) @ occ)
+            np.add.at(box, (d[:, 0], d[:, 1], d[:, 2]), val)
+    return box / omega
+
+
+def hartree_table(sys, n, n0):
+    """dV_g = 4 pi (n_g - n0_g) / |g|^2 on the table box, 0 at g = 0 (the
+    Poisson equation in G space; g cartesian from the reciprocal vectors)."""
+    dim = np.asarray(sys["vt_dim"])
+    e = (dim - 1) // 2
+    r = [np.arange(-x, x + 1) for x in e]
+    d1, d2, d3 = np.meshgrid(r[0], r[1], r[2], indexing="ij")
+    gc = np.stack([d1, d2, d3], axis=-1).astype(np.float64) @ np.asarray(sys["recip"])
+    g2 = np.einsum("...i,...i->...", gc, gc)
+    out = np.zeros_like(n)
+    nz = g2 > 0
+    out[nz] = 4.0 * math.pi * (n[nz] - n0[nz]) / g2[nz]
+    return out
 
 
 def hamiltonian(ops, a_vec, c_light, dv_mat=None, dv_scale=0.0):
@@ -216,7 +255,7 @@ class Oracle:
 
     # Eq. auxiliary_hamiltonian_with_parts with VV(t) = VV(0) + dVV(t),
     # T + VV(0) = CC^H H0 CC, dVV(t) = CC^H (s dV_1) CC recomputed per step
-    def subspace_hamiltonian(self, ik, a_vec, dv_scale=0.0):
+    def subspace_hamiltonian(self, ik, a_vec, dv_scale=0.0, extra=None):
         kp = self.kp[ik]
         a = np.asarray(a_vec, dtype=np.float64)
         h = kp["h0sub"].copy()
@@ -226,7 +265,23 @@ class Oracle:
         if kp["dv"] is not None and dv_scale != 0.0:
             cc = kp["caux"]
             h += cc.conj().T @ (dv_scale * kp["dv"]) @ cc
+        if extra is not None:
+            cc = kp["caux"]
+            h += cc.conj().T @ extra @ cc
         return h
+
+    def hartree_matrices(self, thetas, n0):
+        """Dense interstitial Hartree potential change of every k-point for the
+        state C = CC theta (its density against the reference n0)."""
+        cs = [kp["caux"] @ t for kp, t in zip(self.kp, thetas)]
+        table = hartree_table(self.sys, interstitial_density(self.sys, cs, self.occ, self.wk, self.omega), n0)
+        out = []
+        for ik, kp in enumerate(self.kp):
+            ng = kp["ops"]["ng"]
+            m = np.zeros((kp["ops"]["nb"], kp["ops"]["nb"]), dtype=np.complex128)
+            m[:ng, :ng] = interstitial_potential(self.sys["g_int"][ik], self.sys["vt_dim"], table)
+            out.append(m)
+        return out, table
 
     def _current_full(self, cs, a_vec):
         a = np.asarray(a_vec, dtype=np.float64)
@@ -253,9 +308,11 @@ class Oracle:
         return j
 
     def run(self, a_samples, dt, propagator="exact", reproject=False, dv_scale=None,
-            thetas=None, keep_states=False):
+            thetas=None, keep_states=False, hartree=False):
         """Propagate len(a_samples) steps.  Returns a dict of per-step records
-        (t, J, J_full, dmu, E, norm_dev, resid, dtcr), final theta and C."""
+        (t, J, J_full, dmu, E, norm_dev, resid, dtcr, n_exc), final theta and C.
+        hartree: the interstitial Hartree potential of the density of C_k
+        (against that of the starting state) acts during step k."""
         a_samples = np.asarray(a_samples, dtype=np.float64)
         n = a_samples.shape[0]
         nk = len(self.kp)
@@ -266,13 +323,21 @@ class Oracle:
         states = []
         dmu = np.zeros(3)
         jind_prev = np.zeros(3)
+        if hartree:
+            cs0 = [kp["caux"] @ t for kp, t in zip(self.kp, th)]
+            n0 = interstitial_density(self.sys, cs0, self.occ, self.wk, self.omega)
+            rec["hartree_l1"] = []
         for k in range(n):
             a = a_samples[k]
             s = 0.0 if dv_scale is None else float(dv_scale[k])
             cs, hcs, e_tot, ndev, res, lam_rng = [], [], 0.0, 0.0, 0.0, []
+            vh = [None] * nk
+            if hartree:
+                vh, table = self.hartree_matrices(th, n0)
+                rec["hartree_l1"].append(float(np.sum(np.abs(table))))
             for ik in range(nk):
                 kp = self.kp[ik]
-                hsub = self.subspace_hamiltonian(ik, a, s)
+                hsub = self.subspace_hamiltonian(ik, a, s, extra=vh[ik])
                 if propagator == "exact":
                     th[ik], lam = propagate_exact(hsub, kp["ssub"], th[ik], dt)
                 elif propagator == "cn":
@@ -284,6 +349,8 @@ class Oracle:
                 c = kp["caux"] @ th[ik]
                 # apply H(t) and S with the explicit matrices
                 h = hamiltonian(kp["ops"], a, self.c, kp["dv"], s)
+                if vh[ik] is not None:
+                    h = h + vh[ik]
                 hc = h @ c
                 sc = kp["ops"]["S"] @ c
                 # project (theta = CC^H S C)

@@ -13,7 +13,8 @@ import scipy.linalg as sla
 
 from oracle import (Oracle, critical_timestep, explicit_dv, explicit_operators,
                     full_basis_propagator, hamiltonian, interstitial_potential,
-                    overall_speedup, polarizability, propagate_cn, propagate_exact, ritz_basis)
+                    overall_speedup, polarizability, propagate_cn, propagate_exact, ritz_basis,
+                    interstitial_density, hartree_table)
 from synth import make_dv, make_system, pulse_samples, tiny_config
 from systems import free_electron_system, permutation_mt_system, plane_wave_basis
 
@@ -416,3 +417,61 @@ def test_polarizability_of_a_proportional_response():
         assert np.max(np.abs(al[:, l, l] - 1j * om * kappa[l] / w)) < 1e-12 * om / w.min()
     assert np.max(np.abs(al[:, 0, 1] - 1j * om / w * kappa[0] * ew[:, 0] / ew[:, 1])) < 1e-9
     assert np.all(al[:, :, 2] == 0)
+
+
+# ------------------------------------------------------- Hartree feedback
+
+def test_interstitial_density_equals_fft_of_the_squared_orbitals(tiny, tiny_oracle):
+    """n_g from the explicit autocorrelation of the plane-wave coefficients
+    equals |psi(r)|^2 summed on a real-space grid and taken back to G space by
+    numpy's FFT (grid wider than the table box, so nothing aliases)."""
+    rng = np.random.default_rng(4)
+    ng = int(tiny["n_g"][0])
+    nb = ng + int(np.sum(tiny["n_lo"]))
+    c = rng.standard_normal((nb, 3)) + 1j * rng.standard_normal((nb, 3))
+    occ = np.array([2.0, 1.0, 0.5])
+    n = interstitial_density(tiny, [c], occ, np.array([1.0]), tiny["omega"])
+    dim = np.asarray(tiny["vt_dim"])
+    e = (dim - 1) // 2
+    F = dim + 3
+    gi = np.asarray(tiny["g_int"][0])
+    dens = np.zeros(tuple(F))
+    for j in range(3):
+        grid = np.zeros(tuple(F), dtype=np.complex128)
+        grid[gi[:, 0] % F[0], gi[:, 1] % F[1], gi[:, 2] % F[2]] = c[:ng, j]
+        psi = np.fft.ifftn(grid) * np.prod(F)       # sum_G C_G e^{+2 pi i G.r/F}
+        dens += occ[j] * np.abs(psi) ** 2
+    ng_fft = np.fft.fftn(dens) / np.prod(F) / tiny["omega"]
+    r = [np.arange(-x, x + 1) for x in e]
+    d1, d2, d3 = np.meshgrid(r[0], r[1], r[2], indexing="ij")
+    ref = ng_fft[d1 % F[0], d2 % F[1], d3 % F[2]]
+    assert _rel(n, ref) < 1e-12
+    # the density is real: n_{-g} = conj(n_g)
+    assert np.max(np.abs(n - np.conj(n[::-1, ::-1, ::-1]))) < 1e-15 * np.max(np.abs(n))
+
+
+def test_hartree_potential_has_positive_energy_and_zero_mean(tiny):
+    rng = np.random.default_rng(6)
+    dim = tuple(int(x) for x in tiny["vt_dim"])
+    z = rng.standard_normal(dim) + 1j * rng.standard_normal(dim)
+    dn = 0.5 * (z + np.conj(z[::-1, ::-1, ::-1]))  # a real density change
+    dv = hartree_table(tiny, dn, np.zeros(dim))
+    e = [(x - 1) // 2 for x in dim]
+    assert dv[e[0], e[1], e[2]] == 0.0
+    # E_H = (Omega/2) sum_g dV_g conj(dn_g) = (Omega/2) sum_g 4 pi |dn_g|^2/|g|^2 > 0
+    eh = 0.5 * tiny["omega"] * np.sum(dv * np.conj(dn))
+    assert abs(eh.imag) < 1e-12 * abs(eh.real) and eh.real > 0
+    # the potential of a real density is real in space: dV_{-g} = conj(dV_g)
+    assert np.max(np.abs(dv - np.conj(dv[::-1, ::-1, ::-1]))) < 1e-15 * np.max(np.abs(dv))
+
+
+def test_hartree_feedback_is_inert_without_field_and_keeps_the_norm(tiny_oracle, tiny):
+    still = tiny_oracle.run(np.zeros((12, 3)), 0.1, hartree=True)
+    plain = tiny_oracle.run(np.zeros((12, 3)), 0.1)
+    assert np.max(np.abs(still["theta"][0] - plain["theta"][0])) < 1e-13
+    a = pulse_samples(tiny, n_steps=20, a0=20.0)
+    r = tiny_oracle.run(a, tiny["dt"], hartree=True)
+    assert r["norm_dev"].max() < 1e-10
+    assert r["resid"].max() < 1e-12
+    r0 = tiny_oracle.run(a, tiny["dt"])
+    assert np.max(np.abs(r["dmu"] - r0["dmu"])) > 1e-6 * np.max(np.abs(r0["dmu"]))

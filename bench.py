@@ -35,7 +35,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # precision forms timed beside the headline one ("+fft": FFT route of the interstitial sum)
-FORMS = ("fp64", "fp32", "bf16x3", "fp16x3", "fp64+fft", "fp32+fft")
+FORMS = ("fp64", "fp32", "bf16x3", "fp16x3", "fp64+fft", "fp32+fft", "fp64+fft+hartree", "fp32+fft+hartree")
 METRIC = "state*steps/sec per GB300, plain FP64 vs split-precision/batched at stated error"
 UNIT = "state*steps/s"
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; the profiling recipe's table)
@@ -293,9 +293,11 @@ def run_ours(args, rank, world, local_rank):
 
     def timed_form(form, nsteps, nwarm):
         # a form is a precision form, with "+fft" for the FFT route of the interstitial sum
-        prec, _, route = form.partition("+")
-        ctx = Context(s, precision=prec, graph_steps=1, a_max=a0, max_record=nsteps + nwarm + 8,
-                      stream=stream.cuda_stream, interstitial="fft" if route == "fft" else "toeplitz")
+        # and "+hartree" for the density feedback (the per-step potential from the density)
+        parts = form.split("+")
+        ctx = Context(s, precision=parts[0], graph_steps=1, a_max=a0, max_record=nsteps + nwarm + 8,
+                      stream=stream.cuda_stream, interstitial="fft" if "fft" in parts else "toeplitz",
+                      hartree="hartree" in parts)
         assert ctx.stream_handle() == stream.cuda_stream
         d_a = torch.from_numpy(a_all[:nsteps + nwarm]).to(dev)
         for i in range(nwarm):
@@ -365,8 +367,11 @@ def run_ours(args, rank, world, local_rank):
                            "steps": args.fp64_steps}
             form_obs[prec] = o2
     if "fp64" in form_obs:
-        ref = form_obs["fp64"]
         for prec, o in form_obs.items():
+            # the density feedback is another model: its forms compare with its FP64 form
+            ref = form_obs.get("fp64+fft+hartree") if "hartree" in prec else form_obs["fp64"]
+            if ref is None:
+                continue
             n = min(len(o["t"]), len(ref["t"]))
             if n == 0:
                 continue

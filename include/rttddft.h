@@ -128,6 +128,8 @@ typedef struct {
     const double* caux; /* complex; per k: N_basis x n_aux; trial vectors (RITZ) or CC(0) (GIVEN) */
     const double* eps;  /* [n_k][n_aux] eigenvalues for GIVEN mode; NULL for RITZ */
     const double* c0;   /* complex; NULL (C(0) = first n_s columns of CC(0)) or per k N_basis x n_s */
+    double recip[9];    /* reciprocal lattice vectors b_1, b_2, b_3 (rows, 1/bohr): G = n_1 b_1 + n_2 b_2 + n_3 b_3;
+                           needed by the Hartree feedback only (zeros otherwise) */
 } rttddft_system;
 
 typedef struct {
@@ -145,6 +147,15 @@ typedef struct {
                            from the samples of each call (device samples are then read back) */
     double s_max;       /* bound on |s_k| of the potential change; 0: from the samples */
     int interstitial;   /* RTTDDFT_INTERSTITIAL_* (default TOEPLITZ) */
+    /* 1: the potential change of every step is the Hartree potential of the interstitial density's
+     * change since the start, dV_g = 4 pi (n_g(t_k) - n_g(0)) / |g|^2 on the table box (g != 0),
+     * n_g = (1/Omega) sum_k w_k sum_j f_j sum_G C_Gj conj(C_(G-g)j) from the plane-wave rows of C_k;
+     * it enters HH and the operator of step k (Sec. 2: VV(t) is the part rebuilt every step).
+     * Needs the FFT route and recip; rttddft_set_dv and dv_scale are then refused (ERR_ARG), the
+     * adjoint is not built (ERR_UNSUPPORTED).  Default 0. */
+    int hartree;
+    double hartree_bound; /* bound on sum_g |dV_g| >= ||dVV||_2 used for the Chebyshev interval; a step whose
+                             change exceeds it fails with ERR_ARG (default 0.1 Ha) */
 } rttddft_options;
 
 /* Per-step records (all k-points summed with their weights), caller-allocated

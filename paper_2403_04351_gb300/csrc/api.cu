@@ -69,6 +69,8 @@ struct rttddft_ctx {
     FftPlan* fft = nullptr;                     // FFT route of the interstitial convolution
     ToepDesc* td_op = nullptr;                  // per k {C, th}: the operator's convolution
     unsigned* d_tile_cnt = nullptr;             // row-tile counters of the fused split-K sums
+    GemmDesc* gd_exp64 = nullptr;               // Hartree feedback, FP32 form: C in FP64 for the density
+    ToepDesc* td_dens = nullptr;                // per k {C of the density, -}
     cudaStream_t side = nullptr;                // the FFT route's interstitial rows overlap the matching rows
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double dtcr0 = 0;
@@ -214,7 +216,7 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.vstep32 = ctx->d_vstep32;
     a.vsteps = ctx->d_vsteps;
     a.a = ctx->d_a;
-    a.dvs = dv_on ? ctx->d_dvs : nullptr;
+    a.dvs = (dv_on && !ctx->opt.hartree) ? ctx->d_dvs : nullptr;  // the density feedback runs with s = 1
     a.st = ctx->d_st;
     a.rec = ctx->d_rec;
     a.part_jmt = ctx->d_part_jmt;
@@ -240,6 +242,7 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.at_n = ctx->at.n;
     a.at_maxm = ctx->maxm;
     a.ith = (ctx->opt.precision >= RTTDDFT_PREC_BF16X3 || ctx->fft) ? 1 : 0;
+    a.hartree = ctx->opt.hartree;
     return a;
 }
 
@@ -280,6 +283,13 @@ static StepPlan make_plan(rttddft_ctx* ctx) {
     p.side = ctx->side;
     p.ev_fork = ctx->ev_fork;
     p.ev_join = ctx->ev_join;
+    p.gd_exp64 = ctx->gd_exp64;
+    p.td_dens = ctx->td_dens ? ctx->td_dens : ctx->td_op;
+    {
+        int F[3], fused = 0;
+        fft_plan_info(ctx->fft, F, &fused);
+        p.fft_launches = ctx->fft ? (fused ? 3 : 5) : 0;
+    }
     return p;
 }
 
@@ -519,6 +529,19 @@ static void validate(const rttddft_system* s, const rttddft_options* o) {
         fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown interstitial route");
     if (o->interstitial == RTTDDFT_INTERSTITIAL_FFT && o->precision > RTTDDFT_PREC_FP32)
         fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "the FFT interstitial route runs in the FP64 and FP32 forms");
+    if (o->hartree != 0 && o->hartree != 1) fail(ctx, RTTDDFT_ERR_ARG, "hartree must be 0 or 1");
+    if (o->hartree) {
+        if (o->interstitial != RTTDDFT_INTERSTITIAL_FFT)
+            fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "the Hartree feedback needs the FFT interstitial route");
+        if (!(o->hartree_bound > 0.0) || !std::isfinite(o->hartree_bound))
+            fail(ctx, RTTDDFT_ERR_ARG, "hartree_bound must be positive");
+        double r2 = 0.0;
+        for (int i = 0; i < 9; ++i) {
+            if (!std::isfinite(s->recip[i])) fail(ctx, RTTDDFT_ERR_NONFINITE, "recip not finite");
+            r2 += s->recip[i] * s->recip[i];
+        }
+        if (r2 == 0.0) fail(ctx, RTTDDFT_ERR_ARG, "the Hartree feedback needs the reciprocal vectors (recip)");
+    }
     if (o->aux_mode < 0 || o->aux_mode > 1) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown aux_mode");
     if (o->aux_mode == RTTDDFT_AUX_GIVEN && !s->eps) fail(ctx, RTTDDFT_ERR_ARG, "GIVEN mode needs eps");
     if (o->max_record < 1 || o->graph_steps < 0 || o->max_sweeps < 1) fail(ctx, RTTDDFT_ERR_ARG, "bad option value");
@@ -544,6 +567,8 @@ void rttddft_default_options(rttddft_options* opt) {
     opt->a_max = 0.0;
     opt->s_max = 0.0;
     opt->interstitial = RTTDDFT_INTERSTITIAL_TOEPLITZ;
+    opt->hartree = 0;
+    opt->hartree_bound = 0.1;
 }
 
 const char* rttddft_version(void) { return "rttddft-gb300 0.1 (sm_103a)"; }
@@ -1148,6 +1173,88 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             launch_subspace_current(a, 1, ctx->stream);
             KCHECK();
         }
+        // ---- Hartree feedback: the potential change is the Hartree potential of
+        // the density's change since the start; its interstitial rebuild needs
+        // CC_G convolved over N_aux columns and projected
+        if (o->hartree) {
+            std::string why;
+            int e = fft_hartree_init(ctx->fft, s->recip, ctx->vt_dim, ctx->omega, o->hartree_bound, ns, ctx->stream,
+                                     &why);
+            if (!e) e = fft_reserve_columns(ctx->fft, naux, ctx->stream, &why);
+            if (e) fail(ctx, e, why);
+            std::vector<GemmDesc> gi;
+            std::vector<ToepDesc> td;
+            for (int k = 0; k < nk; ++k) {
+                KDev& K = ctx->hkd[k];
+                K.dvsub = dalloc<zd>(ctx, (size_t)naux * naux);
+                zd* T = dalloc<zd>(ctx, (size_t)K.ng * naux);
+                td.push_back(ToepDesc{K.caux, T, K.nb, K.ng});
+                GemmDesc d{};
+                d.A = K.caux;
+                d.B = T;
+                d.C = K.dvsub;
+                d.M = naux;
+                d.K = K.ng;
+                d.lda = K.nb;
+                d.ldb = K.ng;
+                d.ldc = naux;
+                gi.push_back(d);
+            }
+            ctx->gd_dvi = upload_descs(ctx, gi);
+            ctx->td_dv = dupload(ctx, td.data(), td.size());
+            if (f32) {
+                // the density is a small change of a large quantity: it is taken from
+                // C = CC theta expanded in FP64 (the FP32 expansion's rounding would
+                // swamp n(t) - n(0))
+                std::vector<GemmDesc> ge;
+                std::vector<ToepDesc> tdd;
+                for (int k = 0; k < nk; ++k) {
+                    KDev& K = ctx->hkd[k];
+                    zd* cd = dalloc<zd>(ctx, (size_t)K.nb * ns);
+                    GemmDesc g{};
+                    g.A = K.caux;
+                    g.B = K.theta;
+                    g.C = cd;
+                    g.M = K.nb;
+                    g.K = naux;
+                    g.lda = K.nb;
+                    g.ldb = naux;
+                    g.ldc = K.nb;
+                    ge.push_back(g);
+                    tdd.push_back(ToepDesc{cd, nullptr, K.nb, K.ng});
+                }
+                ctx->gd_exp64 = upload_descs(ctx, ge);
+                ctx->td_dens = dupload(ctx, tdd.data(), tdd.size());
+                // the projection CC_G^H T from the FP32 copy of CC, K slices of 256
+                ctx->kc_dvi = 256;
+                size_t off = 0;
+                std::vector<GemmDesc> g32 = gi;
+                for (int k = 0; k < nk; ++k) {
+                    g32[k].A = ctx->hkd[k].caux32;
+                    g32[k].part_off = off;
+                    off += (size_t)((ctx->hkd[k].ng + 255) / 256) * naux * naux;
+                }
+                ctx->gd_dvi32 = upload_descs(ctx, g32);
+                ctx->d_part_dv = dalloc<zd>(ctx, off);
+            }
+            CK(cudaMemcpy(ctx->d_kd, ctx->hkd.data(), nk * sizeof(KDev), cudaMemcpyHostToDevice));
+            for (int k = 0; k < nk; ++k) ctx->dvnorm[k] = o->hartree_bound;
+            ctx->dv_set = true;
+            ctx->a_max_cur = -1.0;
+            // C(0) = CC theta(0) and the density it carries: the reference of the change
+            StepArgs a = make_args(ctx, 0);
+            StepPlan p = make_plan(ctx);
+            if (p.gd_exp64) {
+                launch_gemm_nn(p.gd_exp64, nk, p.maxnb, naux, ns, 0, nullptr, 0, false, nullptr, ctx->stream);
+            } else {
+                launch_gemm_nn(p.gd_expand, nk, p.maxnb, naux, ns, p.kc_expand, p.kc_expand > 0 ? p.part : nullptr, 0,
+                               f32, nullptr, ctx->stream);
+                if (p.kc_expand > 0)
+                    launch_split_reduce(p.gd_expand, nk, p.maxnb, ns, p.kc_expand, p.part, 0, ctx->stream);
+            }
+            launch_fft_density(ctx->fft, p.td_dens, nk, ns, a.occ, a.wk, 1, ctx->stream);
+            KCHECK();
+        }
         CK(cudaStreamSynchronize(ctx->stream));
         *out = ctx;
         return RTTDDFT_OK;
@@ -1286,6 +1393,8 @@ static void sync_and_check(rttddft_ctx* ctx) {
         if (flag & 8) fail(ctx, RTTDDFT_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
         if (flag & 32)
             fail(ctx, RTTDDFT_ERR_NONFINITE, "a scaled operand of the split-FP16 form left the fp16 range");
+        if (flag & 64)
+            fail(ctx, RTTDDFT_ERR_ARG, "the Hartree potential change exceeded hartree_bound (the spectral interval)");
         fail(ctx, RTTDDFT_ERR_ARG, "a pulse sample or dv scale exceeded a_max / s_max");
     }
 }
@@ -1311,6 +1420,8 @@ int rttddft_step(rttddft_ctx* ctx, int nsteps, const double* a_samples, const do
         if (ctx->rec_count + nsteps > ctx->opt.max_record)
             fail(ctx, RTTDDFT_ERR_ARG, "record capacity exceeded: call rttddft_observables with clear");
         if (dv_scale && !ctx->dv_set) fail(ctx, RTTDDFT_ERR_ARG, "dv_scale given before rttddft_set_dv");
+        if (dv_scale && ctx->opt.hartree)
+            fail(ctx, RTTDDFT_ERR_ARG, "dv_scale is not taken with the Hartree feedback (the density sets the change)");
         {
             int flag = 0;  // errors raised by earlier, finished work
             if (cudaStreamQuery(ctx->stream) == cudaSuccess) {
@@ -1366,6 +1477,7 @@ int rttddft_step(rttddft_ctx* ctx, int nsteps, const double* a_samples, const do
                 s_need = ctx->opt.s_max;
             }
         }
+        if (ctx->opt.hartree) s_need = 1.0;  // dVV = 1 x the Hartree change, bounded by hartree_bound
         ensure_interval(ctx, a_need, s_need);
         if (!a_dev) stage_host(ctx, a_samples, na, ctx->d_a);
         if (dv_scale && !s_dev) {
@@ -1375,7 +1487,7 @@ int rttddft_step(rttddft_ctx* ctx, int nsteps, const double* a_samples, const do
         if ((a_dev && ctx->opt.a_max > 0) || (s_dev && ctx->opt.s_max > 0))
             launch_check_samples(ctx->d_a, a_dev ? nsteps : 0, ctx->a_max_cur, ctx->d_dvs,
                                  s_dev ? nsteps : 0, ctx->s_max_cur, ctx->d_flag, ctx->stream);
-        run_steps(ctx, nsteps, dv_scale ? 1 : 0);
+        run_steps(ctx, nsteps, (dv_scale || ctx->opt.hartree) ? 1 : 0);
         ctx->rec_count += nsteps;
         ctx->steps_done += nsteps;
         ctx->time += nsteps * ctx->opt.dt;
@@ -1497,6 +1609,7 @@ int rttddft_get_info(rttddft_ctx* ctx, rttddft_info* info) {
 int rttddft_set_dv(rttddft_ctx* ctx, const double* dh, const double* dvtab) {
     if (!ctx) return RTTDDFT_ERR_ARG;
     try {
+        if (ctx->opt.hartree) fail(ctx, RTTDDFT_ERR_ARG, "with the Hartree feedback the potential change comes from the density");
         const AtomTab& at = ctx->at;
         size_t nblk = 0;
         for (int a = 0; a < at.n; ++a) nblk += (size_t)at.m[a] * at.m[a];
@@ -1663,7 +1776,7 @@ int rttddft_apply(rttddft_ctx* ctx, int k, int ncols, const double* x, const dou
         StepPlan p = make_plan(ctx);
         p.gd_fwd = ctx->gd_fwd + k;
         p.maxng = K.ng;
-        if (dv_on) launch_vstep(a, ctx->stream);
+        if (dv_on && !ctx->opt.hartree) launch_vstep(a, ctx->stream);
         const zd* xz = (const zd*)x;
         zd* hz = (zd*)hx;
         zd* sz = (zd*)sx;
@@ -1695,6 +1808,8 @@ int rttddft_trace_steps(rttddft_ctx* ctx, int nsteps, const double* a_samples, c
         if (ctx->rec_count + nsteps > ctx->opt.max_record)
             fail(ctx, RTTDDFT_ERR_ARG, "record capacity exceeded: call rttddft_observables with clear");
         if (dv_scale && !ctx->dv_set) fail(ctx, RTTDDFT_ERR_ARG, "dv_scale given before rttddft_set_dv");
+        if (dv_scale && ctx->opt.hartree)
+            fail(ctx, RTTDDFT_ERR_ARG, "dv_scale is not taken with the Hartree feedback (the density sets the change)");
         sync_and_check(ctx);
         ensure_call_cap(ctx, nsteps);
         const size_t na = 3 * (size_t)nsteps;
@@ -1707,10 +1822,11 @@ int rttddft_trace_steps(rttddft_ctx* ctx, int nsteps, const double* a_samples, c
             for (int i = 0; i < nsteps; ++i) s_need = std::max(s_need, fabs(dv_scale[i]));
             if (ctx->opt.s_max > 0) s_need = std::max(s_need, ctx->opt.s_max);
         }
+        if (ctx->opt.hartree) s_need = 1.0;
         ensure_interval(ctx, a_need, s_need);
         CK(cudaMemcpy(ctx->d_a, a_samples, na * sizeof(double), cudaMemcpyHostToDevice));
         if (dv_scale) CK(cudaMemcpy(ctx->d_dvs, dv_scale, nsteps * sizeof(double), cudaMemcpyHostToDevice));
-        const int dv_on = dv_scale ? 1 : 0;
+        const int dv_on = (dv_scale || ctx->opt.hartree) ? 1 : 0;
         StepArgs a = make_args(ctx, dv_on);
         StepPlan p = make_plan(ctx);
         CK(cudaMemsetAsync(&ctx->d_st->cstep, 0, sizeof(int), ctx->stream));
@@ -1772,11 +1888,15 @@ int rttddft_adjoint(rttddft_ctx* ctx, int nsteps, const double* a_samples, const
     std::vector<zd*> theta_saved;
     bool restore = false;
     try {
+        if (ctx->opt.hartree)
+            fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "the adjoint of the Hartree feedback (a state-dependent potential) is not built");
         if (nsteps < 1 || !a_samples || !gdir || !grad || ckpt_every < 1)
             fail(ctx, RTTDDFT_ERR_ARG, "bad argument to rttddft_adjoint");
         if (ctx->opt.propagator != RTTDDFT_PROP_CHEBYSHEV)
             fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "the adjoint differentiates the Chebyshev propagator only");
         if (dv_scale && !ctx->dv_set) fail(ctx, RTTDDFT_ERR_ARG, "dv_scale given before rttddft_set_dv");
+        if (dv_scale && ctx->opt.hartree)
+            fail(ctx, RTTDDFT_ERR_ARG, "dv_scale is not taken with the Hartree feedback (the density sets the change)");
         sync_and_check(ctx);
         const int nk = ctx->nk, ns = ctx->ns, naux = ctx->naux;
         const size_t vs = (size_t)naux * ns;
@@ -2000,6 +2120,8 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         if (k < 0 || k >= ctx->nk || ncols < 1 || !x || !a_vec || !hx || !sx)
             fail(ctx, RTTDDFT_ERR_ARG, "bad argument to rttddft_apply_noalloc");
         if (dv_scale != 0.0 && !ctx->dv_set) fail(ctx, RTTDDFT_ERR_ARG, "dv_scale != 0 before rttddft_set_dv");
+        if (dv_scale != 0.0 && ctx->opt.hartree)
+            fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "rttddft_apply_noalloc has no Hartree potential (use rttddft_apply)");
         if (!is_device_ptr(x) || !is_device_ptr(hx) || !is_device_ptr(sx))
             fail(ctx, RTTDDFT_ERR_ARG, "rttddft_apply_noalloc takes device pointers for x, hx and sx");
         const KDev& K = ctx->hkd[k];

@@ -86,6 +86,20 @@ struct FftPlan {
     void* b3 = nullptr;
     void* b2 = nullptr;
     std::vector<void*> tables;  // per-k index arrays
+    // Hartree feedback: density grid (forward transformed), its value at the
+    // start, the box extents, the reciprocal vectors, the l1 accumulator
+    // (the density and its potential are FP64 in every form: the change n(t) - n(0)
+    // is a small difference of two densities, which FP32 rounding would swamp)
+    zd* rho = nullptr;
+    zd* rho0 = nullptr;
+    zd* b3d = nullptr;  // FP64 transform buffers of the density (FP32 plans only)
+    zd* b2d = nullptr;
+    int fused_d = 0;    // the density's plane pass fused (FP64 plane in shared memory)
+    double* l1 = nullptr;
+    int hartree = 0;
+    int e[3] = {0, 0, 0};
+    double recip[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double omega = 1.0, bound = 0.0;
 };
 
 // ---------------------------------------------------------------- complex ops
@@ -421,6 +435,162 @@ __global__ void __launch_bounds__(FFT_PTHREADS) k_fft_plane(FftArgs f, int fwd) 
     }
 }
 
+// Interstitial density of the propagated states on the grid: for every
+// (r2, r3) line of axis 1 the inverse transform of each (k, state) column
+// (planes from the plane pass), |psi|^2 summed with the weights w_k f_j in
+// (k, j) order; n(r) = that sum / Omega (psi~ = sqrt(Omega) psi here)
+template <typename C>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_density(FftArgs f, int nk, const double* __restrict__ occ,
+                                                          const double* __restrict__ wk, double inv_omega, C* rho) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const int F1 = f.F1, F2 = f.F2, F3 = f.F3;
+    C* W = (C*)fsm;
+    C* x = W + F1;
+    C* y = x + FFT_LPB * F1;
+    const int nch = (F3 + FFT_LPB - 1) / FFT_LPB;
+    const int r2 = blockIdx.x / nch, i30 = (blockIdx.x - r2 * nch) * FFT_LPB;
+    const int nl = min(FFT_LPB, F3 - i30);
+    load_tw(W, f.w[0], F1);
+    const size_t pst = (size_t)F2 * F3;
+    const size_t off = (size_t)r2 * F3 + i30;
+    constexpr int PV = FFT_MAX_N * FFT_LPB / FFT_THREADS;
+    double acc[PV];
+#pragma unroll
+    for (int u = 0; u < PV; ++u) acc[u] = 0.0;
+    for (int k = 0; k < nk; ++k) {
+        const FftK K = f.fk[k];
+        for (int c = 0; c < f.ncol; ++c) {
+            const C* b2 = (const C*)f.b2 + ((size_t)k * f.ncol + c) * f.b2_col;
+            for (int i = threadIdx.x; i < F1 * nl; i += blockDim.x) {
+                const int r1 = i / nl, l = i - r1 * nl;
+                const int p = K.plane_of[r1];
+                x[l * F1 + r1] = (p >= 0) ? b2[(size_t)p * pst + off + l] : cmk<C>(0, 0);
+            }
+            __syncthreads();
+            const C* r = fft_lines(x, y, nl, F1, f.rad[0], f.nst[0], W, true);
+            const double wf = wk[k] * occ[c];
+#pragma unroll
+            for (int u = 0; u < PV; ++u) {
+                const int i = threadIdx.x + u * FFT_THREADS;
+                if (i < F1 * nl) {
+                    const int r1 = i / nl, l = i - r1 * nl;
+                    const C v = r[l * F1 + r1];
+                    acc[u] += wf * ((double)v.x * v.x + (double)v.y * v.y);
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < PV; ++u) {
+        const int i = threadIdx.x + u * FFT_THREADS;
+        if (i < F1 * nl) {
+            const int r1 = i / nl, l = i - r1 * nl;
+            rho[(size_t)r1 * pst + off + l] = cmk<C>((typename Rt<C>::R)(acc[u] * inv_omega), 0);
+        }
+    }
+}
+
+// A full-grid 1-D pass along `axis` (0, 1, 2) in place, every line
+template <typename C>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_full(FftArgs f, C* buf, int axis, int inv) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const int F1 = f.F1, F2 = f.F2, F3 = f.F3;
+    const int L = axis == 0 ? F1 : (axis == 1 ? F2 : F3);
+    C* W = (C*)fsm;
+    C* x = W + L;
+    C* y = x + FFT_LPB * L;
+    load_tw(W, f.w[axis], L);
+    size_t base, es, ls;
+    int nl;
+    if (axis == 2) {
+        const int l0 = blockIdx.x * FFT_LPB;
+        nl = min(FFT_LPB, F1 * F2 - l0);
+        base = (size_t)l0 * F3;
+        es = 1;
+        ls = F3;
+    } else {
+        const int nch = (F3 + FFT_LPB - 1) / FFT_LPB;
+        const int o = blockIdx.x / nch, i30 = (blockIdx.x - o * nch) * FFT_LPB;
+        nl = min(FFT_LPB, F3 - i30);
+        es = axis == 1 ? (size_t)F3 : (size_t)F2 * F3;
+        base = (axis == 1 ? (size_t)o * F2 * F3 : (size_t)o * F3) + i30;
+        ls = 1;
+    }
+    // element j of line l at base + l ls + j es; coalesced along l for axes 0, 1
+    for (int i = threadIdx.x; i < nl * L; i += blockDim.x) {
+        int l, j;
+        if (axis == 2) {
+            l = i / L;
+            j = i - l * L;
+        } else {
+            j = i / nl;
+            l = i - j * nl;
+        }
+        x[l * L + j] = buf[base + l * ls + j * es];
+    }
+    __syncthreads();
+    const C* r = fft_lines(x, y, nl, L, f.rad[axis], f.nst[axis], W, inv != 0);
+    for (int i = threadIdx.x; i < nl * L; i += blockDim.x) {
+        int l, j;
+        if (axis == 2) {
+            l = i / L;
+            j = i - l * L;
+        } else {
+            j = i / nl;
+            l = i - j * nl;
+        }
+        buf[base + l * ls + j * es] = r[l * L + j];
+    }
+}
+
+// Poisson equation on the table box: vd(g) = 4 pi (N - N0)(g) / (F^6 |g|^2)
+// at the residues of |g_i| <= e_i, g != 0, zero elsewhere (N = F^3 n_g; the
+// second F^3 is the normalisation of the potential's grid image), and the sum
+// of |dV_g| for the bound check
+template <typename C>
+__global__ void k_hartree(const C* __restrict__ N, const C* __restrict__ N0, C* vd, int F1, int F2, int F3, int e0,
+                          int e1, int e2, double b00, double b01, double b02, double b10, double b11, double b12,
+                          double b20, double b21, double b22, double inv_f3, double* l1) {
+    __shared__ double part[8];
+    const size_t n = (size_t)F1 * F2 * F3;
+    double mine = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int r2 = (int)(i % F3), r1 = (int)((i / F3) % F2), r0 = (int)(i / ((size_t)F2 * F3));
+        const int d0 = r0 <= e0 ? r0 : (r0 >= F1 - e0 ? r0 - F1 : 1 << 20);
+        const int d1 = r1 <= e1 ? r1 : (r1 >= F2 - e1 ? r1 - F2 : 1 << 20);
+        const int d2 = r2 <= e2 ? r2 : (r2 >= F3 - e2 ? r2 - F3 : 1 << 20);
+        C out = cmk<C>(0, 0);
+        if (d0 != (1 << 20) && d1 != (1 << 20) && d2 != (1 << 20) && (d0 | d1 | d2) != 0) {
+            const double gx = d0 * b00 + d1 * b10 + d2 * b20;
+            const double gy = d0 * b01 + d1 * b11 + d2 * b21;
+            const double gz = d0 * b02 + d1 * b12 + d2 * b22;
+            const double g2 = gx * gx + gy * gy + gz * gz;
+            const double f = 4.0 * 3.14159265358979323846 * inv_f3 / g2;  // 4 pi / (F^3 |g|^2)
+            const double dre = ((double)N[i].x - (double)N0[i].x) * inv_f3;
+            const double dim = ((double)N[i].y - (double)N0[i].y) * inv_f3;
+            out = cmk<C>((typename Rt<C>::R)(f * dre), (typename Rt<C>::R)(f * dim));
+            mine += f * sqrt(dre * dre + dim * dim) / inv_f3;
+        }
+        vd[i] = out;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    mine = warp_sum(mine);
+    if (lane == 0) part[warp] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        atomicAdd(l1, t);  // only compared with the bound: the order does not matter
+    }
+}
+
+// the l1 norm of dV against the bound of the spectral interval; flag bit 6
+__global__ void k_hartree_check(double* l1, double bound, int* flag) {
+    if (*l1 > bound) atomicOr(flag, 64);
+    *l1 = 0.0;
+}
+
 // ---------------------------------------------------------------- set-up kernels
 // V~ placed on the grid by residue
 __global__ void k_fft_place(const zd* tab, int d0, int d1, int d2, int F1, int F2, int F3, zd* grid) {
@@ -696,13 +866,21 @@ int fft_set_dv(FftPlan* pl, const zd* dvtab_dev, const int vt_dim[3], int ncol, 
     return 0;
 }
 
+// transform buffers for at least ncol columns per k-point
+int fft_reserve_columns(FftPlan* pl, int ncol, cudaStream_t st, std::string* why) {
+    if (ncol <= pl->ncol) return 0;
+    cudaStreamSynchronize(st);
+    return fft_alloc_buffers(pl, ncol, why) ? 0 : RTTDDFT_ERR_OOM;
+}
+
 void fft_plan_destroy(FftPlan* pl) {
     if (!pl) return;
     for (int a = 0; a < 3; ++a) {
         if (pl->w64[a]) cudaFree(pl->w64[a]);
         if (pl->w32[a]) cudaFree(pl->w32[a]);
     }
-    for (void* p : {(void*)pl->v64, (void*)pl->v32, (void*)pl->vd64, (void*)pl->vd32, (void*)pl->d_fk, pl->b3, pl->b2})
+    for (void* p : {(void*)pl->v64, (void*)pl->v32, (void*)pl->vd64, (void*)pl->vd32, (void*)pl->d_fk, pl->b3, pl->b2,
+                    (void*)pl->rho, (void*)pl->rho0, (void*)pl->l1, (void*)pl->b3d, (void*)pl->b2d})
         if (p) cudaFree(p);
     for (void* p : pl->tables) cudaFree(p);
     delete pl;
@@ -816,4 +994,139 @@ int fft_tune(FftPlan* pl, const ToepDesc* td, int ncol, cudaStream_t st) {
     pl->ms_fused = ms[1] / 3;
     pl->fused = ms[1] < ms[0] ? 1 : 0;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------- Hartree feedback
+// launch arguments of the FP64 density passes
+static FftArgs fft_args64(const FftPlan* pl, const ToepDesc* td, int kofs, int ncol) {
+    FftArgs f;
+    f.F1 = pl->F[0];
+    f.F2 = pl->F[1];
+    f.F3 = pl->F[2];
+    for (int a = 0; a < 3; ++a) {
+        f.nst[a] = pl->nst[a];
+        for (int i = 0; i < FFT_MAX_ST; ++i) f.rad[a][i] = pl->rad[a][i];
+        f.w[a] = (const void*)pl->w64[a];
+    }
+    f.fk = pl->d_fk + kofs;
+    f.td = td + kofs;
+    f.b3 = pl->prec == 0 ? pl->b3 : (void*)pl->b3d;
+    f.b2 = pl->prec == 0 ? pl->b2 : (void*)pl->b2d;
+    f.b3_col = (size_t)pl->max_lines * f.F3;
+    f.b2_col = (size_t)pl->max_planes * f.F2 * f.F3;
+    f.ncol = ncol;
+    f.vmode = 0;
+    f.use_vd = 0;
+    f.v = nullptr;
+    f.vd = nullptr;
+    f.s = nullptr;
+    return f;
+}
+
+// Set up the density feedback: grids for n, its starting value and the
+// potential change; recip rows are the reciprocal vectors b_i (1/bohr).
+int fft_hartree_init(FftPlan* pl, const double recip[9], const int vt_dim[3], double omega, double bound, int ns,
+                     cudaStream_t st, std::string* why) {
+    const size_t n3 = (size_t)pl->F[0] * pl->F[1] * pl->F[2];
+    bool ok = true;
+    if (cudaMalloc((void**)&pl->rho, n3 * sizeof(zd)) != cudaSuccess ||
+        cudaMalloc((void**)&pl->rho0, n3 * sizeof(zd)) != cudaSuccess ||
+        cudaMalloc((void**)&pl->l1, sizeof(double)) != cudaSuccess)
+        ok = false;
+    if (ok && !pl->vd64) ok = cudaMalloc((void**)&pl->vd64, n3 * sizeof(zd)) == cudaSuccess;
+    if (ok && pl->prec != 0 && !pl->vd32) ok = cudaMalloc((void**)&pl->vd32, n3 * sizeof(zf)) == cudaSuccess;
+    if (ok && pl->prec != 0) {
+        // FP64 buffers for the N_s columns of the density
+        const size_t c3 = (size_t)pl->max_lines * pl->F[2], c2 = (size_t)pl->max_planes * pl->F[1] * pl->F[2];
+        ok = cudaMalloc((void**)&pl->b3d, std::max<size_t>((size_t)pl->nk * ns * c3, 1) * sizeof(zd)) == cudaSuccess &&
+             cudaMalloc((void**)&pl->b2d, std::max<size_t>((size_t)pl->nk * ns * c2, 1) * sizeof(zd)) == cudaSuccess;
+    }
+    if (!ok) {
+        if (why) *why = "Hartree feedback: device allocation failed";
+        return RTTDDFT_ERR_OOM;
+    }
+    cudaMemsetAsync(pl->l1, 0, sizeof(double), st);
+    cudaMemsetAsync(pl->vd64, 0, n3 * sizeof(zd), st);
+    if (pl->vd32) cudaMemsetAsync(pl->vd32, 0, n3 * sizeof(zf), st);
+    const size_t psm = fft_plane_smem(pl->F[1], pl->F[2], sizeof(zd));
+    pl->fused_d = (pl->prec == 0) ? pl->fused : (psm <= FFT_PLANE_SMEM_MAX ? 1 : 0);
+    for (int i = 0; i < 9; ++i) pl->recip[i] = recip[i];
+    for (int a = 0; a < 3; ++a) pl->e[a] = (vt_dim[a] - 1) / 2;
+    pl->omega = omega;
+    pl->bound = bound;
+    pl->hartree = 1;
+    const int mx = (int)fft_smem(std::max(pl->F[0], std::max(pl->F[1], pl->F[2])), (int)sizeof(zd));
+    cudaFuncSetAttribute(k_fft_density<zd>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_full<zd>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_a<zd>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_bd<zd>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (pl->fused_d) cudaFuncSetAttribute(k_fft_plane<zd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+    if (cudaGetLastError() != cudaSuccess) {
+        if (why) *why = "Hartree feedback: set-up failed";
+        return RTTDDFT_ERR_CUDA;
+    }
+    return 0;
+}
+
+template <typename C>
+static int density_launches(const FftPlan* pl, const FftArgs& f, int nk, const double* occ, const double* wk, C* rho,
+                            cudaStream_t st) {
+    const int nch = (f.F3 + FFT_LPB - 1) / FFT_LPB;
+    int nl = 0;
+    // the planes of every (k, state) column after the inverse transforms of axes 3 and 2
+    if (pl->fused_d) {
+        k_fft_plane<C><<<dim3(pl->max_planes, f.ncol, nk), FFT_PTHREADS, fft_plane_smem(f.F2, f.F3, sizeof(C)), st>>>(f, 0);
+        ++nl;
+    } else {
+        k_fft_a<C><<<dim3((pl->max_lines + FFT_LPB - 1) / FFT_LPB, f.ncol, nk), FFT_THREADS, fft_smem(f.F3, sizeof(C)),
+                     st>>>(f);
+        k_fft_bd<C><<<dim3(pl->max_planes * nch, f.ncol, nk), FFT_THREADS, fft_smem(f.F2, sizeof(C)), st>>>(f, 0);
+        nl += 2;
+    }
+    k_fft_density<C><<<f.F2 * nch, FFT_THREADS, fft_smem(f.F1, sizeof(C)), st>>>(f, nk, occ, wk, 1.0 / pl->omega, rho);
+    ++nl;
+    // N(g) = sum_r n(r) e^{-2 pi i g.r/F}
+    const int ga[3] = {f.F2 * nch, f.F1 * nch, (f.F1 * f.F2 + FFT_LPB - 1) / FFT_LPB};
+    for (int a = 2; a >= 0; --a) {
+        const int L = pl->F[a];
+        k_fft_full<C><<<ga[a], FFT_THREADS, fft_smem(L, sizeof(C)), st>>>(f, rho, a, 0);
+        ++nl;
+    }
+    return nl;
+}
+
+// The density of the current C (td: per k {C, .}) transformed to G space; with
+// reference = 1 it becomes the starting density n(0).  Returns the launches.
+int launch_fft_density(const FftPlan* pl, const ToepDesc* td, int nk, int ns, const double* occ, const double* wk,
+                       int reference, cudaStream_t st) {
+    const FftArgs f = fft_args64(pl, td, 0, ns);
+    const size_t n3 = (size_t)pl->F[0] * pl->F[1] * pl->F[2];
+    const int nl = density_launches<zd>(pl, f, nk, occ, wk, pl->rho, st);
+    if (reference) cudaMemcpyAsync(pl->rho0, pl->rho, n3 * sizeof(zd), cudaMemcpyDeviceToDevice, st);
+    return nl;
+}
+
+// After a step: the density of C_{k+1}, its Hartree potential change against
+// n(0) on the table box, and that potential's grid image for the next step's
+// operator and potential-change rebuild.  Returns the launches.
+int launch_fft_hartree(const FftPlan* pl, const ToepDesc* td, int nk, int ns, const double* occ, const double* wk,
+                       int* flag, cudaStream_t st) {
+    int nl = launch_fft_density(pl, td, nk, ns, occ, wk, 0, st);
+    const FftArgs f = fft_args64(pl, td, 0, ns);
+    const double inv_f3 = 1.0 / ((double)pl->F[0] * pl->F[1] * pl->F[2]);
+    const double* b = pl->recip;
+    const int nch = (f.F3 + FFT_LPB - 1) / FFT_LPB;
+    const int ga[3] = {f.F2 * nch, f.F1 * nch, (f.F1 * f.F2 + FFT_LPB - 1) / FFT_LPB};
+    k_hartree<zd><<<152, 256, 0, st>>>(pl->rho, pl->rho0, pl->vd64, f.F1, f.F2, f.F3, pl->e[0], pl->e[1], pl->e[2],
+                                       b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7], b[8], inv_f3, pl->l1);
+    for (int a = 0; a < 3; ++a)
+        k_fft_full<zd><<<ga[a], FFT_THREADS, fft_smem(pl->F[a], sizeof(zd)), st>>>(f, pl->vd64, a, 1);
+    if (pl->prec != 0) {
+        // the FP32 operator reads its copy of the grid image
+        const size_t n3 = (size_t)f.F1 * f.F2 * f.F3;
+        k_fft_to32<<<(int)std::min<size_t>((n3 + 255) / 256, 4096), 256, 0, st>>>(pl->vd64, pl->vd32, n3);
+        ++nl;
+    }
+    k_hartree_check<<<1, 1, 0, st>>>(pl->l1, pl->bound, flag);
+    return nl + 5;
 }

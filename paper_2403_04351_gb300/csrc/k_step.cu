@@ -23,7 +23,7 @@ __global__ void k_set_cur(StepArgs a) {
     st->cur_a[0] = av[0];
     st->cur_a[1] = av[1];
     st->cur_a[2] = av[2];
-    st->cur_s = a.dvs ? a.dvs[cs] : 0.0;
+    st->cur_s = a.dvs ? a.dvs[cs] : (a.hartree ? 1.0 : 0.0);
     st->cur_aa = (av[0] * av[0] + av[1] * av[1] + av[2] * av[2]) * a.half_inv_c2;
 }
 
@@ -184,7 +184,9 @@ __device__ bool grid_barrier(unsigned* count, unsigned target, int* flag) {
 // pipe, not memory, bounds a term on GB300).  Only the newest vector y_{n-1}
 // is exchanged through global memory (two slots, read through L2 with
 // ld.global.cg); each block keeps y_{n-1}, y_{n-2} and the partial sum of
-// its own rows in shared memory.  A grid barrier separates the terms.
+// its own rows in shared memory.  A grid barrier separates the terms (per-block
+// epoch flags polled by every block measured slower on GB300: 107 against 80 us
+// per series at N_aux = 200).
 #define CHEB_THREADS 64
 #define CHEB_JU 4  // row entries per thread held at once (n_aux <= 256 in one pass)
 template <int NT>
@@ -1603,6 +1605,22 @@ int launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, T
 // interstitial convolution runs on tcgen05 (split-BF16) and its projection in
 // FP32; otherwise both in FP64.  Returns the launches.
 static int launch_dv_rebuild(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr) {
+    if (a.hartree) {
+        // the Hartree potential of the density has no muffin-tin part:
+        // dVV = CC_G^H (dV~ * CC_G) with dV~ from the previous step's density
+        launch_fft_conv(p.fft, p.td_dv, a.kofs, a.nk, a.naux, 1, 1, &a.st->cur_s, s);
+        mark(tr, "hartree_interstitial_fft", s);
+        if (p.gd_dvi32) {
+            // FP32 form: CC_G^H T streaming the FP32 copy of CC, FP64 sums of the K slices
+            launch_gemm_cn(p.gd_dvi32, a.nk, a.naux, p.maxng, a.naux, p.kc_dvi, p.part_dv, 0, true, nullptr, s);
+            launch_split_reduce(p.gd_dvi32, a.nk, a.naux, a.naux, p.kc_dvi, p.part_dv, 0, s);
+            mark(tr, "hartree_project", s);
+            return 1;
+        }
+        launch_gemm_cn(p.gd_dvi, a.nk, a.naux, p.maxng, a.naux, 0, nullptr, 0, false, nullptr, s);
+        mark(tr, "hartree_project", s);
+        return 0;  // counted by the caller with the FFT launches
+    }
     launch_gemm_nn(p.gd_dvw, p.n_dvw, p.maxm, p.maxm, a.naux, 0, nullptr, 0, false, &a.st->cur_s, s);
     mark(tr, "dv_mt_blocks", s);
     launch_gemm_cn(p.gd_dvg, a.nk, a.naux, a.lrows, a.naux, 0, nullptr, 0, false, nullptr, s);
@@ -1637,11 +1655,16 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
     if (a.dv_on) {
         k_set_cur<<<1, 1, 0, s>>>(a);
         mark(tr, "set_cur", s);
-        // Eq. v_MT and Eq. v_interstitial rebuilt from the scaled blocks:
-        // dVV = L^H (s dh) L + CC_G^H (s dV~ * CC_G)
-        k_vstep<<<(a.nvt + 255) / 256, 256, 0, s>>>(a);
-        mark(tr, "dv_table", s);
-        nl += 2 + launch_dv_rebuild(a, p, s, tr);
+        ++nl;
+        if (a.hartree) {
+            nl += launch_dv_rebuild(a, p, s, tr) + (p.fft_launches > 0 ? p.fft_launches : 5) + 1;
+        } else {
+            // Eq. v_MT and Eq. v_interstitial rebuilt from the scaled blocks:
+            // dVV = L^H (s dh) L + CC_G^H (s dV~ * CC_G)
+            k_vstep<<<(a.nvt + 255) / 256, 256, 0, s>>>(a);
+            mark(tr, "dv_table", s);
+            nl += 1 + launch_dv_rebuild(a, p, s, tr);
+        }
     }
     if (!(a.prop != 1 && a.coop_grid > 0 && cheb_direct(a))) {
         k_hsub<<<dim3((nn + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
@@ -1711,6 +1734,15 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
         k_finalize<<<1, 256, 0, s>>>(a, 0);
         mark(tr, "finalize", s);
         ++nl;
+    }
+    if (a.hartree) {
+        // the density of C_{k+1} sets the potential change of the next step
+        if (p.gd_exp64) {
+            launch_gemm_nn(p.gd_exp64, a.nk, p.maxnb, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
+            ++nl;
+        }
+        nl += launch_fft_hartree(p.fft, p.td_dens, a.nk, a.ns, a.occ, a.wk, a.flag, s);
+        mark(tr, "hartree_density_poisson", s);
     }
     if (nlaunch) *nlaunch = nl;
 }

@@ -147,6 +147,7 @@ struct StepArgs {
     int at_n, at_maxm;        // atoms, and the largest local block m = N_A + n_lo
     int tc_fmt;               // tensor-core operand format: 1 bf16, 0 fp16
     int ith;                  // the interstitial sum arrives in K.th (tensor cores or FFT)
+    int hartree;              // the potential change is the Hartree potential of the density (FFT route)
     double tc_st;             // scale of the split table (fp16 range)
 };
 #define POST_STRIDE 36        // part_post row: residual, J_sub (3), then theta^H theta~ (ns <= 4)
@@ -193,6 +194,9 @@ struct StepPlan {
     const struct FftPlan* fft;  // FFT route of the interstitial convolution or null
     unsigned* tile_cnt;         // zeroed row-tile counters of the fused split-K sums (or null)
     cudaStream_t side;          // second stream for work that overlaps the main chain (or null)
+    int fft_launches;           // launches of one FFT convolution (3 or 5)
+    const GemmDesc* gd_exp64;   // Hartree feedback in the FP32 form: C in FP64 for the density (or null)
+    const ToepDesc* td_dens;    // per k: the C the density is taken from
     cudaEvent_t ev_fork, ev_join;
     const ToepDesc* td_op;      // per k: {C, th}: the operator's convolution source and destination
 };
@@ -247,6 +251,13 @@ int fft_set_dv(FftPlan* pl, const zd* dvtab_dev, const int vt_dim[3], int ncol, 
 void fft_plan_destroy(FftPlan* pl);
 void fft_plan_info(const FftPlan* pl, int F[3], int* fused);
 int fft_tune(FftPlan* pl, const ToepDesc* td, int ncol, cudaStream_t st);
+int fft_reserve_columns(FftPlan* pl, int ncol, cudaStream_t st, std::string* why);
+int fft_hartree_init(FftPlan* pl, const double recip[9], const int vt_dim[3], double omega, double bound, int ns,
+                     cudaStream_t st, std::string* why);
+int launch_fft_density(const FftPlan* pl, const ToepDesc* td, int nk, int ns, const double* occ, const double* wk,
+                       int reference, cudaStream_t st);
+int launch_fft_hartree(const FftPlan* pl, const ToepDesc* td, int nk, int ns, const double* occ, const double* wk,
+                       int* flag, cudaStream_t st);
 int launch_fft_conv(const FftPlan* pl, const ToepDesc* td, int kofs, int nk, int ncol, int vmode, int use_vd,
                     const double* s, cudaStream_t st);
 

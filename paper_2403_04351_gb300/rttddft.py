@@ -41,7 +41,7 @@ class rttddft_system(ctypes.Structure):
                 ("occ", _dp), ("wk", _dp), ("n_g", _ip), ("g_int", _ip), ("gk", _dp),
                 ("n_a", _ip), ("n_lo", _ip), ("amat", _dp), ("h", _dp), ("o", _dp), ("p", _dp),
                 ("vt_dim", ctypes.c_int * 3), ("vtab", _dp), ("caux", _dp), ("eps", _dp),
-                ("c0", _dp)]
+                ("c0", _dp), ("recip", ctypes.c_double * 9)]
 
 
 class rttddft_options(ctypes.Structure):
@@ -50,7 +50,8 @@ class rttddft_options(ctypes.Structure):
                 ("max_record", ctypes.c_int), ("graph_steps", ctypes.c_int),
                 ("cheb_tol", ctypes.c_double), ("ortho_tol", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int), ("a_max", ctypes.c_double),
-                ("s_max", ctypes.c_double), ("interstitial", ctypes.c_int)]
+                ("s_max", ctypes.c_double), ("interstitial", ctypes.c_int), ("hartree", ctypes.c_int),
+                ("hartree_bound", ctypes.c_double)]
 
 
 class rttddft_obs(ctypes.Structure):
@@ -278,7 +279,7 @@ class Context:
     def __init__(self, sys, dt=None, propagator="chebyshev", precision="fp64", reproject=False,
                  aux_mode="ritz", caux=None, eps=None, c0=None, max_record=4096, graph_steps=1,
                  cheb_tol=1e-16, stream=None, max_sweeps=30, a_max=0.0, s_max=0.0,
-                 interstitial="toeplitz"):
+                 interstitial="toeplitz", hartree=False, hartree_bound=None):
         self.n_k = int(sys["n_k"])
         self.n_s = int(sys["n_s"])
         self.n_aux = int(sys["n_aux"]) if caux is None else int(np.asarray(caux[0]).shape[1])
@@ -310,6 +311,8 @@ class Context:
         for name in ("n_g", "g_int", "n_a", "n_lo"):
             setattr(s, name, keep[name].ctypes.data_as(_ip))
         s.vt_dim[:] = [int(x) for x in sys["vt_dim"]]
+        if "recip" in sys:
+            s.recip[:] = [float(x) for x in np.asarray(sys["recip"], dtype=np.float64).ravel()]
         o = rttddft_default_options()
         o.dt = float(sys["dt"] if dt is None else dt)
         o.propagator = PROP[propagator]
@@ -323,6 +326,9 @@ class Context:
         o.a_max = float(a_max)
         o.s_max = float(s_max)
         o.interstitial = INTERSTITIAL[interstitial]
+        o.hartree = int(bool(hartree))
+        if hartree_bound is not None:
+            o.hartree_bound = float(hartree_bound)
         self.options = o
         self.max_record = int(max_record)
         self._stream = stream

@@ -132,3 +132,14 @@ def test_polarizability_arguments_checked_on_the_host(lib):
     wb = np.array([0.5, 0.0])
     assert f(10, 0.0, 0.1, P(j), P(j), 0.0, 2, P(wb), 1.0, None, None, None, None) == -1
     assert f(10, 0.0, 0.1, P(j), P(j), 0.0, 2, P(w), 0.0, None, None, None, None) == -1
+
+
+def test_hartree_options_checked_on_the_host(lib, small):
+    """The density feedback needs the FFT route, the reciprocal vectors and a
+    positive bound; all refused before any device work."""
+    _expect("ERR_UNSUPPORTED", small, hartree=True)
+    _expect("ERR_ARG", small, interstitial="fft", hartree=True, hartree_bound=-1.0)
+    s = dict(small)
+    del s["recip"]
+    _expect("ERR_ARG", s, interstitial="fft", hartree=True)
+    assert rttddft.rttddft_default_options().hartree == 0

@@ -43,7 +43,10 @@ SM_COUNT, SM_MAX_MHZ, FP32_LANES = 152, 2070.0, 128
 
 # dram bytes (read + write) per launch from ncu captures, keyed by kernel slot,
 # form and workload; valid only while the kernel source hashes match.
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/k_cheb_coop_h2_6000_ncu.md: dram__bytes_read.sum + dram__bytes_write.sum
+    ("chebyshev_series", "fp32+fft", "h2_6000", "d9e6bfe7d2fbd5fd"): 675328.0,
+}
 
 
 def _peaks():

@@ -65,3 +65,25 @@ def test_noalloc_apply_rejects_host_pointers_and_oversized_blocks():
         rttddft.rttddft_apply_noalloc(ctx.ctx, 0, 30, dx, np.zeros(3), 0.0, dx.clone(), dx.clone())
     assert e.value.code == -1 and "static limit" in str(e.value)
     ctx.close()
+
+
+def test_noalloc_apply_in_an_fft_route_context():
+    """An FFT-route context: the no-alloc apply takes the direct interstitial sum
+    (its static scratch has no FFT buffers); the two routes agree to rounding."""
+    import torch
+    build()
+    s = make_system("tiny400")
+    ctx = Context(s, interstitial="fft")
+    nb = int(s["n_g"][0]) + int(np.sum(s["n_lo"]))
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((nb, 9)) + 1j * rng.standard_normal((nb, 9))
+    a_vec = (0.2, 0.9, -1.4)
+    hx_ref, sx_ref = ctx.apply(0, x, a_vec, 0.0)
+    dx = _device_block(torch, x)
+    dh = torch.empty_like(dx)
+    ds = torch.empty_like(dx)
+    rttddft.rttddft_apply_noalloc(ctx.ctx, 0, 9, dx, np.ascontiguousarray(a_vec, dtype=np.float64), 0.0, dh, ds)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(dh.cpu().numpy().T - hx_ref)) <= 1e-12 * np.max(np.abs(hx_ref))
+    assert np.max(np.abs(ds.cpu().numpy().T - sx_ref)) <= 1e-12 * np.max(np.abs(sx_ref))
+    ctx.close()

@@ -48,6 +48,7 @@ struct rttddft_ctx {
     double* d_rec = nullptr;
     double *d_part_jmt = nullptr, *d_part_full = nullptr, *d_part_post = nullptr;
     int max_nback = 1, wmax = 1, nseg = 1, segw = BT, ntsel = 2, msegw = 64, nslot = 1, coop_grid = 0;
+    int cheb_tile = 0;
     zd* d_part_t = nullptr;
     zd* d_part = nullptr;
     double *d_a = nullptr, *d_dvs = nullptr;
@@ -236,6 +237,7 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.part_t = ctx->d_part_t;
     a.flag = ctx->d_flag;
     a.coop_grid = ctx->coop_grid;
+    a.cheb_tile = ctx->cheb_tile;
     a.tcback = (ctx->opt.precision >= RTTDDFT_PREC_BF16X3 && tc_has_back(ctx->tc)) ? 1 : 0;
     a.tc_fmt = tc_format(ctx->tc);
     a.tc_st = tc_table_scale(ctx->tc);
@@ -1139,7 +1141,7 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             const int e = prepare_back_kernels(a);
             if (e) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "table window needs more shared memory than a block has");
             CK(cudaStreamSynchronize(ctx->stream));
-            ctx->coop_grid = prepare_cheb_coop(a, ctx->stream);
+            ctx->coop_grid = prepare_cheb_coop(a, ctx->stream, &ctx->cheb_tile);
         }
         // ---- theta(0)
         if (s->c0) {

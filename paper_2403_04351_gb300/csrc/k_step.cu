@@ -11,6 +11,8 @@
 
 #include "rtd.h"
 
+#include <cstdlib>
+
 __device__ __forceinline__ double dsq(double x) { return x * x; }
 
 // ------------------------------------------------------------ step scalars
@@ -312,6 +314,107 @@ __global__ void __launch_bounds__(CHEB_THREADS) k_cheb_coop(StepArgs a, int dire
             }
         }
         if (!last && !grid_barrier(&a.st->bar, (unsigned)nt * gridDim.x, a.flag)) return;
+    }
+}
+
+// The series for many states (4 < N_s <= 64): a block owns a tile of CT_ROWS
+// rows of HH (kept in shared memory for the whole series) and all the
+// columns; a thread accumulates one row x CT_PER columns over the full dot
+// product (independent FMA chains, no cross-lane sums), with y_{n-1} staged
+// through shared memory in chunks of CT_KC rows.  One tile per block, so the
+// per-output recurrence state (y_{n-1}, y_{n-2}, partial sum) stays in
+// registers across the terms.
+#define CT_ROWS 8
+#define CT_THREADS 128
+#define CT_COLS 64
+#define CT_PER (CT_COLS * CT_ROWS / CT_THREADS)
+#define CT_KC 16
+#define CT_YS (CT_COLS + 1)  // padded row of the staged chunk
+static size_t cheb_tile_smem(int n) { return ((size_t)CT_ROWS * n + (size_t)CT_KC * CT_YS) * sizeof(zd); }
+
+__global__ void __launch_bounds__(CT_THREADS) k_cheb_tile(StepArgs a) {
+    extern __shared__ __align__(16) unsigned char ctsm[];
+    const int n = a.naux, ns = a.ns;
+    zd* Hs = (zd*)ctsm;                      // [CT_ROWS][n]
+    zd* Ys = Hs + (size_t)CT_ROWS * n;       // [CT_KC][CT_YS]
+    const int tpk = (n + CT_ROWS - 1) / CT_ROWS;
+    const int k = blockIdx.x / tpk, i0 = (blockIdx.x - k * tpk) * CT_ROWS;
+    const KDev& K = a.kd[k];
+    const int tid = threadIdx.x;
+    const int r = tid / (CT_COLS / CT_PER), cg = tid - r * (CT_COLS / CT_PER);
+    const int i = i0 + r;
+    const bool rok = i < n;
+    const size_t vs = (size_t)n * ns;
+    for (int e = tid; e < CT_ROWS * n; e += CT_THREADS) {
+        const int rr = e / n, j = e - rr * n;
+        Hs[e] = (i0 + rr < n) ? K.hsub[(size_t)(i0 + rr) * n + j] : zmk(0.0, 0.0);
+    }
+    zd y1[CT_PER], y2[CT_PER], ac[CT_PER];
+#pragma unroll
+    for (int u = 0; u < CT_PER; ++u) y1[u] = y2[u] = ac[u] = zmk(0.0, 0.0);
+    const double lc = K.lam[0], ilh = K.lam[2];
+    for (int nt = 1; nt < a.nterms; ++nt) {
+        const int last = (nt == a.nterms - 1);
+        const zd* yin = (nt == 1) ? K.theta : K.ring + ((nt - 1) & 1) * vs;
+        zd* yout = K.ring + (nt & 1) * vs;
+        zd acc[CT_PER];
+#pragma unroll
+        for (int u = 0; u < CT_PER; ++u) acc[u] = zmk(0.0, 0.0);
+        for (int kc = 0; kc < n; kc += CT_KC) {
+            __syncthreads();  // the previous chunk (or the H tile) is complete
+            for (int e = tid; e < CT_KC * CT_COLS; e += CT_THREADS) {
+                const int jj = e % CT_KC, c = e / CT_KC;
+                Ys[jj * CT_YS + c] = (kc + jj < n && c < ns) ? __ldcg(yin + kc + jj + (size_t)c * n) : zmk(0.0, 0.0);
+            }
+            __syncthreads();
+            const int jm = min(CT_KC, n - kc);
+            const zd* hr = Hs + (size_t)r * n + kc;
+            for (int jj = 0; jj < jm; ++jj) {
+                const zd h = hr[jj];
+#pragma unroll
+                for (int u = 0; u < CT_PER; ++u) zfmac(acc[u], h, Ys[jj * CT_YS + cg + u * (CT_COLS / CT_PER)]);
+            }
+        }
+        const zd cn = K.coef[nt];
+        const zd c0 = K.coef[0];
+        zd out[CT_PER];
+#pragma unroll
+        for (int u = 0; u < CT_PER; ++u) {
+            const int c = cg + u * (CT_COLS / CT_PER);
+            out[u] = zmk(0.0, 0.0);
+            if (!rok || c >= ns) continue;
+            const zd yi = (nt == 1) ? K.theta[i + (size_t)c * n] : y1[u];
+            const zd w = zscale(zsub(acc[u], zscale(yi, lc)), ilh);
+            zd y, sm;
+            if (nt == 1) {
+                y = w;
+                sm = zadd(zmul(c0, yi), zmul(cn, y));
+            } else {
+                y = zsub(zscale(w, 2.0), y2[u]);
+                sm = zadd(ac[u], zmul(cn, y));
+            }
+            y2[u] = yi;
+            y1[u] = y;
+            ac[u] = sm;
+            out[u] = y;
+        }
+        if (last) {
+            // theta is the input of the first term: with a two-term series wait for every block
+            if (nt == 1 && !grid_barrier(&a.st->bar, (unsigned)nt * gridDim.x, a.flag)) return;
+            const zd ph = (a.prop == 0) ? zmk(K.lam[3], K.lam[4]) : zmk(1.0, 0.0);
+#pragma unroll
+            for (int u = 0; u < CT_PER; ++u) {
+                const int c = cg + u * (CT_COLS / CT_PER);
+                if (rok && c < ns) K.theta[i + (size_t)c * n] = zmul(ph, ac[u]);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < CT_PER; ++u) {
+                const int c = cg + u * (CT_COLS / CT_PER);
+                if (rok && c < ns) yout[i + (size_t)c * n] = out[u];
+            }
+            if (!grid_barrier(&a.st->bar, (unsigned)nt * gridDim.x, a.flag)) return;
+        }
     }
 }
 
@@ -1370,14 +1473,15 @@ static size_t cheb_coop_smem(const StepArgs& a, int grid) {
 static cudaError_t launch_cheb_coop_raw(const StepArgs& a, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.coop_grid);
-    cfg.blockDim = dim3(CHEB_THREADS);
-    cfg.dynamicSmemBytes = cheb_coop_smem(a, a.coop_grid);
+    cfg.blockDim = dim3(a.cheb_tile ? CT_THREADS : CHEB_THREADS);
+    cfg.dynamicSmemBytes = a.cheb_tile ? cheb_tile_smem(a.naux) : cheb_coop_smem(a, a.coop_grid);
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+    if (a.cheb_tile) return cudaLaunchKernelEx(&cfg, k_cheb_tile, a);
     const int direct = cheb_direct(a);
     if (a.ns <= 2) return cudaLaunchKernelEx(&cfg, k_cheb_coop<2>, a, direct);
     if (a.ns <= 4) return cudaLaunchKernelEx(&cfg, k_cheb_coop<4>, a, direct);
@@ -1388,12 +1492,65 @@ void launch_cheb_coop(const StepArgs& a, cudaStream_t s) { launch_cheb_coop_raw(
 // Blocks for the cooperative series: all must be resident at once (the
 // launch guarantees it or fails), and the launch must be capturable in a
 // graph on this driver; otherwise 0 (one launch per term).
-int prepare_cheb_coop(const StepArgs& a0, cudaStream_t s) {
+// The tile form of the series for 4 < N_s <= 64 when one tile per block fits
+// on the GPU at once: its grid, or 0.
+// It pays when the columns fill most lanes and the tiles cover the GPU (mos2_16k,
+// N_s 60 on 16 x 38 tiles: 8.3 ms against 15.0 ms per series; co_12000, N_s 7 on
+// 50 tiles: 3.0 ms against 0.22 ms).  RTTDDFT_CHEB_TILE=1 or =0 in the
+// environment forces the choice (the tests run both forms).
+static int prepare_cheb_tile(const StepArgs& a0, int nsm) {
+    if (a0.ns <= 4 || a0.ns > CT_COLS) return 0;
+    const int grid = a0.nk * ((a0.naux + CT_ROWS - 1) / CT_ROWS);
+    const char* force = getenv("RTTDDFT_CHEB_TILE");
+    const bool forced = force && force[0] == '1' && force[1] == 0;
+    if (force && force[0] == '0' && force[1] == 0) return 0;
+    if (!forced && (a0.ns < CT_COLS / 2 || grid < nsm)) return 0;
+    const size_t smem = cheb_tile_smem(a0.naux);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_cheb_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_tile, CT_THREADS, smem) != cudaSuccess ||
+        per_sm <= 0 || grid > per_sm * nsm) {
+        cudaGetLastError();
+        return 0;
+    }
+    return grid;
+}
+
+int prepare_cheb_coop(const StepArgs& a0, cudaStream_t s, int* tile) {
     int dev = 0, coop = 0, nsm = 0, per_sm = 0;
+    *tile = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (!coop || nsm <= 0) return 0;
+    if (const int gt = prepare_cheb_tile(a0, nsm)) {
+        StepArgs a = a0;
+        a.coop_grid = gt;
+        a.cheb_tile = 1;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            cudaError_t e1 = launch_cheb_coop_raw(a, s);
+            cudaError_t e2 = cudaStreamEndCapture(s, &g);
+            int ok = (e1 == cudaSuccess && e2 == cudaSuccess && g != nullptr);
+            if (ok) {
+                cudaGraphExec_t x = nullptr;
+                ok = cudaGraphInstantiate(&x, g, 0) == cudaSuccess;
+                if (x) cudaGraphExecDestroy(x);
+            }
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            if (ok) {
+                *tile = 1;
+                return gt;
+            }
+        } else {
+            cudaGetLastError();
+        }
+    }
     // one block per row while the rows last, at most four blocks per SM
     // (more blocks would lengthen the barrier's arrival chain)
     const int nrow = a0.nk * a0.naux;

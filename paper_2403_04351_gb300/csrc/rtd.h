@@ -148,6 +148,7 @@ struct StepArgs {
     int tc_fmt;               // tensor-core operand format: 1 bf16, 0 fp16
     int ith;                  // the interstitial sum arrives in K.th (tensor cores or FFT)
     int hartree;              // the potential change is the Hartree potential of the density (FFT route)
+    int cheb_tile;            // the cooperative series runs as k_cheb_tile (4 < N_s <= 64)
     double tc_st;             // scale of the split table (fp16 range)
 };
 #define POST_STRIDE 36        // part_post row: residual, J_sub (3), then theta^H theta~ (ns <= 4)
@@ -211,7 +212,8 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
 int launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr = nullptr);
 int prepare_back_kernels(const StepArgs& a);
 // blocks for the cooperative Chebyshev launch if it can be captured in a graph, else 0
-int prepare_cheb_coop(const StepArgs& a, cudaStream_t s);
+// tile: set to 1 when the series for many states runs in tiles of HH rows (k_cheb_tile)
+int prepare_cheb_coop(const StepArgs& a, cudaStream_t s, int* tile);
 void launch_cheb_coop(const StepArgs& a, cudaStream_t s);
 void launch_prep_coef(const StepArgs& a, cudaStream_t s);
 void launch_subspace_current(const StepArgs& a, int set_gs, cudaStream_t s);

@@ -162,9 +162,12 @@ def test_fp32_form_many_states_operator():
     ctx.close()
 
 
-def test_many_states_step_matches_oracle():
+@pytest.mark.parametrize("tile", ["0", "1"])
+def test_many_states_step_matches_oracle(tile, monkeypatch):
     """40 states over 30 steps in the split-BF16 and FP32 forms: the dipole
-    from the FP64 subspace state, the full-basis energy within each form's bound."""
+    from the FP64 subspace state, the full-basis energy within each form's bound;
+    the Chebyshev series in row tiles (k_cheb_tile) and in per-row blocks."""
+    monkeypatch.setenv("RTTDDFT_CHEB_TILE", tile)
     s = make_system(tiny_config(n_g=300, n_atoms=2, lmax=2, n_lo_per_atom=2, n_s=40, n_aux=64, seed=5))
     a = pulse_samples(s, n_steps=30, a0=5.0)
     r = Oracle(s).run(a, s["dt"])

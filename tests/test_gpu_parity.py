@@ -292,3 +292,20 @@ def test_h2_6000_bench_configuration_sampled():
         else:
             assert rel(obs["energy"], r["E"]) < 1e-5
         ctx.close()
+
+
+def test_tiled_series_with_ragged_row_tiles_and_k_points(monkeypatch):
+    """The row-tile form of the Chebyshev series (forced): 61 rows (a ragged
+    last tile of 5), 33 states (a ragged column set), four k-points of ragged
+    N_basis; FP64 form, compared with the oracle over 20 steps."""
+    monkeypatch.setenv("RTTDDFT_CHEB_TILE", "1")
+    cfg = tiny_config(name="tile", n_g=0, n_atoms=2, lmax=1, n_lo_per_atom=2, n_s=33, n_aux=61,
+                      n_k=4, kgrid=(2, 2, 1), n_b_range=(120, 150), seed=23, lattice="mos2",
+                      edir=(1.0, 0.0, 0.0))
+    s = make_system(cfg)
+    a = pulse_samples(s, n_steps=20, a0=10.0)
+    r = Oracle(s).run(a, s["dt"])
+    ctx = Context(s, graph_steps=10)
+    ctx.step(a)
+    compare_run(ctx.observables(), r)
+    ctx.close()

@@ -944,26 +944,9 @@ __device__ double block_max(double v, double* sh) {
 // theta and, for N_s <= 4, the row's share of theta^H theta~), and the
 // row's share of J_sub,l = sum_n f_n Re theta_in^* ((PP_l + A_l/c) theta)_in.
 __device__ void post_body(const StepArgs& a, int do_theta, int do_j);
-__device__ void finalize_body(const StepArgs& a, int set_gs);
-// fin: the last block to finish also runs the step's finalize (one launch
-// fewer per step); blocks count themselves in st->post_done
-__global__ void __launch_bounds__(128) k_post(StepArgs a, int do_theta, int do_j, int fin) {
-    post_body(a, do_theta, do_j);
-    if (!fin) return;
-    __shared__ int last;
-    // every writing thread publishes its rows before the block counts itself
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned total = gridDim.x * gridDim.y * gridDim.z;
-        last = (atomicAdd(&a.st->post_done, 1u) == total - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    finalize_body(a, 0);  // reads the other blocks' rows through L2 (ld.global.cg)
-    if (threadIdx.x == 0) a.st->post_done = 0u;
-}
+// (the step's finalize stays a launch of its own: run by the last post block
+// it measured slower, 30 against 25 us at h2_6000, with fewer threads)
+__global__ void __launch_bounds__(128) k_post(StepArgs a, int do_theta, int do_j) { post_body(a, do_theta, do_j); }
 __device__ void post_body(const StepArgs& a, int do_theta, int do_j) {
     // halving warp sums over up to 4 columns at a time (each warp-wide FP64 add
     // is costly on GB300); per-warp scratch for the sums
@@ -1597,7 +1580,7 @@ void launch_prep_coef(const StepArgs& a, cudaStream_t s) {
 
 void launch_subspace_current(const StepArgs& a, int set_gs, cudaStream_t s) {
     dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
-    k_post<<<g, 128, 0, s>>>(a, 0, 1, 0);
+    k_post<<<g, 128, 0, s>>>(a, 0, 1);
     k_finalize<<<1, 256, 0, s>>>(a, set_gs);
 }
 
@@ -1865,13 +1848,10 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
     // theta~ = CC^H (S C): split-K partials, finished per row in k_post
     launch_gemm_cn(p.gd_proj, a.nk, a.naux, p.maxnb, a.ns, p.kc_proj, p.part, 0, f32, nullptr, s);
     mark(tr, "gemm_project", s);
-    // the finalize stays a separate launch (merging it into the last post block
-    // measured slower: the last block runs it with fewer threads)
-    const bool merged = false;
     {
         dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
-        k_post<<<g, 128, 0, s>>>(a, 1, a.reproject ? 0 : 1, merged ? 1 : 0);
-        mark(tr, merged ? "project_current_finalize" : "project_finish_current", s);
+        k_post<<<g, 128, 0, s>>>(a, 1, a.reproject ? 0 : 1);
+        mark(tr, "project_finish_current", s);
     }
     if (a.ns > 4) {
         launch_gemm_cn(p.gd_g1, a.nk, a.ns, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
@@ -1883,15 +1863,13 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
         launch_gemm_cn(p.gd_g2, a.nk, a.ns, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
         k_reproj<<<dim3((a.naux * a.ns + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
         dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
-        k_post<<<g, 128, 0, s>>>(a, 0, 1, 0);
+        k_post<<<g, 128, 0, s>>>(a, 0, 1);
         mark(tr, "reproject", s);
         nl += 3;
     }
-    if (!merged) {
-        k_finalize<<<1, 256, 0, s>>>(a, 0);
-        mark(tr, "finalize", s);
-        ++nl;
-    }
+    k_finalize<<<1, 256, 0, s>>>(a, 0);
+    mark(tr, "finalize", s);
+    ++nl;
     if (a.hartree) {
         // the density of C_{k+1} sets the potential change of the next step
         if (p.gd_exp64) {
@@ -1959,5 +1937,5 @@ void launch_hsub_only(const StepArgs& a, const StepPlan& p, int cstep, cudaStrea
 // J contributions of the current theta (rows into part_post[.][1..3])
 void launch_subspace_j(const StepArgs& a, cudaStream_t s) {
     dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
-    k_post<<<g, 128, 0, s>>>(a, 0, 1, 0);
+    k_post<<<g, 128, 0, s>>>(a, 0, 1);
 }

@@ -99,7 +99,6 @@ struct DevState {
     double cur_aa;      // |A|^2 / (2 c^2)
     int err;            // nonzero: a device iteration limit ran out
     unsigned bar;       // arrival counter of the grid barrier (zeroed by k_hsub and k_finalize)
-    unsigned post_done; // blocks of k_post finished in this step (the last one finalises)
 };
 
 // Everything the step kernels need, passed by value

@@ -45,7 +45,7 @@ SM_COUNT, SM_MAX_MHZ, FP32_LANES = 152, 2070.0, 128
 # form and workload; valid only while the kernel source hashes match.
 TRAFFIC = {
     # profiles/k_cheb_coop_h2_6000_ncu.md: dram__bytes_read.sum + dram__bytes_write.sum
-    ("chebyshev_series", "fp32+fft", "h2_6000", "7abee84067cf8ef4"): 675328.0,
+    ("chebyshev_series", "fp32+fft", "h2_6000", "03e32d7d4661fadf"): 675840.0,
 }
 
 

@@ -115,3 +115,25 @@ def test_adjoint_workload_h2_6000_400_steps_sampled():
         assert abs(grad[kk, 2] - fd) < tol * max(abs(fd), 1e-2 * scale), (kk, hh, grad[kk, 2], fd)
     ref = Oracle(s).dipole_gradient(a, s["dt"], g, [(kk, 2) for kk in picks])
     assert np.max(np.abs(grad[picks, 2] - ref)) < 1e-9 * max(np.max(np.abs(ref)), 1e-12)
+
+
+def test_autograd_function_gives_the_adjoint_gradient():
+    """dipole_increment (a torch.autograd.Function over rttddft_adjoint): its
+    value is the oracle's dipole after the run, and loss.backward() with
+    loss = g . dmu gives the adjoint's gradient for direction g."""
+    import torch
+    from paper_2403_04351_gb300 import dipole_increment
+    s = small_system()
+    n, dt = 25, 0.2
+    a = pulse_samples(s, n_steps=n, dt=dt, a0=30.0, omega=0.6, edir=(0.2, 0.4, 0.9))
+    g = np.array([0.3, -0.5, 0.8])
+    ctx = Context(s, dt=dt)
+    at = torch.tensor(a, dtype=torch.float64, requires_grad=True)
+    dmu = dipole_increment(at, ctx, ckpt_every=7)
+    r = Oracle(s).run(a, dt)
+    assert np.max(np.abs(dmu.detach().numpy() - r["dmu"][-1])) < 1e-9 * np.max(np.abs(r["dmu"][-1]))
+    loss = (dmu * torch.tensor(g, dtype=torch.float64)).sum()
+    loss.backward()
+    grad, _ = ctx.adjoint(a, g, ckpt_every=7)
+    assert np.max(np.abs(at.grad.numpy() - grad)) <= 1e-13 * np.max(np.abs(grad))
+    ctx.close()

@@ -143,3 +143,20 @@ def test_hartree_options_checked_on_the_host(lib, small):
     del s["recip"]
     _expect("ERR_ARG", s, interstitial="fft", hartree=True)
     assert rttddft.rttddft_default_options().hartree == 0
+
+
+def _header_fields(name):
+    text = open(HEADER).read()
+    end = text.index("} " + name + ";")
+    start = text.rfind("typedef struct {", 0, end)
+    body = re.sub(r"/\*.*?\*/", "", text[start + len("typedef struct {"):end], flags=re.S)
+    return re.findall(r"([A-Za-z_][A-Za-z_0-9]*)\s*(?:\[[^\]]*\])?\s*;", body)
+
+
+def test_ctypes_structs_follow_the_header():
+    """The binding's structures list the header's fields in the header's order
+    (the C ABI passes them by pointer, so an order or a missing field would
+    shift every later field)."""
+    for name in ("rttddft_system", "rttddft_options", "rttddft_obs", "rttddft_info", "rttddft_trace"):
+        cls = getattr(rttddft, name)
+        assert [f[0] for f in cls._fields_] == _header_fields(name), name

@@ -475,3 +475,30 @@ def test_hartree_feedback_is_inert_without_field_and_keeps_the_norm(tiny_oracle,
     assert r["resid"].max() < 1e-12
     r0 = tiny_oracle.run(a, tiny["dt"])
     assert np.max(np.abs(r["dmu"] - r0["dmu"])) > 1e-6 * np.max(np.abs(r0["dmu"]))
+
+
+def test_hartree_potential_of_a_single_plane_wave_density():
+    """A density change cos(g0 . r) (n_{+-g0} = 1/2) has the Hartree potential
+    (4 pi / |g0|^2) cos(g0 . r): with |g0| from the real-space cell (b = 2 pi
+    A^-T) of a hexagonal cell, where rows and columns of the reciprocal matrix
+    differ, independently of the system's stored reciprocal vectors."""
+    tiny = make_system(tiny_config(name="hex", n_g=30, n_atoms=1, lmax=1, n_lo_per_atom=1, n_s=1, n_aux=4,
+                                   seed=2, lattice="mos2"))
+    dim = tuple(int(x) for x in tiny["vt_dim"])
+    e = np.array([(x - 1) // 2 for x in dim])
+    b = 2 * math.pi * np.linalg.inv(np.asarray(tiny["lattice"])).T  # rows b_i
+    assert abs(b[0] @ b[1]) > 1e-3  # a non-orthogonal pair
+    for g0 in ([1, 0, 0], [1, 1, 0], [1, -1, 1]):
+        g0 = np.array(g0)
+        assert np.all(np.abs(g0) <= e)  # inside the table box
+        dn = np.zeros(dim, dtype=np.complex128)
+        dn[tuple(e + g0)] = 0.5
+        dn[tuple(e - g0)] = 0.5
+        dv = hartree_table(tiny, dn, np.zeros(dim))
+        gc = g0 @ b
+        expect = 4 * math.pi / float(gc @ gc) * 0.5
+        assert abs(dv[tuple(e + g0)] - expect) < 1e-14 * expect
+        assert abs(dv[tuple(e - g0)] - expect) < 1e-14 * expect
+        mask = np.ones(dim, dtype=bool)
+        mask[tuple(e + g0)] = mask[tuple(e - g0)] = False
+        assert np.max(np.abs(dv[mask])) == 0.0

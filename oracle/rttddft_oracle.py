@@ -43,6 +43,29 @@ Readings where the paper is silent (each listed in the design notes):
   interstitial only: n_g = (1/Omega) sum_k w_k sum_j f_j sum_G C_G conj(C_{G-g})
   over the plane-wave rows, dV_g = 4 pi (n_g(t) - n_g(0)) / |g|^2 (g != 0,
   cartesian g), on the table box; the potential of step k comes from C_k.
+
+What pins each function (tests/test_oracle_pins.py; no function is
+parity-unpinned):
+* interstitial_potential: the FFT convolution of the same sum;
+* embedding, explicit_operators: muffin-tin blocks landing on the matched plane
+  waves, Hermiticity and positivity, the free-electron closed forms;
+* explicit_dv: the four-block form of Eq. v_MT, a Hermitian perturbation;
+* hamiltonian: free-electron closed forms, the discrete work theorem;
+* ritz_basis, fix_phases: orthonormality, diagonal H0, bounds by the exact
+  eigenvalues;
+* propagate_exact, critical_timestep: Pade expm, the two-level closed form;
+* propagate_cn: second-order convergence;
+* full_basis_propagator and Oracle.run: the complete-subspace equivalence,
+  the field-free phase, norm and energy conservation, time reversal,
+  weak-field linearity, k-point weighting;
+* Oracle.excited_electrons: full-basis projection on the LAPACK ground state,
+  second order in a weak field;
+* Oracle.dipole_gradient: central differences;
+* overall_speedup: the speed-ups printed in Table tab:H2;
+* polarizability: the closed-form geometric series, a proportional response;
+* interstitial_density: |psi(r)|^2 on a grid through numpy's FFT;
+* hartree_table: a single plane-wave density in a hexagonal cell, the sign of
+  the Hartree energy; Oracle.run(hartree=True): field-free inertness, norm.
 """
 from __future__ import annotations
 

@@ -393,6 +393,9 @@ def run_ours(args, rank, world, local_rank):
     roof_tc = None
     if "tc_interstitial_and_forward" in tr and dom != "tc_interstitial_and_forward":
         roof_tc = roofline_of("tc_interstitial_and_forward", tr, s, args.precision, info["cheb_terms"])
+    roof_fft = None
+    if "fft_interstitial" in tr and dom != "fft_interstitial":
+        roof_fft = roofline_of("fft_interstitial", tr, s, args.precision, info["cheb_terms"])
     share = {n: round(v[0] / sum(x[0] for x in tr.values()), 4) for n, v in tr.items()}
 
     line = {
@@ -416,6 +419,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "roofline": roof,
         "roofline_tc": roof_tc,
+        "roofline_fft": roof_fft,
         "kernel_share": share,
         "fp64": fp64,
         "forms": forms,

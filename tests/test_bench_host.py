@@ -36,3 +36,15 @@ def test_roofline_entry_of_the_series():
     assert np.isclose(roof["achieved"], fl / 0.05e-3 / 1e12)
     assert np.isclose(roof["frac"], roof["achieved"] / roof["peak"])
     assert roof["traffic"] is None  # no capture for this workload
+
+
+def test_roofline_entry_of_the_fft_slot():
+    s = make_system("h2_6000", with_amat=False)
+    tr = {"fft_interstitial": [0.3, 10]}  # 0.03 ms per step
+    roof = bench.roofline_of("fft_interstitial", tr, s, "fp32+fft", 14)
+    fl, _ = bench.fft_work(s)
+    assert roof["bound"] == "alu"
+    assert np.isclose(roof["peak"], bench.SM_COUNT * bench.FP32_LANES * 2 * bench.SM_MAX_MHZ * 1e6 / 1e12)
+    assert np.isclose(roof["achieved"], fl / 0.03e-3 / 1e12)
+    roof64 = bench.roofline_of("fft_interstitial", tr, s, "fp64+fft", 14)
+    assert roof64["peak"] == bench.FP64_PEAK_TFLOPS

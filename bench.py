@@ -405,9 +405,7 @@ def run_ours(args, rank, world, local_rank):
         "dtype": {"fp64": "f64", "fp32": "f32+f64", "bf16x3": "bf16x3+f32+f64",
                   "fp16x3": "fp16x3+f32+f64"}[args.precision.partition("+")[0]],
         "data": "synthetic (seeded generator shaped like the paper's H2 cell)",
-        "config": {"workload": args.workload, "n_k": int(s["n_k"]), "n_basis": int(s["n_g"][0]) +
-                   int(np.sum(s["n_lo"])), "n_states": int(s["n_s"]), "n_aux": int(s["n_aux"]),
-                   "dt": float(s["dt"]), "precision_form": args.precision.partition("+")[0],
+        "config": {**workload_config(s, args.workload), "precision_form": args.precision.partition("+")[0],
                    "interstitial": "fft" if args.precision.endswith("+fft") else "toeplitz (direct sum)",
                    "propagator": "chebyshev (exact exponential to FP64 round-off)",
                    "l2": "flushed (256 MiB read) before every timed step",
@@ -454,6 +452,12 @@ def cpu_baseline(s, a_all, budget_s):
                       % (n, s["name"], cores)}
 
 
+def workload_config(s, workload):
+    """The workload part of the config, shared by both arms."""
+    return {"workload": workload, "n_k": int(s["n_k"]), "n_basis": int(s["n_g"][0]) + int(np.sum(s["n_lo"])),
+            "n_states": int(s["n_s"]), "n_aux": int(s["n_aux"]), "dt": float(s["dt"])}
+
+
 def run_reference(args):
     from oracle import Oracle
     from synth import make_system, pulse_samples
@@ -473,7 +477,7 @@ def run_reference(args):
             "steps": nsteps, "warmup": args.warmup, "ms_per_step": dt / nsteps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded generator shaped like the paper's H2 cell)",
-            "config": {"workload": args.workload, "precision_form": "fp64 oracle"},
+            "config": {**workload_config(s, args.workload), "precision_form": "fp64 oracle (numpy/scipy, host cores)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d steps of %s (set-up excluded)" % (nsteps, s["name"])},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -81,3 +81,10 @@ def test_reference_arm_prints_one_line_on_rank_zero():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["cpu_baseline"]["kind"] == "oracle"
+    # the workload part of the config matches what the GPU arm reports
+    sys.path.insert(0, ROOT)
+    import bench
+    from synth import make_system
+    s = make_system("tiny400")
+    for key, val in bench.workload_config(s, "tiny400").items():
+        assert d["config"][key] == val, key

@@ -321,8 +321,8 @@ RTTDDFT_API int rttddft_trace_steps(rttddft_ctx* ctx, int nsteps, const double* 
  *   out_j, out_e    [n_w][3] complex J(w), E(w), or NULL;
  *   alpha           [n_w][3][3] complex, row l, column l' (l' fastest), or NULL;
  *                   an entry with E_l'(w) exactly zero is written as 0.
- * Outputs on the host or the device like the inputs; the call returns after the
- * results are written.  Errors: ERR_ARG (sizes, dt <= 0, a host w <= 0, NULL
+ * Each output pointer may be host or device memory (classified like the inputs);
+ * the call returns after the results are written.  Errors: ERR_ARG (sizes, dt <= 0, a host w <= 0, NULL
  * inputs), ERR_CUDA. */
 RTTDDFT_API int rttddft_polarizability(int n_t, double t0, double dt, const double* j_ind, const double* e_field,
                                        double eta, int n_w, const double* w, double omega_cell, double* out_j,

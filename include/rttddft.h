@@ -260,12 +260,22 @@ RTTDDFT_API int rttddft_apply(rttddft_ctx* ctx, int k, int ncols, const double* 
  * first call on each device looks up that array's address (make that first
  * call before starting any stream capture).  Every call shares the array, so
  * calls whose work overlaps on the GPU (different streams or contexts) race;
- * calls on one stream are ordered.  A k-point whose scratch need exceeds
- * 16 MiB (about N_basis x N_states x 48 bytes plus the matching-coefficient
- * partials) is rejected with ERR_ARG and a message giving the need.
+ * calls on one stream are ordered.  The scratch need of a k-point is, in
+ * bytes, 48 N_basis N_states (the staged block and [HX | SX]) + 48 M_A N_states
+ * (Q = A X and the muffin-tin products, M_A = matching rows of all atoms)
+ * + 16 M_A N_states ceil(N_G / K_chunk) (split-K partials of Q) + the
+ * interstitial partials of the direct sum, 32 n_slot n_tsel max_k N_G
+ * (n_slot row segments of the table window, n_tsel column groups; these
+ * dominate) + 16 bytes per V~ table entry when dv_scale != 0 (24 in the
+ * reduced-precision forms) + a few small per-row sums, each part rounded up
+ * to 256 bytes.
+ * Among the benchmark's workloads tiny400 (N_basis 400) fits and co_12000
+ * (N_basis 12000, N_states 7) does not; a k-point that does not fit is
+ * rejected with ERR_ARG and a message giving its need.  The caller's current
+ * device must be the one the context was set up on (ERR_ARG otherwise).
  * It never calls cudaMalloc or cudaFree.
- * Errors: ERR_ARG (bad sizes, NULL or host pointers, scratch limit),
- * ERR_CUDA, ERR_UNSUPPORTED (device ordinal above 255). */
+ * Errors: ERR_ARG (bad sizes, NULL or host pointers, scratch limit, another
+ * current device), ERR_CUDA, ERR_UNSUPPORTED (device ordinal above 255). */
 RTTDDFT_API int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const double* x,
                                       const double* a_vec, double dv_scale, double* hx, double* sx);
 

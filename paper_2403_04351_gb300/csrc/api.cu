@@ -32,6 +32,7 @@ struct rttddft_ctx {
     int nvt = 0, vt_center = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    int device = -1;  // the device current at set-up: every allocation of the context lives there
     std::vector<void*> allocs;
     std::vector<KDev> hkd;
     KDev* d_kd = nullptr;
@@ -713,6 +714,7 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             if (!finite_all(s->c0, 2 * n0)) fail(ctx, RTTDDFT_ERR_NONFINITE, "c0 not finite");
         }
         // ---- device state (all host checks are done)
+        CK(cudaGetDevice(&ctx->device));
         if (cuda_stream) {
             ctx->stream = (cudaStream_t)cuda_stream;
         } else {
@@ -2098,11 +2100,15 @@ static void put_struct(unsigned char* dst, const T& v, cudaStream_t s) {
     k_put_blob<<<1, 128, 0, s>>>(dst, b, (int)sizeof(T));
 }
 
-// Resolve the array's device address for the current device (first call on
-// each device; later calls reuse it).
+// Resolve the array's device address on the context's device (first call on
+// each device; later calls reuse it).  The address is looked up with that
+// device current, so the caller's current device must be the context's.
 static unsigned char* noalloc_base(rttddft_ctx* ctx) {
     int dev = -1;
     CK(cudaGetDevice(&dev));
+    if (dev != ctx->device)
+        fail(ctx, RTTDDFT_ERR_ARG, "rttddft_apply_noalloc: the current device (" + std::to_string(dev) +
+                                       ") is not the context's device (" + std::to_string(ctx->device) + ")");
     if (dev < 0 || dev >= 256) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "device ordinal above 255");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {

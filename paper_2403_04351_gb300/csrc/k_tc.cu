@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -1213,6 +1214,58 @@ static int tco_tune_back(TcPlan* tp, std::vector<TcRowsCand>& tb, const KDev* kd
     return 0;
 }
 
+// Candidate families for tests and measurements: RTTDDFT_TC_FAMILY in the
+// environment holds comma-separated words that restrict the shapes the set-up
+// autotuner times: "window" or "gather" (the interstitial table staged in
+// shared memory or read through L1/L2), "fewslices" or "manyslices" (the
+// largest or smallest K slice of the remaining shapes), "minstages" or
+// "maxstages" (the fewest or most pipeline stages of the remaining shapes).
+// The restriction applies to the interstitial launch, the matching rows and
+// the back-projection alike.  Unset: every shape is timed.
+struct TcFamily {
+    int route = 0;   // 1 window, 2 gather
+    int slices = 0;  // 1 few (largest K slice), 2 many (smallest)
+    int stages = 0;  // 1 min, 2 max
+};
+static TcFamily tc_family_from_env() {
+    TcFamily f;
+    const char* v = getenv("RTTDDFT_TC_FAMILY");
+    if (!v) return f;
+    const std::string s(v);
+    auto has = [&](const char* w) { return s.find(w) != std::string::npos; };
+    f.route = has("window") ? 1 : (has("gather") ? 2 : 0);
+    f.slices = has("fewslices") ? 1 : (has("manyslices") ? 2 : 0);
+    f.stages = has("minstages") ? 1 : (has("maxstages") ? 2 : 0);
+    return f;
+}
+template <typename C, typename KeyF>
+static void tc_keep_extreme(std::vector<C>& v, int which, KeyF key) {
+    if (!which || v.empty()) return;
+    long best = key(v[0]);
+    for (const C& c : v) best = which == 1 ? std::min(best, key(c)) : std::max(best, key(c));
+    std::vector<C> out;
+    for (const C& c : v)
+        if (key(c) == best) out.push_back(c);
+    v.swap(out);
+}
+static void tc_filter_family(const TcFamily& f, std::vector<TcToepCand>& tc, std::vector<TcRowsCand>& ta,
+                             std::vector<TcRowsCand>& tb) {
+    if (f.route) {
+        std::vector<TcToepCand> out;
+        for (const auto& c : tc)
+            if ((f.route == 1) == (c.wn > 0)) out.push_back(c);
+        tc.swap(out);
+    }
+    // few slices = the largest K slice (kbps): keep the maximum of kbps
+    const int sl = f.slices == 1 ? 2 : (f.slices == 2 ? 1 : 0);
+    tc_keep_extreme(tc, sl, [](const TcToepCand& c) { return (long)c.kbps; });
+    tc_keep_extreme(ta, sl, [](const TcRowsCand& c) { return (long)c.kbps; });
+    tc_keep_extreme(tb, sl, [](const TcRowsCand& c) { return (long)c.kbps; });
+    tc_keep_extreme(tc, f.stages, [](const TcToepCand& c) { return (long)c.SA * 100 + c.SB; });
+    tc_keep_extreme(ta, f.stages, [](const TcRowsCand& c) { return (long)c.S; });
+    tc_keep_extreme(tb, f.stages, [](const TcRowsCand& c) { return (long)c.S; });
+}
+
 template <int NT>
 static int tco_tune_t(TcPlan* tp, std::vector<TcToepCand>& tc, std::vector<TcRowsCand>& ta, const KDev* kd, int nk,
                       cudaStream_t s) {
@@ -1504,6 +1557,12 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
     }
     // autotune: time every candidate on these operands (3 launches after one
     // warm-up) and keep the fastest
+    tc_filter_family(tc_family_from_env(), tc_c, ta_c, tb_c);
+    if (tc_c.empty() || (tp->atiles > 0 && ta_c.empty()) || (tp->Dnb > 0 && tb_c.empty())) {
+        tc_plan_destroy(tp);
+        *why = "no tensor-core launch shape of the family in RTTDDFT_TC_FAMILY fits";
+        return RTTDDFT_ERR_UNSUPPORTED;
+    }
     int ti = tco_tune(tp, tc_c, ta_c, d_kd, nk, s);
     if (!ti) ti = tco_tune_back(tp, tb_c, d_kd, nk, s);
     if (ti) {
@@ -1678,10 +1737,16 @@ int tc_dv_prepare(TcPlan* tp, const zd* const* caux_dev, const int* nb, const in
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int smax = 0;
+    cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int sp = std::max(1, std::min(nkb, (2 * nsm + tp->ttiles * tp->nk - 1) / (tp->ttiles * tp->nk)));
-    tp->dv_kbps = (nkb + sp - 1) / sp;
+    // two stages of each operand plus 128 bytes per K block of a slice: cap the
+    // slice so that the block fits in the opt-in shared memory
+    const size_t fixed = 1024 + (size_t)2 * 4 * TC_BM * TC_BK + (size_t)2 * 4 * TC_DV_NT * TC_BK;
+    const int kb_cap = (int)std::max<long>(1, ((long)smax - 512 - (long)fixed) / 128);
+    tp->dv_kbps = std::min((nkb + sp - 1) / sp, kb_cap);
     tp->dv_splits = (nkb + tp->dv_kbps - 1) / tp->dv_kbps;
-    tp->dv_smem = 1024 + (size_t)2 * 4 * TC_BM * TC_BK + (size_t)2 * 4 * TC_DV_NT * TC_BK + (size_t)tp->dv_kbps * 128;
+    tp->dv_smem = fixed + (size_t)tp->dv_kbps * 128;
     const int rows = tp->dv_tiles * TC_DV_NT;
     const size_t ncc = (size_t)tp->nk * rows * tp->Kp;
     const size_t nd = (size_t)tp->nk * tp->dv_splits * tp->ttiles * TC_BM * TC_DV_NT;

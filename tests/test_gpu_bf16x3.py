@@ -206,3 +206,54 @@ def test_potential_change_rebuilt_on_tensor_cores(form):
     assert rel(ctx2.observables()["dmu"], r["dmu"]) > 1e-4
     ctx.close()
     ctx2.close()
+
+
+# Every family of launch shapes the set-up autotuner can pick, forced through
+# RTTDDFT_TC_FAMILY: the interstitial table staged in shared memory or read
+# through L1/L2, the largest or smallest K slice, the fewest or most stages.
+TUNER_FAMILIES = ["window,fewslices,minstages", "window,manyslices,maxstages",
+                  "gather,fewslices,maxstages", "gather,manyslices,minstages"]
+
+
+def _golden():
+    import os
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mos2_16k_oracle.npz")
+    return np.load(p)
+
+
+@pytest.mark.parametrize("family", TUNER_FAMILIES)
+@pytest.mark.parametrize("case", ["ragged", "mos2_16k_largest_k"])
+def test_every_tuner_family_within_split_bound(case, family, monkeypatch):
+    """The split-BF16 operator in each forced family, entrywise within
+    1e-4 (|H||x|) of the oracle: on a ragged 4-k batch (explicit operators)
+    and on the largest k-point of the heterostructure workload (N_basis 9917,
+    sampled rows of the oracle's H X and S X from the committed golden file)."""
+    monkeypatch.setenv("RTTDDFT_TC_FAMILY", family)
+    if case == "ragged":
+        rng = np.random.default_rng(3)
+        s = make_system(ragged_cfg())
+        ctx = Context(s, precision="bf16x3")
+        a_vec = np.array([0.3, -0.7, 1.1]) * 20.0
+        for k in range(int(s["n_k"])):
+            ops = explicit_operators(s, k)
+            nb = ops["nb"]
+            x = rng.standard_normal((nb, 4)) + 1j * rng.standard_normal((nb, 4))
+            hx, sx = ctx.apply(k, x, a_vec, 0.0)
+            h = hamiltonian(ops, a_vec, s["c_light"], None, 0.0)
+            assert np.max(np.abs(hx - h @ x) / (np.abs(h) @ np.abs(x))) < 1e-4, k
+            assert np.max(np.abs(sx - ops["S"] @ x) / (np.abs(ops["S"]) @ np.abs(x))) < 1e-4, k
+    else:
+        from golden.make_mos2_16k_golden import seeded_block
+        g = _golden()
+        k = int(g["keep_k"][1])
+        s = make_system("mos2_16k", k_subset=[k])
+        ctx = Context(s, precision="bf16x3")
+        nb = int(g["n_basis"][k])
+        x = seeded_block(nb, k)
+        hx, sx = ctx.apply(0, x, g["a_apply"], 0.0)
+        rows = g["rows_hx_k%d" % k]
+        assert np.max(np.abs(hx[rows] - g["hx_rows_k%d" % k]) / g["mag_h_k%d" % k]) < 1e-4
+        assert np.max(np.abs(sx[rows] - g["sx_rows_k%d" % k]) / g["mag_s_k%d" % k]) < 1e-4
+    info = ctx.info()["tc"]
+    assert (info["window"] > 0) == ("window" in family), info
+    ctx.close()

@@ -87,3 +87,59 @@ def test_noalloc_apply_in_an_fft_route_context():
     assert np.max(np.abs(dh.cpu().numpy().T - hx_ref)) <= 1e-12 * np.max(np.abs(hx_ref))
     assert np.max(np.abs(ds.cpu().numpy().T - sx_ref)) <= 1e-12 * np.max(np.abs(sx_ref))
     ctx.close()
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16x3"])
+def test_noalloc_apply_in_reduced_precision_contexts(form):
+    """FP32 and split-BF16 contexts with the potential change on, at k-point 1
+    of a ragged 2-k system: the no-alloc apply runs the FP32 contraction form
+    (its static scratch holds no tensor-core operands) and is held to the
+    oracle's explicit H X and S X at the FP32 bound, 1e-5 (|H||x|); in the
+    FP32 context it also matches rttddft_apply of the same context."""
+    import torch
+    from oracle import explicit_dv, explicit_operators, hamiltonian
+    build()
+    cfg = tiny_config(name="ragged2", n_g=0, n_atoms=3, lmax=2, n_lo_per_atom=3, n_s=3, n_aux=20,
+                      n_k=2, kgrid=(2, 1, 1), n_b_range=(130, 181), seed=19, lattice="mos2")
+    s = make_system(cfg)
+    assert s["n_g"][0] != s["n_g"][1]
+    dv = make_dv(s)
+    ctx = Context(s, precision=form)
+    ctx.set_dv(dv)
+    rng = np.random.default_rng(13)
+    a_vec, sdv = (0.6, -1.1, 0.3), 0.7
+    for k in (1, 0):
+        ops = explicit_operators(s, k)
+        nb = ops["nb"]
+        x = rng.standard_normal((nb, 5)) + 1j * rng.standard_normal((nb, 5))
+        dx = _device_block(torch, x)
+        dh = torch.empty_like(dx)
+        ds = torch.empty_like(dx)
+        rttddft.rttddft_apply_noalloc(ctx.ctx, k, 5, dx, np.ascontiguousarray(a_vec, dtype=np.float64), sdv, dh, ds)
+        torch.cuda.synchronize()
+        hx = dh.cpu().numpy().T
+        sxv = ds.cpu().numpy().T
+        h = hamiltonian(ops, a_vec, s["c_light"], explicit_dv(s, k, dv), sdv)
+        assert np.max(np.abs(hx - h @ x) / (np.abs(h) @ np.abs(x))) < 1e-5, (form, k)
+        assert np.max(np.abs(sxv - ops["S"] @ x) / (np.abs(ops["S"]) @ np.abs(x))) < 1e-5, (form, k)
+        if form == "fp32":
+            hx_ref, sx_ref = ctx.apply(k, x, a_vec, sdv)
+            assert np.max(np.abs(hx - hx_ref)) <= 1e-6 * np.max(np.abs(hx_ref)), k
+            assert np.max(np.abs(sxv - sx_ref)) <= 1e-6 * np.max(np.abs(sx_ref)), k
+    ctx.close()
+
+
+def test_noalloc_apply_rejects_the_co_12000_workload():
+    """co_12000 (N_basis 12000, N_states 7) needs more than the 16 MiB static
+    scratch (the interstitial partials of the direct sum dominate): ERR_ARG
+    with the need in the message, nothing launched."""
+    import torch
+    build()
+    s = make_system("co_12000")
+    ctx = Context(s)
+    nb = int(s["n_g"][0]) + int(np.sum(s["n_lo"]))
+    dx = torch.zeros((7, nb), dtype=torch.complex128, device="cuda")
+    with pytest.raises(RttddftError) as e:
+        rttddft.rttddft_apply_noalloc(ctx.ctx, 0, 7, dx, np.zeros(3), 0.0, dx.clone(), dx.clone())
+    assert e.value.code == -1 and "static limit" in str(e.value)
+    ctx.close()

@@ -152,7 +152,7 @@ def algorithmic_work(name, sysd, prec, nterms=1):
     ns, naux = int(sysd["n_s"]), int(sysd["n_aux"])
     ma = int(np.sum(sysd["n_a"]))
     nlo = int(np.sum(sysd["n_lo"]))
-    cb = 8 if prec == "fp32" else 16  # bytes of a stored complex
+    cb = 16 if prec == "fp64" else 8  # bytes of a stored complex (FP32, or a bf16/fp16 hi/lo pair)
     fl, by = 0.0, 0.0
     for ng in np.asarray(sysd["n_g"], dtype=np.float64):
         nb = ng + nlo
@@ -325,11 +325,15 @@ DEFAULT_FORM = "bf16x3"
 # forms timed beside the headline one; "+dv": a prescribed potential change
 # dV(t) = sin(0.1 t) dV_1 rebuilt into the subspace Hamiltonian every step
 COMPARE_FORMS = {
-    "mos2_16k": ("fp64", "fp64+fft", "fp32", "fp32+fft", "fp16x3",
-                 "fp64+fft+dv", "fp32+fft+dv", "bf16x3+dv", "fp16x3+dv"),
+    "mos2_16k": ("fp64", "fp64+fft", "fp32", "fp32+fft", "bf16x3+fft", "fp16x3",
+                 "fp64+fft+dv", "fp32+fft+dv", "bf16x3+dv", "bf16x3+fft+dv", "fp16x3+fft+dv"),
 }
-EXTRA_FORMS = ("fp64", "fp32+fft", "bf16x3", "fp64+fft+dv", "fp32+fft+dv", "bf16x3+dv")
-FORM_STEPS = {"mos2_16k": 4, "co_12000": 20, "h2_6000": 50}
+EXTRA_FORMS = ("fp64", "fp32+fft", "bf16x3", "bf16x3+fft", "fp64+fft+dv", "fp32+fft+dv", "bf16x3+dv",
+               "bf16x3+fft+dv")
+# the basis-size point of the paper's CO table where the two interstitial
+# routes differ most: the direct sum (MM) against the FFT route, FP64 and FP32
+EXTRA_FORMS_BY = {"co_25727": ("fp64", "fp64+fft", "fp32", "fp32+fft", "bf16x3", "bf16x3+fft")}
+FORM_STEPS = {"mos2_16k": 4, "co_12000": 20, "h2_6000": 50, "co_25727": 10}
 
 
 def parse_form(form):
@@ -563,6 +567,10 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         n_g, n_lo = __import__("synth").basis_sizes(cfg)
         mine = shard_kpoints([g + n_lo for g in n_g], world)[rank]
+    if args.k_subset:
+        # a smaller case of the same workload (profiling): these k-points only
+        sub = [int(x) for x in args.k_subset.split(",")]
+        mine = sub if mine is None else [k for k in mine if k in sub]
     s = make_system(args.workload, k_subset=mine)
     K, W = args.steps, args.warmup
     a_all, sc_all = workload_samples(cfg, K + W + args.trace_steps + 64)
@@ -634,7 +642,7 @@ def run_ours(args, rank, world, local_rank):
         for w in [x for x in args.extra_workloads.split(",") if x and x != args.workload]:
             s2 = make_system(w)
             a2, sc2 = workload_samples(CONFIGS[w], 256)
-            fe2, _ = time_forms(timer, s2, EXTRA_FORMS, a2, sc2, FORM_STEPS.get(w, 20), 3)
+            fe2, _ = time_forms(timer, s2, EXTRA_FORMS_BY.get(w, EXTRA_FORMS), a2, sc2, FORM_STEPS.get(w, 20), 3)
             workloads[w] = {"config": workload_config(w), "forms": fe2}
             del s2
     fp64 = forms.get("fp64") if form != "fp64" else None
@@ -743,10 +751,12 @@ def main():
     p.add_argument("--workload", default=DEFAULT_WORKLOAD)
     p.add_argument("--form-steps", type=int, default=-1,
                    help="steps timed for each other form (-1: per workload; 0: none)")
-    p.add_argument("--extra-workloads", default="h2_6000,co_12000")
+    p.add_argument("--extra-workloads", default="h2_6000,co_12000,co_25727")
     p.add_argument("--trace-steps", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--ref-steps", type=int, default=20)
+    p.add_argument("--k-subset", default="",
+                   help="comma-separated k-points of the workload to run (a smaller case for profiling)")
     args = p.parse_args()
     if args.warmup < 3:
         p.error("--warmup must be >= 3")

@@ -90,9 +90,10 @@ extern "C" {
 #define RTTDDFT_INTERSTITIAL_TOEPLITZ 0 /* direct sum over G' with V~_{G-G'} generated from the table */
 /* circular convolution on a grid of F_i >= vt_dim[i] points per axis (the
  * smallest products of 2, 3 and 5, at most 128): pruned inverse and forward
- * 3-D FFTs around a product with the table's real-space image; FP64 and FP32
- * forms only (ERR_UNSUPPORTED otherwise or when an axis needs more than 128
- * points).  Equal to the direct sum up to rounding. */
+ * 3-D FFTs around a product with the table's real-space image, FP64 in the
+ * FP64 form and FP32 in the others (the split forms keep the matching-
+ * coefficient products on the tensor cores); ERR_UNSUPPORTED when an axis
+ * needs more than 128 points.  Equal to the direct sum up to rounding. */
 #define RTTDDFT_INTERSTITIAL_FFT 1
 
 /* how the auxiliary basis CC(0) is obtained at set-up */

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <complex>
 #include <string>
 #include <vector>
@@ -39,6 +40,11 @@ struct rttddft_ctx {
     AtomTab* d_at = nullptr;
     zd *d_h = nullptr, *d_o = nullptr, *d_p = nullptr, *d_dh = nullptr;
     zf *d_h32 = nullptr, *d_o32 = nullptr, *d_p32 = nullptr;
+    TcCC* tcc = nullptr;  // expansion and projection on the tensor cores (split forms, many states)
+    zf* d_mtg = nullptr;  // muffin-tin stacks [h_eff; o; p] (FP32 forms, many states)
+    zd* d_mtw = nullptr;
+    int mtw_stride = 0, mt_maxna = 0, mt_maxlo = 0;
+    GemmDesc *gd_mt1 = nullptr, *gd_mt2 = nullptr;
     size_t nblk = 0;
     zd *d_vtab = nullptr, *d_dvtab = nullptr, *d_vstep = nullptr;
     zf *d_vtab32 = nullptr, *d_vstep32 = nullptr;
@@ -48,7 +54,9 @@ struct rttddft_ctx {
     DevState* d_st = nullptr;
     double* d_rec = nullptr;
     double *d_part_jmt = nullptr, *d_part_full = nullptr, *d_part_post = nullptr;
+    double *d_part_fin = nullptr, *d_gdev = nullptr;
     int max_nback = 1, wmax = 1, nseg = 1, segw = BT, ntsel = 2, msegw = 64, nslot = 1, coop_grid = 0;
+    int toep_global = 0;  // the direct sum's table window does not fit in shared memory: gather from L2
     int cheb_tile = 0;
     zd* d_part_t = nullptr;
     zd* d_part = nullptr;
@@ -58,6 +66,8 @@ struct rttddft_ctx {
     GemmDesc *gd_expand = nullptr, *gd_fwd = nullptr, *gd_proj = nullptr, *gd_g1 = nullptr,
              *gd_g2 = nullptr, *gd_evh = nullptr, *gd_evn = nullptr;
     GemmDesc *gd_dvw = nullptr, *gd_dvg = nullptr, *gd_dvi = nullptr, *gd_dvi32 = nullptr;
+    GemmDesc *gd_dvw32 = nullptr, *gd_dvg32 = nullptr;  // the muffin-tin rebuild in FP32 (reduced-precision forms)
+    zf* d_dh32 = nullptr;
     zd* d_part_dv = nullptr;
     int kc_dvi = 0;
     ToepDesc* td_dv = nullptr;
@@ -224,6 +234,8 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.part_jmt = ctx->d_part_jmt;
     a.part_full = ctx->d_part_full;
     a.part_post = ctx->d_part_post;
+    a.part_fin = ctx->d_part_fin;
+    a.gdev = ctx->d_gdev;
     a.at = ctx->d_at;
     a.gd_proj = ctx->gd_proj;
     a.part_proj = ctx->d_part;
@@ -244,8 +256,12 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.tc_st = tc_table_scale(ctx->tc);
     a.at_n = ctx->at.n;
     a.at_maxm = ctx->maxm;
-    a.ith = (ctx->opt.precision >= RTTDDFT_PREC_BF16X3 || ctx->fft) ? 1 : 0;
+    a.ith = (ctx->opt.precision >= RTTDDFT_PREC_BF16X3 || ctx->fft || ctx->toep_global) ? 1 : 0;
+    a.toep_global = ctx->toep_global;
     a.hartree = ctx->opt.hartree;
+    a.mtg = ctx->d_mtg;
+    a.mtw = ctx->d_mtw;
+    a.mtw_stride = ctx->mtw_stride;
     return a;
 }
 
@@ -269,6 +285,8 @@ static StepPlan make_plan(rttddft_ctx* ctx) {
     p.gd_dvg = ctx->gd_dvg;
     p.gd_dvi = ctx->gd_dvi;
     p.gd_dvi32 = ctx->gd_dvi32;
+    p.gd_dvw32 = ctx->gd_dvw32;
+    p.gd_dvg32 = ctx->gd_dvg32;
     p.part_dv = ctx->d_part_dv;
     p.kc_dvi = ctx->kc_dvi;
     p.td_dv = ctx->td_dv;
@@ -280,6 +298,7 @@ static StepPlan make_plan(rttddft_ctx* ctx) {
     p.jac_vecs = ctx->d_jac_vecs;
     p.max_sweeps = ctx->opt.max_sweeps;
     p.tc = ctx->tc;
+    p.tcc = ctx->tcc;
     p.fft = ctx->fft;
     p.td_op = ctx->td_op;
     p.tile_cnt = ctx->d_tile_cnt;
@@ -287,6 +306,10 @@ static StepPlan make_plan(rttddft_ctx* ctx) {
     p.ev_fork = ctx->ev_fork;
     p.ev_join = ctx->ev_join;
     p.gd_exp64 = ctx->gd_exp64;
+    p.gd_mt1 = ctx->gd_mt1;
+    p.gd_mt2 = ctx->gd_mt2;
+    p.mt_maxna = ctx->mt_maxna;
+    p.mt_maxlo = ctx->mt_maxlo;
     p.td_dens = ctx->td_dens ? ctx->td_dens : ctx->td_op;
     {
         int F[3], fused = 0;
@@ -530,8 +553,6 @@ static void validate(const rttddft_system* s, const rttddft_options* o) {
     if (o->precision < 0 || o->precision > 3) fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown precision form");
     if (o->interstitial != RTTDDFT_INTERSTITIAL_TOEPLITZ && o->interstitial != RTTDDFT_INTERSTITIAL_FFT)
         fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "unknown interstitial route");
-    if (o->interstitial == RTTDDFT_INTERSTITIAL_FFT && o->precision > RTTDDFT_PREC_FP32)
-        fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "the FFT interstitial route runs in the FP64 and FP32 forms");
     if (o->hartree != 0 && o->hartree != 1) fail(ctx, RTTDDFT_ERR_ARG, "hartree must be 0 or 1");
     if (o->hartree) {
         if (o->interstitial != RTTDDFT_INTERSTITIAL_FFT)
@@ -586,6 +607,7 @@ void rttddft_destroy(rttddft_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     tc_plan_destroy(ctx->tc);
+    tc_cc_destroy(ctx->tcc);
     fft_plan_destroy(ctx->fft);
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -755,6 +777,8 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
         CK(cudaMemset(ctx->d_tile_cnt, 0, sizeof(unsigned) * nk * ((std::max(at.ma, 1) + 7) / 8)));
         ctx->d_part_full = dalloc<double>(ctx, (size_t)nk * ctx->max_nback * 5);
         ctx->d_part_post = dalloc<double>(ctx, (size_t)nk * naux * POST_STRIDE);
+        ctx->d_part_fin = dalloc<double>(ctx, (size_t)nk * FIN_CH * FIN_STRIDE);
+        ctx->d_gdev = dalloc<double>(ctx, (size_t)nk * ns);
         CK(cudaMemset(ctx->d_part_jmt, 0, sizeof(double) * nk * std::max(at.lrows, 1) * 5));
         CK(cudaMemset(ctx->d_part_post, 0, sizeof(double) * nk * naux * POST_STRIDE));
         ctx->call_cap = 1024;
@@ -830,6 +854,22 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
                 goff2 += ng;
             }
             ctx->wmax = wm;
+            // the slot kernel stages the window next to a BT x 8 tile of the right operand;
+            // a window beyond shared memory (G sets whose 128-row tiles span several planes
+            // of the table) makes the direct sum gather the table through L1/L2 instead
+            int dev = 0, smax = 0;
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            const size_t need = (size_t)BT * 8 * sizeof(zd) + BT * sizeof(int) + (size_t)wm * sizeof(zd);
+            // RTTDDFT_TOEP_GATHER=1 in the environment takes the gather path at any size (tests)
+            const char* force = getenv("RTTDDFT_TOEP_GATHER");
+            if (need + 1024 > (size_t)smax || (force && force[0] == '1')) {
+                ctx->toep_global = 1;
+                ctx->wmax = 1;
+                for (int k = 0; k < nk; ++k)
+                    if (!ctx->hkd[k].th) ctx->hkd[k].th = dalloc<zd>(ctx, (size_t)ctx->hkd[k].ng * ns);
+                CK(cudaMemcpy(ctx->d_kd, ctx->hkd.data(), nk * sizeof(KDev), cudaMemcpyHostToDevice));
+            }
         }
         // ---- auxiliary basis
         std::vector<zd*> X(nk), L(nk), G1(nk), G2(nk), V1(nk), V2(nk), T1(nk), T2(nk), NEW(nk);
@@ -1024,6 +1064,12 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             KCHECK();
             CK(cudaStreamSynchronize(ctx->stream));
         }
+        if (!ctx->td_op) {
+            // the operator's interstitial source and destination per k: {C, th}
+            std::vector<ToepDesc> td(nk);
+            for (int k = 0; k < nk; ++k) td[k] = ToepDesc{ctx->hkd[k].C, ctx->hkd[k].th, ctx->hkd[k].nb, ctx->hkd[k].ng};
+            ctx->td_op = dupload(ctx, td.data(), td.size());
+        }
         CK(cudaMemcpy(ctx->d_kd, ctx->hkd.data(), nk * sizeof(KDev), cudaMemcpyHostToDevice));
         // ---- step descriptors
         const bool f32 = o->precision != RTTDDFT_PREC_FP64;
@@ -1035,12 +1081,40 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             ctx->kc_fwd = std::min(ctx->kc_fwd, 256);
             ctx->kc_proj = std::min(ctx->kc_proj, 256);
         }
+        // the FP32 64 x 64 tiled kernel (many states): split K only as far as
+        // about four blocks per SM need, in slices of a multiple of 16
+        auto zt_kc = [&](int M, int K) {
+            const int tiles = ((M + 63) / 64) * ((ns + 63) / 64) * nk;
+            const int splits = std::max(1, std::min((K + 255) / 256, (4 * 152 + tiles - 1) / tiles));
+            return splits == 1 ? 0 : ((K + splits - 1) / splits + 15) / 16 * 16;
+        };
+        if (f32 && ns >= ZT_MIN_N) {
+            const int kf = zt_kc(at.ma, ctx->maxng), kp = zt_kc(naux, ctx->maxnb);
+            ctx->kc_fwd = kf > 0 ? kf : ctx->maxng;
+            ctx->kc_proj = kp > 0 ? kp : ctx->maxnb;
+        }
+        if (o->precision >= RTTDDFT_PREC_BF16X3 && ns >= ZT_MIN_N && 2 * ns <= 128) {
+            // split forms, many states: C = CC theta and CC^H (S C) on the tensor cores;
+            // the projection's partials arrive as one slice per k-point
+            std::vector<const zd*> cp(nk);
+            std::vector<int> nbv(nk);
+            for (int k = 0; k < nk; ++k) {
+                cp[k] = ctx->hkd[k].caux;
+                nbv[k] = ctx->hkd[k].nb;
+            }
+            std::string why;
+            const int e = tc_cc_create(&ctx->tcc, nk, naux, ns, nbv.data(), cp.data(), ctx->d_flag, ctx->stream, &why);
+            if (e) fail(ctx, e, why);
+            ctx->kc_proj = ctx->maxnb;
+        }
         {
             // expand: rows are many, K = n_aux is short; split K only in FP64 where the
             // DFMA pipe of every SM is needed
             const int tiles = (ctx->maxnb + 63) / 64;
             ctx->kc_expand = 0;
-            if (f32) {
+            if (f32 && ns >= ZT_MIN_N) {
+                ctx->kc_expand = zt_kc(ctx->maxnb, naux);
+            } else if (f32) {
                 // FP32 streaming kernel: K slices of at most 256; split only while the
                 // row tiles alone leave most SMs idle (a split costs a reduction launch)
                 int splits = (naux + 255) / 256;
@@ -1137,6 +1211,39 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             ctx->d_jac_mats = dupload(ctx, jm.data(), nk);
             ctx->d_jac_vecs = dupload(ctx, jv.data(), nk);
             ctx->d_jac_vals = dupload(ctx, jw.data(), nk);
+        }
+        // ---- muffin-tin products as batched tiled GEMMs (FP32 forms, many states)
+        if (o->precision != RTTDDFT_PREC_FP64 && at.n > 0 && ns >= ZT_MIN_N) {
+            ctx->d_mtg = dalloc<zf>(ctx, 5 * ctx->nblk);
+            ctx->mtw_stride = 5 * ctx->maxm * ns;
+            ctx->d_mtw = dalloc<zd>(ctx, (size_t)nk * at.n * ctx->mtw_stride);
+            std::vector<GemmDesc> m1, m2;
+            for (int k = 0; k < nk; ++k) {
+                const KDev& K = ctx->hkd[k];
+                for (int al = 0; al < at.n; ++al) {
+                    const int m = at.m[al], na = at.na[al];
+                    zd* W = ctx->d_mtw + ((size_t)k * at.n + al) * ctx->mtw_stride;
+                    GemmDesc d{};
+                    d.A = ctx->d_mtg + 5 * at.boff[al];
+                    d.B = K.Q + at.aoff[al];
+                    d.C = W;
+                    d.M = 5 * m;
+                    d.K = na;
+                    d.lda = 5 * m;
+                    d.ldb = std::max(at.ma, 1);
+                    d.ldc = 5 * m;
+                    m1.push_back(d);
+                    d.A = ctx->d_mtg + 5 * at.boff[al] + (size_t)na * 5 * m;
+                    d.B = K.C + K.ng + at.looff[al];
+                    d.K = at.nlo[al];
+                    d.ldb = K.nb;
+                    m2.push_back(d);
+                    ctx->mt_maxna = std::max(ctx->mt_maxna, na);
+                    ctx->mt_maxlo = std::max(ctx->mt_maxlo, at.nlo[al]);
+                }
+            }
+            ctx->gd_mt1 = upload_descs(ctx, m1);
+            ctx->gd_mt2 = upload_descs(ctx, m2);
         }
         {
             StepArgs a = make_args(ctx, 0);
@@ -1682,10 +1789,23 @@ int rttddft_set_dv(rttddft_ctx* ctx, const double* dh, const double* dvtab) {
             ctx->gd_dvw = upload_descs(ctx, w);
             ctx->gd_dvg = upload_descs(ctx, g);
             ctx->gd_dvi = upload_descs(ctx, gi);
+            if (ctx->opt.precision != RTTDDFT_PREC_FP64 && at.n > 0) {
+                // reduced-precision forms: W = (s dh) L and L^H W on the FP32 tiled
+                // kernels, from FP32 copies of dh and of the local coordinates L
+                ctx->d_dh32 = dalloc<zf>(ctx, nblk);
+                std::vector<GemmDesc> w32 = w, g32 = g;
+                for (auto& d : w32) d.A = ctx->d_dh32 + ((const zd*)d.A - ctx->d_dh);
+                for (int k = 0; k < nk; ++k) {
+                    zf* l32 = dalloc<zf>(ctx, (size_t)at.lrows * naux);
+                    launch_convert_f32(ctx->hkd[k].lloc, l32, (size_t)at.lrows * naux, ctx->stream);
+                    g32[k].A = l32;
+                }
+                ctx->gd_dvw32 = upload_descs(ctx, w32);
+                ctx->gd_dvg32 = upload_descs(ctx, g32);
+            }
             ctx->td_dv = dupload(ctx, td.data(), td.size());
-            if (ctx->tc) {
-                // tensor-core forms: the interstitial convolution on tcgen05, its
-                // projection CC_G^H T from the FP32 copy of CC in K slices of 256
+            if (ctx->tc && !ctx->fft) {
+                // tensor-core forms: the interstitial convolution on tcgen05
                 std::vector<const zd*> cp(nk);
                 std::vector<int> nbv(nk), ngv(nk);
                 for (int k = 0; k < nk; ++k) {
@@ -1697,6 +1817,10 @@ int rttddft_set_dv(rttddft_ctx* ctx, const double* dh, const double* dvtab) {
                 const int e = tc_dv_prepare(ctx->tc, cp.data(), nbv.data(), ngv.data(), naux, ctx->nvt,
                                             ctx->stream, &why);
                 if (e) fail(ctx, e, why);
+            }
+            if (ctx->opt.precision != RTTDDFT_PREC_FP64) {
+                // reduced-precision forms: the projection CC_G^H T from the FP32 copy of CC
+                // in K slices of 256, FP64 sums of the slices
                 ctx->kc_dvi = 256;
                 size_t off = 0;
                 std::vector<GemmDesc> g32 = gi;
@@ -1711,8 +1835,13 @@ int rttddft_set_dv(rttddft_ctx* ctx, const double* dh, const double* dvtab) {
             CK(cudaMemcpy(ctx->d_kd, ctx->hkd.data(), nk * sizeof(KDev), cudaMemcpyHostToDevice));
         }
         if (at.n > 0) CK(cudaMemcpy(ctx->d_dh, dh, nblk * sizeof(zd), cudaMemcpyHostToDevice));
+        if (ctx->d_dh32) launch_convert_f32(ctx->d_dh, ctx->d_dh32, nblk, ctx->stream);
         CK(cudaMemcpy(ctx->d_dvtab, dvtab, ctx->nvt * sizeof(zd), cudaMemcpyHostToDevice));
-        if (ctx->tc) tc_dv_set_table(ctx->tc, ctx->d_dvtab, ctx->nvt, ctx->stream);
+        if (ctx->tc && !ctx->fft) {
+            double vmax = 0.0;
+            for (int i = 0; i < 2 * ctx->nvt; ++i) vmax = std::max(vmax, std::fabs(dvtab[i]));
+            tc_dv_set_table(ctx->tc, ctx->d_dvtab, ctx->nvt, vmax, ctx->stream);
+        }
         if (ctx->fft) {
             std::string why;
             const int e = fft_set_dv(ctx->fft, ctx->d_dvtab, ctx->vt_dim, naux, ctx->stream, &why);
@@ -1779,6 +1908,10 @@ int rttddft_apply(rttddft_ctx* ctx, int k, int ncols, const double* x, const dou
         a.kofs = k;
         StepPlan p = make_plan(ctx);
         p.gd_fwd = ctx->gd_fwd + k;
+        if (p.gd_mt1) {
+            p.gd_mt1 = ctx->gd_mt1 + (size_t)k * ctx->at.n;
+            p.gd_mt2 = ctx->gd_mt2 + (size_t)k * ctx->at.n;
+        }
         p.maxng = K.ng;
         if (dv_on && !ctx->opt.hartree) launch_vstep(a, ctx->stream);
         const zd* xz = (const zd*)x;
@@ -2132,6 +2265,9 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
             fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "rttddft_apply_noalloc has no Hartree potential (use rttddft_apply)");
         if (!is_device_ptr(x) || !is_device_ptr(hx) || !is_device_ptr(sx))
             fail(ctx, RTTDDFT_ERR_ARG, "rttddft_apply_noalloc takes device pointers for x, hx and sx");
+        if (ctx->toep_global)
+            fail(ctx, RTTDDFT_ERR_ARG, "rttddft_apply_noalloc: the table window of this G set does not fit in "
+                                       "shared memory (use rttddft_apply)");
         const KDev& K = ctx->hkd[k];
         const int ns = ctx->ns, nb = K.nb, ma = std::max(ctx->at.ma, 1), ng = K.ng;
         const int dv_on = (dv_scale != 0.0) ? 1 : 0;
@@ -2194,6 +2330,8 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         a.part_jmt = (double*)(base + o_jmt);
         a.part_full = (double*)(base + o_pf);
         a.part_t = (zd*)(base + o_pt);
+        a.mtg = nullptr;  // the muffin-tin GEMM buffers belong to the context: per-row kernel instead
+        a.mtw = nullptr;
         if (dv_on) {
             a.vstep = (zd*)(base + o_vs);
             a.vstep32 = f32 ? (zf*)(base + o_vs32) : nullptr;
@@ -2202,6 +2340,7 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         p.fft = nullptr;
         p.side = nullptr;
         p.tile_cnt = nullptr;  // the context's counters may be in use on another stream
+        p.gd_mt1 = p.gd_mt2 = nullptr;
         p.gd_fwd = (const GemmDesc*)(base + o_gd);
         p.maxng = ng;
         p.part = (zd*)(base + o_part);

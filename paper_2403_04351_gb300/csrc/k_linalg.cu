@@ -427,10 +427,119 @@ static void gemm_cn_t(const GemmDesc* d, int nb, int maxM, int maxK, int N, int 
     }
 }
 
+// ---------------------------------------------------------------- FP32 tiles for many columns
+// C[m, n] (+)= sum_k op(A)[m, k] B[k, n] with op(A) = A (CN = false, A is
+// M x K) or A^H (CN = true, A is K x M), A in FP32, B read as FP64 and
+// rounded to FP32 where it is staged.  A block owns a 64 x 64 tile of C and
+// walks its K slice in steps of 16: both operand tiles sit in shared memory
+// and every thread keeps 4 x 4 complex accumulators in registers (rows
+// tx + 16 i, columns ty + 16 j), so each staged value feeds four products.
+// The next step's operands are loaded into registers while the current
+// step's products run.  FP32 sums within a K slice, FP64 across slices.
+#define ZT_BM 64
+#define ZT_BN 64
+#define ZT_BK 16
+template <bool CN>
+__global__ void __launch_bounds__(256) k_zgemm_t32(const GemmDesc* __restrict__ descs, int N, int kchunk,
+                                                   zd* __restrict__ part, int beta_add,
+                                                   const double* __restrict__ dscale) {
+    __shared__ zf As[2][ZT_BK][ZT_BM];
+    __shared__ zf Bs[2][ZT_BK][ZT_BN];
+    const GemmDesc d = descs[blockIdx.z];
+    const int ntn = (N + ZT_BN - 1) / ZT_BN;
+    const int m0 = (blockIdx.x / ntn) * ZT_BM, n0 = (blockIdx.x % ntn) * ZT_BN;
+    const int k0 = blockIdx.y * kchunk;
+    if (m0 >= d.M || k0 >= d.K) return;
+    const int k1 = min(d.K, k0 + kchunk);
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const zf* __restrict__ A = (const zf*)d.A;
+    const zd* __restrict__ B = d.B;
+    zf ra[4], rb[4];
+    // staging loads of one K step (kb): four A and four B values per thread
+    auto fetch = [&](int kb) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (CN) {
+                // conj(A[k, m]): k = kb + (t & 15) (contiguous), m = m0 + (t >> 4) + 16 i
+                const int k = kb + tx, m = m0 + ty + 16 * i;
+                ra[i] = (k < k1 && m < d.M) ? A[(size_t)m * d.lda + k] : make_float2(0.f, 0.f);
+            } else {
+                // A[m, k]: m = m0 + (t & 63) (contiguous), k = kb + (t >> 6) + 4 i
+                const int m = m0 + (t & 63), k = kb + (t >> 6) + 4 * i;
+                ra[i] = (k < k1 && m < d.M) ? A[m + (size_t)k * d.lda] : make_float2(0.f, 0.f);
+            }
+            const int k = kb + tx, n = n0 + ty + 16 * i;
+            rb[i] = (k < k1 && n < N) ? tof(B[k + (size_t)n * d.ldb]) : make_float2(0.f, 0.f);
+        }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (CN) As[buf][tx][ty + 16 * i] = make_float2(ra[i].x, -ra[i].y);
+            else As[buf][(t >> 6) + 4 * i][t & 63] = ra[i];
+            Bs[buf][tx][ty + 16 * i] = rb[i];
+        }
+    };
+    zf acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    fetch(k0);
+    stash(0);
+    __syncthreads();
+    int buf = 0;
+    for (int kb = k0; kb < k1; kb += ZT_BK) {
+        const bool more = kb + ZT_BK < k1;
+        if (more) fetch(kb + ZT_BK);
+#pragma unroll
+        for (int kk = 0; kk < ZT_BK; ++kk) {
+            zf a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+        }
+        if (more) {
+            stash(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
+    }
+    const double sc = dscale ? *dscale : 1.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + tx + 16 * i;
+        if (m >= d.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + ty + 16 * j;
+            if (n >= N) continue;
+            const zd v = zscale(tod(acc[i][j]), sc);
+            if (part) {
+                part[d.part_off + ((size_t)blockIdx.y * N + n) * d.M + m] = v;
+            } else {
+                zd* c = d.C + m + (size_t)n * d.ldc;
+                *c = beta_add ? zadd(*c, v) : v;
+            }
+        }
+    }
+}
+
 // largest K slice of a block in the FP32 streaming kernels
 #define GEMM32_KC 256
 void launch_gemm_nn(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kchunk, zd* part,
                     int beta_add, bool a_fp32, const double* ds, cudaStream_t s) {
+    if (a_fp32 && N >= ZT_MIN_N && nb > 0 && maxM > 0 && maxK > 0) {
+        const int kc = kchunk > 0 ? kchunk : maxK;
+        dim3 grid(((maxM + ZT_BM - 1) / ZT_BM) * ((N + ZT_BN - 1) / ZT_BN), (maxK + kc - 1) / kc, nb);
+        k_zgemm_t32<false><<<grid, 256, 0, s>>>(d, N, kc, part, beta_add, ds);
+        return;
+    }
     if (a_fp32 && nb > 0 && maxM > 0 && maxK > 0 && N > 0 && (kchunk > 0 ? kchunk : maxK) <= GEMM32_KC) {
         const int kc = kchunk > 0 ? kchunk : maxK;
         dim3 grid((maxM + 63) / 64, (maxK + kc - 1) / kc, nb);
@@ -444,6 +553,12 @@ void launch_gemm_nn(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kc
 }
 bool launch_gemm_cn(const GemmDesc* d, int nb, int maxM, int maxK, int N, int kchunk, zd* part,
                     int beta_add, bool a_fp32, const double* ds, cudaStream_t s, unsigned* tile_cnt) {
+    if (a_fp32 && N >= ZT_MIN_N && nb > 0 && maxM > 0 && maxK > 0) {
+        const int kc = kchunk > 0 ? kchunk : maxK;
+        dim3 grid(((maxM + ZT_BM - 1) / ZT_BM) * ((N + ZT_BN - 1) / ZT_BN), (maxK + kc - 1) / kc, nb);
+        k_zgemm_t32<true><<<grid, 256, 0, s>>>(d, N, kc, part, beta_add, ds);
+        return false;
+    }
     if (a_fp32 && nb > 0 && maxM > 0 && maxK > 0 && N > 0 && (kchunk > 0 ? kchunk : maxK) <= GEMM32_KC) {
         const int kc = kchunk > 0 ? kchunk : maxK;
         unsigned* tc = part ? tile_cnt : nullptr;

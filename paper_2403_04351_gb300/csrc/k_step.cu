@@ -730,6 +730,99 @@ __global__ void __launch_bounds__(128) k_local_wide(StepArgs a, int rowchunks) {
     }
 }
 
+// Muffin-tin blocks as GEMMs (FP32 forms, many states).  Per atom the stack
+// G = [h_eff; o; p_x; p_y; p_z] (5m x m, column-major) with
+// h_eff = h + (A/c).p + |A|^2/(2c^2) o (+ s dh) is formed once per step (it
+// does not depend on k); then W = G [Q; C_lo] for every (k, atom) is two
+// batched tiled GEMMs (the Q rows and the local-orbital rows of the
+// right-hand block live in different arrays), and k_mt_epi distributes W:
+// the h_eff and o rows go to Z (matching rows) or to the LO rows of
+// [HC | SC], and the row's occupation-weighted shares of J (p rows) and of
+// E and c^H S c (LO rows) go to part_jmt as in k_local.
+__global__ void k_mt_form(StepArgs a) {
+    const AtomTab& at = *a.at;
+    const int al = blockIdx.y;
+    if (al >= at.n) return;
+    const int m = at.m[al];
+    const size_t mm = (size_t)m * m, bo = at.boff[al];
+    const DevState* st = a.st;
+    const float fx = (float)(st->cur_a[0] * a.inv_c), fy = (float)(st->cur_a[1] * a.inv_c),
+                fz = (float)(st->cur_a[2] * a.inv_c), fa = (float)st->cur_aa;
+    const double sdv = st->cur_s;
+    zf* G = a.mtg + 5 * bo;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < mm; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % m), j = (int)(e / m);  // element (i, j), column-major
+        const zf hv = a.h32[bo + e], ov = a.o32[bo + e];
+        const zf px = a.p32[3 * bo + e], py = a.p32[3 * bo + mm + e], pz = a.p32[3 * bo + 2 * mm + e];
+        zf he;
+        he.x = hv.x + fx * px.x + fy * py.x + fz * pz.x + fa * ov.x;
+        he.y = hv.y + fx * px.y + fy * py.y + fz * pz.y + fa * ov.y;
+        if (a.dh && sdv != 0.0) {
+            const zd d = a.dh[bo + e];
+            he.x += (float)(sdv * d.x);
+            he.y += (float)(sdv * d.y);
+        }
+        zf* col = G + (size_t)j * 5 * m;
+        col[i] = he;
+        col[m + i] = ov;
+        col[2 * m + i] = px;
+        col[3 * m + i] = py;
+        col[4 * m + i] = pz;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_mt_epi(StepArgs a) {
+    const int k = blockIdx.z, al = blockIdx.y;
+    const AtomTab& at = *a.at;
+    if (al >= at.n) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = at.m[al], na = at.na[al];
+    if (i >= m) return;
+    const KDev& K = a.kd[k];
+    const int ns = a.ns, nb = K.nb, ma = at.ma, ng = K.ng;
+    const int aoff = at.aoff[al], lo0 = ng + at.looff[al];
+    const zd* W = a.mtw + ((size_t)(a.kofs + k) * at.n + al) * a.mtw_stride;  // kofs: single-k operator calls
+    const size_t ld = (size_t)5 * m;
+    double jc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int c = 0; c < ns; ++c) {
+        const zd* w = W + (size_t)c * ld;
+        const zd zh = w[i], zs = w[m + i];
+        const zd x = (i < na) ? K.Q[aoff + i + (size_t)c * ma] : K.C[lo0 + (i - na) + (size_t)c * nb];
+        const double f = a.occ[c];
+        if (i < na) {
+            K.Z[aoff + i + (size_t)c * ma] = zh;
+            K.Z[aoff + i + (size_t)(ns + c) * ma] = zs;
+        } else {
+            const int r = lo0 + (i - na);
+            K.Y[r + (size_t)c * nb] = zh;
+            K.Y[r + (size_t)(ns + c) * nb] = zs;
+            jc[3] += f * (x.x * zh.x + x.y * zh.y);
+            jc[4] += f * (x.x * zs.x + x.y * zs.y);
+        }
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            const zd pv = w[(2 + l) * m + i];
+            jc[l] += f * (x.x * pv.x + x.y * pv.y);
+        }
+    }
+    double* pj = a.part_jmt + ((size_t)k * at.lrows + at.loff[al] + i) * 5;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) pj[q] = jc[q];
+}
+
+static int launch_mt_gemm(const StepArgs& a, const StepPlan& p, cudaStream_t s) {
+    k_mt_form<<<dim3(64, a.at_n), 256, 0, s>>>(a);
+    const int n = a.nk * a.at_n;
+    launch_gemm_nn(p.gd_mt1, n, 5 * a.at_maxm, p.mt_maxna, a.ns, 0, nullptr, 0, true, nullptr, s);
+    int nl = 2;
+    if (p.mt_maxlo > 0) {
+        launch_gemm_nn(p.gd_mt2, n, 5 * a.at_maxm, p.mt_maxlo, a.ns, 0, nullptr, 1, true, nullptr, s);
+        ++nl;
+    }
+    k_mt_epi<<<dim3((a.at_maxm + 127) / 128, a.at_n, a.nk), 128, 0, s>>>(a);
+    return nl + 1;
+}
+
 // Plane-wave rows of H C and S C in independent partial sums, one block per
 // (row tile of BT rows G, slot):
 //  - slots 0 .. nseg-1: the interstitial sum of Eq. v_interstitial over one
@@ -844,7 +937,9 @@ __global__ void __launch_bounds__(BT) k_toep_seg(StepArgs a, int n0, int slot0) 
 // summed in a fixed slot order.  The block adds its rows' f-weighted shares of
 // Re c^H HC, Re c^H SC and sum (G+k)|c|^2 into its slot of part_full.
 template <int NT>
-__global__ void __launch_bounds__(BKB) k_back(StepArgs a, int n0) {
+// Columns n0 .. n1-1: at most NT when the slot partials are read; all
+// columns in one launch when both parts arrive whole (K.th and K.tb).
+__global__ void __launch_bounds__(BKB) k_back(StepArgs a, int n0, int n1) {
     __shared__ double rs[8];
     const int k = blockIdx.z;
     const KDev& K = a.kd[k];
@@ -855,7 +950,6 @@ __global__ void __launch_bounds__(BKB) k_back(StepArgs a, int n0) {
     const int g = g0 + tid;
     const bool act = g < ng;
     const int ns = a.ns, nb = K.nb;
-    const int nc = min(NT, ns - n0);
     const zd* __restrict__ X = K.C;
     double red[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (act) {
@@ -865,11 +959,11 @@ __global__ void __launch_bounds__(BKB) k_back(StepArgs a, int n0) {
         const double* q = K.gk + 3 * (size_t)g;
         const double dg = 0.5 * (dsq(q[0] + st->cur_a[0] * a.inv_c) + dsq(q[1] + st->cur_a[1] * a.inv_c) +
                                  dsq(q[2] + st->cur_a[2] * a.inv_c));
-        for (int c = 0; c < NT; ++c) {
-            if (c >= nc) break;
+        for (int cc = n0; cc < n1; ++cc) {
+            const int c = cc - n0;  // column within the slot partials
             zd th = zmk(0.0, 0.0), ts = zmk(0.0, 0.0);
             // slot partials, loads issued four slots at a time (in slot order)
-            const zd* pt = a.part_t + (((size_t)k * a.nslot) * 2 * NT + c) * a.maxng + g;
+            const zd* pt = a.part_t + (((size_t)k * a.nslot) * 2 * NT + (c < NT ? c : 0)) * a.maxng + g;
             const size_t sst = (size_t)2 * NT * a.maxng;
             auto sum4 = [&](int s0, int s1, size_t off) {
                 zd t = zmk(0.0, 0.0);
@@ -1032,6 +1126,102 @@ __device__ void post_body(const StepArgs& a, int do_theta, int do_j) {
     }
 }
 
+// The subspace current for many states through the occupation-weighted
+// density matrix rho = theta F theta^H (F = diag(f)):
+//   J_l = -(1/Omega) sum_k w_k [ Re tr(PP_l rho) + (A_l/c) tr(rho) ],
+// the same quantity as sum_n f_n Re theta_n^H (PP_l + A_l/c) theta_n, at
+// N_aux^2 (N_s / 2 + 3) complex products instead of 3 N_aux^2 N_s.  One block
+// per pair of 32-row tiles (I <= J) of rho; rho is Hermitian and so is PP_l,
+// so an off-diagonal pair counts twice (its mirror gives the conjugate).
+// The block's three shares go to the J slots of row `pair` of part_post (the
+// consumers sum those slots over rows); rows past the last pair get zeros.
+#define JRHO_T 32
+#define JRHO_CH 32
+__global__ void __launch_bounds__(256) k_jrho(StepArgs a) {
+    __shared__ zd sI[JRHO_CH][JRHO_T], sJ[JRHO_CH][JRHO_T];
+    __shared__ double red[8][4];
+    const int k = blockIdx.z;
+    const KDev& K = a.kd[k];
+    const int n = a.naux, ns = a.ns;
+    const int nt = (n + JRHO_T - 1) / JRHO_T;
+    const int npairs = nt * (nt + 1) / 2;
+    const int pair = blockIdx.x;
+    // pair -> (I, J), I <= J, row-major over the upper triangle
+    int I = 0, rem = pair;
+    while (rem >= nt - I) {
+        rem -= nt - I;
+        ++I;
+    }
+    const int J = I + rem;
+    const int tid = threadIdx.x, i = tid & 31, jq = tid >> 5;
+    const int gi = I * JRHO_T + i;
+    zd acc[4] = {zmk(0.0, 0.0), zmk(0.0, 0.0), zmk(0.0, 0.0), zmk(0.0, 0.0)};
+    for (int c0 = 0; c0 < ns; c0 += JRHO_CH) {
+        __syncthreads();
+        for (int e = tid; e < JRHO_CH * JRHO_T; e += 256) {
+            const int cc = e >> 5, r = e & 31, c = c0 + cc;
+            const int ri = I * JRHO_T + r, rj = J * JRHO_T + r;
+            zd vi = zmk(0.0, 0.0), vj = zmk(0.0, 0.0);
+            if (c < ns) {
+                if (ri < n) vi = K.theta[ri + (size_t)c * n];
+                if (rj < n) vj = zscale(K.theta[rj + (size_t)c * n], a.occ[c]);
+            }
+            sI[cc][r] = vi;
+            sJ[cc][r] = vj;
+        }
+        __syncthreads();
+        const int cn = min(JRHO_CH, ns - c0);
+        for (int cc = 0; cc < cn; ++cc) {
+            const zd ti = sI[cc][i];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) zfmac(acc[q], ti, sJ[cc][jq + 8 * q]);  // rho[gj, gi] += f theta_gj conj(theta_gi)
+        }
+    }
+    // shares of Re tr(PP_l rho) and of (A_l/c) tr(rho)
+    double sh[3] = {0.0, 0.0, 0.0};
+    const double wgt = (I == J) ? 1.0 : 2.0;
+    if (gi < n) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int gj = J * JRHO_T + jq + 8 * q;
+            if (gj >= n) continue;
+            for (int l = 0; l < 3; ++l) {
+                const zd pp = K.psub[(size_t)l * n * n + gi + (size_t)gj * n];  // PP_l[gi, gj]
+                double v = wgt * (pp.x * acc[q].x - pp.y * acc[q].y);
+                if (gi == gj) v += a.st->cur_a[l] * a.inv_c * acc[q].x;
+                sh[l] += v;
+            }
+        }
+    }
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int l = 0; l < 3; ++l) {
+        const double v = warp_sum(sh[l]);
+        if (lane == 0) red[warp][l] = v;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w][tid];
+        a.part_post[((size_t)k * n + pair) * POST_STRIDE + 1 + tid] = t;
+        for (int r = pair + npairs; r < n; r += npairs) a.part_post[((size_t)k * n + r) * POST_STRIDE + 1 + tid] = 0.0;
+    }
+}
+
+// The post-projection launch(es): theta~ and its residual per row (do_theta),
+// and the subspace current (do_j), by rows for few states and through the
+// density matrix for many.
+void launch_post(const StepArgs& a, int do_theta, int do_j, cudaStream_t s) {
+    const bool rho = do_j && a.ns > JRHO_MIN_NS;
+    if (do_theta || !rho) {
+        dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
+        k_post<<<g, 128, 0, s>>>(a, do_theta, rho ? 0 : do_j);
+    }
+    if (rho) {
+        const int nt = (a.naux + JRHO_T - 1) / JRHO_T;
+        k_jrho<<<dim3(nt * (nt + 1) / 2, 1, a.nk), 256, 0, s>>>(a);
+    }
+}
+
 // theta <- theta~ (3 I - theta~^H theta~) / 2: one Newton-Schulz step of the
 // polar (Lowdin) factor, exact to O(|theta~^H theta~ - I|^2)
 __global__ void k_reproj(StepArgs a) {
@@ -1053,6 +1243,140 @@ __global__ void k_reproj(StepArgs a) {
 // Sum the step's partials over k-points (weights w_k) in a fixed order,
 // update the dipole by the trapezoid rule (Eq. dipole) and append the
 // record.  One block.
+// First phase of the step's reductions: per (row chunk, k-point) block, the
+// k-weighted sums of the per-row partials of the step (J_sub, E, c^H S c,
+// sum (G+k)|c|^2, J_mt, the occupied ground-state share) and the maxima of
+// the residual and of |C^H S C - I|, into part_fin[k][chunk].  The single
+// block of k_finalize then sums these in (k, chunk) order.
+// 0-2 J_sub, 3 E, 4 c^H S c, 5-7 sum (G+k)|c|^2, 8-10 J_mt, 11 occupied share, 12 max residual, 13 max dev
+__global__ void __launch_bounds__(256) k_fin_part(StepArgs a, int set_gs) {
+    __shared__ double sh[8][16];
+    __shared__ unsigned long long shm[8][2];
+    const int k = blockIdx.y, ch = blockIdx.x;
+    const KDev& K = a.kd[k];
+    const double w = a.wk[k];
+    const int ns = a.ns, n = a.naux, lrows = a.lrows;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int nback = set_gs ? 0 : (K.ng + BKB - 1) / BKB;
+    const int lr = set_gs ? 0 : lrows;
+    const int cnt = max(n, max(nback, lr));
+    double v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = 0.0;
+    double mres = 0.0, mdev = 0.0;
+    for (int i = ch * blockDim.x + tid; i < cnt; i += FIN_CH * blockDim.x) {
+        double pp[4] = {0.0, 0.0, 0.0, 0.0}, pf[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, pj[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        if (i < n) {
+            const double* p = a.part_post + ((size_t)k * n + i) * POST_STRIDE;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pp[q] = __ldcg(p + q);
+        }
+        if (i < nback) {
+            const double* p = a.part_full + ((size_t)k * a.max_nback + i) * 5;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) pf[q] = p[q];
+        }
+        if (i < lr) {
+            const double* p = a.part_jmt + ((size_t)k * lrows + i) * 5;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) pj[q] = p[q];
+        }
+        mres = fmax(mres, pp[0]);
+        v[0] += w * pp[1];
+        v[1] += w * pp[2];
+        v[2] += w * pp[3];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) v[3 + q] += w * pf[q];
+        v[8] += w * pj[0];
+        v[9] += w * pj[1];
+        v[10] += w * pj[2];
+        v[3] += w * pj[3];
+        v[4] += w * pj[4];
+    }
+    if (!set_gs) {
+        for (int e = ch * blockDim.x + tid; e < ns * ns; e += FIN_CH * blockDim.x) {
+            const int i = e % ns, j = e / ns;
+            const zd t = K.theta[i + (size_t)j * n];
+            v[11] += w * a.occ[j] * (t.x * t.x + t.y * t.y);
+        }
+        if (ns <= 4) {
+            // the rows' shares of theta^H theta~ in a fixed order (one warp per entry)
+            __shared__ double gs[8][2];
+            for (int e = ch * nw + warp; e < ns * ns; e += FIN_CH * nw) {
+                double g[2] = {0.0, 0.0};
+                for (int i = lane; i < n; i += 32) {
+                    const double* p = a.part_post + ((size_t)k * n + i) * POST_STRIDE + 4 + 2 * e;
+                    g[0] += __ldcg(p);
+                    g[1] += __ldcg(p + 1);
+                }
+                warp_sum_store<double, 2>(g, lane, gs[warp]);
+                __syncwarp();
+                double gx = gs[warp][0];
+                const double gy = gs[warp][1];
+                if (e % ns == e / ns) gx -= 1.0;
+                mdev = fmax(mdev, hypot(gx, gy));
+                __syncwarp();
+            }
+        } else {
+            for (int j = ch * blockDim.x + tid; j < ns; j += FIN_CH * blockDim.x)
+                mdev = fmax(mdev, a.gdev[(size_t)k * ns + j]);
+        }
+    }
+    warp_sum_store<double, 16>(v, lane, sh[warp]);
+    unsigned long long br = (unsigned long long)__double_as_longlong(mres);
+    unsigned long long bd = (unsigned long long)__double_as_longlong(mdev);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long xr = __shfl_xor_sync(0xffffffffu, br, o);
+        const unsigned long long xd = __shfl_xor_sync(0xffffffffu, bd, o);
+        br = xr > br ? xr : br;
+        bd = xd > bd ? xd : bd;
+    }
+    if (lane == 0) {
+        shm[warp][0] = br;
+        shm[warp][1] = bd;
+    }
+    __syncthreads();
+    double* out = a.part_fin + ((size_t)k * FIN_CH + ch) * FIN_STRIDE;
+    if (tid < 12) {
+        double t = sh[0][tid];
+        for (int ww = 1; ww < nw; ++ww) t += sh[ww][tid];
+        out[tid] = t;
+    } else if (tid < 14) {
+        unsigned long long m = shm[0][tid - 12];
+        for (int ww = 1; ww < nw; ++ww) m = shm[ww][tid - 12] > m ? shm[ww][tid - 12] : m;
+        out[tid] = __longlong_as_double((long long)m);
+    }
+}
+
+// |C^H S C - I| for many states: column j of the gram theta^H theta~ per block
+// (one warp per row i, lanes over the subspace rows), its largest deviation
+// from the identity into gdev[k][j] (FP64).
+__global__ void __launch_bounds__(256) k_gram_dev(StepArgs a) {
+    __shared__ double wm[8];
+    const int k = blockIdx.y, j = blockIdx.x;
+    const KDev& K = a.kd[k];
+    const int n = a.naux, ns = a.ns;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const zd* tt = K.theta_t + (size_t)j * n;
+    double dev = 0.0;
+    for (int i = warp; i < ns; i += 8) {
+        const zd* th = K.theta + (size_t)i * n;
+        zd g = zmk(0.0, 0.0);
+        for (int r = lane; r < n; r += 32) zfmac(g, th[r], tt[r]);
+        g = warp_zsum(g);
+        if (i == j) g.x -= 1.0;
+        dev = fmax(dev, hypot(g.x, g.y));
+    }
+    if (lane == 0) wm[warp] = dev;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = wm[0];
+        for (int w = 1; w < 8; ++w) m = fmax(m, wm[w]);
+        a.gdev[(size_t)k * ns + j] = m;
+    }
+}
+
 __device__ void finalize_body(const StepArgs& a, int set_gs) {
     // the k-weights enter the per-row shares, so one block reduction covers all
     // k-points; sums by halving warp sums (each warp-wide FP64 add is costly on
@@ -1095,79 +1419,20 @@ __device__ void finalize_body(const StepArgs& a, int set_gs) {
             }
         }
     }
-    // 0-2 J_sub, 3 E, 4 c^H S c, 5-7 sum (G+k)|c|^2, 8-10 J_mt, 11 the occupied
-    // ground-state share sum_j f_j sum_{i < N_s} |theta_ij|^2; all times w_k
+    // the per-(k, chunk) partials of k_fin_part, summed in (k, chunk) order
     double v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = 0.0;
     double mres = 0.0, mdev = 0.0;
-    for (int k = 0; k < a.nk; ++k) {
-        const KDev& K = a.kd[k];
-        const double w = a.wk[k];
-        const int nback = set_gs ? 0 : (K.ng + BKB - 1) / BKB;
-        const int lr = set_gs ? 0 : lrows;
-        const int cnt = max(n, max(nback, lr));
-        for (int i0 = 0; i0 < cnt; i0 += blockDim.x) {
-            const int i = i0 + tid;
-            double pp[4] = {0.0, 0.0, 0.0, 0.0}, pf[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, pj[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-            if (i < n) {
-                const double* p = a.part_post + ((size_t)k * n + i) * POST_STRIDE;
+    for (int e = tid; e < a.nk * FIN_CH; e += blockDim.x) {
+        const double* p = a.part_fin + (size_t)e * FIN_STRIDE;
+        double t[14];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) pp[q] = __ldcg(p + q);
-            }
-            if (i < nback) {
-                const double* p = a.part_full + ((size_t)k * a.max_nback + i) * 5;
+        for (int q = 0; q < 14; ++q) t[q] = __ldcg(p + q);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) pf[q] = p[q];
-            }
-            if (i < lr) {
-                const double* p = a.part_jmt + ((size_t)k * lrows + i) * 5;
-#pragma unroll
-                for (int q = 0; q < 5; ++q) pj[q] = p[q];
-            }
-            mres = fmax(mres, pp[0]);
-            v[0] += w * pp[1];
-            v[1] += w * pp[2];
-            v[2] += w * pp[3];
-#pragma unroll
-            for (int q = 0; q < 5; ++q) v[3 + q] += w * pf[q];
-            v[8] += w * pj[0];
-            v[9] += w * pj[1];
-            v[10] += w * pj[2];
-            v[3] += w * pj[3];
-            v[4] += w * pj[4];
-        }
-        if (set_gs) continue;
-        for (int e = tid; e < ns * ns; e += blockDim.x) {
-            const int i = e % ns, j = e / ns;
-            const zd t = K.theta[i + (size_t)j * n];
-            v[11] += w * a.occ[j] * (t.x * t.x + t.y * t.y);
-        }
-        if (ns <= 4) {
-            // the rows' shares of theta^H theta~ in a fixed order (one warp per entry)
-            for (int e = warp; e < ns * ns; e += nw) {
-                double g[2] = {0.0, 0.0};
-                for (int i = lane; i < n; i += 32) {
-                    const double* p = a.part_post + ((size_t)k * n + i) * POST_STRIDE + 4 + 2 * e;
-                    g[0] += __ldcg(p);
-                    g[1] += __ldcg(p + 1);
-                }
-                __shared__ double gs[8][2];
-                warp_sum_store<double, 2>(g, lane, gs[warp]);
-                __syncwarp();
-                double gx = gs[warp][0];
-                const double gy = gs[warp][1];
-                if (e % ns == e / ns) gx -= 1.0;
-                mdev = fmax(mdev, hypot(gx, gy));
-                __syncwarp();
-            }
-        } else {
-            for (int e = tid; e < ns * ns; e += blockDim.x) {
-                zd g = K.gram[e];
-                if (e % ns == e / ns) g.x -= 1.0;
-                mdev = fmax(mdev, hypot(g.x, g.y));
-            }
-        }
+        for (int q = 0; q < 12; ++q) v[q] += t[q];
+        mres = fmax(mres, t[12]);
+        mdev = fmax(mdev, t[13]);
     }
     warp_sum_store<double, 16>(v, lane, sh[warp]);
     unsigned long long br = (unsigned long long)__double_as_longlong(mres);
@@ -1234,6 +1499,12 @@ __device__ void finalize_body(const StepArgs& a, int set_gs) {
 }
 
 __global__ void __launch_bounds__(256) k_finalize(StepArgs a, int set_gs) { finalize_body(a, set_gs); }
+
+void launch_finalize(const StepArgs& a, int set_gs, cudaStream_t s) {
+    k_fin_part<<<dim3(FIN_CH, a.nk), 256, 0, s>>>(a, set_gs);
+    k_finalize<<<1, 256, 0, s>>>(a, set_gs);
+}
+
 
 // ------------------------------------------------------------ Jacobi eigensolver
 // Cyclic two-sided Jacobi for a complex Hermitian matrix (one block per
@@ -1579,9 +1850,8 @@ void launch_prep_coef(const StepArgs& a, cudaStream_t s) {
 }
 
 void launch_subspace_current(const StepArgs& a, int set_gs, cudaStream_t s) {
-    dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
-    k_post<<<g, 128, 0, s>>>(a, 0, 1);
-    k_finalize<<<1, 256, 0, s>>>(a, set_gs);
+    launch_post(a, 0, 1, s);
+    launch_finalize(a, set_gs, s);
 }
 
 static inline void mark(TraceHook* tr, const char* name, cudaStream_t s) {
@@ -1608,14 +1878,19 @@ static int back_launch(const StepArgs& a, int maxng, cudaStream_t s, TraceHook* 
     dim3 gt((maxng + BT - 1) / BT, a.tcback ? 0 : a.nslot - slot0, a.nk);
     dim3 gb((maxng + BKB - 1) / BKB, 1, a.nk);
     int nl = 0;
+    if (gt.y == 0) {
+        // both parts arrive whole (K.th and K.tb): every column in one launch
+        if (join) cudaStreamWaitEvent(s, join, 0);
+        k_back<NT><<<gb, BKB, 0, s>>>(a, 0, a.ns);
+        mark(tr, "back_finish", s);
+        return 1;
+    }
     for (int n0 = 0; n0 < a.ns; n0 += NT) {
-        if (gt.y > 0) {
-            ++nl;
-            k_toep_seg<TA, TT, TC, NT><<<gt, BT, sm, s>>>(a, n0, slot0);
-            mark(tr, slot0 ? "backprojection" : "toeplitz_and_backprojection", s);
-        }
+        ++nl;
+        k_toep_seg<TA, TT, TC, NT><<<gt, BT, sm, s>>>(a, n0, slot0);
+        mark(tr, slot0 ? "backprojection" : "toeplitz_and_backprojection", s);
         if (join && n0 == 0) cudaStreamWaitEvent(s, join, 0);  // the interstitial rows of the side stream
-        k_back<NT><<<gb, BKB, 0, s>>>(a, n0);
+        k_back<NT><<<gb, BKB, 0, s>>>(a, n0, std::min(n0 + NT, a.ns));
         mark(tr, "back_finish", s);
         ++nl;
     }
@@ -1663,31 +1938,40 @@ int launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, T
     const bool f32 = a.prec >= 1;
     int nl = 0;
     // trace mode keeps one stream so that its events time every launch in turn
-    const bool fork = p.fft && p.side && a.prec < 2 && !tr;
+    const bool fork = p.fft && p.side && !tr;
     const cudaEvent_t join = fork ? p.ev_join : nullptr;
+    if (p.fft) {
+        // V~ * C_G by FFT (th), the current table V~ + s dV~ when the change is on.
+        // It needs only C, so it runs on the side stream beside the matching
+        // rows, the muffin-tin blocks and the back-projection, and k_back waits for it.
+        cudaStream_t fs = s;
+        if (fork) {
+            cudaEventRecord(p.ev_fork, s);
+            cudaStreamWaitEvent(p.side, p.ev_fork, 0);
+            fs = p.side;
+        }
+        nl += launch_fft_conv(p.fft, p.td_op, a.kofs, a.nk, a.ns, 0, a.dv_on, &a.st->cur_s, fs);
+        if (fork) cudaEventRecord(p.ev_join, p.side);
+        mark(tr, "fft_interstitial", fs);
+    }
     if (a.prec >= 2) {
-        // tensor cores: V~ * C_G and Q = A C_G in one split-BF16 launch
+        // tensor cores: V~ * C_G (unless the FFT route gives it) and Q = A C_G in
+        // split-BF16 launches
         launch_tc_pack(p.tc, a, s);
         mark(tr, "tc_pack_c", s);
-        nl += launch_tc_operator(p.tc, a, s);
-        mark(tr, "tc_interstitial_and_forward", s);
-        launch_tc_reduce(p.tc, a, s);
+        nl += launch_tc_operator(p.tc, a, s, p.fft != nullptr);
+        mark(tr, p.fft ? "tc_forward" : "tc_interstitial_and_forward", s);
+        launch_tc_reduce(p.tc, a, s, p.fft != nullptr);
         mark(tr, "tc_reduce", s);
         nl += 2;
     } else {
-        if (p.fft) {
-            // V~ * C_G by FFT (th), the current table V~ + s dV~ when the change is on.
-            // It needs only C, so it runs on the side stream beside the matching
-            // rows, the muffin-tin blocks and the back-projection, and k_back waits for it.
-            cudaStream_t fs = s;
-            if (fork) {
-                cudaEventRecord(p.ev_fork, s);
-                cudaStreamWaitEvent(p.side, p.ev_fork, 0);
-                fs = p.side;
-            }
-            nl += launch_fft_conv(p.fft, p.td_op, a.kofs, a.nk, a.ns, 0, a.dv_on, &a.st->cur_s, fs);
-            if (fork) cudaEventRecord(p.ev_join, p.side);
-            mark(tr, "fft_interstitial", fs);
+        if (a.toep_global && !p.fft) {
+            // a table window too large for shared memory: V~ * C_G (V~ + s dV~ when the
+            // change is on) with the table gathered through L1/L2, FP64, into K.th
+            launch_toeplitz(a.kd, p.td_op + a.kofs, a.nk, p.maxng, a.ns, a.dv_on ? a.vstep : a.vtab, a.vt_center, 0,
+                            0, nullptr, s);
+            mark(tr, "toeplitz_global", s);
+            ++nl;
         }
         if (a.ma > 0) {
             // Q = A C_G = (A^H)^H C_G: one warp per matching row; split-K in FP64
@@ -1702,7 +1986,10 @@ int launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, T
             }
         }
     }
-    if (a.lrows > 0) {
+    if (a.lrows > 0 && f32 && p.gd_mt1 && a.mtg) {
+        nl += launch_mt_gemm(a, p, s);
+        mark(tr, "local_mt", s);
+    } else if (a.lrows > 0) {
         ++nl;
         dim3 g(a.lrows, 1, a.nk);
         if (f32 && a.ns > LOCW_MIN_NS) {
@@ -1761,11 +2048,14 @@ static int launch_dv_rebuild(const StepArgs& a, const StepPlan& p, cudaStream_t 
         mark(tr, "hartree_project", s);
         return 0;  // counted by the caller with the FFT launches
     }
-    launch_gemm_nn(p.gd_dvw, p.n_dvw, p.maxm, p.maxm, a.naux, 0, nullptr, 0, false, &a.st->cur_s, s);
+    // the muffin-tin four blocks: FP32 in the reduced-precision forms, FP64 otherwise
+    const bool mt32 = a.prec >= 1 && p.gd_dvw32 && p.gd_dvg32;
+    launch_gemm_nn(mt32 ? p.gd_dvw32 : p.gd_dvw, p.n_dvw, p.maxm, p.maxm, a.naux, 0, nullptr, 0, mt32,
+                   &a.st->cur_s, s);
     mark(tr, "dv_mt_blocks", s);
-    launch_gemm_cn(p.gd_dvg, a.nk, a.naux, a.lrows, a.naux, 0, nullptr, 0, false, nullptr, s);
+    launch_gemm_cn(mt32 ? p.gd_dvg32 : p.gd_dvg, a.nk, a.naux, a.lrows, a.naux, 0, nullptr, 0, mt32, nullptr, s);
     mark(tr, "dv_mt_project", s);
-    if (a.prec >= 2 && p.tc && tc_dv_ready(p.tc) && p.gd_dvi32) {
+    if (a.prec >= 2 && p.tc && !p.fft && tc_dv_ready(p.tc) && p.gd_dvi32) {
         launch_tc_dv_toeplitz(p.tc, a, p.td_dv, s);
         mark(tr, "tc_dv_interstitial", s);
         launch_gemm_cn(p.gd_dvi32, a.nk, a.naux, p.maxng, a.naux, p.kc_dvi, p.part_dv, 0, true, nullptr, s);
@@ -1783,7 +2073,14 @@ static int launch_dv_rebuild(const StepArgs& a, const StepPlan& p, cudaStream_t 
         mark(tr, "dv_interstitial_toeplitz", s);
         ++nl;
     }
-    launch_gemm_cn(p.gd_dvi, a.nk, a.naux, p.maxng, a.naux, 0, nullptr, 1, false, nullptr, s);
+    if (a.prec >= 1 && p.gd_dvi32) {
+        // reduced-precision forms: CC_G^H T from the FP32 copy of CC, FP64 sums of the K slices
+        launch_gemm_cn(p.gd_dvi32, a.nk, a.naux, p.maxng, a.naux, p.kc_dvi, p.part_dv, 0, true, nullptr, s);
+        launch_split_reduce(p.gd_dvi32, a.nk, a.naux, a.naux, p.kc_dvi, p.part_dv, 1, s);
+        ++nl;
+    } else {
+        launch_gemm_cn(p.gd_dvi, a.nk, a.naux, p.maxng, a.naux, 0, nullptr, 1, false, nullptr, s);
+    }
     mark(tr, "dv_interstitial_project", s);
     return nl;
 }
@@ -1835,26 +2132,30 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
         }
     }
     // C = CC theta (Eq. approximation_coefficients)
-    launch_gemm_nn(p.gd_expand, a.nk, p.maxnb, a.naux, a.ns, p.kc_expand, p.kc_expand > 0 ? p.part : nullptr,
-                   0, f32, nullptr, s);
-    mark(tr, "gemm_expand", s);
-    ++nl;
-    if (p.kc_expand > 0) {
+    if (p.tcc) {
+        nl += launch_tcc_expand(p.tcc, a, s);
+        mark(tr, "gemm_expand", s);
+    } else {
+        launch_gemm_nn(p.gd_expand, a.nk, p.maxnb, a.naux, a.ns, p.kc_expand, p.kc_expand > 0 ? p.part : nullptr,
+                       0, f32, nullptr, s);
+        mark(tr, "gemm_expand", s);
+        ++nl;
+    }
+    if (!p.tcc && p.kc_expand > 0) {
         launch_split_reduce(p.gd_expand, a.nk, p.maxnb, a.ns, p.kc_expand, p.part, 0, s);
         mark(tr, "split_reduce_expand", s);
         ++nl;
     }
     nl += launch_operator_pass(a, p, s, tr);
     // theta~ = CC^H (S C): split-K partials, finished per row in k_post
-    launch_gemm_cn(p.gd_proj, a.nk, a.naux, p.maxnb, a.ns, p.kc_proj, p.part, 0, f32, nullptr, s);
+    if (p.tcc) nl += launch_tcc_project(p.tcc, a, p.part, s) - 1;
+    else launch_gemm_cn(p.gd_proj, a.nk, a.naux, p.maxnb, a.ns, p.kc_proj, p.part, 0, f32, nullptr, s);
     mark(tr, "gemm_project", s);
-    {
-        dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
-        k_post<<<g, 128, 0, s>>>(a, 1, a.reproject ? 0 : 1);
-        mark(tr, "project_finish_current", s);
-    }
+    launch_post(a, 1, a.reproject ? 0 : 1, s);
+    mark(tr, "project_finish_current", s);
+    if (!a.reproject && a.ns > JRHO_MIN_NS) ++nl;
     if (a.ns > 4) {
-        launch_gemm_cn(p.gd_g1, a.nk, a.ns, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
+        k_gram_dev<<<dim3(a.ns, a.nk), 256, 0, s>>>(a);
         mark(tr, "gram", s);
         ++nl;
     }
@@ -1862,14 +2163,13 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
     if (a.reproject) {
         launch_gemm_cn(p.gd_g2, a.nk, a.ns, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
         k_reproj<<<dim3((a.naux * a.ns + 255) / 256, 1, a.nk), 256, 0, s>>>(a);
-        dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
-        k_post<<<g, 128, 0, s>>>(a, 0, 1);
+        launch_post(a, 0, 1, s);
         mark(tr, "reproject", s);
         nl += 3;
     }
-    k_finalize<<<1, 256, 0, s>>>(a, 0);
+    launch_finalize(a, 0, s);
     mark(tr, "finalize", s);
-    ++nl;
+    nl += 2;
     if (a.hartree) {
         // the density of C_{k+1} sets the potential change of the next step
         if (p.gd_exp64) {
@@ -1935,7 +2235,4 @@ void launch_hsub_only(const StepArgs& a, const StepPlan& p, int cstep, cudaStrea
 }
 
 // J contributions of the current theta (rows into part_post[.][1..3])
-void launch_subspace_j(const StepArgs& a, cudaStream_t s) {
-    dim3 g((3 * a.naux + 3) / 4, 1, a.nk);
-    k_post<<<g, 128, 0, s>>>(a, 0, 1);
-}
+void launch_subspace_j(const StepArgs& a, cudaStream_t s) { launch_post(a, 0, 1, s); }

@@ -29,6 +29,16 @@
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// The dynamic shared-memory attribute is global per kernel and shared by every
+// context of the process: raise it to `bytes`, never lower it.
+static cudaError_t raise_smem(const void* f, int bytes) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    if (fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
 }
@@ -304,7 +314,7 @@ template <int NT>
 static int tc_launch(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
                      int nkb2, int kbs, dim3 grid, float* D, int M, int N, int* flag, cudaStream_t s) {
     const size_t smem = 1024 + (size_t)TC_STAGES * (TC_BM * TC_BK * 2 + NT * TC_BK * 2);
-    if (cudaFuncSetAttribute(k_tc_gemm<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (raise_smem((const void*)k_tc_gemm<NT>, (int)smem) != cudaSuccess)
         return -1;
     k_tc_gemm<NT><<<grid, 128, smem, s>>>(ah, al, bh, bl, nkb2, kbs, D, M, N, flag);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -426,8 +436,9 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
 
 struct TcOpParams {
     int nk, ns, ma, Dn, kbps, splits, atiles, R, S;
-    int nkb_fixed;  // K blocks of every k-point (0: ceil(N_G(k) / 32))
-    int rows_ng;    // valid output rows: N_G(k) (1) or ma (0)
+    int nkb_fixed;  // K blocks of every k-point (0: ceil(N_G(k) / 32), or ceil(N_basis(k) / 32) with k_nb)
+    int k_nb;       // K runs over the N_basis(k) basis rows
+    int rows_ng;    // valid output rows: ma (0), N_G(k) (1) or N_basis(k) (2)
     int fmt;        // operand format: 1 bf16, 0 fp16
     int kofs;  // k-point of blockIdx.z = 0 in the matching-row operand (single-k calls)
     const KDev* kd;
@@ -446,7 +457,11 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     constexpr int A_BYTES = TC_BM * TC_BK * 2;
     constexpr int B_BYTES = NT * TC_BK * 2;
     constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-    constexpr uint32_t NCOLS = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
+    // hi.hi and hi.lo as one product of N = 2 NT (B_hi and B_lo are adjacent in
+    // shared memory), lo.hi on the first NT columns: two instructions per K step
+    constexpr bool MERGE = 2 * NT <= 256;
+    constexpr int NACC = MERGE ? 2 * NT : NT;
+    constexpr uint32_t NCOLS = NACC <= 32 ? 32 : (NACC <= 64 ? 64 : (NACC <= 128 ? 128 : 256));
     __shared__ __align__(8) uint64_t full[TCO_MAXS], empty[TCO_MAXS], done;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
@@ -455,10 +470,12 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     const KDev& K = p.kd[k];
     const int ng = K.ng;
     const int row0 = tile * TC_BM;
-    const int nkb = p.nkb_fixed > 0 ? p.nkb_fixed : (ng + 31) >> 5;
+    const int nkb = p.nkb_fixed > 0 ? p.nkb_fixed : ((p.k_nb ? K.nb : ng) + 31) >> 5;
     const int kb0 = split * p.kbps;
     const int nk = min(nkb, kb0 + p.kbps) - kb0;
     if (nk <= 0) return;  // the reduction skips these slices
+    const int rows_valid = p.rows_ng == 2 ? K.nb : (p.rows_ng ? ng : p.ma);
+    if (row0 >= rows_valid) return;  // a row tile past this k-point's rows
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
@@ -484,6 +501,8 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | ((uint32_t)p.fmt << 7) | ((uint32_t)p.fmt << 10) | ((uint32_t)(NT >> 3) << 17) |
                                    ((uint32_t)(TC_BM >> 4) << 24);
+            const uint32_t idesc2 = (1u << 4) | ((uint32_t)p.fmt << 7) | ((uint32_t)p.fmt << 10) |
+                                    ((uint32_t)((NACC) >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
             int issued = 0, consumed = 0;
             auto load = [&](int j) {
                 const int s = j % S, kx = (kb0 + j) * TC_BK;
@@ -506,9 +525,14 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
 #pragma unroll
                 for (int kk = 0; kk < TC_BK / 16; ++kk) {
                     const uint32_t o = kk * 32;
-                    umma_bf16(tmem, umma_desc(ah + o), umma_desc(bh + o), idesc, (j > 0 || kk > 0) ? 1u : 0u);
-                    umma_bf16(tmem, umma_desc(ah + o), umma_desc(bl + o), idesc, 1u);
-                    umma_bf16(tmem, umma_desc(al + o), umma_desc(bh + o), idesc, 1u);
+                    if constexpr (MERGE) {
+                        umma_bf16(tmem, umma_desc(ah + o), umma_desc(bh + o), idesc2, (j > 0 || kk > 0) ? 1u : 0u);
+                        umma_bf16(tmem, umma_desc(al + o), umma_desc(bh + o), idesc, 1u);
+                    } else {
+                        umma_bf16(tmem, umma_desc(ah + o), umma_desc(bh + o), idesc, (j > 0 || kk > 0) ? 1u : 0u);
+                        umma_bf16(tmem, umma_desc(ah + o), umma_desc(bl + o), idesc, 1u);
+                        umma_bf16(tmem, umma_desc(al + o), umma_desc(bh + o), idesc, 1u);
+                    }
                 }
                 umma_commit(&empty[s]);
                 const int jp = j - 1;
@@ -540,11 +564,18 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
                 : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c));
+            uint32_t v2[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+            if constexpr (MERGE)
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                    : "=r"(v2[0]), "=r"(v2[1]), "=r"(v2[2]), "=r"(v2[3]), "=r"(v2[4]), "=r"(v2[5]), "=r"(v2[6]),
+                      "=r"(v2[7])
+                    : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(NT + c)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (lrow < (p.rows_ng ? ng : p.ma)) {
+            if (lrow < rows_valid) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
-                    if (c + u < p.Dn) drow[c + u] = __uint_as_float(v[u]);
+                    if (c + u < p.Dn) drow[c + u] = __uint_as_float(v[u]) + __uint_as_float(v2[u]);
             }
         }
     } else if (tid == 0 && !okd) {
@@ -587,7 +618,11 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     constexpr int A_BYTES = TC_BM * TC_BK * 2;
     constexpr int B_BYTES = NT * TC_BK * 2;
-    constexpr uint32_t NCOLS = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
+    // hi.hi and hi.lo as one product of N = 2 NT (B_hi and B_lo are adjacent in
+    // shared memory), lo.hi on the first NT columns: two instructions per K step
+    constexpr bool MERGE = 2 * NT <= 256;
+    constexpr int NACC = MERGE ? 2 * NT : NT;
+    constexpr uint32_t NCOLS = NACC <= 32 ? 32 : (NACC <= 64 ? 64 : (NACC <= 128 ? 128 : 256));
     __shared__ __align__(8) uint64_t fullA[TCT_MAXSA], emptyA[TCT_MAXSA], fullB[TCT_MAXSB], emptyB[TCT_MAXSB], done;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
@@ -654,6 +689,8 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
         } else if (lane == 0) {
             const uint32_t idesc = (1u << 4) | ((uint32_t)p.fmt << 7) | ((uint32_t)p.fmt << 10) | ((uint32_t)(NT >> 3) << 17) |
                                    ((uint32_t)(TC_BM >> 4) << 24);
+            const uint32_t idesc2 = (1u << 4) | ((uint32_t)p.fmt << 7) | ((uint32_t)p.fmt << 10) |
+                                    ((uint32_t)((NACC) >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
             int issued = 0, consumed = 0;
             auto loadB = [&](int j) {
                 const int s = j % SB, kx = (kb0 + j) * TC_BK;
@@ -675,9 +712,14 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
 #pragma unroll
                 for (int kk = 0; kk < TC_BK / 16; ++kk) {
                     const uint32_t o = kk * 32;
-                    umma_bf16(tmem, umma_desc(ah + o), umma_desc(bh + o), idesc, (j > 0 || kk > 0) ? 1u : 0u);
-                    umma_bf16(tmem, umma_desc(ah + o), umma_desc(bl + o), idesc, 1u);
-                    umma_bf16(tmem, umma_desc(al + o), umma_desc(bh + o), idesc, 1u);
+                    if constexpr (MERGE) {
+                        umma_bf16(tmem, umma_desc(ah + o), umma_desc(bh + o), idesc2, (j > 0 || kk > 0) ? 1u : 0u);
+                        umma_bf16(tmem, umma_desc(al + o), umma_desc(bh + o), idesc, 1u);
+                    } else {
+                        umma_bf16(tmem, umma_desc(ah + o), umma_desc(bh + o), idesc, (j > 0 || kk > 0) ? 1u : 0u);
+                        umma_bf16(tmem, umma_desc(ah + o), umma_desc(bl + o), idesc, 1u);
+                        umma_bf16(tmem, umma_desc(al + o), umma_desc(bh + o), idesc, 1u);
+                    }
                 }
                 umma_commit(&emptyA[sa]);
                 umma_commit(&emptyB[sb]);
@@ -772,11 +814,18 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
                 : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c));
+            uint32_t v2[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+            if constexpr (MERGE)
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                    : "=r"(v2[0]), "=r"(v2[1]), "=r"(v2[2]), "=r"(v2[3]), "=r"(v2[4]), "=r"(v2[5]), "=r"(v2[6]),
+                      "=r"(v2[7])
+                    : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(NT + c)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (lrow < ng) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
-                    if (c + u < p.Dn) drow[c + u] = __uint_as_float(v[u]);
+                    if (c + u < p.Dn) drow[c + u] = __uint_as_float(v[u]) + __uint_as_float(v2[u]);
             }
         }
     } else if (tid == 0 && !okd) {
@@ -883,65 +932,82 @@ struct TcRedParams {
     int ns, ma, Dn, kbps_t, splits_t, kbps_a, splits_a, Rt, Ra;
     int part;  // 0: interstitial and matching rows, 1: interstitial only, 2: matching only, 3: back-projection
     int Dnb, kbps_b, splits_b, nkb_b, Rb;
+    int maxng;                   // largest N_G (the row tiles of the interstitial part)
     double inv_t, inv_a, inv_b;  // undo the operand scales of the split-FP16 form
     const KDev* kd;
     const float* Dt;
     const float* Da;
     const float* Db;
 };
-// sum of nsp slices of one output pair, loads issued four slices at a time
-// (predicated, so short sums do not serialise on a scalar tail)
-__device__ __forceinline__ void tc_sum_slices(const float* d, size_t stride, int nsp, int c, int ns, double& re,
-                                              double& im) {
-    for (int s = 0; s < nsp; s += 4) {
-        float a[4], b[4];
+// A tile of TC_RT output rows of one product: the FP32 slice partials
+// D[s][row][Dn] (real columns c < nc: Re, nc + c: Im) summed over the nsp
+// slices in slice order in FP64, staged in shared memory so that the loads
+// run along the rows of D and the stores along the columns of the
+// column-major output out[row + c ld].
+#define TC_RT 16
+__device__ void tc_red_tile(const float* __restrict__ D, size_t sstride, int nsp, int Dn, int nc, int row0,
+                            int nrow, double scale, zd* __restrict__ out, size_t ld, double (*tile)[257]) {
+    const int n2 = 2 * nc;
+    for (int e = threadIdx.x; e < TC_RT * n2; e += blockDim.x) {
+        const int r = e / n2, c = e % n2, row = row0 + r;
+        double v = 0.0;
+        if (row < nrow) {
+            const float* d = D + (size_t)row * Dn + c;
+            for (int s0 = 0; s0 < nsp; s0 += 4) {
+                float a[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const bool ok = s + u < nsp;
-            a[u] = ok ? d[(size_t)(s + u) * stride + c] : 0.f;
-            b[u] = ok ? d[(size_t)(s + u) * stride + ns + c] : 0.f;
-        }
+                for (int u = 0; u < 4; ++u) a[u] = (s0 + u < nsp) ? d[(size_t)(s0 + u) * sstride] : 0.f;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            re += (double)a[u];
-            im += (double)b[u];
+                for (int u = 0; u < 4; ++u) v += (double)a[u];
+            }
         }
+        tile[r][c] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < TC_RT * nc; e += blockDim.x) {
+        const int r = e % TC_RT, c = e / TC_RT, row = row0 + r;
+        if (row < nrow) out[row + (size_t)c * ld] = zmk(tile[r][c] * scale, tile[r][nc + c] * scale);
     }
 }
-__global__ void k_tc_opred(TcRedParams p) {
+
+// Split-K sums of the operator's tensor-core products: the interstitial rows
+// into K.th and the matching rows into K.Q (part 0, or 1 / 2 for one of
+// them), the back-projection into K.tb (part 3).  Blocks: row tiles of the
+// interstitial rows (over the largest N_G), then of the matching rows.
+__global__ void __launch_bounds__(256) k_tc_opred(TcRedParams p) {
+    __shared__ double tile[TC_RT][257];
     const int k = blockIdx.z;
     const KDev& K = p.kd[k];
     const int ng = K.ng, ns = p.ns;
     const int nkb = (ng + 31) >> 5;
     if (p.part == 3) {
-        // back-projection: K.tb[g + c ng] for c < 2 ns (H part, then S part)
-        const int nc = 2 * ns;
-        const int e = blockIdx.x * 256 + threadIdx.x;
-        if (e >= ng * nc) return;
-        const int g = e % ng, c = e / ng;
         const int nsp = min(p.splits_b, (p.nkb_b + p.kbps_b - 1) / p.kbps_b);
-        double re = 0.0, im = 0.0;
-        tc_sum_slices(p.Db + ((size_t)k * p.splits_b * p.Rb + g) * p.Dnb, (size_t)p.Rb * p.Dnb, nsp, c, nc, re, im);
-        K.tb[g + (size_t)c * ng] = zmk(re * p.inv_b, im * p.inv_b);
+        const int row0 = blockIdx.x * TC_RT;
+        if (row0 >= ng) return;
+        tc_red_tile(p.Db + (size_t)k * p.splits_b * p.Rb * p.Dnb, (size_t)p.Rb * p.Dnb, nsp, p.Dnb, 2 * ns, row0, ng,
+                    p.inv_b, K.tb, ng, tile);
         return;
     }
-    const int r0 = (p.part == 2) ? ng : 0;
-    const int r1 = (p.part == 1) ? ng : ng + p.ma;
-    const int nrow = r1 - r0;
-    const int e = blockIdx.x * 256 + threadIdx.x;
-    if (e >= nrow * ns) return;
-    const int row = r0 + e % nrow, c = e / nrow;
-    double re = 0.0, im = 0.0;
-    if (row < ng) {
+    const int tiles_t = (p.part == 2) ? 0 : (p.maxng + TC_RT - 1) / TC_RT;
+    if ((int)blockIdx.x < tiles_t) {
+        const int row0 = blockIdx.x * TC_RT;
+        if (row0 >= ng) return;
         const int nsp = min(p.splits_t, (nkb + p.kbps_t - 1) / p.kbps_t);
-        tc_sum_slices(p.Dt + ((size_t)k * p.splits_t * p.Rt + row) * p.Dn, (size_t)p.Rt * p.Dn, nsp, c, ns, re, im);
-        K.th[row + (size_t)c * ng] = zmk(re * p.inv_t, im * p.inv_t);
-    } else {
-        const int r = row - ng;
+        tc_red_tile(p.Dt + (size_t)k * p.splits_t * p.Rt * p.Dn, (size_t)p.Rt * p.Dn, nsp, p.Dn, ns, row0, ng, p.inv_t,
+                    K.th, ng, tile);
+    } else if (p.part != 1) {
+        const int row0 = (blockIdx.x - tiles_t) * TC_RT;
+        if (row0 >= p.ma) return;
         const int nsp = min(p.splits_a, (nkb + p.kbps_a - 1) / p.kbps_a);
-        tc_sum_slices(p.Da + ((size_t)k * p.splits_a * p.Ra + r) * p.Dn, (size_t)p.Ra * p.Dn, nsp, c, ns, re, im);
-        K.Q[r + (size_t)c * p.ma] = zmk(re * p.inv_a, im * p.inv_a);
+        tc_red_tile(p.Da + (size_t)k * p.splits_a * p.Ra * p.Dn, (size_t)p.Ra * p.Dn, nsp, p.Dn, ns, row0, p.ma,
+                    p.inv_a, K.Q, p.ma, tile);
     }
+}
+static dim3 tc_red_grid(int part, int maxng, int ma, int nk) {
+    const int tt = (maxng + TC_RT - 1) / TC_RT, ta = (ma + TC_RT - 1) / TC_RT;
+    if (part == 3 || part == 1) return dim3(tt, 1, nk);
+    if (part == 2) return dim3(ta, 1, nk);
+    return dim3(tt + ta, 1, nk);
 }
 
 // ------------------------------------------------------------ operator plan
@@ -966,6 +1032,7 @@ struct TcPlan {
     // potential-change rebuild T = dV~ * CC_G (Eq. v_interstitial), N_aux columns in
     // tiles of 128 complex columns, split-BF16, table gathered through L2
     int dv_ready = 0, naux = 0, dv_tiles = 0, dv_kbps = 0, dv_splits = 0;
+    double dv_sc = 1.0, dv_st = 1.0;  // fp16 form: scales of the packed CC_G and of the split dV~ table
     size_t dv_smem = 0;
     CUtensorMap tch, tcl;
     unsigned short *cch = nullptr, *ccl = nullptr;
@@ -1016,11 +1083,11 @@ static int tc_tmap3(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t 
 
 template <int NT>
 static cudaError_t tco_set_smem(int bytes_opfwd, int bytes_toep) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_opfwd<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_opfwd);
+    cudaError_t e = raise_smem((const void*)k_tc_opfwd<NT>, bytes_opfwd);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_toep<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_toep);
+    e = raise_smem((const void*)k_tc_toep<NT, false>, bytes_toep);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tc_toep<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_toep);
+    return raise_smem((const void*)k_tc_toep<NT, true>, bytes_toep);
 }
 
 void tc_plan_destroy(TcPlan* tp) {
@@ -1103,7 +1170,8 @@ static void tco_launch_toep(const TcPlan* tp, const TcToepCand& c, const KDev* k
     r.inv_t = 1.0 / (tp->sT * tp->sC);
     r.kd = kd;
     r.Dt = tp->Dt;
-    k_tc_opred<<<dim3((tp->maxng * tp->ns + 255) / 256, 1, nk), 256, 0, s>>>(r);
+    r.maxng = tp->maxng;
+    k_tc_opred<<<tc_red_grid(r.part, tp->maxng, tp->ma, nk), 256, 0, s>>>(r);
 }
 template <int NT>
 static void tco_launch_rows(const TcPlan* tp, const TcRowsCand& c, const KDev* kd, int nk, cudaStream_t s) {
@@ -1133,7 +1201,8 @@ static void tco_launch_rows(const TcPlan* tp, const TcRowsCand& c, const KDev* k
     r.inv_a = 1.0 / (tp->sA * tp->sC);
     r.kd = kd;
     r.Da = tp->Da;
-    k_tc_opred<<<dim3((tp->ma * tp->ns + 255) / 256, 1, nk), 256, 0, s>>>(r);
+    r.maxng = tp->maxng;
+    k_tc_opred<<<tc_red_grid(r.part, tp->maxng, tp->ma, nk), 256, 0, s>>>(r);
 }
 
 template <int NT>
@@ -1169,7 +1238,8 @@ static void tco_launch_back(const TcPlan* tp, const TcRowsCand& c, const KDev* k
     r.inv_b = 1.0 / (tp->sA * tp->sZ);
     r.kd = kd;
     r.Db = tp->Db;
-    k_tc_opred<<<dim3((tp->maxng * 2 * tp->ns + 255) / 256, 1, nk), 256, 0, s>>>(r);
+    r.maxng = tp->maxng;
+    k_tc_opred<<<tc_red_grid(r.part, tp->maxng, tp->ma, nk), 256, 0, s>>>(r);
 }
 
 static void tco_launch_back_any(const TcPlan* tp, const TcRowsCand& c, const KDev* kd, int nk, cudaStream_t s,
@@ -1535,7 +1605,7 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
         cudaError_t cb = cudaSuccess;
         switch (tp->NTb) {
 #define RTD_TCO(n) \
-    case n: cb = cudaFuncSetAttribute(k_tc_opfwd<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(max_sm_b, std::max(max_sm_a, (size_t)1024))); break;
+    case n: cb = raise_smem((const void*)k_tc_opfwd<n>, (int)std::max(max_sm_b, std::max(max_sm_a, (size_t)1024))); break;
             RTD_TCO(16) RTD_TCO(32) RTD_TCO(48) RTD_TCO(64) RTD_TCO(96) RTD_TCO(128) RTD_TCO(160) RTD_TCO(192)
             RTD_TCO(224) RTD_TCO(256)
 #undef RTD_TCO
@@ -1617,7 +1687,7 @@ void launch_tc_pack(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
     k_tc_pack_c<<<g, 256, 0, s>>>(a.kd, tp->ns, tp->Kp, tp->Rp, tp->bh, tp->bl, tp->fmt, tp->sC, a.flag);
 }
 
-int launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
+int launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s, bool rows_only) {
     const TcToepParams pt = tco_toep_params(tp, a);
     const TcOpParams pa = tco_rows_params(tp, a);
     dim3 gt(tp->ttiles, tp->splits_t, a.nk);
@@ -1625,15 +1695,19 @@ int launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
     switch (tp->NT) {
 #define RTD_TCO(n)                                                                                    \
     case n:                                                                                           \
-        if (tp->wcap > 0) k_tc_toep<n, false><<<gt, TCO_THREADS, tp->smem_t, s>>>(tp->tbh, tp->tbl, pt); \
-        else k_tc_toep<n, true><<<gt, TCO_THREADS, tp->smem_t, s>>>(tp->tbh, tp->tbl, pt);             \
+        if (rows_only) {                                                                              \
+        } else if (tp->wcap > 0) {                                                                    \
+            k_tc_toep<n, false><<<gt, TCO_THREADS, tp->smem_t, s>>>(tp->tbh, tp->tbl, pt);              \
+        } else {                                                                                      \
+            k_tc_toep<n, true><<<gt, TCO_THREADS, tp->smem_t, s>>>(tp->tbh, tp->tbl, pt);               \
+        }                                                                                             \
         if (tp->atiles > 0) k_tc_opfwd<n><<<ga, TCO_THREADS, tp->smem_a, s>>>(tp->tbh, tp->tbl, tp->tah, tp->tal, pa); \
         break;
         RTD_TCO(16) RTD_TCO(32) RTD_TCO(48) RTD_TCO(64) RTD_TCO(96) RTD_TCO(128) RTD_TCO(160) RTD_TCO(192)
         RTD_TCO(224) RTD_TCO(256)
 #undef RTD_TCO
     }
-    return tp->atiles > 0 ? 2 : 1;
+    return (rows_only ? 0 : 1) + (tp->atiles > 0 ? 1 : 0);
 }
 
 bool tc_has_back(const TcPlan* tp) { return tp && tp->NTb > 0; }
@@ -1646,7 +1720,7 @@ int launch_tc_back(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
     return 3;
 }
 
-void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
+void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s, bool rows_only) {
     TcRedParams p{};
     p.ns = tp->ns;
     p.ma = tp->ma;
@@ -1657,14 +1731,15 @@ void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
     p.splits_a = tp->splits_a;
     p.Rt = tp->ttiles * TC_BM;
     p.Ra = tp->Mp;
-    p.part = 0;
+    p.part = rows_only ? 2 : 0;
     p.inv_t = 1.0 / (tp->sT * tp->sC);
     p.inv_a = 1.0 / (tp->sA * tp->sC);
     p.kd = a.kd;
     p.Dt = tp->Dt;
     p.Da = tp->Da;
-    dim3 g(((tp->maxng + tp->ma) * tp->ns + 255) / 256, 1, a.nk);
-    k_tc_opred<<<g, 256, 0, s>>>(p);
+    p.maxng = tp->maxng;
+    if (rows_only && tp->ma == 0) return;
+    k_tc_opred<<<tc_red_grid(p.part, tp->maxng, tp->ma, a.nk), 256, 0, s>>>(p);
 }
 
 void tc_plan_info(const TcPlan* tp, int* v) {
@@ -1687,7 +1762,8 @@ int tc_format(const TcPlan* tp) { return tp ? tp->fmt : 1; }
 // tile's h_j columns, rows [j NTV + h_j, j NTV + 2 h_j) hold [Im CC | Re CC].
 #define TC_DV_NT 256
 __global__ void k_tc_pack_cc(const zd* __restrict__ caux, int nb, int ng, int naux, int Kp, int rows, int k,
-                             unsigned short* __restrict__ bh, unsigned short* __restrict__ bl, int* flag) {
+                             unsigned short* __restrict__ bh, unsigned short* __restrict__ bl, int fmt, double sc,
+                             int* flag) {
     const size_t e = (size_t)blockIdx.x * 256 + threadIdx.x;
     if (e >= (size_t)naux * ng) return;
     const int gp = (int)(e % ng), col = (int)(e / ng);
@@ -1697,33 +1773,32 @@ __global__ void k_tc_pack_cc(const zd* __restrict__ caux, int nb, int ng, int na
     const int kb = gp >> 5, o = gp & 31;
     const size_t re_row = ((size_t)k * rows + (size_t)j * TC_DV_NT + cl) * Kp + (size_t)kb * 64;
     const size_t im_row = ((size_t)k * rows + (size_t)j * TC_DV_NT + h + cl) * Kp + (size_t)kb * 64;
-    put16(c.x, 1, 1.0, bh, bl, re_row + o, flag);
-    put16(c.x, 1, 1.0, bh, bl, im_row + 32 + o, flag);
-    put16(c.y, 1, 1.0, bh, bl, im_row + o, flag);
-    put16(-c.y, 1, 1.0, bh, bl, re_row + 32 + o, flag);
+    put16(c.x, fmt, sc, bh, bl, re_row + o, flag);
+    put16(c.x, fmt, sc, bh, bl, im_row + 32 + o, flag);
+    put16(c.y, fmt, sc, bh, bl, im_row + o, flag);
+    put16(-c.y, fmt, sc, bh, bl, re_row + 32 + o, flag);
 }
 
 // T[G + (c0 + c) ng] = s sum over slices (tile of h columns); T is the per-k
 // buffer of the descriptor's B operand (dv[k].X of the Toeplitz descriptor)
 struct TcDvRedParams {
     int splits, kbps, Rt, h, c0;
+    double inv;  // 1 / (scale of CC_G x scale of the table)
     const KDev* kd;
     const ToepDesc* td;
     const float* D;
     const DevState* st;
 };
-__global__ void k_tc_dvred(TcDvRedParams p) {
+__global__ void __launch_bounds__(256) k_tc_dvred(TcDvRedParams p) {
+    __shared__ double tile[TC_RT][257];
     const int k = blockIdx.z;
     const KDev& K = p.kd[k];
     const int ng = K.ng, nkb = (ng + 31) >> 5;
-    const int e = blockIdx.x * 256 + threadIdx.x;
-    if (e >= ng * p.h) return;
-    const int g = e % ng, c = e / ng;
+    const int row0 = blockIdx.x * TC_RT;
+    if (row0 >= ng) return;
     const int nsp = min(p.splits, (nkb + p.kbps - 1) / p.kbps);
-    double re = 0.0, im = 0.0;
-    tc_sum_slices(p.D + ((size_t)k * p.splits * p.Rt + g) * TC_DV_NT, (size_t)p.Rt * TC_DV_NT, nsp, c, p.h, re, im);
-    const double sc = p.st->cur_s;
-    p.td[k].Y[g + (size_t)(p.c0 + c) * ng] = zmk(re * sc, im * sc);
+    tc_red_tile(p.D + (size_t)k * p.splits * p.Rt * TC_DV_NT, (size_t)p.Rt * TC_DV_NT, nsp, TC_DV_NT, p.h, row0, ng,
+                p.st->cur_s * p.inv, p.td[k].Y + (size_t)p.c0 * ng, ng, tile);
 }
 
 // Set-up of the rebuild operands (at the first rttddft_set_dv): CC_G packed,
@@ -1759,15 +1834,17 @@ int tc_dv_prepare(TcPlan* tp, const zd* const* caux_dev, const int* nb, const in
     }
     cudaMemsetAsync(tp->cch, 0, ncc * 2, s);
     cudaMemsetAsync(tp->ccl, 0, ncc * 2, s);
+    // fp16 form: the plane-wave rows of an S-orthonormal CC have |c| <= 1 (S >= I on
+    // them), so 2^14 keeps every packed value inside the fp16 range
+    tp->dv_sc = tp->fmt ? 1.0 : 16384.0;
     for (int k = 0; k < tp->nk; ++k) {
         const size_t n = (size_t)naux * ng[k];
         k_tc_pack_cc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(caux_dev[k], nb[k], ng[k], naux, tp->Kp, rows, k,
-                                                                 tp->cch, tp->ccl, tp->tflag);
+                                                                 tp->cch, tp->ccl, tp->fmt, tp->dv_sc, tp->tflag);
     }
     int e = tc_tmap3(&tp->tch, tp->cch, tp->Kp, rows, tp->nk, TC_DV_NT) |
             tc_tmap3(&tp->tcl, tp->ccl, tp->Kp, rows, tp->nk, TC_DV_NT);
-    const cudaError_t ce = cudaFuncSetAttribute(k_tc_toep<TC_DV_NT, true>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp->dv_smem);
+    const cudaError_t ce = raise_smem((const void*)k_tc_toep<TC_DV_NT, true>, (int)tp->dv_smem);
     if (e || ce != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         *why = "potential-change operand set-up failed";
         return RTTDDFT_ERR_CUDA;
@@ -1776,9 +1853,13 @@ int tc_dv_prepare(TcPlan* tp, const zd* const* caux_dev, const int* nb, const in
     return RTTDDFT_OK;
 }
 
-// the pre-split dV~ table (every rttddft_set_dv)
-void tc_dv_set_table(TcPlan* tp, const zd* dvtab, int nvt, cudaStream_t s) {
-    if (nvt > 0) k_tc_split_table<<<(nvt + 255) / 256, 256, 0, s>>>(dvtab, tp->dvtabs, nvt, 1, 1.0, tp->tflag);
+// the pre-split dV~ table (every rttddft_set_dv); vmax: its largest |Re|, |Im|
+// (the fp16 form scales it by a power of two to about 2^14)
+void tc_dv_set_table(TcPlan* tp, const zd* dvtab, int nvt, double vmax, cudaStream_t s) {
+    tp->dv_st = 1.0;
+    if (!tp->fmt && vmax > 0.0) tp->dv_st = std::ldexp(1.0, (int)std::floor(std::log2(16384.0 / vmax)));
+    if (nvt > 0)
+        k_tc_split_table<<<(nvt + 255) / 256, 256, 0, s>>>(dvtab, tp->dvtabs, nvt, tp->fmt, tp->dv_st, tp->tflag);
 }
 
 bool tc_dv_ready(const TcPlan* tp) { return tp && tp->dv_ready; }
@@ -1796,7 +1877,7 @@ void launch_tc_dv_toeplitz(const TcPlan* tp, const StepArgs& a, const ToepDesc* 
     p.vt_center = tp->vt_center;
     p.SA = 2;
     p.SB = 2;
-    p.fmt = 1;
+    p.fmt = tp->fmt;
     p.kd = a.kd;
     p.tab = tp->dvtabs;
     p.D = tp->Dd;
@@ -1810,11 +1891,253 @@ void launch_tc_dv_toeplitz(const TcPlan* tp, const StepArgs& a, const ToepDesc* 
         r.kbps = tp->dv_kbps;
         r.Rt = tp->ttiles * TC_BM;
         r.c0 = j * (TC_DV_NT / 2);
+        r.inv = 1.0 / (tp->dv_sc * tp->dv_st);
         r.h = std::min(TC_DV_NT / 2, tp->naux - r.c0);
         r.kd = a.kd;
         r.td = td;
         r.D = tp->Dd;
         r.st = a.st;
-        k_tc_dvred<<<dim3((tp->maxng * r.h + 255) / 256, 1, a.nk), 256, 0, s>>>(r);
+        k_tc_dvred<<<dim3((tp->maxng + TC_RT - 1) / TC_RT, 1, a.nk), 256, 0, s>>>(r);
     }
+}
+
+// ------------------------------------------------------------ products with the auxiliary basis
+// Expansion C = CC theta (Eq. approximation_coefficients) and projection
+// theta~ = CC^H (S C) (Eq. evolution_of_projection_coeff) as split-BF16
+// tensor-core products on the matching-row pipeline (k_tc_opfwd).  CC is
+// split and packed once at set-up as the left operand of both: its rows with
+// K over the auxiliary vectors (expansion), and the rows of CC^H with K over
+// the basis rows (projection).  The right operand, theta or the S C columns
+// of the operator pass, is packed every step.
+struct TcCC {
+    int nk = 0, naux = 0, ns = 0, NT = 0, Dn = 0, maxnb = 0;
+    int Mp_e = 0, Kp_e = 0, nkb_e = 0, tiles_e = 0;
+    int Mp_p = 0, Kp_p = 0, nkb_p = 0, tiles_p = 0, kbps_p = 0, splits_p = 0;
+    int S = 2;
+    size_t smem = 0;
+    unsigned short *aeh = nullptr, *ael = nullptr, *aph = nullptr, *apl = nullptr;
+    unsigned short *beh = nullptr, *bel = nullptr, *bph = nullptr, *bpl = nullptr;
+    float *De = nullptr, *Dp = nullptr;
+    CUtensorMap taeh, tael, taph, tapl, tbeh, tbel, tbph, tbpl;
+};
+
+void tc_cc_destroy(TcCC* t) {
+    if (!t) return;
+    for (void* q : {(void*)t->aeh, (void*)t->ael, (void*)t->aph, (void*)t->apl, (void*)t->beh, (void*)t->bel,
+                    (void*)t->bph, (void*)t->bpl, (void*)t->De, (void*)t->Dp})
+        cudaFree(q);
+    delete t;
+}
+
+// left operands from CC (nb x naux, column-major): the expansion's rows b with
+// K over i, the projection's rows i (of CC^H) with K over b
+__global__ void k_tc_pack_cce(const zd* __restrict__ cc, int nb, int naux, int Kp, int Mp, int k,
+                              unsigned short* __restrict__ ah, unsigned short* __restrict__ al, int* flag) {
+    const size_t e = (size_t)blockIdx.x * 256 + threadIdx.x;
+    if (e >= (size_t)nb * naux) return;
+    const int b = (int)(e % nb), i = (int)(e / nb);
+    const zd v = cc[e];
+    const size_t row = ((size_t)k * Mp + b) * Kp + (size_t)(i >> 5) * 64 + (i & 31);
+    put16(v.x, 1, 1.0, ah, al, row, flag);
+    put16(v.y, 1, 1.0, ah, al, row + 32, flag);
+}
+__global__ void k_tc_pack_ccp(const zd* __restrict__ cc, int nb, int naux, int Kp, int Mp, int k,
+                              unsigned short* __restrict__ ah, unsigned short* __restrict__ al, int* flag) {
+    const size_t e = (size_t)blockIdx.x * 256 + threadIdx.x;
+    if (e >= (size_t)nb * naux) return;
+    const int b = (int)(e % nb), i = (int)(e / nb);
+    const zd v = cc[e];
+    const size_t row = ((size_t)k * Mp + i) * Kp + (size_t)(b >> 5) * 64 + (b & 31);
+    put16(v.x, 1, 1.0, ah, al, row, flag);
+    put16(-v.y, 1, 1.0, ah, al, row + 32, flag);
+}
+// right operand of a step: theta (mode 0, naux rows) or S C (mode 1, the S
+// half of [HC | SC], nb rows); rows c < ns hold [Re x | -Im x], rows ns + c
+// hold [Im x | Re x] over K
+__global__ void k_tc_pack_cols(const KDev* __restrict__ kd, int mode, int ns, int naux, int maxr, int Kp, int Rp,
+                               unsigned short* __restrict__ bh, unsigned short* __restrict__ bl, int* flag) {
+    const int k = blockIdx.z;
+    const KDev& K = kd[k];
+    const int nr = mode ? K.nb : naux;
+    const int e = blockIdx.x * 256 + threadIdx.x;
+    if (e >= maxr * ns) return;
+    const int r = e % maxr, c = e / maxr;
+    if (r >= nr) return;
+    const zd x = mode ? K.Y[(size_t)(ns + c) * K.nb + r] : K.theta[r + (size_t)c * naux];
+    const int kb = r >> 5, o = r & 31;
+    const size_t re_row = ((size_t)k * Rp + c) * Kp + (size_t)kb * 64;
+    const size_t im_row = ((size_t)k * Rp + ns + c) * Kp + (size_t)kb * 64;
+    put16(x.x, 1, 1.0, bh, bl, re_row + o, flag);
+    put16(x.x, 1, 1.0, bh, bl, im_row + 32 + o, flag);
+    put16(x.y, 1, 1.0, bh, bl, im_row + o, flag);
+    put16(-x.y, 1, 1.0, bh, bl, re_row + 32 + o, flag);
+}
+// split-K sums: the expansion into K.C (mode 0), the projection into the
+// single-slice projection partials that the post kernel finishes (mode 1)
+struct TcCCRed {
+    int mode, ns, naux, Dn, R, splits, kbps;
+    const KDev* kd;
+    const float* D;
+    zd* part;
+};
+__global__ void __launch_bounds__(256) k_tc_ccred(TcCCRed p) {
+    __shared__ double tile[TC_RT][257];
+    const int k = blockIdx.z;
+    const KDev& K = p.kd[k];
+    const int row0 = blockIdx.x * TC_RT;
+    const int nrow = p.mode ? p.naux : K.nb;
+    if (row0 >= nrow) return;
+    const int nsp = p.mode ? min(p.splits, (((K.nb + 31) >> 5) + p.kbps - 1) / p.kbps) : 1;
+    zd* out = p.mode ? p.part + (size_t)k * p.naux * p.ns : K.C;
+    tc_red_tile(p.D + (size_t)k * p.splits * p.R * p.Dn, (size_t)p.R * p.Dn, nsp, p.Dn, p.ns, row0, nrow, 1.0, out,
+                p.mode ? p.naux : K.nb, tile);
+}
+
+int tc_cc_create(TcCC** out, int nk, int naux, int ns, const int* nb, const zd* const* cc_dev, int* flag,
+                 cudaStream_t s, std::string* why) {
+    *out = nullptr;
+    if (!get_encode()) {
+        *why = "the driver has no tensor-map encoder";
+        return RTTDDFT_ERR_UNSUPPORTED;
+    }
+    TcCC* t = new TcCC();
+    t->nk = nk;
+    t->naux = naux;
+    t->ns = ns;
+    t->Dn = 2 * ns;
+    for (int nt : TCO_NTS)
+        if (nt >= t->Dn) {
+            t->NT = nt;
+            break;
+        }
+    if (!t->NT || t->NT > 128) {
+        delete t;
+        *why = "the tensor-core products with the auxiliary basis take at most 64 states";
+        return RTTDDFT_ERR_UNSUPPORTED;
+    }
+    for (int k = 0; k < nk; ++k) t->maxnb = std::max(t->maxnb, nb[k]);
+    int dev = 0, nsm = 148, smax = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    t->nkb_e = (naux + 31) / 32;
+    t->Kp_e = t->nkb_e * TC_BK;
+    t->tiles_e = (t->maxnb + TC_BM - 1) / TC_BM;
+    t->Mp_e = t->tiles_e * TC_BM;
+    t->nkb_p = (t->maxnb + 31) / 32;
+    t->Kp_p = t->nkb_p * TC_BK;
+    t->tiles_p = (naux + TC_BM - 1) / TC_BM;
+    t->Mp_p = t->tiles_p * TC_BM;
+    {
+        // projection: K slices so that about two blocks per SM work
+        int sp = std::max(1, std::min(t->nkb_p, (2 * nsm + t->tiles_p * nk - 1) / (t->tiles_p * nk)));
+        t->kbps_p = (t->nkb_p + sp - 1) / sp;
+        t->splits_p = (t->nkb_p + t->kbps_p - 1) / t->kbps_p;
+    }
+    const size_t stage = (size_t)2 * TC_BM * TC_BK * 2 + (size_t)2 * t->NT * TC_BK * 2;
+    t->S = 4;
+    while (t->S > 2 && 1024 + t->S * stage > (size_t)smax - 512) --t->S;
+    t->smem = 1024 + t->S * stage;
+    const size_t nae = (size_t)nk * t->Mp_e * t->Kp_e, nap = (size_t)nk * t->Mp_p * t->Kp_p;
+    const size_t nbe = (size_t)nk * t->NT * t->Kp_e, nbp = (size_t)nk * t->NT * t->Kp_p;
+    const size_t nde = (size_t)nk * t->Mp_e * t->Dn, ndp = (size_t)nk * t->splits_p * t->Mp_p * t->Dn;
+    if (cudaMalloc(&t->aeh, nae * 2) != cudaSuccess || cudaMalloc(&t->ael, nae * 2) != cudaSuccess ||
+        cudaMalloc(&t->aph, nap * 2) != cudaSuccess || cudaMalloc(&t->apl, nap * 2) != cudaSuccess ||
+        cudaMalloc(&t->beh, nbe * 2) != cudaSuccess || cudaMalloc(&t->bel, nbe * 2) != cudaSuccess ||
+        cudaMalloc(&t->bph, nbp * 2) != cudaSuccess || cudaMalloc(&t->bpl, nbp * 2) != cudaSuccess ||
+        cudaMalloc(&t->De, nde * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&t->Dp, ndp * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        tc_cc_destroy(t);
+        *why = "out of device memory for the tensor-core products with the auxiliary basis";
+        return RTTDDFT_ERR_OOM;
+    }
+    for (auto pr : {std::make_pair((void*)t->aeh, nae), std::make_pair((void*)t->ael, nae),
+                    std::make_pair((void*)t->aph, nap), std::make_pair((void*)t->apl, nap),
+                    std::make_pair((void*)t->beh, nbe), std::make_pair((void*)t->bel, nbe),
+                    std::make_pair((void*)t->bph, nbp), std::make_pair((void*)t->bpl, nbp)})
+        cudaMemsetAsync(pr.first, 0, pr.second * 2, s);
+    for (int k = 0; k < nk; ++k) {
+        const size_t n = (size_t)nb[k] * naux;
+        k_tc_pack_cce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cc_dev[k], nb[k], naux, t->Kp_e, t->Mp_e, k, t->aeh,
+                                                                  t->ael, flag);
+        k_tc_pack_ccp<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cc_dev[k], nb[k], naux, t->Kp_p, t->Mp_p, k, t->aph,
+                                                                  t->apl, flag);
+    }
+    int e = tc_tmap3(&t->taeh, t->aeh, t->Kp_e, t->Mp_e, nk, TC_BM) | tc_tmap3(&t->tael, t->ael, t->Kp_e, t->Mp_e, nk, TC_BM) |
+            tc_tmap3(&t->taph, t->aph, t->Kp_p, t->Mp_p, nk, TC_BM) | tc_tmap3(&t->tapl, t->apl, t->Kp_p, t->Mp_p, nk, TC_BM) |
+            tc_tmap3(&t->tbeh, t->beh, t->Kp_e, t->NT, nk, t->NT) | tc_tmap3(&t->tbel, t->bel, t->Kp_e, t->NT, nk, t->NT) |
+            tc_tmap3(&t->tbph, t->bph, t->Kp_p, t->NT, nk, t->NT) | tc_tmap3(&t->tbpl, t->bpl, t->Kp_p, t->NT, nk, t->NT);
+    // the attribute is global per kernel: raise it to this plan's need, never lower it
+    cudaError_t ce = cudaSuccess;
+    switch (t->NT) {
+#define RTD_TCO(n) \
+    case n: ce = raise_smem((const void*)k_tc_opfwd<n>, (int)t->smem); break;
+        RTD_TCO(16) RTD_TCO(32) RTD_TCO(48) RTD_TCO(64) RTD_TCO(96) RTD_TCO(128)
+#undef RTD_TCO
+    }
+    if (e || ce != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        tc_cc_destroy(t);
+        *why = "set-up of the tensor-core products with the auxiliary basis failed";
+        return RTTDDFT_ERR_CUDA;
+    }
+    *out = t;
+    return RTTDDFT_OK;
+}
+
+static void tcc_product(const TcCC* t, int proj, const KDev* kd, int nk, int* flag, cudaStream_t s) {
+    TcOpParams p{};
+    p.nk = nk;
+    p.ns = t->ns;
+    p.Dn = t->Dn;
+    p.S = t->S;
+    p.fmt = 1;
+    p.kd = kd;
+    p.flag = flag;
+    if (proj) {
+        p.ma = t->naux;
+        p.kbps = t->kbps_p;
+        p.splits = t->splits_p;
+        p.atiles = t->tiles_p;
+        p.R = t->Mp_p;
+        p.k_nb = 1;
+        p.rows_ng = 0;
+        p.D = t->Dp;
+    } else {
+        p.kbps = t->nkb_e;
+        p.splits = 1;
+        p.atiles = t->tiles_e;
+        p.R = t->Mp_e;
+        p.nkb_fixed = t->nkb_e;
+        p.rows_ng = 2;
+        p.D = t->De;
+    }
+    dim3 g(p.atiles, p.splits, nk);
+    const CUtensorMap &bh = proj ? t->tbph : t->tbeh, &bl = proj ? t->tbpl : t->tbel;
+    const CUtensorMap &ah = proj ? t->taph : t->taeh, &al = proj ? t->tapl : t->tael;
+    switch (t->NT) {
+#define RTD_TCO(n) \
+    case n: k_tc_opfwd<n><<<g, TCO_THREADS, t->smem, s>>>(bh, bl, ah, al, p); break;
+        RTD_TCO(16) RTD_TCO(32) RTD_TCO(48) RTD_TCO(64) RTD_TCO(96) RTD_TCO(128)
+#undef RTD_TCO
+    }
+}
+
+// C = CC theta: pack theta, the product, the sums into K.C; returns the launches
+int launch_tcc_expand(const TcCC* t, const StepArgs& a, cudaStream_t s) {
+    k_tc_pack_cols<<<dim3((t->naux * t->ns + 255) / 256, 1, a.nk), 256, 0, s>>>(a.kd, 0, t->ns, t->naux, t->naux,
+                                                                                t->Kp_e, t->NT, t->beh, t->bel, a.flag);
+    tcc_product(t, 0, a.kd, a.nk, a.flag, s);
+    TcCCRed r{0, t->ns, t->naux, t->Dn, t->Mp_e, 1, t->nkb_e, a.kd, t->De, nullptr};
+    k_tc_ccred<<<dim3((t->maxnb + TC_RT - 1) / TC_RT, 1, a.nk), 256, 0, s>>>(r);
+    return 3;
+}
+// theta~ partials = CC^H (S C) into part (one slice per k-point, k * naux * ns apart)
+int launch_tcc_project(const TcCC* t, const StepArgs& a, zd* part, cudaStream_t s) {
+    k_tc_pack_cols<<<dim3((t->maxnb * t->ns + 255) / 256, 1, a.nk), 256, 0, s>>>(a.kd, 1, t->ns, t->naux, t->maxnb,
+                                                                                 t->Kp_p, t->NT, t->bph, t->bpl, a.flag);
+    tcc_product(t, 1, a.kd, a.nk, a.flag, s);
+    TcCCRed r{1, t->ns, t->naux, t->Dn, t->Mp_p, t->splits_p, t->kbps_p, a.kd, t->Dp, part};
+    k_tc_ccred<<<dim3((t->naux + TC_RT - 1) / TC_RT, 1, a.nk), 256, 0, s>>>(r);
+    return 3;
 }

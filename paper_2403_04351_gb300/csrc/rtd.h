@@ -149,7 +149,17 @@ struct StepArgs {
     int hartree;              // the potential change is the Hartree potential of the density (FFT route)
     int cheb_tile;            // the cooperative series runs as k_cheb_tile (4 < N_s <= 64)
     double tc_st;             // scale of the split table (fp16 range)
+    double* part_fin;         // [nk][FIN_CH][FIN_STRIDE] first-phase sums of the step's reductions
+    double* gdev;             // [nk][ns] largest |C^H S C - I| per column (many states)
+    int toep_global;          // the direct sum gathers the table through L1/L2 into K.th (window too large)
+    zf* mtg;                  // muffin-tin products as GEMMs: per atom the 5m x m stack [h_eff; o; p_x; p_y; p_z]
+    zd* mtw;                  //   per (k, atom) its product with [Q; C_lo] (5m x N_s, stride mtw_stride)
+    int mtw_stride;
 };
+#define ZT_MIN_N 16           // columns from which the FP32 contractions take the 64 x 64 tiled kernel
+#define JRHO_MIN_NS 8         // above this many states the subspace current goes through rho = theta F theta^H
+#define FIN_CH 8              // row chunks per k-point of the first reduction phase
+#define FIN_STRIDE 16
 #define POST_STRIDE 36        // part_post row: residual, J_sub (3), then theta^H theta~ (ns <= 4)
 
 // ---- k_linalg.cu
@@ -182,6 +192,7 @@ struct StepPlan {
     // potential change (a2)
     const GemmDesc *gd_dvw, *gd_dvg, *gd_dvi;   // W = dh L, dV = L^H W, dV += C_G^H T
     const GemmDesc* gd_dvi32;                    // dV += C_G^H T with FP32 C_G (tensor-core forms)
+    const GemmDesc *gd_dvw32, *gd_dvg32;         // W = dh L, dV = L^H W from FP32 dh and L (or null)
     zd* part_dv;                                 // its split-K partials
     int kc_dvi;
     const ToepDesc* td_dv;                       // T = dV~ C_G
@@ -191,6 +202,7 @@ struct StepPlan {
     zd* const* jac_mats; double* const* jac_vals; zd* const* jac_vecs;
     int max_sweeps;
     const struct TcPlan* tc;  // tensor-core operator plan (split-BF16 form) or null
+    const struct TcCC* tcc;   // tensor-core expansion and projection (split forms, many states) or null
     const struct FftPlan* fft;  // FFT route of the interstitial convolution or null
     unsigned* tile_cnt;         // zeroed row-tile counters of the fused split-K sums (or null)
     cudaStream_t side;          // second stream for work that overlaps the main chain (or null)
@@ -199,6 +211,8 @@ struct StepPlan {
     const ToepDesc* td_dens;    // per k: the C the density is taken from
     cudaEvent_t ev_fork, ev_join;
     const ToepDesc* td_op;      // per k: {C, th}: the operator's convolution source and destination
+    const GemmDesc *gd_mt1, *gd_mt2;  // per (k, atom): [h_eff; o; p] times Q, then times C_lo (or null)
+    int mt_maxna, mt_maxlo;
 };
 // Optional per-kernel tracing: an event is recorded after every launch of a step.
 struct TraceHook {
@@ -272,16 +286,23 @@ void tc_plan_destroy(TcPlan* tp);
 // interstitial launch, candidates tuned, tuned interstitial and matching-row times (ns)
 void tc_plan_info(const TcPlan* tp, int* v);
 void launch_tc_pack(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
-int launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
-void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
+int launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s, bool rows_only = false);
+void launch_tc_reduce(const TcPlan* tp, const StepArgs& a, cudaStream_t s, bool rows_only = false);
 bool tc_has_back(const TcPlan* tp);  // the back-projection runs on the tensor cores (4 N_s <= 256)
 int tc_dv_prepare(TcPlan* tp, const zd* const* caux_dev, const int* nb, const int* ng, int naux, int nvt,
                   cudaStream_t s, std::string* why);
-void tc_dv_set_table(TcPlan* tp, const zd* dvtab, int nvt, cudaStream_t s);
+void tc_dv_set_table(TcPlan* tp, const zd* dvtab, int nvt, double vmax, cudaStream_t s);
 bool tc_dv_ready(const TcPlan* tp);
 int tc_dv_tiles(const TcPlan* tp);
 void launch_tc_dv_toeplitz(const TcPlan* tp, const StepArgs& a, const ToepDesc* td, cudaStream_t s);
 int launch_tc_back(const TcPlan* tp, const StepArgs& a, cudaStream_t s);
+// expansion and projection with the auxiliary basis on the tensor cores (split-BF16, many states)
+struct TcCC;
+int tc_cc_create(TcCC** out, int nk, int naux, int ns, const int* nb, const zd* const* cc_dev, int* flag,
+                 cudaStream_t s, std::string* why);
+void tc_cc_destroy(TcCC* t);
+int launch_tcc_expand(const TcCC* t, const StepArgs& a, cudaStream_t s);
+int launch_tcc_project(const TcCC* t, const StepArgs& a, zd* part, cudaStream_t s);
 // ---- tensor-core split-BF16 complex GEMM (k_tc.cu); returns an RTTDDFT_* code
 int tc_zgemm(int opA, int M, int N, int K, const zd* A, int lda, const zd* X, int ldx, zd* C, int ldc,
              int beta_add, cudaStream_t s);

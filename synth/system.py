@@ -96,6 +96,9 @@ CONFIGS = {
     "h2_6000": Config("h2_6000", 2, 2, 8, 50, 2, 200, 0.2, 2000, "h2box", n_g=5900),
     # CO-like cell: 11800 PW + 200 LO, 7 states, N_aux 400
     "co_12000": Config("co_12000", 3, 2, 8, 100, 7, 400, 0.2, 1000, "h2box", n_g=11800),
+    # CO-like cell at the largest basis of the paper's basis-size table (N_basis 25727,
+    # where the FFT route of the interstitial sum pays most): 25527 PW + 200 LO
+    "co_25727": Config("co_25727", 6, 2, 8, 100, 7, 400, 0.2, 1000, "h2box", n_g=25527),
     # heterostructure: 22 atoms, 16 k-points, N_basis in [7000, 10000]
     "mos2_16k": Config("mos2_16k", 4, 22, 8, 5, 60, 300, 0.2, 500, "mos2", n_k=16,
                        n_b_range=(7000, 10000), kgrid=(4, 4, 1), edir=(1.0, 0.0, 0.0)),

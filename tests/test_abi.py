@@ -108,11 +108,9 @@ def test_setup_rejects_non_finite_and_small_table(lib, small):
 
 
 def test_fft_route_options_are_checked_on_the_host(lib, small):
-    """The FFT interstitial route exists in the FP64 and FP32 forms only, and
-    an unknown route value is refused before any device work."""
+    """The direct sum is the default interstitial route, and an unknown route
+    value is refused before any device work."""
     assert rttddft.rttddft_default_options().interstitial == 0
-    _expect("ERR_UNSUPPORTED", small, precision="bf16x3", interstitial="fft")
-    _expect("ERR_UNSUPPORTED", small, precision="fp16x3", interstitial="fft")
     o = rttddft.INTERSTITIAL
     try:
         rttddft.INTERSTITIAL = dict(o, bogus=7)

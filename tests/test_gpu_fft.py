@@ -66,10 +66,13 @@ def system_for(case):
 
 
 @pytest.mark.parametrize("launches", ["5", "3"])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "fp16x3"])
 @pytest.mark.parametrize("case", ["tiny400", "ragged", "free", "dv", "wide"])
 def test_operator_by_fft_equals_explicit(case, prec, launches, monkeypatch):
-    """Both launch sets (five line passes; plane-fused three) on every case."""
+    """Both launch sets (five line passes; plane-fused three) on every case.
+    The split forms take the interstitial sum by FP32 FFTs and the
+    matching-coefficient products on the tensor cores: their bound is the
+    split one, 1e-4 (|H||x|)."""
     rng = np.random.default_rng(4)
     s, dv = system_for(case)
     monkeypatch.setenv("RTTDDFT_FFT_LAUNCHES", launches)
@@ -94,8 +97,9 @@ def test_operator_by_fft_equals_explicit(case, prec, launches, monkeypatch):
             assert rel(hx, ref_h) < 1e-12, (k, rel(hx, ref_h))
             assert rel(sx, ref_s) < 1e-12
         else:
-            assert np.max(np.abs(hx - ref_h) / (np.abs(h) @ np.abs(x))) < 1e-5
-            assert np.max(np.abs(sx - ref_s) / (np.abs(ops["S"]) @ np.abs(x))) < 1e-5
+            tol = 1e-5 if prec == "fp32" else 1e-4
+            assert np.max(np.abs(hx - ref_h) / (np.abs(h) @ np.abs(x))) < tol
+            assert np.max(np.abs(sx - ref_s) / (np.abs(ops["S"]) @ np.abs(x))) < tol
     ctx.close()
 
 
@@ -154,12 +158,12 @@ def test_ragged_multi_k_step_by_fft():
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "fp16x3"])
 def test_potential_change_rebuilt_by_fft(prec):
     """dVV = L^H (s dh) L + CC_G^H (s dV~ * CC_G) with the interstitial part by
     FFT over the N_aux columns, every step.  In FP64 the dipole keeps 1e-8; in
-    the FP32 route the rebuilt dVV carries FP32 rounding into the FP64
-    subspace Hamiltonian (bound 1e-6, as the split forms)."""
+    the reduced-precision forms the rebuilt dVV carries FP32 rounding into the
+    FP64 subspace Hamiltonian (bound 1e-6, the split forms' target)."""
     s = make_system("tiny400")
     dv = make_dv(s)
     a = pulse_samples(s, n_steps=30, a0=10.0)
@@ -174,7 +178,7 @@ def test_potential_change_rebuilt_by_fft(prec):
         assert rel(obs["energy"], r["E"]) < 1e-10
     else:
         assert rel(obs["dmu"], r["dmu"]) < 1e-6
-        assert rel(obs["energy"], r["E"]) < 1e-5
+        assert rel(obs["energy"], r["E"]) < (1e-5 if prec == "fp32" else 1e-4)
     ctx.close()
 
 
@@ -195,3 +199,22 @@ def test_h2_6000_by_fft_sampled():
         assert rel(obs["energy"], r["E"]) < (1e-10 if prec == "fp64" else 1e-5)
         ctx.close()
 
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+def test_split_forms_by_fft_over_200_steps(prec):
+    """The split forms with the FFT route: the dipole and the current of
+    record from the FP64 subspace (1e-8, 1e-10), the full-basis observables
+    within the split bounds."""
+    s = make_system("tiny400")
+    a = pulse_samples(s, a0=5.0)
+    r = Oracle(s).run(a, s["dt"])
+    ctx = Context(s, precision=prec, interstitial="fft", graph_steps=10)
+    ctx.step(a)
+    obs = ctx.observables()
+    assert rel(obs["dmu"], r["dmu"]) < 1e-8
+    assert rel(obs["j"], r["J"]) < 1e-10
+    assert rel(obs["energy"], r["E"]) < 1e-4
+    assert rel(obs["j_full"], r["J_full"]) < 1e-3
+    assert np.max(obs["norm_dev"]) < 1e-4
+    ctx.close()

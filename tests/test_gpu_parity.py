@@ -309,3 +309,67 @@ def test_tiled_series_with_ragged_row_tiles_and_k_points(monkeypatch):
     ctx.step(a)
     compare_run(ctx.observables(), r)
     ctx.close()
+
+
+def test_potential_change_pattern_replaced_between_steps():
+    """A potential change whose pattern changes during the run: ten steps
+    with dV_1, then rttddft_set_dv with another pattern dV_2 and ten more
+    steps.  The rebuild takes the pattern current at each step (nothing
+    projected is cached), so theta after the twenty steps equals the
+    oracle's run of the two halves with their own patterns (1e-9)."""
+    s = make_system("tiny400")
+    dv1, dv2 = make_dv(s), make_dv(s, seed_offset=7)
+    a = pulse_samples(s, n_steps=20, a0=5.0)
+    sc = dv_scale_samples(20, s["dt"])
+    r1 = Oracle(s, dv=dv1).run(a[:10], s["dt"], dv_scale=sc[:10])
+    r2 = Oracle(s, dv=dv2).run(a[10:], s["dt"], dv_scale=sc[10:], thetas=r1["theta"])
+    ctx = Context(s)
+    ctx.set_dv(dv1)
+    ctx.step(a[:10], sc[:10])
+    ctx.set_dv(dv2)
+    ctx.step(a[10:], sc[10:])
+    th = ctx.get_state(0)
+    assert rel(th, r2["theta"][0]) < 1e-9
+    # and the second pattern mattered: keeping dV_1 for all twenty steps ends elsewhere
+    r_same = Oracle(s, dv=dv1).run(a, s["dt"], dv_scale=sc)
+    assert rel(r_same["theta"][0], r2["theta"][0]) > 1e-6
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_direct_sum_with_the_table_gathered_through_l2(prec, monkeypatch):
+    """When the table window of a row tile does not fit in shared memory (G
+    sets whose 128-row tiles span several planes of the table, e.g. the
+    N_basis 25727 cell) the direct sum gathers V~ through L1/L2 into the
+    interstitial buffer; forced here on the small system: the operator equals
+    the explicit H X (1e-12 FP64, 1e-5 (|H||x|) FP32), with and without the
+    potential change, and a 30-step run keeps the oracle's dipole (1e-8)."""
+    monkeypatch.setenv("RTTDDFT_TOEP_GATHER", "1")
+    rng = np.random.default_rng(12)
+    a_vec = np.array([0.4, -0.9, 1.3])
+    for s in (make_system("tiny400"), make_system(ragged_cfg())):
+        dv = make_dv(s)
+        ctx = Context(s, precision=prec)
+        ctx.set_dv(dv)
+        for k in range(int(s["n_k"])):
+            ops = explicit_operators(s, k)
+            nb = ops["nb"]
+            x = rng.standard_normal((nb, 5)) + 1j * rng.standard_normal((nb, 5))
+            for sdv in (0.0, 0.7):
+                hx, sx = ctx.apply(k, x, a_vec, sdv)
+                h = hamiltonian(ops, a_vec, s["c_light"], explicit_dv(s, k, dv), sdv)
+                if prec == "fp64":
+                    assert rel(hx, h @ x) < 1e-12, k
+                    assert rel(sx, ops["S"] @ x) < 1e-12, k
+                else:
+                    assert np.max(np.abs(hx - h @ x) / (np.abs(h) @ np.abs(x))) < 1e-5, k
+        ctx.close()
+    s = make_system("tiny400")
+    a = pulse_samples(s, n_steps=30, a0=5.0)
+    r = Oracle(s).run(a, s["dt"])
+    ctx = Context(s, precision=prec, graph_steps=10)
+    ctx.step(a)
+    obs = ctx.observables()
+    assert rel(obs["dmu"], r["dmu"]) < 1e-8
+    assert rel(obs["energy"], r["E"]) < (1e-10 if prec == "fp64" else 1e-5)
+    ctx.close()

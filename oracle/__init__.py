@@ -7,10 +7,10 @@ from .rttddft_oracle import (Oracle, explicit_operators, explicit_dv, hamiltonia
                              interstitial_potential, embedding, ritz_basis, fix_phases,
                              propagate_exact, propagate_cn, critical_timestep,
                              overall_speedup, full_basis_propagator, polarizability, F_CRIT,
-                             interstitial_density, hartree_table)
+                             interstitial_density, hartree_table, mt_density)
 
 __all__ = ["Oracle", "explicit_operators", "explicit_dv", "hamiltonian",
            "interstitial_potential", "embedding", "ritz_basis", "fix_phases",
            "propagate_exact", "propagate_cn", "critical_timestep", "overall_speedup",
            "full_basis_propagator", "polarizability", "F_CRIT",
-           "interstitial_density", "hartree_table"]
+           "interstitial_density", "hartree_table", "mt_density"]

@@ -39,10 +39,14 @@ Readings where the paper is silent (each listed in the design notes):
   given trial vectors (S-orthonormal, H0 diagonal on them), each scaled so
   that the sum of its coefficients is real and positive;
 * the per-step potential from the evolving density (Sec. 2: VV(t) is what
-  changes from step to step) is modelled by its Hartree part in the
-  interstitial only: n_g = (1/Omega) sum_k w_k sum_j f_j sum_G C_G conj(C_{G-g})
+  changes from step to step) is modelled by its Hartree part: in the
+  interstitial n_g = (1/Omega) sum_k w_k sum_j f_j sum_G C_G conj(C_{G-g})
   over the plane-wave rows, dV_g = 4 pi (n_g(t) - n_g(0)) / |g|^2 (g != 0,
-  cartesian g), on the table box; the potential of step k comes from C_k.
+  cartesian g), on the table box; in the spheres, optionally, the density
+  matrix n_a = sum_k w_k sum_j f_j (E_a c)(E_a c)^H of each atom's channels
+  and the on-site blocks dh_a = U (n_a(t) - n_a(0)) (a contact stand-in for
+  the sphere's Hartree response, whose radial functions and Gaunt
+  coefficients are not available); the potential of step k comes from C_k.
 
 What pins each function (tests/test_oracle_pins.py; no function is
 parity-unpinned):
@@ -65,7 +69,12 @@ parity-unpinned):
 * polarizability: the closed-form geometric series, a proportional response;
 * interstitial_density: |psi(r)|^2 on a grid through numpy's FFT;
 * hartree_table: a single plane-wave density in a hexagonal cell, the sign of
-  the Hartree energy; Oracle.run(hartree=True): field-free inertness, norm.
+  the Hartree energy; Oracle.run(hartree=True): field-free inertness, norm;
+* mt_density: the closed form of a system whose matching coefficients are
+  phased unit rows (each channel reads one plane-wave coefficient);
+  Oracle.run(hartree=True, mt_u): field-free inertness, its effect on the
+  dipole, and the muffin-tin potential matrix against its own blocks placed
+  on the matched plane waves.
 """
 from __future__ import annotations
 
@@ -158,6 +167,23 @@ def interstitial_density(sys, cs, occ, wk, omega):
             val = wk[ik] * ((cg[g][None, :] * np.conj(cg)) @ occ)
             np.add.at(box, (d[:, 0], d[:, 1], d[:, 2]), val)
     return box / omega
+
+
+def mt_density(sys, cs, occ, wk):
+    """Muffin-tin density matrices of every atom: n_a = sum_k w_k sum_j f_j
+    v_kj v_kj^H with v_kj = E_a c_kj = [A_a c_G ; c_lo(a)], the occupations of
+    the atom's matching (u, u') and local-orbital channels, i.e. the
+    coefficients of the sphere's density in products of its radial functions
+    (Appendix A, the muffin-tin part of Eq. v_MT).  cs[k] is n_b x n_s."""
+    out = []
+    for a in range(int(sys["n_atoms"])):
+        m = int(sys["n_a"][a]) + int(sys["n_lo"][a])
+        n = np.zeros((m, m), dtype=np.complex128)
+        for ik, c in enumerate(cs):
+            v = embedding(sys, ik, a) @ np.asarray(c)
+            n += wk[ik] * (v * np.asarray(occ)[None, :]) @ v.conj().T
+        out.append(n)
+    return out
 
 
 def hartree_table(sys, n, n0):
@@ -293,16 +319,25 @@ class Oracle:
             h += cc.conj().T @ extra @ cc
         return h
 
-    def hartree_matrices(self, thetas, n0):
-        """Dense interstitial Hartree potential change of every k-point for the
-        state C = CC theta (its density against the reference n0)."""
+    def hartree_matrices(self, thetas, n0, mt0=None, mt_u=0.0):
+        """Dense potential change of every k-point for the state C = CC theta:
+        the interstitial Hartree potential of its density against the
+        reference n0 and, when mt_u != 0, the muffin-tin blocks
+        dh_a = mt_u (n_a - mt0_a) of its muffin-tin density matrices."""
         cs = [kp["caux"] @ t for kp, t in zip(self.kp, thetas)]
         table = hartree_table(self.sys, interstitial_density(self.sys, cs, self.occ, self.wk, self.omega), n0)
+        dh = None
+        if mt_u != 0.0:
+            dh = [mt_u * (na - n0a) for na, n0a in zip(mt_density(self.sys, cs, self.occ, self.wk), mt0)]
         out = []
         for ik, kp in enumerate(self.kp):
             ng = kp["ops"]["ng"]
             m = np.zeros((kp["ops"]["nb"], kp["ops"]["nb"]), dtype=np.complex128)
             m[:ng, :ng] = interstitial_potential(self.sys["g_int"][ik], self.sys["vt_dim"], table)
+            if dh is not None:
+                for a in range(int(self.sys["n_atoms"])):
+                    e = embedding(self.sys, ik, a)
+                    m += e.conj().T @ dh[a] @ e
             out.append(m)
         return out, table
 
@@ -331,11 +366,12 @@ class Oracle:
         return j
 
     def run(self, a_samples, dt, propagator="exact", reproject=False, dv_scale=None,
-            thetas=None, keep_states=False, hartree=False):
+            thetas=None, keep_states=False, hartree=False, mt_u=0.0):
         """Propagate len(a_samples) steps.  Returns a dict of per-step records
         (t, J, J_full, dmu, E, norm_dev, resid, dtcr, n_exc), final theta and C.
         hartree: the interstitial Hartree potential of the density of C_k
-        (against that of the starting state) acts during step k."""
+        (against that of the starting state) acts during step k; with
+        mt_u != 0 also the muffin-tin blocks mt_u (n_a(C_k) - n_a(C_0))."""
         a_samples = np.asarray(a_samples, dtype=np.float64)
         n = a_samples.shape[0]
         nk = len(self.kp)
@@ -349,6 +385,7 @@ class Oracle:
         if hartree:
             cs0 = [kp["caux"] @ t for kp, t in zip(self.kp, th)]
             n0 = interstitial_density(self.sys, cs0, self.occ, self.wk, self.omega)
+            mt0 = mt_density(self.sys, cs0, self.occ, self.wk) if mt_u != 0.0 else None
             rec["hartree_l1"] = []
         for k in range(n):
             a = a_samples[k]
@@ -356,7 +393,7 @@ class Oracle:
             cs, hcs, e_tot, ndev, res, lam_rng = [], [], 0.0, 0.0, 0.0, []
             vh = [None] * nk
             if hartree:
-                vh, table = self.hartree_matrices(th, n0)
+                vh, table = self.hartree_matrices(th, n0, mt0, mt_u)
                 rec["hartree_l1"].append(float(np.sum(np.abs(table))))
             for ik in range(nk):
                 kp = self.kp[ik]

@@ -14,7 +14,7 @@ import scipy.linalg as sla
 from oracle import (Oracle, critical_timestep, explicit_dv, explicit_operators,
                     full_basis_propagator, hamiltonian, interstitial_potential,
                     overall_speedup, polarizability, propagate_cn, propagate_exact, ritz_basis,
-                    interstitial_density, hartree_table)
+                    interstitial_density, hartree_table, mt_density)
 from synth import make_dv, make_system, pulse_samples, tiny_config
 from systems import free_electron_system, permutation_mt_system, plane_wave_basis
 
@@ -502,3 +502,78 @@ def test_hartree_potential_of_a_single_plane_wave_density():
         mask = np.ones(dim, dtype=bool)
         mask[tuple(e + g0)] = mask[tuple(e - g0)] = False
         assert np.max(np.abs(dv[mask])) == 0.0
+
+
+# ------------------------------------------------ muffin-tin density feedback
+
+def test_muffin_tin_density_of_phased_unit_rows():
+    """With A_alpha[p, pi(p)] = d_p every matching channel p of an atom reads
+    one plane-wave coefficient, v_p = d_p c_pi(p), and the local-orbital
+    channels read the LO rows: n_a[p, q] = sum_j f_j v_p conj(v_q), written
+    here entry by entry from the coefficients (no embedding matrix)."""
+    s, perm, d = permutation_mt_system()
+    ng = int(s["n_g"][0])
+    na = int(s["n_a"][0])
+    nlo = int(s["n_lo"][0])
+    nb = ng + 2 * nlo
+    rng = np.random.default_rng(21)
+    c = rng.standard_normal((nb, 3)) + 1j * rng.standard_normal((nb, 3))
+    occ = np.array([2.0, 1.5, 0.25])
+    n = mt_density(s, [c], occ, np.array([0.5]))
+    for atom in range(2):
+        m = na + nlo
+        ref = np.zeros((m, m), dtype=np.complex128)
+        for p in range(m):
+            for q in range(m):
+                for j in range(3):
+                    vp = d[atom * na + p] * c[perm[atom * na + p], j] if p < na else c[ng + atom * nlo + p - na, j]
+                    vq = d[atom * na + q] * c[perm[atom * na + q], j] if q < na else c[ng + atom * nlo + q - na, j]
+                    ref[p, q] += 0.5 * occ[j] * vp * np.conj(vq)
+        assert _rel(n[atom], ref) < 1e-14
+        assert np.max(np.abs(n[atom] - n[atom].conj().T)) < 1e-15 * np.max(np.abs(ref))
+
+
+def test_muffin_tin_feedback_inert_without_field_effective_with_one(tiny_oracle, tiny):
+    """The ground state keeps its muffin-tin density (only phases change), so
+    the contact feedback does nothing without a field; with a pulse it changes
+    the dipole, and the run keeps the norm."""
+    still = tiny_oracle.run(np.zeros((10, 3)), 0.1, hartree=True, mt_u=0.5)
+    plain = tiny_oracle.run(np.zeros((10, 3)), 0.1)
+    assert np.max(np.abs(still["theta"][0] - plain["theta"][0])) < 1e-13
+    a = pulse_samples(tiny, n_steps=20, a0=20.0)
+    r_mt = tiny_oracle.run(a, tiny["dt"], hartree=True, mt_u=0.5)
+    r_i = tiny_oracle.run(a, tiny["dt"], hartree=True)
+    assert r_mt["norm_dev"].max() < 1e-10
+    assert np.max(np.abs(r_mt["dmu"] - r_i["dmu"])) > 1e-6 * np.max(np.abs(r_i["dmu"]))
+
+
+def test_muffin_tin_potential_lands_on_matched_plane_waves():
+    """The feedback's potential matrix for a state with a muffin-tin density
+    change: its blocks sit on the matched plane waves exactly as Eq. v_MT
+    places h (conj(d_p) dh_pq d_q on (pi(p), pi(q))), with dh = U (n - n0)."""
+    from oracle.rttddft_oracle import Oracle
+    s, perm, d = permutation_mt_system()
+    ng = int(s["n_g"][0])
+    na = int(s["n_a"][0])
+    nlo = int(s["n_lo"][0])
+    orc = Oracle(s)
+    th0 = [kp["theta0"] for kp in orc.kp]
+    rng = np.random.default_rng(5)
+    th1 = [t + 0.1 * (rng.standard_normal(t.shape) + 1j * rng.standard_normal(t.shape)) for t in th0]
+    cs0 = [kp["caux"] @ t for kp, t in zip(orc.kp, th0)]
+    cs1 = [kp["caux"] @ t for kp, t in zip(orc.kp, th1)]
+    n0 = interstitial_density(s, cs0, orc.occ, orc.wk, orc.omega)
+    mt0 = mt_density(s, cs0, orc.occ, orc.wk)
+    mt1 = mt_density(s, cs1, orc.occ, orc.wk)
+    u = 0.7
+    vh, _ = orc.hartree_matrices(th1, n0, mt0, u)
+    vi, _ = orc.hartree_matrices(th1, n0)
+    vmt = vh[0] - vi[0]
+    for atom in range(2):
+        rows = np.arange(atom * na, (atom + 1) * na)
+        pg, dd = perm[rows], d[rows]
+        lo = ng + atom * nlo + np.arange(nlo)
+        dh = u * (mt1[atom] - mt0[atom])
+        assert np.allclose(vmt[np.ix_(pg, pg)], np.conj(dd)[:, None] * dh[:na, :na] * dd[None, :], atol=1e-14)
+        assert np.allclose(vmt[np.ix_(pg, lo)], np.conj(dd)[:, None] * dh[:na, na:], atol=1e-14)
+        assert np.allclose(vmt[np.ix_(lo, lo)], dh[na:, na:], atol=1e-14)

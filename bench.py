@@ -492,11 +492,13 @@ class _Timer:
         barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
+        torch.cuda.nvtx.range_push("timed_steps")  # lets a profiler select these launches
         for i in range(nsteps):
             self.flush()
             ev[i][0].record(stream)
             one(nwarm + i)
             ev[i][1].record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - t0
         barrier()

@@ -157,6 +157,14 @@ typedef struct {
     int hartree;
     double hartree_bound; /* bound on sum_g |dV_g| >= ||dVV||_2 used for the Chebyshev interval; a step whose
                              change exceeds it fails with ERR_ARG (default 0.1 Ha) */
+    /* with hartree = 1: the muffin-tin part of the feedback.  0 (default): none.  U != 0: per atom the
+     * density matrix of its matching and local-orbital channels, n_a = sum_k w_k sum_j f_j (E_a c_j)(E_a c_j)^H
+     * with E_a = [A_a 0; 0 I] (Appendix A), taken in FP64 from theta through the atom's rows of E_a CC, and
+     * the on-site blocks dh_a = U (n_a(t_k) - n_a(0)) act like the dh of rttddft_set_dv with s = 1 (the
+     * radial functions that would turn n_a into a potential are not part of this interface; the contact
+     * form stands in for them).  The bound above then covers sum_g |dV_g| + sum_a ||dh_a||_F max_k ||L_ka||_F^2
+     * (L_ka the atom's rows of E_a CC at k-point k). */
+    double hartree_mt_u;
 } rttddft_options;
 
 /* Per-step records (all k-points summed with their weights), caller-allocated

@@ -43,8 +43,9 @@ struct rttddft_ctx {
     TcCC* tcc = nullptr;  // expansion and projection on the tensor cores (split forms, many states)
     zf* d_mtg = nullptr;  // muffin-tin stacks [h_eff; o; p] (FP32 forms, many states)
     zd* d_mtw = nullptr;
-    int mtw_stride = 0, mt_maxna = 0, mt_maxlo = 0;
-    GemmDesc *gd_mt1 = nullptr, *gd_mt2 = nullptr;
+    zd* d_mtv = nullptr;  // per (k, atom) the gathered right-hand block [Q; C_lo] (m x N_s)
+    int mtw_stride = 0, mtv_stride = 0;
+    GemmDesc* gd_mt1 = nullptr;
     size_t nblk = 0;
     zd *d_vtab = nullptr, *d_dvtab = nullptr, *d_vstep = nullptr;
     zf *d_vtab32 = nullptr, *d_vstep32 = nullptr;
@@ -68,6 +69,10 @@ struct rttddft_ctx {
     GemmDesc *gd_dvw = nullptr, *gd_dvg = nullptr, *gd_dvi = nullptr, *gd_dvi32 = nullptr;
     GemmDesc *gd_dvw32 = nullptr, *gd_dvg32 = nullptr;  // the muffin-tin rebuild in FP32 (reduced-precision forms)
     zf* d_dh32 = nullptr;
+    // muffin-tin part of the density feedback
+    zd *d_mtn0 = nullptr, *d_mty = nullptr;
+    double *d_mt_lnorm = nullptr, *d_mt_fn2 = nullptr;
+    GemmDesc* gd_mty = nullptr;
     zd* d_part_dv = nullptr;
     int kc_dvi = 0;
     ToepDesc* td_dv = nullptr;
@@ -235,6 +240,12 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.part_full = ctx->d_part_full;
     a.part_post = ctx->d_part_post;
     a.part_fin = ctx->d_part_fin;
+    a.mt_u = (ctx->opt.hartree && ctx->d_mtn0) ? ctx->opt.hartree_mt_u : 0.0;
+    a.mtn0 = ctx->d_mtn0;
+    a.mty = ctx->d_mty;
+    a.mt_lnorm = ctx->d_mt_lnorm;
+    a.mt_fn2 = ctx->d_mt_fn2;
+    a.dh32 = ctx->d_dh32;
     a.gdev = ctx->d_gdev;
     a.at = ctx->d_at;
     a.gd_proj = ctx->gd_proj;
@@ -261,9 +272,13 @@ static StepArgs make_args(rttddft_ctx* ctx, int dv_on) {
     a.hartree = ctx->opt.hartree;
     a.mtg = ctx->d_mtg;
     a.mtw = ctx->d_mtw;
+    a.mtv = ctx->d_mtv;
+    a.mtv_stride = ctx->mtv_stride;
     a.mtw_stride = ctx->mtw_stride;
     return a;
 }
+
+static void build_mt_rebuild(rttddft_ctx* ctx);
 
 static StepPlan make_plan(rttddft_ctx* ctx) {
     StepPlan p{};
@@ -307,9 +322,7 @@ static StepPlan make_plan(rttddft_ctx* ctx) {
     p.ev_join = ctx->ev_join;
     p.gd_exp64 = ctx->gd_exp64;
     p.gd_mt1 = ctx->gd_mt1;
-    p.gd_mt2 = ctx->gd_mt2;
-    p.mt_maxna = ctx->mt_maxna;
-    p.mt_maxlo = ctx->mt_maxlo;
+    p.gd_mty = ctx->gd_mty;
     p.td_dens = ctx->td_dens ? ctx->td_dens : ctx->td_op;
     {
         int F[3], fused = 0;
@@ -559,6 +572,7 @@ static void validate(const rttddft_system* s, const rttddft_options* o) {
             fail(ctx, RTTDDFT_ERR_UNSUPPORTED, "the Hartree feedback needs the FFT interstitial route");
         if (!(o->hartree_bound > 0.0) || !std::isfinite(o->hartree_bound))
             fail(ctx, RTTDDFT_ERR_ARG, "hartree_bound must be positive");
+        if (!std::isfinite(o->hartree_mt_u)) fail(ctx, RTTDDFT_ERR_NONFINITE, "hartree_mt_u not finite");
         double r2 = 0.0;
         for (int i = 0; i < 9; ++i) {
             if (!std::isfinite(s->recip[i])) fail(ctx, RTTDDFT_ERR_NONFINITE, "recip not finite");
@@ -593,6 +607,7 @@ void rttddft_default_options(rttddft_options* opt) {
     opt->interstitial = RTTDDFT_INTERSTITIAL_TOEPLITZ;
     opt->hartree = 0;
     opt->hartree_bound = 0.1;
+    opt->hartree_mt_u = 0.0;
 }
 
 const char* rttddft_version(void) { return "rttddft-gb300 0.1 (sm_103a)"; }
@@ -860,7 +875,8 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
             int dev = 0, smax = 0;
             CK(cudaGetDevice(&dev));
             CK(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-            const size_t need = (size_t)BT * 8 * sizeof(zd) + BT * sizeof(int) + (size_t)wm * sizeof(zd);
+            const size_t cb = o->precision == RTTDDFT_PREC_FP64 ? sizeof(zd) : sizeof(zf);  // the form's table entries
+            const size_t need = (size_t)BT * 8 * cb + BT * sizeof(int) + (size_t)wm * cb;
             // RTTDDFT_TOEP_GATHER=1 in the environment takes the gather path at any size (tests)
             const char* force = getenv("RTTDDFT_TOEP_GATHER");
             if (need + 1024 > (size_t)smax || (force && force[0] == '1')) {
@@ -1216,34 +1232,26 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
         if (o->precision != RTTDDFT_PREC_FP64 && at.n > 0 && ns >= ZT_MIN_N) {
             ctx->d_mtg = dalloc<zf>(ctx, 5 * ctx->nblk);
             ctx->mtw_stride = 5 * ctx->maxm * ns;
+            ctx->mtv_stride = ctx->maxm * ns;
             ctx->d_mtw = dalloc<zd>(ctx, (size_t)nk * at.n * ctx->mtw_stride);
-            std::vector<GemmDesc> m1, m2;
+            ctx->d_mtv = dalloc<zd>(ctx, (size_t)nk * at.n * ctx->mtv_stride);
+            std::vector<GemmDesc> m1;
             for (int k = 0; k < nk; ++k) {
-                const KDev& K = ctx->hkd[k];
                 for (int al = 0; al < at.n; ++al) {
-                    const int m = at.m[al], na = at.na[al];
-                    zd* W = ctx->d_mtw + ((size_t)k * at.n + al) * ctx->mtw_stride;
+                    const int m = at.m[al];
                     GemmDesc d{};
                     d.A = ctx->d_mtg + 5 * at.boff[al];
-                    d.B = K.Q + at.aoff[al];
-                    d.C = W;
+                    d.B = ctx->d_mtv + ((size_t)k * at.n + al) * ctx->mtv_stride;
+                    d.C = ctx->d_mtw + ((size_t)k * at.n + al) * ctx->mtw_stride;
                     d.M = 5 * m;
-                    d.K = na;
+                    d.K = m;
                     d.lda = 5 * m;
-                    d.ldb = std::max(at.ma, 1);
+                    d.ldb = m;
                     d.ldc = 5 * m;
                     m1.push_back(d);
-                    d.A = ctx->d_mtg + 5 * at.boff[al] + (size_t)na * 5 * m;
-                    d.B = K.C + K.ng + at.looff[al];
-                    d.K = at.nlo[al];
-                    d.ldb = K.nb;
-                    m2.push_back(d);
-                    ctx->mt_maxna = std::max(ctx->mt_maxna, na);
-                    ctx->mt_maxlo = std::max(ctx->mt_maxlo, at.nlo[al]);
                 }
             }
             ctx->gd_mt1 = upload_descs(ctx, m1);
-            ctx->gd_mt2 = upload_descs(ctx, m2);
         }
         {
             StepArgs a = make_args(ctx, 0);
@@ -1348,6 +1356,34 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
                 ctx->gd_dvi32 = upload_descs(ctx, g32);
                 ctx->d_part_dv = dalloc<zd>(ctx, off);
             }
+            if (o->hartree_mt_u != 0.0 && at.n > 0) {
+                // the muffin-tin part: dh = U (n - n0) per atom, rebuilt into dVV by the
+                // four-block form like a prescribed change (s = 1)
+                ctx->d_dh = dalloc<zd>(ctx, ctx->nblk);
+                CK(cudaMemset(ctx->d_dh, 0, ctx->nblk * sizeof(zd)));
+                ctx->d_mtn0 = dalloc<zd>(ctx, ctx->nblk);
+                ctx->d_mty = dalloc<zd>(ctx, (size_t)nk * at.lrows * ns);
+                ctx->d_mt_lnorm = dalloc<double>(ctx, at.n);
+                ctx->d_mt_fn2 = dalloc<double>(ctx, at.n);
+                CK(cudaMemset(ctx->d_mt_lnorm, 0, at.n * sizeof(double)));
+                CK(cudaMemset(ctx->d_mt_fn2, 0, at.n * sizeof(double)));
+                build_mt_rebuild(ctx);
+                if (ctx->d_dh32) CK(cudaMemset(ctx->d_dh32, 0, ctx->nblk * sizeof(zf)));
+                std::vector<GemmDesc> gy;
+                for (int k = 0; k < nk; ++k) {
+                    GemmDesc d{};
+                    d.A = ctx->hkd[k].lloc;
+                    d.B = ctx->hkd[k].theta;
+                    d.C = ctx->d_mty + (size_t)k * at.lrows * ns;
+                    d.M = at.lrows;
+                    d.K = naux;
+                    d.lda = at.lrows;
+                    d.ldb = naux;
+                    d.ldc = at.lrows;
+                    gy.push_back(d);
+                }
+                ctx->gd_mty = upload_descs(ctx, gy);
+            }
             CK(cudaMemcpy(ctx->d_kd, ctx->hkd.data(), nk * sizeof(KDev), cudaMemcpyHostToDevice));
             for (int k = 0; k < nk; ++k) ctx->dvnorm[k] = o->hartree_bound;
             ctx->dv_set = true;
@@ -1364,6 +1400,11 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
                     launch_split_reduce(p.gd_expand, nk, p.maxnb, ns, p.kc_expand, p.part, 0, ctx->stream);
             }
             launch_fft_density(ctx->fft, p.td_dens, nk, ns, a.occ, a.wk, 1, ctx->stream);
+            if (ctx->d_mtn0) {
+                // the reference muffin-tin densities of theta(0) and the bound's factors
+                launch_mt_feedback(a, p, 1, nullptr, ctx->stream);
+                launch_mt_lnorm(a, ctx->stream);
+            }
             KCHECK();
         }
         CK(cudaStreamSynchronize(ctx->stream));
@@ -1717,6 +1758,64 @@ int rttddft_get_info(rttddft_ctx* ctx, rttddft_info* info) {
     return RTTDDFT_OK;
 }
 
+}  // extern "C"
+
+// The muffin-tin four blocks of the potential-change rebuild (Eq. v_MT):
+// W = dh L per atom and dVV = L^H W per k-point, with L the atoms' rows of the
+// local coordinates of CC; FP32 copies of dh and L for the reduced-precision
+// forms.  Allocates the per-k W buffers; d_dh and the K.dvsub must exist.
+static void build_mt_rebuild(rttddft_ctx* ctx) {
+    const AtomTab& at = ctx->at;
+    const int nk = ctx->nk, naux = ctx->naux;
+    size_t nblk = 0;
+    for (int a = 0; a < at.n; ++a) nblk += (size_t)at.m[a] * at.m[a];
+    std::vector<GemmDesc> w, g;
+    for (int k = 0; k < nk; ++k) {
+        KDev& K = ctx->hkd[k];
+        zd* W = dalloc<zd>(ctx, (size_t)std::max(at.lrows, 1) * naux);
+        for (int a = 0; a < at.n; ++a) {
+            GemmDesc d{};
+            d.A = ctx->d_dh + at.boff[a];
+            d.B = K.lloc + at.loff[a];
+            d.C = W + at.loff[a];
+            d.M = at.m[a];
+            d.K = at.m[a];
+            d.lda = at.m[a];
+            d.ldb = at.lrows;
+            d.ldc = at.lrows;
+            w.push_back(d);
+        }
+        GemmDesc d{};
+        d.A = K.lloc;
+        d.B = W;
+        d.C = K.dvsub;
+        d.M = naux;
+        d.K = at.lrows;
+        d.lda = std::max(at.lrows, 1);
+        d.ldb = std::max(at.lrows, 1);
+        d.ldc = naux;
+        g.push_back(d);
+    }
+    ctx->gd_dvw = upload_descs(ctx, w);
+    ctx->gd_dvg = upload_descs(ctx, g);
+    if (ctx->opt.precision != RTTDDFT_PREC_FP64 && at.n > 0) {
+        // reduced-precision forms: W = (s dh) L and L^H W on the FP32 tiled
+        // kernels, from FP32 copies of dh and of the local coordinates L
+        ctx->d_dh32 = dalloc<zf>(ctx, nblk);
+        std::vector<GemmDesc> w32 = w, g32 = g;
+        for (auto& d : w32) d.A = ctx->d_dh32 + ((const zd*)d.A - ctx->d_dh);
+        for (int k = 0; k < nk; ++k) {
+            zf* l32 = dalloc<zf>(ctx, (size_t)at.lrows * naux);
+            launch_convert_f32(ctx->hkd[k].lloc, l32, (size_t)at.lrows * naux, ctx->stream);
+            g32[k].A = l32;
+        }
+        ctx->gd_dvw32 = upload_descs(ctx, w32);
+        ctx->gd_dvg32 = upload_descs(ctx, g32);
+    }
+}
+
+extern "C" {
+
 int rttddft_set_dv(rttddft_ctx* ctx, const double* dh, const double* dvtab) {
     if (!ctx) return RTTDDFT_ERR_ARG;
     try {
@@ -1745,37 +1844,14 @@ int rttddft_set_dv(rttddft_ctx* ctx, const double* dh, const double* dvtab) {
             ctx->d_vstep = dalloc<zd>(ctx, ctx->nvt);
             if (ctx->opt.precision != RTTDDFT_PREC_FP64) ctx->d_vstep32 = dalloc<zf>(ctx, ctx->nvt);
             if (ctx->opt.precision >= RTTDDFT_PREC_BF16X3) ctx->d_vsteps = dalloc<uint2>(ctx, ctx->nvt);
-            std::vector<GemmDesc> w, g, gi;
+            std::vector<GemmDesc> gi;
             std::vector<ToepDesc> td;
             for (int k = 0; k < nk; ++k) {
                 KDev& K = ctx->hkd[k];
                 K.dvsub = dalloc<zd>(ctx, (size_t)naux * naux);
-                zd* W = dalloc<zd>(ctx, (size_t)std::max(at.lrows, 1) * naux);
                 zd* T = dalloc<zd>(ctx, (size_t)K.ng * naux);
-                for (int a = 0; a < at.n; ++a) {
-                    GemmDesc d{};
-                    d.A = ctx->d_dh + at.boff[a];
-                    d.B = K.lloc + at.loff[a];
-                    d.C = W + at.loff[a];
-                    d.M = at.m[a];
-                    d.K = at.m[a];
-                    d.lda = at.m[a];
-                    d.ldb = at.lrows;
-                    d.ldc = at.lrows;
-                    w.push_back(d);
-                }
-                GemmDesc d{};
-                d.A = K.lloc;
-                d.B = W;
-                d.C = K.dvsub;
-                d.M = naux;
-                d.K = at.lrows;
-                d.lda = std::max(at.lrows, 1);
-                d.ldb = std::max(at.lrows, 1);
-                d.ldc = naux;
-                g.push_back(d);
                 td.push_back(ToepDesc{K.caux, T, K.nb, K.ng});
-                d = GemmDesc{};
+                GemmDesc d{};
                 d.A = K.caux;
                 d.B = T;
                 d.C = K.dvsub;
@@ -1786,23 +1862,8 @@ int rttddft_set_dv(rttddft_ctx* ctx, const double* dh, const double* dvtab) {
                 d.ldc = naux;
                 gi.push_back(d);
             }
-            ctx->gd_dvw = upload_descs(ctx, w);
-            ctx->gd_dvg = upload_descs(ctx, g);
+            build_mt_rebuild(ctx);
             ctx->gd_dvi = upload_descs(ctx, gi);
-            if (ctx->opt.precision != RTTDDFT_PREC_FP64 && at.n > 0) {
-                // reduced-precision forms: W = (s dh) L and L^H W on the FP32 tiled
-                // kernels, from FP32 copies of dh and of the local coordinates L
-                ctx->d_dh32 = dalloc<zf>(ctx, nblk);
-                std::vector<GemmDesc> w32 = w, g32 = g;
-                for (auto& d : w32) d.A = ctx->d_dh32 + ((const zd*)d.A - ctx->d_dh);
-                for (int k = 0; k < nk; ++k) {
-                    zf* l32 = dalloc<zf>(ctx, (size_t)at.lrows * naux);
-                    launch_convert_f32(ctx->hkd[k].lloc, l32, (size_t)at.lrows * naux, ctx->stream);
-                    g32[k].A = l32;
-                }
-                ctx->gd_dvw32 = upload_descs(ctx, w32);
-                ctx->gd_dvg32 = upload_descs(ctx, g32);
-            }
             ctx->td_dv = dupload(ctx, td.data(), td.size());
             if (ctx->tc && !ctx->fft) {
                 // tensor-core forms: the interstitial convolution on tcgen05
@@ -1908,10 +1969,7 @@ int rttddft_apply(rttddft_ctx* ctx, int k, int ncols, const double* x, const dou
         a.kofs = k;
         StepPlan p = make_plan(ctx);
         p.gd_fwd = ctx->gd_fwd + k;
-        if (p.gd_mt1) {
-            p.gd_mt1 = ctx->gd_mt1 + (size_t)k * ctx->at.n;
-            p.gd_mt2 = ctx->gd_mt2 + (size_t)k * ctx->at.n;
-        }
+        if (p.gd_mt1) p.gd_mt1 = ctx->gd_mt1 + (size_t)k * ctx->at.n;
         p.maxng = K.ng;
         if (dv_on && !ctx->opt.hartree) launch_vstep(a, ctx->stream);
         const zd* xz = (const zd*)x;
@@ -2340,7 +2398,7 @@ extern "C" int rttddft_apply_noalloc(rttddft_ctx* ctx, int k, int ncols, const d
         p.fft = nullptr;
         p.side = nullptr;
         p.tile_cnt = nullptr;  // the context's counters may be in use on another stream
-        p.gd_mt1 = p.gd_mt2 = nullptr;
+        p.gd_mt1 = nullptr;
         p.gd_fwd = (const GemmDesc*)(base + o_gd);
         p.maxng = ng;
         p.part = (zd*)(base + o_part);

@@ -585,6 +585,10 @@ __global__ void k_hartree(const C* __restrict__ N, const C* __restrict__ N0, C* 
     }
 }
 
+// the device accumulator compared with the bound after every step (other parts of
+// the potential change add their own bounds to it before the check)
+double* fft_l1(const FftPlan* pl) { return pl ? pl->l1 : nullptr; }
+
 // the l1 norm of dV against the bound of the spectral interval; flag bit 6
 __global__ void k_hartree_check(double* l1, double bound, int* flag) {
     if (*l1 > bound) atomicOr(flag, 64);

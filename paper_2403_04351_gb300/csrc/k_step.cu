@@ -733,9 +733,9 @@ __global__ void __launch_bounds__(128) k_local_wide(StepArgs a, int rowchunks) {
 // Muffin-tin blocks as GEMMs (FP32 forms, many states).  Per atom the stack
 // G = [h_eff; o; p_x; p_y; p_z] (5m x m, column-major) with
 // h_eff = h + (A/c).p + |A|^2/(2c^2) o (+ s dh) is formed once per step (it
-// does not depend on k); then W = G [Q; C_lo] for every (k, atom) is two
-// batched tiled GEMMs (the Q rows and the local-orbital rows of the
-// right-hand block live in different arrays), and k_mt_epi distributes W:
+// does not depend on k); the right-hand block [Q; C_lo] of every (k, atom) is
+// gathered contiguous, W = G [Q; C_lo] is one batched tiled GEMM, and
+// k_mt_epi distributes W:
 // the h_eff and o rows go to Z (matching rows) or to the LO rows of
 // [HC | SC], and the row's occupation-weighted shares of J (p rows) and of
 // E and c^H S c (LO rows) go to part_jmt as in k_local.
@@ -771,6 +771,21 @@ __global__ void k_mt_form(StepArgs a) {
     }
 }
 
+// the right-hand block [Q_alpha; C_lo,alpha] of every (k, atom), contiguous
+__global__ void k_mt_gather(StepArgs a) {
+    const int k = blockIdx.z, al = blockIdx.y;
+    const AtomTab& at = *a.at;
+    if (al >= at.n) return;
+    const KDev& K = a.kd[k];
+    const int m = at.m[al], na = at.na[al], ns = a.ns;
+    const int aoff = at.aoff[al], lo0 = K.ng + at.looff[al];
+    zd* V = a.mtv + ((size_t)(a.kofs + k) * at.n + al) * a.mtv_stride;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * ns; e += gridDim.x * blockDim.x) {
+        const int i = e % m, c = e / m;
+        V[e] = (i < na) ? K.Q[aoff + i + (size_t)c * at.ma] : K.C[lo0 + (i - na) + (size_t)c * K.nb];
+    }
+}
+
 __global__ void __launch_bounds__(128) k_mt_epi(StepArgs a) {
     const int k = blockIdx.z, al = blockIdx.y;
     const AtomTab& at = *a.at;
@@ -781,13 +796,15 @@ __global__ void __launch_bounds__(128) k_mt_epi(StepArgs a) {
     const KDev& K = a.kd[k];
     const int ns = a.ns, nb = K.nb, ma = at.ma, ng = K.ng;
     const int aoff = at.aoff[al], lo0 = ng + at.looff[al];
-    const zd* W = a.mtw + ((size_t)(a.kofs + k) * at.n + al) * a.mtw_stride;  // kofs: single-k operator calls
+    const size_t ent = (size_t)(a.kofs + k) * at.n + al;  // kofs: single-k operator calls
+    const zd* W = a.mtw + ent * a.mtw_stride;
+    const zd* V = a.mtv + ent * a.mtv_stride;
     const size_t ld = (size_t)5 * m;
     double jc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int c = 0; c < ns; ++c) {
         const zd* w = W + (size_t)c * ld;
         const zd zh = w[i], zs = w[m + i];
-        const zd x = (i < na) ? K.Q[aoff + i + (size_t)c * ma] : K.C[lo0 + (i - na) + (size_t)c * nb];
+        const zd x = V[i + (size_t)c * m];
         const double f = a.occ[c];
         if (i < na) {
             K.Z[aoff + i + (size_t)c * ma] = zh;
@@ -812,15 +829,10 @@ __global__ void __launch_bounds__(128) k_mt_epi(StepArgs a) {
 
 static int launch_mt_gemm(const StepArgs& a, const StepPlan& p, cudaStream_t s) {
     k_mt_form<<<dim3(64, a.at_n), 256, 0, s>>>(a);
-    const int n = a.nk * a.at_n;
-    launch_gemm_nn(p.gd_mt1, n, 5 * a.at_maxm, p.mt_maxna, a.ns, 0, nullptr, 0, true, nullptr, s);
-    int nl = 2;
-    if (p.mt_maxlo > 0) {
-        launch_gemm_nn(p.gd_mt2, n, 5 * a.at_maxm, p.mt_maxlo, a.ns, 0, nullptr, 1, true, nullptr, s);
-        ++nl;
-    }
+    k_mt_gather<<<dim3((a.at_maxm * a.ns + 255) / 256, a.at_n, a.nk), 256, 0, s>>>(a);
+    launch_gemm_nn(p.gd_mt1, a.nk * a.at_n, 5 * a.at_maxm, a.at_maxm, a.ns, 0, nullptr, 0, true, nullptr, s);
     k_mt_epi<<<dim3((a.at_maxm + 127) / 128, a.at_n, a.nk), 128, 0, s>>>(a);
-    return nl + 1;
+    return 4;
 }
 
 // Plane-wave rows of H C and S C in independent partial sums, one block per
@@ -1870,10 +1882,10 @@ static size_t toep_smem(const StepArgs& a, size_t tc, size_t tt) {
 
 template <typename TA, typename TT, typename TC, int NT>
 static int back_launch(const StepArgs& a, int maxng, cudaStream_t s, TraceHook* tr, cudaEvent_t join) {
-    const size_t sm = toep_smem<NT>(a, sizeof(TC), sizeof(TT));
     // in the tensor-core form the interstitial slots are done already: only
-    // the back-projection slots run here
+    // the back-projection slots run here, and they need no table window
     const int slot0 = a.ith ? a.nseg : 0;
+    const size_t sm = slot0 ? (size_t)a.msegw * 2 * NT * sizeof(TC) : toep_smem<NT>(a, sizeof(TC), sizeof(TT));
     // with the back-projection on the tensor cores too, no slot kernel runs
     dim3 gt((maxng + BT - 1) / BT, a.tcback ? 0 : a.nslot - slot0, a.nk);
     dim3 gb((maxng + BKB - 1) / BKB, 1, a.nk);
@@ -1928,8 +1940,13 @@ int prepare_back_kernels(const StepArgs& a) {
         }                                                                                            \
         ++slot;                                                                                      \
     }
-    RTD_SET(zd, zd, zd, 2) RTD_SET(zd, zd, zd, 4) RTD_SET(zd, zd, zd, 8)
-    RTD_SET(zf, zf, zf, 2) RTD_SET(zf, zf, zf, 4) RTD_SET(zf, zf, zf, 8)
+    // only the instances of the context's form (FP64 entries, or FP32 ones)
+    if (a.prec == 0) {
+        RTD_SET(zd, zd, zd, 2) RTD_SET(zd, zd, zd, 4) RTD_SET(zd, zd, zd, 8)
+    } else {
+        slot = 3;
+        RTD_SET(zf, zf, zf, 2) RTD_SET(zf, zf, zf, 4) RTD_SET(zf, zf, zf, 8)
+    }
 #undef RTD_SET
     return 0;
 }
@@ -2033,20 +2050,31 @@ int launch_operator_pass(const StepArgs& a, const StepPlan& p, cudaStream_t s, T
 // FP32; otherwise both in FP64.  Returns the launches.
 static int launch_dv_rebuild(const StepArgs& a, const StepPlan& p, cudaStream_t s, TraceHook* tr) {
     if (a.hartree) {
-        // the Hartree potential of the density has no muffin-tin part:
-        // dVV = CC_G^H (dV~ * CC_G) with dV~ from the previous step's density
+        // dVV = [sum_a L^H dh_a L] + CC_G^H (dV~ * CC_G) with dV~ (and dh, when the
+        // muffin-tin part is on) from the previous step's density
+        int nl = 0, beta = 0;
+        if (a.mt_u != 0.0 && p.gd_dvw) {
+            const bool mt32 = a.prec >= 1 && p.gd_dvw32 && p.gd_dvg32;
+            launch_gemm_nn(mt32 ? p.gd_dvw32 : p.gd_dvw, p.n_dvw, p.maxm, p.maxm, a.naux, 0, nullptr, 0, mt32,
+                           &a.st->cur_s, s);
+            launch_gemm_cn(mt32 ? p.gd_dvg32 : p.gd_dvg, a.nk, a.naux, a.lrows, a.naux, 0, nullptr, 0, mt32, nullptr,
+                           s);
+            mark(tr, "hartree_mt_blocks", s);
+            nl += 2;
+            beta = 1;
+        }
         launch_fft_conv(p.fft, p.td_dv, a.kofs, a.nk, a.naux, 1, 1, &a.st->cur_s, s);
         mark(tr, "hartree_interstitial_fft", s);
         if (p.gd_dvi32) {
             // FP32 form: CC_G^H T streaming the FP32 copy of CC, FP64 sums of the K slices
             launch_gemm_cn(p.gd_dvi32, a.nk, a.naux, p.maxng, a.naux, p.kc_dvi, p.part_dv, 0, true, nullptr, s);
-            launch_split_reduce(p.gd_dvi32, a.nk, a.naux, a.naux, p.kc_dvi, p.part_dv, 0, s);
+            launch_split_reduce(p.gd_dvi32, a.nk, a.naux, a.naux, p.kc_dvi, p.part_dv, beta, s);
             mark(tr, "hartree_project", s);
-            return 1;
+            return nl + 1;
         }
-        launch_gemm_cn(p.gd_dvi, a.nk, a.naux, p.maxng, a.naux, 0, nullptr, 0, false, nullptr, s);
+        launch_gemm_cn(p.gd_dvi, a.nk, a.naux, p.maxng, a.naux, 0, nullptr, beta, false, nullptr, s);
         mark(tr, "hartree_project", s);
-        return 0;  // counted by the caller with the FFT launches
+        return nl;  // the FFT launches are counted by the caller
     }
     // the muffin-tin four blocks: FP32 in the reduced-precision forms, FP64 otherwise
     const bool mt32 = a.prec >= 1 && p.gd_dvw32 && p.gd_dvg32;
@@ -2176,6 +2204,7 @@ void launch_step(const StepArgs& a, const StepPlan& p, cudaStream_t s, int* nlau
             launch_gemm_nn(p.gd_exp64, a.nk, p.maxnb, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
             ++nl;
         }
+        if (a.mt_u != 0.0 && p.gd_mty) nl += launch_mt_feedback(a, p, 0, fft_l1(p.fft), s);
         nl += launch_fft_hartree(p.fft, p.td_dens, a.nk, a.ns, a.occ, a.wk, a.flag, s);
         mark(tr, "hartree_density_poisson", s);
     }
@@ -2236,3 +2265,102 @@ void launch_hsub_only(const StepArgs& a, const StepPlan& p, int cstep, cudaStrea
 
 // J contributions of the current theta (rows into part_post[.][1..3])
 void launch_subspace_j(const StepArgs& a, cudaStream_t s) { launch_post(a, 0, 1, s); }
+
+// ------------------------------------------------------------ muffin-tin density feedback
+// Per atom the density matrix of its matching and local-orbital channels,
+// n_a = sum_k w_k sum_j f_j y_kaj y_kaj^H with y = the atom's rows of the
+// state's local coordinates L theta (FP64: L = E_a CC from set-up, theta the
+// FP64 state), one thread per entry (i, j) of the atom's m x m block.
+// reference: store n_a as n0; otherwise dh_a = U (n_a - n0_a) (and its FP32
+// copy), with sum |dh_a|^2 per atom added to mt_fn2 for the bound.
+__global__ void k_mt_density(StepArgs a, int reference) {
+    __shared__ double red[8];
+    const AtomTab& at = *a.at;
+    const int al = blockIdx.y;
+    if (al >= at.n) return;
+    const int m = at.m[al], lr = a.lrows, ns = a.ns;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (e < m * m) {
+        const int i = e % m, j = e / m;
+        const int ri = at.loff[al] + i, rj = at.loff[al] + j;
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k < a.nk; ++k) {
+            const zd* Y = a.mty + (size_t)k * lr * ns;
+            double kr = 0.0, ki = 0.0;
+            for (int c = 0; c < ns; ++c) {
+                const zd yi = Y[ri + (size_t)c * lr], yj = Y[rj + (size_t)c * lr];
+                const double f = a.occ[c];
+                kr += f * (yi.x * yj.x + yi.y * yj.y);  // yi conj(yj)
+                ki += f * (yi.y * yj.x - yi.x * yj.y);
+            }
+            re += a.wk[k] * kr;
+            im += a.wk[k] * ki;
+        }
+        const size_t idx = at.boff[al] + i + (size_t)j * m;
+        if (reference) {
+            ((zd*)a.mtn0)[idx] = zmk(re, im);
+        } else {
+            const zd n0 = a.mtn0[idx];
+            const zd d = zmk(a.mt_u * (re - n0.x), a.mt_u * (im - n0.y));
+            ((zd*)a.dh)[idx] = d;
+            if (a.dh32) a.dh32[idx] = tof(d);
+            sq = d.x * d.x + d.y * d.y;
+        }
+    }
+    if (reference) return;
+    sq = warp_sum(sq);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        atomicAdd(a.mt_fn2 + al, t);  // only compared with a bound: the order does not matter
+    }
+}
+// sum_a ||dh_a||_F max_k ||L_ka||_F^2 >= ||sum_a L_ka^H dh_a L_ka||_2 added to the
+// accumulator that the step compares with the Chebyshev interval's bound
+__global__ void k_mt_bound(StepArgs a, double* l1) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double b = 0.0;
+    for (int al = 0; al < a.at->n; ++al) {
+        b += sqrt(a.mt_fn2[al]) * a.mt_lnorm[al];
+        a.mt_fn2[al] = 0.0;
+    }
+    *l1 += b;
+}
+// per atom max_k ||L_ka||_F^2 (set-up), as the integer maximum of non-negative doubles
+__global__ void k_mt_lnorm(StepArgs a) {
+    __shared__ double red[8];
+    const AtomTab& at = *a.at;
+    const int al = blockIdx.y, k = blockIdx.z;
+    if (al >= at.n) return;
+    const KDev& K = a.kd[k];
+    const int m = at.m[al], n = a.naux;
+    double sq = 0.0;
+    for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
+        const zd v = K.lloc[at.loff[al] + e % m + (size_t)(e / m) * a.lrows];
+        sq += v.x * v.x + v.y * v.y;
+    }
+    sq = warp_sum(sq);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        atomicMax((unsigned long long*)(a.mt_lnorm + al), (unsigned long long)__double_as_longlong(t));
+    }
+}
+
+int launch_mt_feedback(const StepArgs& a, const StepPlan& p, int reference, double* l1, cudaStream_t s) {
+    // the state's local coordinates L theta (FP64, every k)
+    launch_gemm_nn(p.gd_mty, a.nk, a.lrows, a.naux, a.ns, 0, nullptr, 0, false, nullptr, s);
+    const int mm = a.at_maxm * a.at_maxm;
+    k_mt_density<<<dim3((mm + 255) / 256, a.at_n), 256, 0, s>>>(a, reference);
+    if (reference) return 2;
+    k_mt_bound<<<1, 32, 0, s>>>(a, l1);
+    return 3;
+}
+void launch_mt_lnorm(const StepArgs& a, cudaStream_t s) { k_mt_lnorm<<<dim3(1, a.at_n, a.nk), 256, 0, s>>>(a); }

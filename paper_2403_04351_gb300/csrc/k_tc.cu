@@ -737,17 +737,16 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
         }
         __syncwarp();
     } else if (!*ab) {
-        // generators: thread (r, h) writes row r, G' 16h .. 16h+15 of every K block
+        // generators: thread (r, h) writes row r, G' 16h .. 16h+15 of every K block.
+        // The table entries of block j + 1 are fetched before block j is written, so
+        // that their latency (L1/L2 in the gather form) overlaps the permutes and stores.
         const int r = tid & (TC_BM - 1), h = tid >> 7;
         const int g = row0 + r;
         const bool valid = g < ng;
         const int lb = (valid ? K.glin[g] : 0) + p.vt_center - wlo;
         const uint32_t sw = (uint32_t)(r & 7);
-        for (int j = 0; j < nk; ++j) {
-            const int sa = j % SA;
-            if (j >= SA && !mbar_wait_ab(&emptyA[sa], (uint32_t)(((j / SA) - 1) & 1), ab)) break;
+        auto fetch = [&](int j, uint2* u) {
             const int gq = (kb0 + j) * 32 + 16 * h;
-            uint2 u[16];
             if (valid && gq + 16 <= gp_hi) {
                 const int4* g4 = (const int4*)(gl_s + (gq - gp_lo));
 #pragma unroll
@@ -777,6 +776,10 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
                     }
                 }
             }
+        };
+        auto store = [&](int j, const uint2* u) -> bool {
+            const int sa = j % SA;
+            if (j >= SA && !mbar_wait_ab(&emptyA[sa], (uint32_t)(((j / SA) - 1) & 1), ab)) return false;
             unsigned char* rowp = ringA + (size_t)sa * 2 * A_BYTES + r * 128;
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
@@ -798,6 +801,18 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&fullA[sa]);
+            return true;
+        };
+        // two register sets in turn: the loads of one block stay in flight while
+        // the previous block is written
+        uint2 u0[16], u1[16];
+        fetch(0, u0);
+        for (int j = 0; j < nk; j += 2) {
+            if (j + 1 < nk) fetch(j + 1, u1);
+            if (!store(j, u0)) break;
+            if (j + 1 >= nk) break;
+            if (j + 2 < nk) fetch(j + 2, u0);
+            if (!store(j + 1, u1)) break;
         }
     }
     __syncthreads();

@@ -149,12 +149,19 @@ struct StepArgs {
     int hartree;              // the potential change is the Hartree potential of the density (FFT route)
     int cheb_tile;            // the cooperative series runs as k_cheb_tile (4 < N_s <= 64)
     double tc_st;             // scale of the split table (fp16 range)
+    double mt_u;              // muffin-tin part of the density feedback: dh = mt_u (n - n0) (0: off)
+    const zd* mtn0;           //   reference muffin-tin density matrices n_a(0) (atom blocks at boff)
+    zd* mty;                  //   per k the local coordinates L theta of the state (lrows x ns)
+    const double* mt_lnorm;   //   per atom max_k ||L_ka||_F^2 (the bound's factor)
+    double* mt_fn2;           //   per atom ||dh_a||_F^2 of the step (accumulated, reset by k_mt_bound)
+    zf* dh32;                 //   FP32 copy of dh (reduced-precision rebuild)
     double* part_fin;         // [nk][FIN_CH][FIN_STRIDE] first-phase sums of the step's reductions
     double* gdev;             // [nk][ns] largest |C^H S C - I| per column (many states)
     int toep_global;          // the direct sum gathers the table through L1/L2 into K.th (window too large)
     zf* mtg;                  // muffin-tin products as GEMMs: per atom the 5m x m stack [h_eff; o; p_x; p_y; p_z]
     zd* mtw;                  //   per (k, atom) its product with [Q; C_lo] (5m x N_s, stride mtw_stride)
-    int mtw_stride;
+    zd* mtv;                  //   per (k, atom) the gathered [Q; C_lo] (m x N_s, stride mtv_stride)
+    int mtw_stride, mtv_stride;
 };
 #define ZT_MIN_N 16           // columns from which the FP32 contractions take the 64 x 64 tiled kernel
 #define JRHO_MIN_NS 8         // above this many states the subspace current goes through rho = theta F theta^H
@@ -211,8 +218,8 @@ struct StepPlan {
     const ToepDesc* td_dens;    // per k: the C the density is taken from
     cudaEvent_t ev_fork, ev_join;
     const ToepDesc* td_op;      // per k: {C, th}: the operator's convolution source and destination
-    const GemmDesc *gd_mt1, *gd_mt2;  // per (k, atom): [h_eff; o; p] times Q, then times C_lo (or null)
-    int mt_maxna, mt_maxlo;
+    const GemmDesc* gd_mt1;     // per (k, atom): [h_eff; o; p] times the gathered [Q; C_lo] (or null)
+    const GemmDesc* gd_mty;     // per k: L theta, the state's local coordinates (muffin-tin feedback) or null
 };
 // Optional per-kernel tracing: an event is recorded after every launch of a step.
 struct TraceHook {
@@ -245,6 +252,9 @@ void launch_scale_cols(zd* const* mats, const double* const* vals, int nbatch, i
 void launch_propagate_only(const StepArgs& a, const StepPlan& p, int cstep, cudaStream_t s);
 void launch_hsub_only(const StepArgs& a, const StepPlan& p, int cstep, cudaStream_t s);
 void launch_subspace_j(const StepArgs& a, cudaStream_t s);
+// muffin-tin density matrices of theta: the reference n0 (set-up) or dh = U (n - n0) and its bound term
+int launch_mt_feedback(const StepArgs& a, const StepPlan& p, int reference, double* l1, cudaStream_t s);
+void launch_mt_lnorm(const StepArgs& a, cudaStream_t s);
 void launch_adj_fwd_term(const StepArgs& a, zd* Yh, int nterm, int nt, cudaStream_t s);
 void launch_adj_bwd_init(const StepArgs& a, zd* Yb, const zd* lam, int nterm, cudaStream_t s);
 void launch_adj_bwd_term(const StepArgs& a, zd* Yb, int nterm, int nt, cudaStream_t s);
@@ -271,6 +281,7 @@ int fft_hartree_init(FftPlan* pl, const double recip[9], const int vt_dim[3], do
                      cudaStream_t st, std::string* why);
 int launch_fft_density(const FftPlan* pl, const ToepDesc* td, int nk, int ns, const double* occ, const double* wk,
                        int reference, cudaStream_t st);
+double* fft_l1(const FftPlan* pl);
 int launch_fft_hartree(const FftPlan* pl, const ToepDesc* td, int nk, int ns, const double* occ, const double* wk,
                        int* flag, cudaStream_t st);
 int launch_fft_conv(const FftPlan* pl, const ToepDesc* td, int kofs, int nk, int ncol, int vmode, int use_vd,

@@ -51,7 +51,7 @@ class rttddft_options(ctypes.Structure):
                 ("cheb_tol", ctypes.c_double), ("ortho_tol", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int), ("a_max", ctypes.c_double),
                 ("s_max", ctypes.c_double), ("interstitial", ctypes.c_int), ("hartree", ctypes.c_int),
-                ("hartree_bound", ctypes.c_double)]
+                ("hartree_bound", ctypes.c_double), ("hartree_mt_u", ctypes.c_double)]
 
 
 class rttddft_obs(ctypes.Structure):
@@ -279,7 +279,7 @@ class Context:
     def __init__(self, sys, dt=None, propagator="chebyshev", precision="fp64", reproject=False,
                  aux_mode="ritz", caux=None, eps=None, c0=None, max_record=4096, graph_steps=1,
                  cheb_tol=1e-16, stream=None, max_sweeps=30, a_max=0.0, s_max=0.0,
-                 interstitial="toeplitz", hartree=False, hartree_bound=None):
+                 interstitial="toeplitz", hartree=False, hartree_bound=None, hartree_mt_u=0.0):
         self.n_k = int(sys["n_k"])
         self.n_s = int(sys["n_s"])
         self.n_aux = int(sys["n_aux"]) if caux is None else int(np.asarray(caux[0]).shape[1])
@@ -329,6 +329,7 @@ class Context:
         o.hartree = int(bool(hartree))
         if hartree_bound is not None:
             o.hartree_bound = float(hartree_bound)
+        o.hartree_mt_u = float(hartree_mt_u)
         self.options = o
         self.max_record = int(max_record)
         self._stream = stream

@@ -89,11 +89,13 @@ extern "C" {
  * evaluated (Sec. 3: matrix products against FFTs) */
 #define RTTDDFT_INTERSTITIAL_TOEPLITZ 0 /* direct sum over G' with V~_{G-G'} generated from the table */
 /* circular convolution on a grid of F_i >= vt_dim[i] points per axis (the
- * smallest products of 2, 3 and 5, at most 128): pruned inverse and forward
+ * smallest products of 2, 3 and 5, at most 512): pruned inverse and forward
  * 3-D FFTs around a product with the table's real-space image, FP64 in the
  * FP64 form and FP32 in the others (the split forms keep the matching-
  * coefficient products on the tensor cores); ERR_UNSUPPORTED when an axis
- * needs more than 128 points.  Equal to the direct sum up to rounding. */
+ * needs more than 512 points, ERR_OOM when the transform buffers (N_aux
+ * columns of the planes holding a G, per k-point) do not fit.  Equal to the
+ * direct sum up to rounding. */
 #define RTTDDFT_INTERSTITIAL_FFT 1
 
 /* how the auxiliary basis CC(0) is obtained at set-up */
@@ -206,6 +208,8 @@ typedef struct {
     int interstitial;      /* RTTDDFT_INTERSTITIAL_* of the context */
     int fft_grid[3];       /* FFT route: grid points per axis (0 otherwise) */
     int fft_fused;         /*   1: a plane's two in-plane axes in one launch (chosen at set-up by timing) */
+    int tc_gen_threads;    /* split forms: threads generating the interstitial operand per block (256 or 512) */
+    int tc_a_tmem;         /*   1: that operand is written to tensor memory (0: shared memory) */
 } rttddft_info;
 
 RTTDDFT_API void rttddft_default_options(rttddft_options* opt);

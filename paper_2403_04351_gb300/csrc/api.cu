@@ -1742,7 +1742,7 @@ int rttddft_get_info(rttddft_ctx* ctx, rttddft_info* info) {
     info->dt_cr0 = ctx->dtcr0;
     info->kernel_launches_per_step = ctx->launches_per_step;
     info->precision = ctx->opt.precision;
-    int v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int v[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (ctx->tc) tc_plan_info(ctx->tc, v);
     info->tc_candidates = v[6];
     info->tc_interstitial_ns = v[7];
@@ -1753,6 +1753,8 @@ int rttddft_get_info(rttddft_ctx* ctx, rttddft_info* info) {
     info->tc_slices = v[3];
     info->tc_window = v[4];
     info->tc_smem = v[5];
+    info->tc_gen_threads = v[9];
+    info->tc_a_tmem = v[10];
     info->interstitial = ctx->opt.interstitial;
     fft_plan_info(ctx->fft, info->fft_grid, &info->fft_fused);
     return RTTDDFT_OK;

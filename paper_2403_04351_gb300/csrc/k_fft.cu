@@ -31,11 +31,16 @@
 #include <string>
 #include <vector>
 
-#define FFT_LPB 16      // lines per block
+#define FFT_LPB 16        // lines per block at most
+#define FFT_BLK_PTS 2048  // points of a line block at most: lines per block = min(16, 2048 / L)
 #define FFT_THREADS 128
+#define FFT_PV (FFT_BLK_PTS / FFT_THREADS)  // points of a block per thread
 #define FFT_PTHREADS 256  // plane kernels
-#define FFT_MAX_N 128   // longest axis
+#define FFT_MAX_N 512     // longest axis
 #define FFT_MAX_ST 8
+
+// lines of length L per block of a line pass
+static inline int fft_lpb(int L) { return std::min(FFT_LPB, FFT_BLK_PTS / std::max(L, 1)); }
 
 struct FftK {
     int nline, nplane;
@@ -52,6 +57,7 @@ struct FftArgs {
     int F1, F2, F3;
     int nst[3];
     int rad[3][FFT_MAX_ST];
+    int lpb[3];             // lines per block of the passes along each axis
     const void* w[3];       // twiddles e^{-2 pi i m / F_a}, m < F_a (FP64 or FP32 complex)
     const FftK* fk;         // per k-point of the launch
     const ToepDesc* td;     // per k-point: source X (ld ldx) and destination Y (ld ldy)
@@ -219,15 +225,15 @@ __device__ __forceinline__ void load_tw(C* W, const void* src, int L) {
 template <typename C>
 __global__ void __launch_bounds__(FFT_THREADS) k_fft_a(FftArgs f) {
     extern __shared__ __align__(16) unsigned char fsm[];
-    const int F3 = f.F3;
+    const int F3 = f.F3, LPB = f.lpb[2];
     C* W = (C*)fsm;
     C* x = W + F3;
-    C* y = x + FFT_LPB * F3;
+    C* y = x + LPB * F3;
     const int k = blockIdx.z, c = blockIdx.y;
     const FftK K = f.fk[k];
-    const int l0 = blockIdx.x * FFT_LPB;
+    const int l0 = blockIdx.x * LPB;
     if (l0 >= K.nline) return;
-    const int nl = min(FFT_LPB, K.nline - l0);
+    const int nl = min(LPB, K.nline - l0);
     load_tw(W, f.w[2], F3);
     for (int i = threadIdx.x; i < nl * F3; i += blockDim.x) x[i] = cmk<C>(0, 0);
     __syncthreads();
@@ -243,20 +249,20 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_a(FftArgs f) {
 }
 
 // B (fwd = 0) and D (fwd = 1): axis 2 on the planes holding a G; a block
-// takes FFT_LPB consecutive r3 of one plane
+// takes lpb[1] consecutive r3 of one plane
 template <typename C>
 __global__ void __launch_bounds__(FFT_THREADS) k_fft_bd(FftArgs f, int fwd) {
     extern __shared__ __align__(16) unsigned char fsm[];
-    const int F2 = f.F2, F3 = f.F3;
+    const int F2 = f.F2, F3 = f.F3, LPB = f.lpb[1];
     C* W = (C*)fsm;
     C* x = W + F2;
-    C* y = x + FFT_LPB * F2;
+    C* y = x + LPB * F2;
     const int k = blockIdx.z, c = blockIdx.y;
     const FftK K = f.fk[k];
-    const int nch = (F3 + FFT_LPB - 1) / FFT_LPB;
-    const int p = blockIdx.x / nch, i30 = (blockIdx.x - p * nch) * FFT_LPB;
+    const int nch = (F3 + LPB - 1) / LPB;
+    const int p = blockIdx.x / nch, i30 = (blockIdx.x - p * nch) * LPB;
     if (p >= K.nplane) return;
-    const int nl = min(FFT_LPB, F3 - i30);
+    const int nl = min(LPB, F3 - i30);
     load_tw(W, f.w[1], F2);
     C* b3 = (C*)f.b3 + ((size_t)k * f.ncol + c) * f.b3_col;
     C* b2 = (C*)f.b2 + ((size_t)k * f.ncol + c) * f.b2_col + (size_t)p * F2 * F3;
@@ -290,15 +296,15 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_bd(FftArgs f, int fwd) {
 template <typename C>
 __global__ void __launch_bounds__(FFT_THREADS) k_fft_c(FftArgs f) {
     extern __shared__ __align__(16) unsigned char fsm[];
-    const int F1 = f.F1, F2 = f.F2, F3 = f.F3;
+    const int F1 = f.F1, F2 = f.F2, F3 = f.F3, LPB = f.lpb[0];
     C* W = (C*)fsm;
     C* x = W + F1;
-    C* y = x + FFT_LPB * F1;
+    C* y = x + LPB * F1;
     const int k = blockIdx.z, c = blockIdx.y;
     const FftK K = f.fk[k];
-    const int nch = (F3 + FFT_LPB - 1) / FFT_LPB;
-    const int r2 = blockIdx.x / nch, i30 = (blockIdx.x - r2 * nch) * FFT_LPB;
-    const int nl = min(FFT_LPB, F3 - i30);
+    const int nch = (F3 + LPB - 1) / LPB;
+    const int r2 = blockIdx.x / nch, i30 = (blockIdx.x - r2 * nch) * LPB;
+    const int nl = min(LPB, F3 - i30);
     load_tw(W, f.w[0], F1);
     C* b2 = (C*)f.b2 + ((size_t)k * f.ncol + c) * f.b2_col;
     const size_t pst = (size_t)F2 * F3;
@@ -310,7 +316,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_c(FftArgs f) {
     }
     // the potential of this block's points, loaded (coalesced along r3) before
     // the inverse transform so that the loads overlap it
-    constexpr int PV = FFT_MAX_N * FFT_LPB / FFT_THREADS;
+    constexpr int PV = FFT_PV;  // F1 nl <= FFT_BLK_PTS
     C pv[PV];
     {
         const C* v = (const C*)f.v;
@@ -360,15 +366,15 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_c(FftArgs f) {
 template <typename C>
 __global__ void __launch_bounds__(FFT_THREADS) k_fft_e(FftArgs f) {
     extern __shared__ __align__(16) unsigned char fsm[];
-    const int F3 = f.F3;
+    const int F3 = f.F3, LPB = f.lpb[2];
     C* W = (C*)fsm;
     C* x = W + F3;
-    C* y = x + FFT_LPB * F3;
+    C* y = x + LPB * F3;
     const int k = blockIdx.z, c = blockIdx.y;
     const FftK K = f.fk[k];
-    const int l0 = blockIdx.x * FFT_LPB;
+    const int l0 = blockIdx.x * LPB;
     if (l0 >= K.nline) return;
-    const int nl = min(FFT_LPB, K.nline - l0);
+    const int nl = min(LPB, K.nline - l0);
     load_tw(W, f.w[2], F3);
     const int base = l0 * F3;
     const C* in = (const C*)f.b3 + ((size_t)k * f.ncol + c) * f.b3_col + (size_t)base;
@@ -443,17 +449,17 @@ template <typename C>
 __global__ void __launch_bounds__(FFT_THREADS) k_fft_density(FftArgs f, int nk, const double* __restrict__ occ,
                                                           const double* __restrict__ wk, double inv_omega, C* rho) {
     extern __shared__ __align__(16) unsigned char fsm[];
-    const int F1 = f.F1, F2 = f.F2, F3 = f.F3;
+    const int F1 = f.F1, F2 = f.F2, F3 = f.F3, LPB = f.lpb[0];
     C* W = (C*)fsm;
     C* x = W + F1;
-    C* y = x + FFT_LPB * F1;
-    const int nch = (F3 + FFT_LPB - 1) / FFT_LPB;
-    const int r2 = blockIdx.x / nch, i30 = (blockIdx.x - r2 * nch) * FFT_LPB;
-    const int nl = min(FFT_LPB, F3 - i30);
+    C* y = x + LPB * F1;
+    const int nch = (F3 + LPB - 1) / LPB;
+    const int r2 = blockIdx.x / nch, i30 = (blockIdx.x - r2 * nch) * LPB;
+    const int nl = min(LPB, F3 - i30);
     load_tw(W, f.w[0], F1);
     const size_t pst = (size_t)F2 * F3;
     const size_t off = (size_t)r2 * F3 + i30;
-    constexpr int PV = FFT_MAX_N * FFT_LPB / FFT_THREADS;
+    constexpr int PV = FFT_PV;
     double acc[PV];
 #pragma unroll
     for (int u = 0; u < PV; ++u) acc[u] = 0.0;
@@ -497,22 +503,23 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_full(FftArgs f, C* buf, int
     extern __shared__ __align__(16) unsigned char fsm[];
     const int F1 = f.F1, F2 = f.F2, F3 = f.F3;
     const int L = axis == 0 ? F1 : (axis == 1 ? F2 : F3);
+    const int LPB = f.lpb[axis];
     C* W = (C*)fsm;
     C* x = W + L;
-    C* y = x + FFT_LPB * L;
+    C* y = x + LPB * L;
     load_tw(W, f.w[axis], L);
     size_t base, es, ls;
     int nl;
     if (axis == 2) {
-        const int l0 = blockIdx.x * FFT_LPB;
-        nl = min(FFT_LPB, F1 * F2 - l0);
+        const int l0 = blockIdx.x * LPB;
+        nl = min(LPB, F1 * F2 - l0);
         base = (size_t)l0 * F3;
         es = 1;
         ls = F3;
     } else {
-        const int nch = (F3 + FFT_LPB - 1) / FFT_LPB;
-        const int o = blockIdx.x / nch, i30 = (blockIdx.x - o * nch) * FFT_LPB;
-        nl = min(FFT_LPB, F3 - i30);
+        const int nch = (F3 + LPB - 1) / LPB;
+        const int o = blockIdx.x / nch, i30 = (blockIdx.x - o * nch) * LPB;
+        nl = min(LPB, F3 - i30);
         es = axis == 1 ? (size_t)F3 : (size_t)F2 * F3;
         base = (axis == 1 ? (size_t)o * F2 * F3 : (size_t)o * F3) + i30;
         ls = 1;
@@ -658,7 +665,7 @@ static int smooth_at_least(int n) {
     }
 }
 
-static size_t fft_smem(int L, int elt) { return (size_t)(L + 2 * FFT_LPB * L) * elt; }
+static size_t fft_smem(int L, int elt) { return (size_t)(L + 2 * fft_lpb(L) * L) * elt; }
 static size_t fft_plane_smem(int F2, int F3, int elt) { return (size_t)(F2 + F3 + 2 * F2 * F3) * elt; }
 #define FFT_PLANE_SMEM_MAX (200 * 1024)
 
@@ -727,7 +734,7 @@ int fft_plan_create(FftPlan** out, int nk, const int* ng, const int* const* gint
     pl->prec = prec;
     pl->nk = nk;
     if (fft_grid_for(vt_dim, pl->F)) {
-        if (why) *why = "FFT route: a table extent needs more than 128 grid points";
+        if (why) *why = "FFT route: a table extent needs more than 512 grid points";
         delete pl;
         return RTTDDFT_ERR_UNSUPPORTED;
     }
@@ -907,6 +914,7 @@ static int launch_fft_any(const FftPlan* pl, int fused, const ToepDesc* td, int 
     for (int a = 0; a < 3; ++a) {
         f.nst[a] = pl->nst[a];
         for (int i = 0; i < FFT_MAX_ST; ++i) f.rad[a][i] = pl->rad[a][i];
+        f.lpb[a] = fft_lpb(pl->F[a]);
         f.w[a] = pl->prec == 0 ? (const void*)pl->w64[a] : (const void*)pl->w32[a];
     }
     f.fk = pl->d_fk + kofs;
@@ -921,10 +929,10 @@ static int launch_fft_any(const FftPlan* pl, int fused, const ToepDesc* td, int 
     f.v = pl->prec == 0 ? (const void*)pl->v64 : (const void*)pl->v32;
     f.vd = pl->prec == 0 ? (const void*)pl->vd64 : (const void*)pl->vd32;
     f.s = s;
-    const int nch = (f.F3 + FFT_LPB - 1) / FFT_LPB;
-    const dim3 ga((pl->max_lines + FFT_LPB - 1) / FFT_LPB, ncol, nk);
-    const dim3 gb(pl->max_planes * nch, ncol, nk);
-    const dim3 gc(f.F2 * nch, ncol, nk);
+    const int ch1 = (f.F3 + f.lpb[1] - 1) / f.lpb[1], ch0 = (f.F3 + f.lpb[0] - 1) / f.lpb[0];
+    const dim3 ga((pl->max_lines + f.lpb[2] - 1) / f.lpb[2], ncol, nk);
+    const dim3 gb(pl->max_planes * ch1, ncol, nk);
+    const dim3 gc(f.F2 * ch0, ncol, nk);
     if (fused) {
         const dim3 gp(pl->max_planes, ncol, nk);
         if (pl->prec == 0) {
@@ -1010,6 +1018,7 @@ static FftArgs fft_args64(const FftPlan* pl, const ToepDesc* td, int kofs, int n
     for (int a = 0; a < 3; ++a) {
         f.nst[a] = pl->nst[a];
         for (int i = 0; i < FFT_MAX_ST; ++i) f.rad[a][i] = pl->rad[a][i];
+        f.lpb[a] = fft_lpb(pl->F[a]);
         f.w[a] = (const void*)pl->w64[a];
     }
     f.fk = pl->d_fk + kofs;
@@ -1075,22 +1084,22 @@ int fft_hartree_init(FftPlan* pl, const double recip[9], const int vt_dim[3], do
 template <typename C>
 static int density_launches(const FftPlan* pl, const FftArgs& f, int nk, const double* occ, const double* wk, C* rho,
                             cudaStream_t st) {
-    const int nch = (f.F3 + FFT_LPB - 1) / FFT_LPB;
+    const int ch0 = (f.F3 + f.lpb[0] - 1) / f.lpb[0], ch1 = (f.F3 + f.lpb[1] - 1) / f.lpb[1];
     int nl = 0;
     // the planes of every (k, state) column after the inverse transforms of axes 3 and 2
     if (pl->fused_d) {
         k_fft_plane<C><<<dim3(pl->max_planes, f.ncol, nk), FFT_PTHREADS, fft_plane_smem(f.F2, f.F3, sizeof(C)), st>>>(f, 0);
         ++nl;
     } else {
-        k_fft_a<C><<<dim3((pl->max_lines + FFT_LPB - 1) / FFT_LPB, f.ncol, nk), FFT_THREADS, fft_smem(f.F3, sizeof(C)),
-                     st>>>(f);
-        k_fft_bd<C><<<dim3(pl->max_planes * nch, f.ncol, nk), FFT_THREADS, fft_smem(f.F2, sizeof(C)), st>>>(f, 0);
+        k_fft_a<C><<<dim3((pl->max_lines + f.lpb[2] - 1) / f.lpb[2], f.ncol, nk), FFT_THREADS,
+                     fft_smem(f.F3, sizeof(C)), st>>>(f);
+        k_fft_bd<C><<<dim3(pl->max_planes * ch1, f.ncol, nk), FFT_THREADS, fft_smem(f.F2, sizeof(C)), st>>>(f, 0);
         nl += 2;
     }
-    k_fft_density<C><<<f.F2 * nch, FFT_THREADS, fft_smem(f.F1, sizeof(C)), st>>>(f, nk, occ, wk, 1.0 / pl->omega, rho);
+    k_fft_density<C><<<f.F2 * ch0, FFT_THREADS, fft_smem(f.F1, sizeof(C)), st>>>(f, nk, occ, wk, 1.0 / pl->omega, rho);
     ++nl;
     // N(g) = sum_r n(r) e^{-2 pi i g.r/F}
-    const int ga[3] = {f.F2 * nch, f.F1 * nch, (f.F1 * f.F2 + FFT_LPB - 1) / FFT_LPB};
+    const int ga[3] = {f.F2 * ch0, f.F1 * ch1, (f.F1 * f.F2 + f.lpb[2] - 1) / f.lpb[2]};
     for (int a = 2; a >= 0; --a) {
         const int L = pl->F[a];
         k_fft_full<C><<<ga[a], FFT_THREADS, fft_smem(L, sizeof(C)), st>>>(f, rho, a, 0);
@@ -1119,8 +1128,8 @@ int launch_fft_hartree(const FftPlan* pl, const ToepDesc* td, int nk, int ns, co
     const FftArgs f = fft_args64(pl, td, 0, ns);
     const double inv_f3 = 1.0 / ((double)pl->F[0] * pl->F[1] * pl->F[2]);
     const double* b = pl->recip;
-    const int nch = (f.F3 + FFT_LPB - 1) / FFT_LPB;
-    const int ga[3] = {f.F2 * nch, f.F1 * nch, (f.F1 * f.F2 + FFT_LPB - 1) / FFT_LPB};
+    const int ch0 = (f.F3 + f.lpb[0] - 1) / f.lpb[0], ch1 = (f.F3 + f.lpb[1] - 1) / f.lpb[1];
+    const int ga[3] = {f.F2 * ch0, f.F1 * ch1, (f.F1 * f.F2 + f.lpb[2] - 1) / f.lpb[2]};
     k_hartree<zd><<<152, 256, 0, st>>>(pl->rho, pl->rho0, pl->vd64, f.F1, f.F2, f.F3, pl->e[0], pl->e[1], pl->e[2],
                                        b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7], b[8], inv_f3, pl->l1);
     for (int a = 0; a < 3; ++a)

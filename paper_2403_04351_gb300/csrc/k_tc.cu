@@ -91,6 +91,27 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// D (TMEM) (+)= A (TMEM, 128 lanes = rows, 16 packed bf16/fp16 K values in 8
+// columns) x B (shared-memory descriptor)
+__device__ __forceinline__ void umma_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t db, uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "r"(tmem_a), "l"(db), "r"(idesc), "r"(accum)
+        : "memory");
+}
+// a warp's 32 lanes x W consecutive 32-bit TMEM columns from W registers per thread
+template <int W>
+__device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t* v) {
+    if constexpr (W == 8)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                     "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                     : "memory");
+    else
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v[0]),
+                     "r"(v[1]), "r"(v[2]), "r"(v[3])
+                     : "memory");
+}
 
 // D[split][m][n] (FP32, row-major M x N) = sum over this split's K blocks
 // of A^ B^^T; grid (M tiles, K splits, N tiles).
@@ -608,10 +629,19 @@ struct TcToepParams {
     int* flag;
 };
 
-template <int NT, bool GW>
-__global__ void __launch_bounds__(TCO_THREADS, 1)
+template <int NT, bool GW, int GEN, bool TA>
+__global__ void __launch_bounds__(GEN + 32, 1)
     k_tc_toep(const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, TcToepParams p) {
-    // GW: gather the table from global memory (L1/L2) instead of a shared window
+    // TA: the generated left operand goes to tensor memory (tcgen05.st, 64 columns a
+    // stage from column 256: hi Re | hi Im | lo Re | lo Im, 16 columns each) and the
+    // products read it there, instead of a swizzled shared-memory tile: no shared-
+    // memory traffic and no proxy fence for the left operand.
+    // GW: gather the table from global memory (L1/L2) instead of a shared window.
+    // GEN: generating threads (256 or 512: 2 or 4 per output row, each writing 16 or
+    // 8 G' of a K block, with the table loads of 1 or 3 blocks ahead in flight).
+    static_assert(GEN == 256 || GEN == 512, "two or four generating threads per row");
+    constexpr int PER = 32 * TC_BM / GEN;  // G' per thread and K block
+    constexpr int MW = GEN / 32;           // the issuing warp
     extern __shared__ unsigned char smem_raw[];
     // aligned by offsetting the shared array itself, so that the compiler keeps
     // shared-memory (not generic) addressing for every access through smem
@@ -622,7 +652,10 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     // shared memory), lo.hi on the first NT columns: two instructions per K step
     constexpr bool MERGE = 2 * NT <= 256;
     constexpr int NACC = MERGE ? 2 * NT : NT;
-    constexpr uint32_t NCOLS = NACC <= 32 ? 32 : (NACC <= 64 ? 64 : (NACC <= 128 ? 128 : 256));
+    constexpr uint32_t NCOLS_ACC = NACC <= 32 ? 32 : (NACC <= 64 ? 64 : (NACC <= 128 ? 128 : 256));
+    constexpr uint32_t NCOLS = TA ? 512 : NCOLS_ACC;
+    constexpr uint32_t ACOL0 = 256;  // TA: first column of the left-operand stages
+    static_assert(!TA || TCT_MAXSA * 64 + ACOL0 <= 512, "left-operand stages beyond tensor memory");
     __shared__ __align__(8) uint64_t fullA[TCT_MAXSA], emptyA[TCT_MAXSA], fullB[TCT_MAXSB], emptyB[TCT_MAXSB], done;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
@@ -636,13 +669,13 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     const int nk = min(nkb, kb0 + p.kbps) - kb0;
     if (nk <= 0 || row0 >= ng) return;  // the reduction skips these pairs
     unsigned char* ringA = smem;
-    unsigned char* ringB = smem + (size_t)SA * 2 * A_BYTES;
+    unsigned char* ringB = smem + (TA ? (size_t)0 : (size_t)SA * 2 * A_BYTES);
     int* gl_s = (int*)(ringB + (size_t)SB * 2 * B_BYTES);
     uint2* win = (uint2*)(gl_s + p.kbps * 32);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < SA; ++s) {
-            mbar_init(&fullA[s], TCO_GEN / 32);
+            mbar_init(&fullA[s], MW);
             mbar_init(&emptyA[s], 1);
         }
         for (int s = 0; s < SB; ++s) {
@@ -653,7 +686,7 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 8) {
+    if (warp == MW) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                      "r"(NCOLS)
                      : "memory");
@@ -661,7 +694,7 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     }
     const int gp_lo = kb0 * 32, gp_hi = min(ng, (kb0 + nk) * 32);
     int wlo = 0;
-    if (tid < TCO_GEN) {
+    if (tid < GEN) {
         const int* __restrict__ glin = K.glin;
         const int g1 = min(row0 + TC_BM, ng) - 1;
         wlo = glin[row0] - glin[gp_hi - 1] + p.vt_center;
@@ -672,10 +705,10 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
                 abort_flag = 1;
                 if (tid == 0) atomicOr(p.flag, 8);
             } else {
-                for (int e = tid; e < wn; e += TCO_GEN) win[e] = p.tab[wlo + e];
+                for (int e = tid; e < wn; e += GEN) win[e] = p.tab[wlo + e];
             }
         }
-        for (int i = tid; i < gp_hi - gp_lo; i += TCO_GEN) gl_s[i] = glin[gp_lo + i];
+        for (int i = tid; i < gp_hi - gp_lo; i += GEN) gl_s[i] = glin[gp_lo + i];
     }
     const uint2* __restrict__ gtab = p.tab + wlo;  // GW: the same offsets into the table
     tc_fence_before();
@@ -683,7 +716,7 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     volatile int* ab = &abort_flag;
-    if (warp == 8) {
+    if (warp == MW) {
         if (lane == 0 && *ab) {
             umma_commit(&done);
         } else if (lane == 0) {
@@ -707,18 +740,34 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
                 consumed = j + 1;
                 if (!mbar_wait_ab(&fullA[sa], (uint32_t)((j / SA) & 1), ab)) break;
                 tc_fence_after();
-                const uint32_t ah = smem_u32(ringA + (size_t)sa * 2 * A_BYTES), al = ah + A_BYTES;
                 const uint32_t bh = smem_u32(ringB + (size_t)sb * 2 * B_BYTES), bl = bh + B_BYTES;
+                if constexpr (TA) {
+                    const uint32_t th = tmem + ACOL0 + 64u * (uint32_t)sa, tl = th + 32u;
 #pragma unroll
-                for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                    const uint32_t o = kk * 32;
-                    if constexpr (MERGE) {
-                        umma_bf16(tmem, umma_desc(ah + o), umma_desc(bh + o), idesc2, (j > 0 || kk > 0) ? 1u : 0u);
-                        umma_bf16(tmem, umma_desc(al + o), umma_desc(bh + o), idesc, 1u);
-                    } else {
-                        umma_bf16(tmem, umma_desc(ah + o), umma_desc(bh + o), idesc, (j > 0 || kk > 0) ? 1u : 0u);
-                        umma_bf16(tmem, umma_desc(ah + o), umma_desc(bl + o), idesc, 1u);
-                        umma_bf16(tmem, umma_desc(al + o), umma_desc(bh + o), idesc, 1u);
+                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                        const uint32_t o = kk * 32, c = kk * 8;
+                        if constexpr (MERGE) {
+                            umma_ts(tmem, th + c, umma_desc(bh + o), idesc2, (j > 0 || kk > 0) ? 1u : 0u);
+                            umma_ts(tmem, tl + c, umma_desc(bh + o), idesc, 1u);
+                        } else {
+                            umma_ts(tmem, th + c, umma_desc(bh + o), idesc, (j > 0 || kk > 0) ? 1u : 0u);
+                            umma_ts(tmem, th + c, umma_desc(bl + o), idesc, 1u);
+                            umma_ts(tmem, tl + c, umma_desc(bh + o), idesc, 1u);
+                        }
+                    }
+                } else {
+                    const uint32_t ah = smem_u32(ringA + (size_t)sa * 2 * A_BYTES), al = ah + A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                        const uint32_t o = kk * 32;
+                        if constexpr (MERGE) {
+                            umma_bf16(tmem, umma_desc(ah + o), umma_desc(bh + o), idesc2, (j > 0 || kk > 0) ? 1u : 0u);
+                            umma_bf16(tmem, umma_desc(al + o), umma_desc(bh + o), idesc, 1u);
+                        } else {
+                            umma_bf16(tmem, umma_desc(ah + o), umma_desc(bh + o), idesc, (j > 0 || kk > 0) ? 1u : 0u);
+                            umma_bf16(tmem, umma_desc(ah + o), umma_desc(bl + o), idesc, 1u);
+                            umma_bf16(tmem, umma_desc(al + o), umma_desc(bh + o), idesc, 1u);
+                        }
                     }
                 }
                 umma_commit(&emptyA[sa]);
@@ -737,20 +786,21 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
         }
         __syncwarp();
     } else if (!*ab) {
-        // generators: thread (r, h) writes row r, G' 16h .. 16h+15 of every K block.
-        // The table entries of block j + 1 are fetched before block j is written, so
-        // that their latency (L1/L2 in the gather form) overlaps the permutes and stores.
+        // generators: thread (r, h) writes row r, G' PER h .. PER h + PER - 1 of every
+        // K block.  The table entries of block j + 1 are fetched before block j is
+        // written, so that their latency (L1/L2 in the gather form) overlaps the
+        // permutes and stores.
         const int r = tid & (TC_BM - 1), h = tid >> 7;
         const int g = row0 + r;
         const bool valid = g < ng;
         const int lb = (valid ? K.glin[g] : 0) + p.vt_center - wlo;
         const uint32_t sw = (uint32_t)(r & 7);
         auto fetch = [&](int j, uint2* u) {
-            const int gq = (kb0 + j) * 32 + 16 * h;
-            if (valid && gq + 16 <= gp_hi) {
+            const int gq = (kb0 + j) * 32 + PER * h;
+            if (valid && gq + PER <= gp_hi) {
                 const int4* g4 = (const int4*)(gl_s + (gq - gp_lo));
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < PER / 4; ++q) {
                     const int4 t = g4[q];
                     if constexpr (GW) {
                         u[4 * q + 0] = __ldg(gtab + (lb - t.x));
@@ -766,7 +816,7 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
                 }
             } else {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
+                for (int i = 0; i < PER; ++i) {
                     const int gp = gq + i;
                     if (valid && gp < gp_hi) {
                         const int x = lb - gl_s[gp - gp_lo];
@@ -779,12 +829,39 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
         };
         auto store = [&](int j, const uint2* u) -> bool {
             const int sa = j % SA;
-            if (j >= SA && !mbar_wait_ab(&emptyA[sa], (uint32_t)(((j / SA) - 1) & 1), ab)) return false;
+            // warp-uniform: the stores below are whole-warp instructions
+            const bool okw = (j < SA) || mbar_wait_ab(&emptyA[sa], (uint32_t)(((j / SA) - 1) & 1), ab);
+            if (!__all_sync(0xffffffffu, okw)) return false;
+            if constexpr (TA) {
+                // the row's words in the warp's lane quadrant: word q of a part holds
+                // G' PER h + 2q (low half) and + 2q + 1 (high half)
+                tc_fence_after();
+                constexpr int W = PER / 2;
+                uint32_t rh[W], ih[W], rl[W], il[W];
+#pragma unroll
+                for (int q = 0; q < W; ++q) {
+                    rh[q] = __byte_perm(u[2 * q].x, u[2 * q + 1].x, 0x5410);
+                    ih[q] = __byte_perm(u[2 * q].y, u[2 * q + 1].y, 0x5410);
+                    rl[q] = __byte_perm(u[2 * q].x, u[2 * q + 1].x, 0x7632);
+                    il[q] = __byte_perm(u[2 * q].y, u[2 * q + 1].y, 0x7632);
+                }
+                const uint32_t t0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + ACOL0 + 64u * (uint32_t)sa +
+                                    (uint32_t)(W * h);
+                tmem_st<W>(t0, rh);
+                tmem_st<W>(t0 + 16, ih);
+                tmem_st<W>(t0 + 32, rl);
+                tmem_st<W>(t0 + 48, il);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&fullA[sa]);
+                return true;
+            }
             unsigned char* rowp = ringA + (size_t)sa * 2 * A_BYTES + r * 128;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < PER / 8; ++q) {
                 const uint2* w = u + 8 * q;
-                const uint32_t cre = (uint32_t)(2 * h + q), cim = cre + 4;
+                const uint32_t cre = (uint32_t)((PER / 8) * h + q), cim = cre + 4;
                 uint4* p0 = (uint4*)(rowp + ((cre ^ sw) << 4));
                 uint4* p1 = (uint4*)(rowp + ((cim ^ sw) << 4));
                 *p0 = make_uint4(__byte_perm(w[0].x, w[1].x, 0x5410), __byte_perm(w[2].x, w[3].x, 0x5410),
@@ -803,27 +880,38 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
             if (lane == 0) mbar_arrive(&fullA[sa]);
             return true;
         };
-        // two register sets in turn: the loads of one block stay in flight while
-        // the previous block is written
-        uint2 u0[16], u1[16];
-        fetch(0, u0);
-        for (int j = 0; j < nk; j += 2) {
-            if (j + 1 < nk) fetch(j + 1, u1);
-            if (!store(j, u0)) break;
-            if (j + 1 >= nk) break;
-            if (j + 2 < nk) fetch(j + 2, u0);
-            if (!store(j + 1, u1)) break;
+        // NB register sets in turn: the loads of the next NB - 1 blocks stay in
+        // flight while a block is written (2 sets with 16 G' per thread, 4 with 8)
+        constexpr int NB = (GEN == 512) ? 4 : 2;
+        uint2 ub[NB][PER];
+#pragma unroll
+        for (int q = 0; q < NB - 1; ++q)
+            if (q < nk) fetch(q, ub[q]);
+        bool going = true;
+        for (int j0 = 0; j0 < nk && going; j0 += NB) {
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                const int j = j0 + q;
+                if (j >= nk) break;
+                if (j + NB - 1 < nk) fetch(j + NB - 1, ub[(q + NB - 1) % NB]);
+                if (!store(j, ub[q])) {
+                    going = false;
+                    break;
+                }
+            }
         }
     }
     __syncthreads();
     const bool okd = mbar_wait(&done, 0);
     tc_fence_after();
-    if (warp < 8 && okd && !*ab) {
-        const int q = warp & 3, half = warp >> 2;
+    if (warp < MW && okd && !*ab) {
+        // warp w reads the TMEM lanes of its quadrant w % 4 (32 rows), every
+        // (MW / 4)-th group of 8 columns
+        const int q = warp & 3, part = warp >> 2;
         const int lrow = row0 + q * 32 + lane;
         float* drow = p.D + (((size_t)k * p.splits + split) * ((size_t)p.ttiles * TC_BM) + lrow) * p.Dn;
 #pragma unroll 1
-        for (int c = half * (NT / 2); c < (half + 1) * (NT / 2); c += 8) {
+        for (int c = part * 8; c < NT; c += 2 * MW) {
             uint32_t v[8];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -848,7 +936,7 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 8)
+    if (warp == MW)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
 }
 
@@ -963,20 +1051,50 @@ struct TcRedParams {
 __device__ void tc_red_tile(const float* __restrict__ D, size_t sstride, int nsp, int Dn, int nc, int row0,
                             int nrow, double scale, zd* __restrict__ out, size_t ld, double (*tile)[257]) {
     const int n2 = 2 * nc;
-    for (int e = threadIdx.x; e < TC_RT * n2; e += blockDim.x) {
-        const int r = e / n2, c = e % n2, row = row0 + r;
-        double v = 0.0;
-        if (row < nrow) {
-            const float* d = D + (size_t)row * Dn + c;
-            for (int s0 = 0; s0 < nsp; s0 += 4) {
-                float a[4];
+    if ((n2 & 3) == 0 && (Dn & 3) == 0 && (sstride & 3) == 0 && ((uintptr_t)D & 15) == 0) {
+        // four adjacent columns per thread (16-byte loads), the same slice order
+        const int q4 = n2 >> 2;
+        for (int e = threadIdx.x; e < TC_RT * q4; e += blockDim.x) {
+            const int r = e / q4, c = (e % q4) * 4, row = row0 + r;
+            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+            if (row < nrow) {
+                const float* d = D + (size_t)row * Dn + c;
+                for (int s0 = 0; s0 < nsp; s0 += 4) {
+                    float4 a[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) a[u] = (s0 + u < nsp) ? d[(size_t)(s0 + u) * sstride] : 0.f;
+                    for (int u = 0; u < 4; ++u)
+                        a[u] = (s0 + u < nsp) ? __ldcs((const float4*)(d + (size_t)(s0 + u) * sstride))
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) v += (double)a[u];
+                    for (int u = 0; u < 4; ++u) {
+                        v0 += (double)a[u].x;
+                        v1 += (double)a[u].y;
+                        v2 += (double)a[u].z;
+                        v3 += (double)a[u].w;
+                    }
+                }
             }
+            tile[r][c] = v0;
+            tile[r][c + 1] = v1;
+            tile[r][c + 2] = v2;
+            tile[r][c + 3] = v3;
         }
-        tile[r][c] = v;
+    } else {
+        for (int e = threadIdx.x; e < TC_RT * n2; e += blockDim.x) {
+            const int r = e / n2, c = e % n2, row = row0 + r;
+            double v = 0.0;
+            if (row < nrow) {
+                const float* d = D + (size_t)row * Dn + c;
+                for (int s0 = 0; s0 < nsp; s0 += 4) {
+                    float a[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) a[u] = (s0 + u < nsp) ? d[(size_t)(s0 + u) * sstride] : 0.f;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v += (double)a[u];
+                }
+            }
+            tile[r][c] = v;
+        }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < TC_RT * nc; e += blockDim.x) {
@@ -1030,7 +1148,7 @@ struct TcPlan {
     int nk = 0, ns = 0, ma = 0, Dn = 0, NT = 0, ttiles = 0, atiles = 0, Kp = 0, Mp = 0, Rp = 0;
     int maxng = 0, vt_center = 0;
     // interstitial rows
-    int SA = 0, SB = 0, kbps_t = 0, splits_t = 0, wcap = 0;
+    int SA = 0, SB = 0, kbps_t = 0, splits_t = 0, wcap = 0, gen_t = 256, ta_t = 0;
     size_t smem_t = 0;
     // matching rows
     int S_a = 0, kbps_a = 0, splits_a = 0;
@@ -1100,9 +1218,14 @@ template <int NT>
 static cudaError_t tco_set_smem(int bytes_opfwd, int bytes_toep) {
     cudaError_t e = raise_smem((const void*)k_tc_opfwd<NT>, bytes_opfwd);
     if (e != cudaSuccess) return e;
-    e = raise_smem((const void*)k_tc_toep<NT, false>, bytes_toep);
-    if (e != cudaSuccess) return e;
-    return raise_smem((const void*)k_tc_toep<NT, true>, bytes_toep);
+    const void* fs[] = {(const void*)k_tc_toep<NT, false, 256, false>, (const void*)k_tc_toep<NT, true, 256, false>,
+                        (const void*)k_tc_toep<NT, true, 512, false>, (const void*)k_tc_toep<NT, true, 256, true>,
+                        (const void*)k_tc_toep<NT, true, 512, true>};
+    for (const void* f : fs) {
+        e = raise_smem(f, bytes_toep);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 void tc_plan_destroy(TcPlan* tp) {
@@ -1143,8 +1266,22 @@ static int tco_best_splits(int tiles, int nk, int nkb, int nsm, int per_sm) {
     return best;
 }
 
+// one launch of the interstitial kernel in the variant (window or gather, generating
+// threads, left operand in shared or tensor memory)
+template <int NT>
+static void toep_variant(int wn, int gen, int ta, dim3 g, size_t smem, cudaStream_t s, const CUtensorMap& bh,
+                         const CUtensorMap& bl, const TcToepParams& p) {
+    if (wn > 0) k_tc_toep<NT, false, 256, false><<<g, 288, smem, s>>>(bh, bl, p);
+    else if (gen == 512 && ta) k_tc_toep<NT, true, 512, true><<<g, 544, smem, s>>>(bh, bl, p);
+    else if (gen == 512) k_tc_toep<NT, true, 512, false><<<g, 544, smem, s>>>(bh, bl, p);
+    else if (ta) k_tc_toep<NT, true, 256, true><<<g, 288, smem, s>>>(bh, bl, p);
+    else k_tc_toep<NT, true, 256, false><<<g, 288, smem, s>>>(bh, bl, p);
+}
+
 struct TcToepCand {
     int kbps, splits, SA, SB, wn;  // wn = 0: table gathered from global memory
+    int gen;                       // generating threads (512 only with the gathered table)
+    int ta;                        // left operand in tensor memory (gathered table only)
     size_t smem;
     float ms;
 };
@@ -1171,8 +1308,7 @@ static void tco_launch_toep(const TcPlan* tp, const TcToepCand& c, const KDev* k
     p.tab = tp->tabs;
     p.D = tp->Dt;
     p.flag = tp->tflag;
-    if (c.wn > 0) k_tc_toep<NT, false><<<dim3(tp->ttiles, c.splits, nk), TCO_THREADS, c.smem, s>>>(tp->tbh, tp->tbl, p);
-    else k_tc_toep<NT, true><<<dim3(tp->ttiles, c.splits, nk), TCO_THREADS, c.smem, s>>>(tp->tbh, tp->tbl, p);
+    toep_variant<NT>(c.wn, c.gen, c.ta, dim3(tp->ttiles, c.splits, nk), c.smem, s, tp->tbh, tp->tbl, p);
     // with the sum of its slices, so that many slices pay for their reduction
     TcRedParams r{};
     r.ns = tp->ns;
@@ -1304,13 +1440,19 @@ static int tco_tune_back(TcPlan* tp, std::vector<TcRowsCand>& tb, const KDev* kd
 // autotuner times: "window" or "gather" (the interstitial table staged in
 // shared memory or read through L1/L2), "fewslices" or "manyslices" (the
 // largest or smallest K slice of the remaining shapes), "minstages" or
-// "maxstages" (the fewest or most pipeline stages of the remaining shapes).
+// "maxstages" (the fewest or most pipeline stages of the remaining shapes),
+// "gen8" or "gen16" (8 or 16 generating warps in the interstitial launch;
+// 16 only with the gathered table), "asmem" or "atmem" (its generated left
+// operand in shared or tensor memory; tensor memory only with the gathered
+// table).
 // The restriction applies to the interstitial launch, the matching rows and
 // the back-projection alike.  Unset: every shape is timed.
 struct TcFamily {
     int route = 0;   // 1 window, 2 gather
     int slices = 0;  // 1 few (largest K slice), 2 many (smallest)
     int stages = 0;  // 1 min, 2 max
+    int gen = 0;     // generating warps of the interstitial launch: 8 or 16
+    int ta = 0;      // its left operand: 1 shared memory, 2 tensor memory
 };
 static TcFamily tc_family_from_env() {
     TcFamily f;
@@ -1321,6 +1463,8 @@ static TcFamily tc_family_from_env() {
     f.route = has("window") ? 1 : (has("gather") ? 2 : 0);
     f.slices = has("fewslices") ? 1 : (has("manyslices") ? 2 : 0);
     f.stages = has("minstages") ? 1 : (has("maxstages") ? 2 : 0);
+    f.gen = has("gen16") ? 16 : (has("gen8") ? 8 : 0);
+    f.ta = has("atmem") ? 2 : (has("asmem") ? 1 : 0);
     return f;
 }
 template <typename C, typename KeyF>
@@ -1339,6 +1483,18 @@ static void tc_filter_family(const TcFamily& f, std::vector<TcToepCand>& tc, std
         std::vector<TcToepCand> out;
         for (const auto& c : tc)
             if ((f.route == 1) == (c.wn > 0)) out.push_back(c);
+        tc.swap(out);
+    }
+    if (f.gen) {
+        std::vector<TcToepCand> out;
+        for (const auto& c : tc)
+            if (c.gen == 32 * f.gen) out.push_back(c);
+        tc.swap(out);
+    }
+    if (f.ta) {
+        std::vector<TcToepCand> out;
+        for (const auto& c : tc)
+            if (c.ta == f.ta - 1) out.push_back(c);
         tc.swap(out);
     }
     // few slices = the largest K slice (kbps): keep the maximum of kbps
@@ -1387,6 +1543,8 @@ static int tco_tune_t(TcPlan* tp, std::vector<TcToepCand>& tc, std::vector<TcRow
     tp->SA = c.SA;
     tp->SB = c.SB;
     tp->wcap = c.wn;
+    tp->gen_t = c.gen;
+    tp->ta_t = c.ta;
     tp->smem_t = c.smem;
     tp->ms_t = c.ms / 3;
     if (!ta.empty()) {
@@ -1479,7 +1637,7 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
                     if (SB > TCT_MAXSB) continue;
                     const size_t need = 1024 + (size_t)SA * A2 + (size_t)SB * B2 + (size_t)kbps * 128 + (size_t)wn * 8;
                     if ((int)need <= budget) {
-                        tc_c.push_back({kbps, sp, SA, SB, wn, need, 0.f});
+                        tc_c.push_back({kbps, sp, SA, SB, wn, 256, 0, need, 0.f});
                         any = true;
                     }
                 }
@@ -1495,7 +1653,14 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
             for (int SA = 2; SA <= TCT_MAXSA; ++SA)
                 for (int SB : {2, 4, 8}) {
                     const size_t need = 1024 + (size_t)SA * A2 + (size_t)SB * B2 + (size_t)kbps * 128;
-                    if ((int)need <= budget) tc_c.push_back({kbps, sp, SA, SB, 0, need, 0.f});
+                    if ((int)need <= budget)
+                        for (int gen : {256, 512}) tc_c.push_back({kbps, sp, SA, SB, 0, gen, 0, need, 0.f});
+                    // left operand in tensor memory: no shared-memory stages for it; at least
+                    // 120 KB requested so that one block holds an SM (it allocates all 512
+                    // tensor-memory columns)
+                    const size_t need_ta = std::max<size_t>(1024 + (size_t)SB * B2 + (size_t)kbps * 128, 120 * 1024);
+                    if ((int)need_ta <= budget)
+                        for (int gen : {256, 512}) tc_c.push_back({kbps, sp, SA, SB, 0, gen, 1, need_ta, 0.f});
                 }
             if (kbps == 1) break;
         }
@@ -1711,10 +1876,8 @@ int launch_tc_operator(const TcPlan* tp, const StepArgs& a, cudaStream_t s, bool
 #define RTD_TCO(n)                                                                                    \
     case n:                                                                                           \
         if (rows_only) {                                                                              \
-        } else if (tp->wcap > 0) {                                                                    \
-            k_tc_toep<n, false><<<gt, TCO_THREADS, tp->smem_t, s>>>(tp->tbh, tp->tbl, pt);              \
         } else {                                                                                      \
-            k_tc_toep<n, true><<<gt, TCO_THREADS, tp->smem_t, s>>>(tp->tbh, tp->tbl, pt);               \
+            toep_variant<n>(tp->wcap, tp->gen_t, tp->ta_t, gt, tp->smem_t, s, tp->tbh, tp->tbl, pt);      \
         }                                                                                             \
         if (tp->atiles > 0) k_tc_opfwd<n><<<ga, TCO_THREADS, tp->smem_a, s>>>(tp->tbh, tp->tbl, tp->tah, tp->tal, pa); \
         break;
@@ -1767,6 +1930,8 @@ void tc_plan_info(const TcPlan* tp, int* v) {
     v[6] = tp->ncand;
     v[7] = (int)(tp->ms_t * 1e6f);  // ns
     v[8] = (int)(tp->ms_a * 1e6f);
+    v[9] = tp->gen_t;
+    v[10] = tp->ta_t;
 }
 
 double tc_table_scale(const TcPlan* tp) { return tp ? tp->sT : 1.0; }
@@ -1859,7 +2024,7 @@ int tc_dv_prepare(TcPlan* tp, const zd* const* caux_dev, const int* nb, const in
     }
     int e = tc_tmap3(&tp->tch, tp->cch, tp->Kp, rows, tp->nk, TC_DV_NT) |
             tc_tmap3(&tp->tcl, tp->ccl, tp->Kp, rows, tp->nk, TC_DV_NT);
-    const cudaError_t ce = raise_smem((const void*)k_tc_toep<TC_DV_NT, true>, (int)tp->dv_smem);
+    const cudaError_t ce = raise_smem((const void*)k_tc_toep<TC_DV_NT, true, 256, false>, (int)tp->dv_smem);
     if (e || ce != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         *why = "potential-change operand set-up failed";
         return RTTDDFT_ERR_CUDA;
@@ -1899,7 +2064,7 @@ void launch_tc_dv_toeplitz(const TcPlan* tp, const StepArgs& a, const ToepDesc* 
     p.flag = a.flag;
     for (int j = 0; j < tp->dv_tiles; ++j) {
         p.brow0 = j * TC_DV_NT;
-        k_tc_toep<TC_DV_NT, true><<<dim3(tp->ttiles, tp->dv_splits, a.nk), TCO_THREADS, tp->dv_smem, s>>>(tp->tch,
+        k_tc_toep<TC_DV_NT, true, 256, false><<<dim3(tp->ttiles, tp->dv_splits, a.nk), 288, tp->dv_smem, s>>>(tp->tch,
                                                                                                          tp->tcl, p);
         TcDvRedParams r{};
         r.splits = tp->dv_splits;

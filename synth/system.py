@@ -75,7 +75,7 @@ class Config:
     n_aux: int
     dt: float
     n_steps: int
-    lattice: str               # "h2box" or "mos2"
+    lattice: str               # "h2box", "mos2" or "chain"
     n_k: int = 1
     n_g: int = 0               # plane waves (single k) ...
     n_b_range: tuple = (0, 0)  # ... or per-k basis size drawn uniformly
@@ -128,6 +128,8 @@ def _lattice(kind):
         return np.array([[3 * a, 0.0, 0.0],
                          [1.5 * a, 1.5 * a * math.sqrt(3.0), 0.0],
                          [0.0, 0.0, c]])
+    if kind == "chain":  # a long thin box (6 x 6 x 120 bohr^3): many plane waves along z
+        return np.diag([6.0, 6.0, 120.0])
     raise ValueError(kind)
 
 

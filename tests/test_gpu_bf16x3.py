@@ -210,9 +210,12 @@ def test_potential_change_rebuilt_on_tensor_cores(form):
 
 # Every family of launch shapes the set-up autotuner can pick, forced through
 # RTTDDFT_TC_FAMILY: the interstitial table staged in shared memory or read
-# through L1/L2, the largest or smallest K slice, the fewest or most stages.
+# through L1/L2, the largest or smallest K slice, the fewest or most stages,
+# 8 or 16 generating warps, the generated operand in shared or tensor memory.
 TUNER_FAMILIES = ["window,fewslices,minstages", "window,manyslices,maxstages",
-                  "gather,fewslices,maxstages", "gather,manyslices,minstages"]
+                  "gather,fewslices,maxstages,gen8,asmem", "gather,manyslices,minstages,gen8,asmem",
+                  "gather,fewslices,minstages,gen16,asmem", "gather,manyslices,maxstages,gen16,asmem",
+                  "gather,fewslices,maxstages,gen8,atmem", "gather,manyslices,minstages,gen16,atmem"]
 
 
 def _golden():
@@ -256,4 +259,9 @@ def test_every_tuner_family_within_split_bound(case, family, monkeypatch):
         assert np.max(np.abs(sx[rows] - g["sx_rows_k%d" % k]) / g["mag_s_k%d" % k]) < 1e-4
     info = ctx.info()["tc"]
     assert (info["window"] > 0) == ("window" in family), info
+    if "gen16" in family:
+        assert info["gen_threads"] == 512, info
+    if "gen8" in family or "window" in family:
+        assert info["gen_threads"] == 256, info
+    assert info["a_tmem"] == (1 if "atmem" in family else 0), info
     ctx.close()

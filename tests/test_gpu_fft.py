@@ -39,6 +39,13 @@ def ragged_cfg():
                        edir=(1.0, 0.0, 0.0))
 
 
+def chain_cfg(n_g=600):
+    """A long thin cell (6 x 6 x 120 bohr^3): the table box needs more than 128
+    grid points along z (161 at 600 plane waves, 162 on the FFT grid)."""
+    return tiny_config(name="chain", n_g=n_g, n_atoms=2, lmax=2, n_lo_per_atom=2, n_s=3, n_aux=24,
+                       lattice="chain", seed=23)
+
+
 def smooth(n):
     m = n
     while True:
@@ -60,6 +67,8 @@ def system_for(case):
         s = make_system(ragged_cfg())
     elif case == "free":
         s = free_electron_system(n_g=50, n_s=2, n_aux=6)
+    elif case == "chain":
+        s = make_system(chain_cfg())
     else:  # many states, several column chunks of the operator
         s = make_system(tiny_config(n_g=300, n_atoms=2, lmax=2, n_lo_per_atom=2, n_s=40, n_aux=64, seed=5))
     return s, dv
@@ -67,7 +76,7 @@ def system_for(case):
 
 @pytest.mark.parametrize("launches", ["5", "3"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "fp16x3"])
-@pytest.mark.parametrize("case", ["tiny400", "ragged", "free", "dv", "wide"])
+@pytest.mark.parametrize("case", ["tiny400", "ragged", "free", "dv", "wide", "chain"])
 def test_operator_by_fft_equals_explicit(case, prec, launches, monkeypatch):
     """Both launch sets (five line passes; plane-fused three) on every case.
     The split forms take the interstitial sum by FP32 FFTs and the
@@ -119,6 +128,41 @@ def test_fft_and_direct_sum_agree_to_rounding():
     assert rel(s2, s1) < 1e-14
     c1.close()
     c2.close()
+
+
+@pytest.mark.parametrize("n_g", [600, 3000])
+def test_long_axis_fft_equals_direct_sum(n_g):
+    """Axes beyond 128 grid points (fewer lines per block of a pass): the FFT
+    route equals the FP64 direct sum to rounding at z extents of 162 and 270
+    points."""
+    s = make_system(chain_cfg(n_g))
+    rng = np.random.default_rng(9)
+    nb = int(s["n_g"][0]) + int(np.sum(s["n_lo"]))
+    x = rng.standard_normal((nb, 5)) + 1j * rng.standard_normal((nb, 5))
+    a_vec = np.array([0.2, -0.1, 0.5])
+    c1 = Context(s, interstitial="toeplitz")
+    c2 = Context(s, interstitial="fft")
+    assert c2.info()["fft_grid"][2] == smooth(int(s["vt_dim"][2])) > 128
+    h1, s1 = c1.apply(0, x, a_vec, 0.0)
+    h2, s2 = c2.apply(0, x, a_vec, 0.0)
+    assert rel(h2, h1) < 1e-13
+    assert rel(s2, s1) < 1e-14
+    c1.close()
+    c2.close()
+
+
+def test_long_axis_hartree_feedback_matches_oracle():
+    """The density passes (full-grid transforms of every axis) on the long
+    cell against the oracle's direct density and Hartree matrix."""
+    s = make_system(chain_cfg())
+    a = pulse_samples(s, n_steps=15, a0=20.0)
+    r = Oracle(s).run(a, s["dt"], hartree=True)
+    ctx = Context(s, interstitial="fft", hartree=True, graph_steps=5)
+    ctx.step(a)
+    obs = ctx.observables()
+    assert rel(obs["dmu"], r["dmu"]) < 1e-8
+    assert rel(obs["energy"], r["E"]) < 1e-10
+    ctx.close()
 
 
 @pytest.mark.parametrize("launches", ["5", "3"])

@@ -210,6 +210,7 @@ typedef struct {
     int fft_fused;         /*   1: a plane's two in-plane axes in one launch (chosen at set-up by timing) */
     int tc_gen_threads;    /* split forms: threads generating the interstitial operand per block (256 or 512) */
     int tc_a_tmem;         /*   1: that operand is written to tensor memory (0: shared memory) */
+    int tc_back_parts;     /*   back-projection launched in 1 or 2 output-column parts (0: none) */
 } rttddft_info;
 
 RTTDDFT_API void rttddft_default_options(rttddft_options* opt);

@@ -41,6 +41,7 @@ struct rttddft_ctx {
     zd *d_h = nullptr, *d_o = nullptr, *d_p = nullptr, *d_dh = nullptr;
     zf *d_h32 = nullptr, *d_o32 = nullptr, *d_p32 = nullptr;
     TcCC* tcc = nullptr;  // expansion and projection on the tensor cores (split forms, many states)
+    TcMT* tcmt = nullptr; // muffin-tin blocks on the tensor cores (split-BF16 form, many states)
     zf* d_mtg = nullptr;  // muffin-tin stacks [h_eff; o; p] (FP32 forms, many states)
     zd* d_mtw = nullptr;
     zd* d_mtv = nullptr;  // per (k, atom) the gathered right-hand block [Q; C_lo] (m x N_s)
@@ -314,6 +315,7 @@ static StepPlan make_plan(rttddft_ctx* ctx) {
     p.max_sweeps = ctx->opt.max_sweeps;
     p.tc = ctx->tc;
     p.tcc = ctx->tcc;
+    p.tcmt = ctx->tcmt;
     p.fft = ctx->fft;
     p.td_op = ctx->td_op;
     p.tile_cnt = ctx->d_tile_cnt;
@@ -623,6 +625,7 @@ void rttddft_destroy(rttddft_ctx* ctx) {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     tc_plan_destroy(ctx->tc);
     tc_cc_destroy(ctx->tcc);
+    tc_mt_destroy(ctx->tcmt);
     fft_plan_destroy(ctx->fft);
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -1252,6 +1255,12 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
                 }
             }
             ctx->gd_mt1 = upload_descs(ctx, m1);
+            if (o->precision == RTTDDFT_PREC_BF16X3 && 2 * ns <= 128) {
+                // split-BF16 form: the same products as one batch on the tensor cores
+                std::string why;
+                const int e = tc_mt_create(&ctx->tcmt, nk, at.n, ctx->maxm, ns, ctx->d_flag, ctx->stream, &why);
+                if (e) fail(ctx, e, why);
+            }
         }
         {
             StepArgs a = make_args(ctx, 0);
@@ -1742,7 +1751,7 @@ int rttddft_get_info(rttddft_ctx* ctx, rttddft_info* info) {
     info->dt_cr0 = ctx->dtcr0;
     info->kernel_launches_per_step = ctx->launches_per_step;
     info->precision = ctx->opt.precision;
-    int v[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int v[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (ctx->tc) tc_plan_info(ctx->tc, v);
     info->tc_candidates = v[6];
     info->tc_interstitial_ns = v[7];
@@ -1755,6 +1764,7 @@ int rttddft_get_info(rttddft_ctx* ctx, rttddft_info* info) {
     info->tc_smem = v[5];
     info->tc_gen_threads = v[9];
     info->tc_a_tmem = v[10];
+    info->tc_back_parts = v[11];
     info->interstitial = ctx->opt.interstitial;
     fft_plan_info(ctx->fft, info->fft_grid, &info->fft_fused);
     return RTTDDFT_OK;

@@ -828,6 +828,13 @@ __global__ void __launch_bounds__(128) k_mt_epi(StepArgs a) {
 }
 
 static int launch_mt_gemm(const StepArgs& a, const StepPlan& p, cudaStream_t s) {
+    if (p.tcmt) {
+        // split-BF16 form: the stacks formed in FP64 and the products on the tensor cores
+        k_mt_gather<<<dim3((a.at_maxm * a.ns + 255) / 256, a.at_n, a.nk), 256, 0, s>>>(a);
+        const int nl = launch_tc_mt(p.tcmt, a, s);
+        k_mt_epi<<<dim3((a.at_maxm + 127) / 128, a.at_n, a.nk), 128, 0, s>>>(a);
+        return nl + 2;
+    }
     k_mt_form<<<dim3(64, a.at_n), 256, 0, s>>>(a);
     k_mt_gather<<<dim3((a.at_maxm * a.ns + 255) / 256, a.at_n, a.nk), 256, 0, s>>>(a);
     launch_gemm_nn(p.gd_mt1, a.nk * a.at_n, 5 * a.at_maxm, a.at_maxm, a.ns, 0, nullptr, 0, true, nullptr, s);

@@ -462,6 +462,11 @@ struct TcOpParams {
     int rows_ng;    // valid output rows: ma (0), N_G(k) (1) or N_basis(k) (2)
     int fmt;        // operand format: 1 bf16, 0 fp16
     int kofs;  // k-point of blockIdx.z = 0 in the matching-row operand (single-k calls)
+    // batched products that are not per k-point (the muffin-tin blocks): a_zmod > 0
+    // takes the left operand's slice blockIdx.z % a_zmod and the right operand's
+    // blockIdx.z + bz0; the per-k tables are then not read (rows_ng 0, nkb_fixed > 0)
+    int a_zmod, bz0;
+    int nh;  // > 1: blockIdx.x = tile nh + part, part q takes right-operand rows and output columns q NT ..
     const KDev* kd;
     float* D;  // [nk][splits][R][Dn]
     int* flag;
@@ -487,15 +492,19 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     const int S = p.S;
-    const int k = blockIdx.z, tile = blockIdx.x, split = blockIdx.y;
-    const KDev& K = p.kd[k];
-    const int ng = K.ng;
+    const int nh = p.nh > 1 ? p.nh : 1;
+    const int k = blockIdx.z, tile = blockIdx.x / nh, part = blockIdx.x % nh, split = blockIdx.y;
+    const int brow = part * NT;  // first right-operand row and output column of this block
+    const bool per_k = p.a_zmod <= 0;
+    const int ng = per_k ? p.kd[k].ng : 0;
+    const int nbk = per_k ? p.kd[k].nb : 0;
     const int row0 = tile * TC_BM;
-    const int nkb = p.nkb_fixed > 0 ? p.nkb_fixed : ((p.k_nb ? K.nb : ng) + 31) >> 5;
+    const int nkb = p.nkb_fixed > 0 ? p.nkb_fixed : ((p.k_nb ? nbk : ng) + 31) >> 5;
     const int kb0 = split * p.kbps;
     const int nk = min(nkb, kb0 + p.kbps) - kb0;
     if (nk <= 0) return;  // the reduction skips these slices
-    const int rows_valid = p.rows_ng == 2 ? K.nb : (p.rows_ng ? ng : p.ma);
+    const int rows_valid = p.rows_ng == 2 ? nbk : (p.rows_ng ? ng : p.ma);
+    const int za = per_k ? k + p.kofs : k % p.a_zmod, zb = per_k ? k : k + p.bz0;
     if (row0 >= rows_valid) return;  // a row tile past this k-point's rows
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -529,10 +538,10 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
                 const int s = j % S, kx = (kb0 + j) * TC_BK;
                 unsigned char* st = smem + (size_t)s * STAGE;
                 mbar_expect_tx(&full[s], STAGE);
-                tma_load_3d(st + 2 * A_BYTES, &tmBh, kx, 0, k, &full[s]);
-                tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tmBl, kx, 0, k, &full[s]);
-                tma_load_3d(st, &tmAh, kx, row0, k + p.kofs, &full[s]);
-                tma_load_3d(st + A_BYTES, &tmAl, kx, row0, k + p.kofs, &full[s]);
+                tma_load_3d(st + 2 * A_BYTES, &tmBh, kx, brow, zb, &full[s]);
+                tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tmBl, kx, brow, zb, &full[s]);
+                tma_load_3d(st, &tmAh, kx, row0, za, &full[s]);
+                tma_load_3d(st + A_BYTES, &tmAl, kx, row0, za, &full[s]);
                 issued = j + 1;
             };
             for (int j = 0; j < min(nk, S); ++j) load(j);
@@ -577,7 +586,7 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
     if (warp < 8 && okd && !*ab) {
         const int q = warp & 3, half = warp >> 2;
         const int lrow = row0 + q * 32 + lane;
-        float* drow = p.D + (((size_t)k * p.splits + split) * p.R + lrow) * p.Dn;
+        float* drow = p.D + (((size_t)k * p.splits + split) * p.R + lrow) * p.Dn + brow;
 #pragma unroll 1
         for (int c = half * (NT / 2); c < (half + 1) * (NT / 2); c += 8) {
             uint32_t v[8];
@@ -596,7 +605,7 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
             if (lrow < rows_valid) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
-                    if (c + u < p.Dn) drow[c + u] = __uint_as_float(v[u]) + __uint_as_float(v2[u]);
+                    if (brow + c + u < p.Dn) drow[c + u] = __uint_as_float(v[u]) + __uint_as_float(v2[u]);
             }
         }
     } else if (tid == 0 && !okd) {
@@ -630,7 +639,7 @@ struct TcToepParams {
 };
 
 template <int NT, bool GW, int GEN, bool TA>
-__global__ void __launch_bounds__(GEN + 32, 1)
+__global__ void __launch_bounds__(GEN + 64, 1)
     k_tc_toep(const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, TcToepParams p) {
     // TA: the generated left operand goes to tensor memory (tcgen05.st, 64 columns a
     // stage from column 256: hi Re | hi Im | lo Re | lo Im, 16 columns each) and the
@@ -641,7 +650,7 @@ __global__ void __launch_bounds__(GEN + 32, 1)
     // 8 G' of a K block, with the table loads of 1 or 3 blocks ahead in flight).
     static_assert(GEN == 256 || GEN == 512, "two or four generating threads per row");
     constexpr int PER = 32 * TC_BM / GEN;  // G' per thread and K block
-    constexpr int MW = GEN / 32;           // the issuing warp
+    constexpr int MW = GEN / 32;           // the issuing warp; warp MW + 1 copies the right operand
     extern __shared__ unsigned char smem_raw[];
     // aligned by offsetting the shared array itself, so that the compiler keeps
     // shared-memory (not generic) addressing for every access through smem
@@ -724,20 +733,9 @@ __global__ void __launch_bounds__(GEN + 32, 1)
                                    ((uint32_t)(TC_BM >> 4) << 24);
             const uint32_t idesc2 = (1u << 4) | ((uint32_t)p.fmt << 7) | ((uint32_t)p.fmt << 10) |
                                     ((uint32_t)((NACC) >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
-            int issued = 0, consumed = 0;
-            auto loadB = [&](int j) {
-                const int s = j % SB, kx = (kb0 + j) * TC_BK;
-                unsigned char* st = ringB + (size_t)s * 2 * B_BYTES;
-                mbar_expect_tx(&fullB[s], 2 * B_BYTES);
-                tma_load_3d(st, &tmBh, kx, p.brow0, k, &fullB[s]);
-                tma_load_3d(st + B_BYTES, &tmBl, kx, p.brow0, k, &fullB[s]);
-                issued = j + 1;
-            };
-            for (int j = 0; j < min(nk, SB); ++j) loadB(j);
             for (int j = 0; j < nk; ++j) {
                 const int sa = j % SA, sb = j % SB;
                 if (!mbar_wait_ab(&fullB[sb], (uint32_t)((j / SB) & 1), ab)) break;
-                consumed = j + 1;
                 if (!mbar_wait_ab(&fullA[sa], (uint32_t)((j / SA) & 1), ab)) break;
                 tc_fence_after();
                 const uint32_t bh = smem_u32(ringB + (size_t)sb * 2 * B_BYTES), bl = bh + B_BYTES;
@@ -772,16 +770,29 @@ __global__ void __launch_bounds__(GEN + 32, 1)
                 }
                 umma_commit(&emptyA[sa]);
                 umma_commit(&emptyB[sb]);
-                const int jp = j - 1;
-                if (jp >= 0 && jp + SB < nk) {
-                    if (!mbar_wait_ab(&emptyB[jp % SB], (uint32_t)((jp / SB) & 1), ab)) break;
-                    loadB(jp + SB);
-                }
             }
             umma_commit(&done);
+            if (*ab) atomicOr(p.flag, 8);
+        }
+        __syncwarp();
+    } else if (warp == MW + 1) {
+        // the right operand's copies, SB blocks ahead of the products: a stage is
+        // refilled once the products that read it have completed
+        if (lane == 0 && !*ab) {
+            int issued = 0;
+            for (int j = 0; j < nk; ++j) {
+                const int s = j % SB;
+                if (j >= SB && !mbar_wait_ab(&emptyB[s], (uint32_t)(((j / SB) - 1) & 1), ab)) break;
+                unsigned char* st = ringB + (size_t)s * 2 * B_BYTES;
+                const int kx = (kb0 + j) * TC_BK;
+                mbar_expect_tx(&fullB[s], 2 * B_BYTES);
+                tma_load_3d(st, &tmBh, kx, p.brow0, k, &fullB[s]);
+                tma_load_3d(st + B_BYTES, &tmBl, kx, p.brow0, k, &fullB[s]);
+                issued = j + 1;
+            }
             if (*ab) {
-                atomicOr(p.flag, 8);
-                for (int j = consumed; j < issued; ++j) mbar_wait(&fullB[j % SB], (uint32_t)((j / SB) & 1));
+                // the copies in flight land before the block's shared memory goes away
+                for (int j = max(0, issued - SB); j < issued; ++j) mbar_wait(&fullB[j % SB], (uint32_t)((j / SB) & 1));
             }
         }
         __syncwarp();
@@ -1172,10 +1183,11 @@ struct TcPlan {
     uint2* dvtabs = nullptr;
     float* Dd = nullptr;
     // back-projection Y_G = A^H [hQ | oQ]: rows G, K over the matching rows
-    int NTb = 0, Dnb = 0, nkb_b = 0, Kpb = 0, Rpb = 0, S_b = 0, kbps_b = 0, splits_b = 0;
+    int NTb = 0, Dnb = 0, nkb_b = 0, Kpb = 0, Rpb = 0, S_b = 0, kbps_b = 0, splits_b = 0, nh_b = 1;
     size_t smem_b = 0;
     float ms_b = 0.f;
     CUtensorMap tzh, tzl, tabh, tabl;
+    CUtensorMap tzh2, tzl2;  // the right operand in boxes of 128 rows (column parts)
     unsigned short *zh = nullptr, *zl = nullptr, *abh = nullptr, *abl = nullptr;
     float* Db = nullptr;
 };
@@ -1271,11 +1283,12 @@ static int tco_best_splits(int tiles, int nk, int nkb, int nsm, int per_sm) {
 template <int NT>
 static void toep_variant(int wn, int gen, int ta, dim3 g, size_t smem, cudaStream_t s, const CUtensorMap& bh,
                          const CUtensorMap& bl, const TcToepParams& p) {
-    if (wn > 0) k_tc_toep<NT, false, 256, false><<<g, 288, smem, s>>>(bh, bl, p);
-    else if (gen == 512 && ta) k_tc_toep<NT, true, 512, true><<<g, 544, smem, s>>>(bh, bl, p);
-    else if (gen == 512) k_tc_toep<NT, true, 512, false><<<g, 544, smem, s>>>(bh, bl, p);
-    else if (ta) k_tc_toep<NT, true, 256, true><<<g, 288, smem, s>>>(bh, bl, p);
-    else k_tc_toep<NT, true, 256, false><<<g, 288, smem, s>>>(bh, bl, p);
+    // generating warps + the issuing warp + the copy warp
+    if (wn > 0) k_tc_toep<NT, false, 256, false><<<g, 256 + 64, smem, s>>>(bh, bl, p);
+    else if (gen == 512 && ta) k_tc_toep<NT, true, 512, true><<<g, 512 + 64, smem, s>>>(bh, bl, p);
+    else if (gen == 512) k_tc_toep<NT, true, 512, false><<<g, 512 + 64, smem, s>>>(bh, bl, p);
+    else if (ta) k_tc_toep<NT, true, 256, true><<<g, 256 + 64, smem, s>>>(bh, bl, p);
+    else k_tc_toep<NT, true, 256, false><<<g, 256 + 64, smem, s>>>(bh, bl, p);
 }
 
 struct TcToepCand {
@@ -1289,6 +1302,7 @@ struct TcRowsCand {
     int kbps, splits, S;
     size_t smem;
     float ms;
+    int nh;  // back-projection: output column parts of 128 (1: one part of NTb)
 };
 
 template <int NT>
@@ -1376,7 +1390,13 @@ static void tco_launch_back(const TcPlan* tp, const TcRowsCand& c, const KDev* k
     p.kd = kd;
     p.D = tp->Db;
     p.flag = flag ? flag : tp->tflag;
-    k_tc_opfwd<NT><<<dim3(tp->ttiles, c.splits, nk), TCO_THREADS, c.smem, s>>>(tp->tzh, tp->tzl, tp->tabh, tp->tabl, p);
+    p.nh = c.nh;
+    if (c.nh > 1)  // column parts of 128: right-operand boxes of 128 rows
+        k_tc_opfwd<128><<<dim3(tp->ttiles * c.nh, c.splits, nk), TCO_THREADS, c.smem, s>>>(tp->tzh2, tp->tzl2, tp->tabh,
+                                                                                         tp->tabl, p);
+    else
+        k_tc_opfwd<NT><<<dim3(tp->ttiles, c.splits, nk), TCO_THREADS, c.smem, s>>>(tp->tzh, tp->tzl, tp->tabh, tp->tabl,
+                                                                                  p);
     TcRedParams r{};
     r.ns = tp->ns;
     r.ma = tp->ma;
@@ -1429,6 +1449,7 @@ static int tco_tune_back(TcPlan* tp, std::vector<TcRowsCand>& tb, const KDev* kd
     tp->S_b = tb[best].S;
     tp->kbps_b = tb[best].kbps;
     tp->splits_b = tb[best].splits;
+    tp->nh_b = tb[best].nh;
     tp->smem_b = tb[best].smem;
     tp->ms_b = tb[best].ms / 3;
     tp->ncand += (int)tb.size();
@@ -1444,7 +1465,8 @@ static int tco_tune_back(TcPlan* tp, std::vector<TcRowsCand>& tb, const KDev* kd
 // "gen8" or "gen16" (8 or 16 generating warps in the interstitial launch;
 // 16 only with the gathered table), "asmem" or "atmem" (its generated left
 // operand in shared or tensor memory; tensor memory only with the gathered
-// table).
+// table), "bparts1" or "bparts2" (the back-projection's output columns in one
+// part of up to 256 or in parts of 128; parts only above 128 columns).
 // The restriction applies to the interstitial launch, the matching rows and
 // the back-projection alike.  Unset: every shape is timed.
 struct TcFamily {
@@ -1453,6 +1475,7 @@ struct TcFamily {
     int stages = 0;  // 1 min, 2 max
     int gen = 0;     // generating warps of the interstitial launch: 8 or 16
     int ta = 0;      // its left operand: 1 shared memory, 2 tensor memory
+    int bparts = 0;  // back-projection output column parts: 1 or 2
 };
 static TcFamily tc_family_from_env() {
     TcFamily f;
@@ -1465,6 +1488,7 @@ static TcFamily tc_family_from_env() {
     f.stages = has("minstages") ? 1 : (has("maxstages") ? 2 : 0);
     f.gen = has("gen16") ? 16 : (has("gen8") ? 8 : 0);
     f.ta = has("atmem") ? 2 : (has("asmem") ? 1 : 0);
+    f.bparts = has("bparts2") ? 2 : (has("bparts1") ? 1 : 0);
     return f;
 }
 template <typename C, typename KeyF>
@@ -1496,6 +1520,12 @@ static void tc_filter_family(const TcFamily& f, std::vector<TcToepCand>& tc, std
         for (const auto& c : tc)
             if (c.ta == f.ta - 1) out.push_back(c);
         tc.swap(out);
+    }
+    if (f.bparts) {
+        std::vector<TcRowsCand> out;
+        for (const auto& c : tb)
+            if (c.nh == f.bparts) out.push_back(c);
+        tb.swap(out);
     }
     // few slices = the largest K slice (kbps): keep the maximum of kbps
     const int sl = f.slices == 1 ? 2 : (f.slices == 2 ? 1 : 0);
@@ -1682,7 +1712,7 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
             last_kbps = kbps;
             for (int S = 2; S <= TCO_MAXS; ++S) {
                 const size_t need = 1024 + (size_t)S * (A2 + B2) + (size_t)kbps * 128;
-                if ((int)need <= budget) ta_c.push_back({kbps, (nkb + kbps - 1) / kbps, S, need, 0.f});
+                if ((int)need <= budget) ta_c.push_back({kbps, (nkb + kbps - 1) / kbps, S, need, 0.f, 1});
             }
         }
     }
@@ -1750,7 +1780,14 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
             if ((double)nk * spl * tp->ttiles * TC_BM * tp->Dnb * 4.0 > 4.0e9) break;
             for (int S = 2; S <= TCO_MAXS; ++S) {
                 const size_t need = 1024 + (size_t)S * (A2 + Bb2);
-                if ((int)need <= budget) tb_c.push_back({kbps, spl, S, need, 0.f});
+                if ((int)need <= budget) tb_c.push_back({kbps, spl, S, need, 0.f, 1});
+                // two column parts of 128 (right-operand boxes of 128 rows): smaller
+                // stages, more of them; the parts of a row tile read the same left-
+                // operand blocks at about the same time, so the second read is an L2 hit
+                if (tp->NTb > 128) {
+                    const size_t need2 = 1024 + (size_t)S * (A2 + 4 * 128 * TC_BK);
+                    if ((int)need2 <= budget) tb_c.push_back({kbps, spl, S, need2, 0.f, 2});
+                }
             }
         }
         int max_sp_b = 1;
@@ -1780,6 +1817,9 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
         }
         e |= tc_tmap3(&tp->tzh, tp->zh, tp->Kpb, tp->Rpb, nk, tp->NTb) |
              tc_tmap3(&tp->tzl, tp->zl, tp->Kpb, tp->Rpb, nk, tp->NTb) |
+             (tp->NTb > 128 ? (tc_tmap3(&tp->tzh2, tp->zh, tp->Kpb, tp->Rpb, nk, 128) |
+                               tc_tmap3(&tp->tzl2, tp->zl, tp->Kpb, tp->Rpb, nk, 128))
+                            : 0) |
              tc_tmap3(&tp->tabh, tp->abh, tp->Kpb, (uint64_t)tp->ttiles * TC_BM, nk, TC_BM) |
              tc_tmap3(&tp->tabl, tp->abl, tp->Kpb, (uint64_t)tp->ttiles * TC_BM, nk, TC_BM);
         cudaError_t cb = cudaSuccess;
@@ -1790,6 +1830,8 @@ int tc_plan_create(TcPlan** out, int nk, int ns, int ma, const int* ng, const in
             RTD_TCO(224) RTD_TCO(256)
 #undef RTD_TCO
         }
+        if (cb == cudaSuccess && tp->NTb > 128)
+            cb = raise_smem((const void*)k_tc_opfwd<128>, (int)std::max(max_sm_b, std::max(max_sm_a, (size_t)1024)));
         if (cb != cudaSuccess) e |= 1;
     }
     cudaError_t ce = cudaSuccess;
@@ -1893,7 +1935,7 @@ bool tc_has_back(const TcPlan* tp) { return tp && tp->NTb > 0; }
 int launch_tc_back(const TcPlan* tp, const StepArgs& a, cudaStream_t s) {
     dim3 gz((2 * tp->ns * tp->ma + 255) / 256, 1, a.nk);
     k_tc_pack_z<<<gz, 256, 0, s>>>(a.kd, tp->ns, tp->ma, tp->Kpb, tp->Rpb, tp->zh, tp->zl, tp->fmt, tp->sZ, a.flag);
-    TcRowsCand c{tp->kbps_b, tp->splits_b, tp->S_b, tp->smem_b, 0.f};
+    TcRowsCand c{tp->kbps_b, tp->splits_b, tp->S_b, tp->smem_b, 0.f, tp->nh_b};
     tco_launch_back_any(tp, c, a.kd, a.nk, s, a.kofs, a.flag);  // single-k calls: left operand of k-point kofs
     return 3;
 }
@@ -1932,6 +1974,7 @@ void tc_plan_info(const TcPlan* tp, int* v) {
     v[8] = (int)(tp->ms_a * 1e6f);
     v[9] = tp->gen_t;
     v[10] = tp->ta_t;
+    v[11] = tp->NTb > 0 ? tp->nh_b : 0;
 }
 
 double tc_table_scale(const TcPlan* tp) { return tp ? tp->sT : 1.0; }
@@ -2064,7 +2107,7 @@ void launch_tc_dv_toeplitz(const TcPlan* tp, const StepArgs& a, const ToepDesc* 
     p.flag = a.flag;
     for (int j = 0; j < tp->dv_tiles; ++j) {
         p.brow0 = j * TC_DV_NT;
-        k_tc_toep<TC_DV_NT, true, 256, false><<<dim3(tp->ttiles, tp->dv_splits, a.nk), 288, tp->dv_smem, s>>>(tp->tch,
+        k_tc_toep<TC_DV_NT, true, 256, false><<<dim3(tp->ttiles, tp->dv_splits, a.nk), 256 + 64, tp->dv_smem, s>>>(tp->tch,
                                                                                                          tp->tcl, p);
         TcDvRedParams r{};
         r.splits = tp->dv_splits;
@@ -2320,4 +2363,199 @@ int launch_tcc_project(const TcCC* t, const StepArgs& a, zd* part, cudaStream_t 
     TcCCRed r{1, t->ns, t->naux, t->Dn, t->Mp_p, t->splits_p, t->kbps_p, a.kd, t->Dp, part};
     k_tc_ccred<<<dim3((t->naux + TC_RT - 1) / TC_RT, 1, a.nk), 256, 0, s>>>(r);
     return 3;
+}
+
+// ============================================================================
+// The muffin-tin blocks of the operator (Eq. v_MT, with the momentum blocks of
+// the current) as one batch of split-BF16 products on the matching-row
+// pipeline: per (k, atom) W = G V with G the atom's 5m x m stack
+// [h_eff; o; p_x; p_y; p_z] (h_eff = h + (A/c).p + |A|^2/2c^2 o + s dh, formed in
+// FP64 each step) and V = [Q_alpha; C_lo,alpha] (m x N_s).  G is the left
+// operand (K over the atom's m channels), V the right one; the FP32 products
+// are converted into the FP64 W that the muffin-tin epilogue distributes.
+// ============================================================================
+struct TcMT {
+    int nat = 0, nent = 0, maxm = 0, ns = 0, NT = 0, Dn = 0, Mp = 0, Kp = 0, nkb = 0, tiles = 0, S = 2;
+    size_t smem = 0;
+    unsigned short *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
+    float* D = nullptr;
+    CUtensorMap tah, tal, tbh, tbl;
+};
+
+void tc_mt_destroy(TcMT* t) {
+    if (!t) return;
+    for (void* q : {(void*)t->ah, (void*)t->al, (void*)t->bh, (void*)t->bl, (void*)t->D}) cudaFree(q);
+    delete t;
+}
+
+int tc_mt_create(TcMT** out, int nk, int nat, int maxm, int ns, int* flag, cudaStream_t s, std::string* why) {
+    *out = nullptr;
+    if (!get_encode()) {
+        *why = "the driver has no tensor-map encoder";
+        return RTTDDFT_ERR_UNSUPPORTED;
+    }
+    TcMT* t = new TcMT();
+    t->nat = nat;
+    t->nent = nk * nat;
+    t->maxm = maxm;
+    t->ns = ns;
+    t->Dn = 2 * ns;
+    for (int nt : TCO_NTS)
+        if (nt >= t->Dn) {
+            t->NT = nt;
+            break;
+        }
+    if (!t->NT || t->NT > 128) {
+        delete t;
+        *why = "the tensor-core muffin-tin products take at most 64 states";
+        return RTTDDFT_ERR_UNSUPPORTED;
+    }
+    int dev = 0, smax = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    t->nkb = (maxm + 31) / 32;
+    t->Kp = t->nkb * TC_BK;
+    t->tiles = (5 * maxm + TC_BM - 1) / TC_BM;
+    t->Mp = t->tiles * TC_BM;
+    const size_t stage = (size_t)2 * TC_BM * TC_BK * 2 + (size_t)2 * t->NT * TC_BK * 2;
+    t->S = 4;
+    while (t->S > 2 && 1024 + t->S * stage > (size_t)smax - 512) --t->S;
+    t->smem = 1024 + t->S * stage;
+    const size_t na = (size_t)nat * t->Mp * t->Kp, nb = (size_t)t->nent * t->NT * t->Kp;
+    const size_t nd = (size_t)t->nent * t->Mp * t->Dn;
+    if (cudaMalloc(&t->ah, na * 2) != cudaSuccess || cudaMalloc(&t->al, na * 2) != cudaSuccess ||
+        cudaMalloc(&t->bh, nb * 2) != cudaSuccess || cudaMalloc(&t->bl, nb * 2) != cudaSuccess ||
+        cudaMalloc(&t->D, nd * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        tc_mt_destroy(t);
+        *why = "out of device memory for the tensor-core muffin-tin products";
+        return RTTDDFT_ERR_OOM;
+    }
+    // padding rows and K columns stay zero: the packers write the atoms' own entries only
+    for (auto pr : {std::make_pair((void*)t->ah, na), std::make_pair((void*)t->al, na),
+                    std::make_pair((void*)t->bh, nb), std::make_pair((void*)t->bl, nb)})
+        cudaMemsetAsync(pr.first, 0, pr.second * 2, s);
+    int e = tc_tmap3(&t->tah, t->ah, t->Kp, t->Mp, nat, TC_BM) | tc_tmap3(&t->tal, t->al, t->Kp, t->Mp, nat, TC_BM) |
+            tc_tmap3(&t->tbh, t->bh, t->Kp, t->NT, t->nent, t->NT) |
+            tc_tmap3(&t->tbl, t->bl, t->Kp, t->NT, t->nent, t->NT);
+    cudaError_t ce = cudaSuccess;
+    switch (t->NT) {
+#define RTD_TCO(n) \
+    case n: ce = raise_smem((const void*)k_tc_opfwd<n>, (int)t->smem); break;
+        RTD_TCO(16) RTD_TCO(32) RTD_TCO(48) RTD_TCO(64) RTD_TCO(96) RTD_TCO(128)
+#undef RTD_TCO
+    }
+    (void)flag;
+    if (e || ce != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        tc_mt_destroy(t);
+        *why = "set-up of the tensor-core muffin-tin products failed";
+        return RTTDDFT_ERR_CUDA;
+    }
+    *out = t;
+    return RTTDDFT_OK;
+}
+
+// left operand of a step: per atom the rows of [h_eff; o; p_x; p_y; p_z] with K
+// over the columns j of the m x m blocks (row r of the stack: [Re G(r, .) | Im
+// G(r, .)] per K block of 32), one thread per (i, j) of the atom's blocks
+__global__ void k_tc_mt_pack_a(StepArgs a, int Mp, int Kp, unsigned short* __restrict__ ah,
+                               unsigned short* __restrict__ al) {
+    const AtomTab& at = *a.at;
+    const int atom = blockIdx.y;
+    if (atom >= at.n) return;
+    const int m = at.m[atom];
+    const size_t mm = (size_t)m * m, bo = at.boff[atom];
+    const DevState* st = a.st;
+    const double fx = st->cur_a[0] * a.inv_c, fy = st->cur_a[1] * a.inv_c, fz = st->cur_a[2] * a.inv_c;
+    const double fa = st->cur_aa, sdv = st->cur_s;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < mm; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % m), j = (int)(e / m);
+        const zd hv = a.h[bo + e], ov = a.o[bo + e];
+        const zd px = a.p[3 * bo + e], py = a.p[3 * bo + mm + e], pz = a.p[3 * bo + 2 * mm + e];
+        zd he = zmk(hv.x + fx * px.x + fy * py.x + fz * pz.x + fa * ov.x,
+                    hv.y + fx * px.y + fy * py.y + fz * pz.y + fa * ov.y);
+        if (a.dh && sdv != 0.0) {
+            const zd d = a.dh[bo + e];
+            he.x += sdv * d.x;
+            he.y += sdv * d.y;
+        }
+        const zd blk[5] = {he, ov, px, py, pz};
+        const size_t col = (size_t)(j >> 5) * 64 + (j & 31);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const size_t row = ((size_t)atom * Mp + q * m + i) * Kp + col;
+            put16(blk[q].x, 1, 1.0, ah, al, row, a.flag);
+            put16(blk[q].y, 1, 1.0, ah, al, row + 32, a.flag);
+        }
+    }
+}
+// right operand of a step from the gathered V = [Q; C_lo] of every (k, atom) of
+// the call: rows c < ns hold [Re V | -Im V], rows ns + c [Im V | Re V] over K = i
+__global__ void k_tc_mt_pack_b(StepArgs a, int NT, int Kp, unsigned short* __restrict__ bh,
+                               unsigned short* __restrict__ bl) {
+    const AtomTab& at = *a.at;
+    const int atom = blockIdx.y, k = blockIdx.z;
+    if (atom >= at.n) return;
+    const int m = at.m[atom], ns = a.ns;
+    const size_t ent = (size_t)(a.kofs + k) * at.n + atom;
+    const zd* V = a.mtv + ent * a.mtv_stride;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * ns; e += gridDim.x * blockDim.x) {
+        const int i = e % m, c = e / m;
+        const zd x = V[e];
+        const size_t kc = (size_t)(i >> 5) * 64 + (i & 31);
+        const size_t re_row = (ent * NT + c) * Kp + kc, im_row = (ent * NT + ns + c) * Kp + kc;
+        put16(x.x, 1, 1.0, bh, bl, re_row, a.flag);
+        put16(-x.y, 1, 1.0, bh, bl, re_row + 32, a.flag);
+        put16(x.y, 1, 1.0, bh, bl, im_row, a.flag);
+        put16(x.x, 1, 1.0, bh, bl, im_row + 32, a.flag);
+    }
+}
+// W (FP64, 5m x N_s per (k, atom), column-major) from the FP32 products
+// D[z][row][Re c | Im c] of the call's entries z = k n_atoms + atom
+__global__ void k_tc_mt_w(StepArgs a, const float* __restrict__ D, int Mp, int Dn) {
+    const AtomTab& at = *a.at;
+    const int atom = blockIdx.y, k = blockIdx.z;
+    if (atom >= at.n) return;
+    const int m5 = 5 * at.m[atom], ns = a.ns;
+    const size_t z = (size_t)k * at.n + atom;
+    const size_t ent = (size_t)(a.kofs + k) * at.n + atom;
+    zd* W = a.mtw + ent * a.mtw_stride;
+    const float* d = D + z * Mp * Dn;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m5 * ns; e += gridDim.x * blockDim.x) {
+        const int r = e % m5, c = e / m5;
+        W[e] = zmk((double)d[(size_t)r * Dn + c], (double)d[(size_t)r * Dn + ns + c]);
+    }
+}
+
+int launch_tc_mt(const TcMT* t, const StepArgs& a, cudaStream_t s) {
+    const int nat = t->nat;
+    k_tc_mt_pack_a<<<dim3(64, nat), 256, 0, s>>>(a, t->Mp, t->Kp, t->ah, t->al);
+    k_tc_mt_pack_b<<<dim3((t->maxm * t->ns + 255) / 256, nat, a.nk), 256, 0, s>>>(a, t->NT, t->Kp, t->bh, t->bl);
+    TcOpParams p{};
+    p.nk = a.nk * nat;
+    p.ns = t->ns;
+    p.ma = t->Mp;
+    p.Dn = t->Dn;
+    p.kbps = t->nkb;
+    p.splits = 1;
+    p.atiles = t->tiles;
+    p.R = t->Mp;
+    p.S = t->S;
+    p.nkb_fixed = t->nkb;
+    p.rows_ng = 0;
+    p.fmt = 1;
+    p.a_zmod = nat;
+    p.bz0 = a.kofs * nat;
+    p.kd = a.kd;
+    p.D = t->D;
+    p.flag = a.flag;
+    const dim3 g(t->tiles, 1, a.nk * nat);
+    switch (t->NT) {
+#define RTD_TCO(n) \
+    case n: k_tc_opfwd<n><<<g, TCO_THREADS, t->smem, s>>>(t->tbh, t->tbl, t->tah, t->tal, p); break;
+        RTD_TCO(16) RTD_TCO(32) RTD_TCO(48) RTD_TCO(64) RTD_TCO(96) RTD_TCO(128)
+#undef RTD_TCO
+    }
+    k_tc_mt_w<<<dim3((5 * t->maxm * t->ns + 255) / 256, nat, a.nk), 256, 0, s>>>(a, t->D, t->Mp, t->Dn);
+    return 4;
 }

@@ -210,6 +210,7 @@ struct StepPlan {
     int max_sweeps;
     const struct TcPlan* tc;  // tensor-core operator plan (split-BF16 form) or null
     const struct TcCC* tcc;   // tensor-core expansion and projection (split forms, many states) or null
+    const struct TcMT* tcmt;  // tensor-core muffin-tin blocks (split-BF16 form, many states) or null
     const struct FftPlan* fft;  // FFT route of the interstitial convolution or null
     unsigned* tile_cnt;         // zeroed row-tile counters of the fused split-K sums (or null)
     cudaStream_t side;          // second stream for work that overlaps the main chain (or null)
@@ -314,6 +315,11 @@ int tc_cc_create(TcCC** out, int nk, int naux, int ns, const int* nb, const zd* 
 void tc_cc_destroy(TcCC* t);
 int launch_tcc_expand(const TcCC* t, const StepArgs& a, cudaStream_t s);
 int launch_tcc_project(const TcCC* t, const StepArgs& a, zd* part, cudaStream_t s);
+// the muffin-tin blocks of every (k, atom) as one batch on the tensor cores (split-BF16, many states)
+struct TcMT;
+int tc_mt_create(TcMT** out, int nk, int nat, int maxm, int ns, int* flag, cudaStream_t s, std::string* why);
+void tc_mt_destroy(TcMT* t);
+int launch_tc_mt(const TcMT* t, const StepArgs& a, cudaStream_t s);
 // ---- tensor-core split-BF16 complex GEMM (k_tc.cu); returns an RTTDDFT_* code
 int tc_zgemm(int opA, int M, int N, int K, const zd* A, int lda, const zd* X, int ldx, zd* C, int ldc,
              int beta_add, cudaStream_t s);

@@ -69,7 +69,8 @@ class rttddft_info(ctypes.Structure):
                 ("tc_smem", ctypes.c_int), ("tc_candidates", ctypes.c_int),
                 ("tc_interstitial_ns", ctypes.c_int), ("tc_matching_ns", ctypes.c_int),
                 ("interstitial", ctypes.c_int), ("fft_grid", ctypes.c_int * 3), ("fft_fused", ctypes.c_int),
-                ("tc_gen_threads", ctypes.c_int), ("tc_a_tmem", ctypes.c_int)]
+                ("tc_gen_threads", ctypes.c_int), ("tc_a_tmem", ctypes.c_int),
+                ("tc_back_parts", ctypes.c_int)]
 
 
 class rttddft_trace(ctypes.Structure):
@@ -407,7 +408,7 @@ class Context:
                             slices=i.tc_slices, window=i.tc_window, smem=i.tc_smem,
                             candidates=i.tc_candidates, interstitial_ns=i.tc_interstitial_ns,
                             matching_ns=i.tc_matching_ns, gen_threads=i.tc_gen_threads,
-                            a_tmem=i.tc_a_tmem),
+                            a_tmem=i.tc_a_tmem, back_parts=i.tc_back_parts),
                     interstitial=i.interstitial, fft_grid=tuple(int(x) for x in i.fft_grid),
                     fft_fused=i.fft_fused)
 

@@ -224,6 +224,27 @@ def _golden():
     return np.load(p)
 
 
+@pytest.mark.parametrize("family", ["bparts1", "bparts2"])
+def test_back_projection_column_parts_within_split_bound(family, monkeypatch):
+    """The back-projection in one launch part of 256 output columns or in two
+    parts of 128 (the largest k-point of the heterostructure workload: 4 N_s =
+    240 columns), sampled rows of H X and S X against the oracle's golden file."""
+    from golden.make_mos2_16k_golden import seeded_block
+    monkeypatch.setenv("RTTDDFT_TC_FAMILY", family)
+    g = _golden()
+    k = int(g["keep_k"][1])
+    s = make_system("mos2_16k", k_subset=[k])
+    ctx = Context(s, precision="bf16x3")
+    assert ctx.info()["tc"]["back_parts"] == int(family[-1])
+    nb = int(g["n_basis"][k])
+    x = seeded_block(nb, k)
+    hx, sx = ctx.apply(0, x, g["a_apply"], 0.0)
+    rows = g["rows_hx_k%d" % k]
+    assert np.max(np.abs(hx[rows] - g["hx_rows_k%d" % k]) / g["mag_h_k%d" % k]) < 1e-4
+    assert np.max(np.abs(sx[rows] - g["sx_rows_k%d" % k]) / g["mag_s_k%d" % k]) < 1e-4
+    ctx.close()
+
+
 @pytest.mark.parametrize("family", TUNER_FAMILIES)
 @pytest.mark.parametrize("case", ["ragged", "mos2_16k_largest_k"])
 def test_every_tuner_family_within_split_bound(case, family, monkeypatch):

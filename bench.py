@@ -57,8 +57,14 @@ SM_COUNT, SM_MAX_MHZ, FP32_LANES = 152, 2070.0, 128
 # dram bytes (read + write) per launch from ncu captures, keyed by kernel slot,
 # form and workload; valid only while the kernel source hashes match.
 TRAFFIC = {
-    # profiles/k_cheb_coop_h2_6000_ncu.md: dram__bytes_read.sum + dram__bytes_write.sum
-    ("chebyshev_series", "fp32+fft", "h2_6000", "03e32d7d4661fadf"): 675840.0,
+    # dram__bytes_read.sum + dram__bytes_write.sum per launch, keyed by the kernel
+    # sources they were taken on.  mos2_16k: an ncu capture of the DRAM counters on two
+    # of its k-points (--k-subset 0,1), scaled to all 16: the series by the
+    # k-points (8x, every k-point has the same N_aux), the interstitial and matching-
+    # row products by sum_k N_G (6.833x; their streams are the matching coefficients
+    # and the packed C_G, both proportional to N_G).
+    ("chebyshev_series", "bf16x3", "mos2_16k", "d0352726545c4245"): 27918336.0,
+    ("tc_interstitial_and_forward", "bf16x3", "mos2_16k", "d0352726545c4245"): 4535055194.0,
 }
 
 

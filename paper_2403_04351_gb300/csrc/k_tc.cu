@@ -429,8 +429,8 @@ int tc_zgemm(int opA, int M, int N, int K, const zd* A, int lda, const zd* X, in
 // through one ring of stages; one thread issues the products (hi.hi, hi.lo,
 // lo.hi per block); waits are bounded and abort together.
 // ============================================================================
-#define TCO_GEN 256  // threads of the generating / epilogue warps (8 warps); warp 8 issues
-#define TCO_THREADS 288
+#define TCO_GEN 256  // threads of the generating / epilogue warps (8 warps); warp 8 issues, warp 9 copies
+#define TCO_THREADS 320
 #define TCO_MAXS 4
 
 __device__ bool mbar_wait_ab(uint64_t* b, uint32_t phase, volatile int* ab) {
@@ -533,22 +533,9 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
                                    ((uint32_t)(TC_BM >> 4) << 24);
             const uint32_t idesc2 = (1u << 4) | ((uint32_t)p.fmt << 7) | ((uint32_t)p.fmt << 10) |
                                     ((uint32_t)((NACC) >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
-            int issued = 0, consumed = 0;
-            auto load = [&](int j) {
-                const int s = j % S, kx = (kb0 + j) * TC_BK;
-                unsigned char* st = smem + (size_t)s * STAGE;
-                mbar_expect_tx(&full[s], STAGE);
-                tma_load_3d(st + 2 * A_BYTES, &tmBh, kx, brow, zb, &full[s]);
-                tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tmBl, kx, brow, zb, &full[s]);
-                tma_load_3d(st, &tmAh, kx, row0, za, &full[s]);
-                tma_load_3d(st + A_BYTES, &tmAl, kx, row0, za, &full[s]);
-                issued = j + 1;
-            };
-            for (int j = 0; j < min(nk, S); ++j) load(j);
             for (int j = 0; j < nk; ++j) {
                 const int s = j % S;
                 if (!mbar_wait_ab(&full[s], (uint32_t)((j / S) & 1), ab)) break;
-                consumed = j + 1;
                 tc_fence_after();
                 const uint32_t ah = smem_u32(smem + (size_t)s * STAGE), al = ah + A_BYTES;
                 const uint32_t bh = ah + 2 * A_BYTES, bl = bh + B_BYTES;
@@ -565,17 +552,30 @@ __global__ void __launch_bounds__(TCO_THREADS, 1)
                     }
                 }
                 umma_commit(&empty[s]);
-                const int jp = j - 1;
-                if (jp >= 0 && jp + S < nk) {
-                    if (!mbar_wait_ab(&empty[jp % S], (uint32_t)((jp / S) & 1), ab)) break;
-                    load(jp + S);
-                }
             }
             umma_commit(&done);
+            if (*ab) atomicOr(p.flag, 8);
+        }
+        __syncwarp();
+    } else if (warp == 9) {
+        // both operands' copies, S blocks ahead of the products: a stage is refilled
+        // once the products that read it have completed
+        if (lane == 0) {
+            int issued = 0;
+            for (int j = 0; j < nk; ++j) {
+                const int s = j % S, kx = (kb0 + j) * TC_BK;
+                if (j >= S && !mbar_wait_ab(&empty[s], (uint32_t)(((j / S) - 1) & 1), ab)) break;
+                unsigned char* st = smem + (size_t)s * STAGE;
+                mbar_expect_tx(&full[s], STAGE);
+                tma_load_3d(st + 2 * A_BYTES, &tmBh, kx, brow, zb, &full[s]);
+                tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tmBl, kx, brow, zb, &full[s]);
+                tma_load_3d(st, &tmAh, kx, row0, za, &full[s]);
+                tma_load_3d(st + A_BYTES, &tmAl, kx, row0, za, &full[s]);
+                issued = j + 1;
+            }
             if (*ab) {
-                atomicOr(p.flag, 8);
-                // the copies already issued land before the block's shared memory goes away
-                for (int j = consumed; j < issued; ++j) mbar_wait(&full[j % S], (uint32_t)((j / S) & 1));
+                // the copies in flight land before the block's shared memory goes away
+                for (int j = max(0, issued - S); j < issued; ++j) mbar_wait(&full[j % S], (uint32_t)((j / S) & 1));
             }
         }
         __syncwarp();

@@ -73,8 +73,9 @@ extern "C" {
 #define RTTDDFT_PREC_FP32 1
 /* split-BF16 on the tensor cores: the interstitial convolution and the
  * matching-coefficient products of the operator run as tcgen05 products of
- * bf16 hi/lo splits (hi.hi + hi.lo + lo.hi, FP32 accumulation, FP64 sums of
- * the K slices, relative error a few 2^-16); the other full-basis
+ * bf16 hi/lo splits (hi.hi + hi.lo + lo.hi, FP32 accumulation, the K slices
+ * summed as FP32 two-sum pairs into FP64, relative error a few 2^-16); the
+ * muffin-tin blocks too when there are 16 to 64 states; the other full-basis
  * contractions as in RTTDDFT_PREC_FP32.  At most 128 states. */
 #define RTTDDFT_PREC_BF16X3 2
 /* split-FP16: the same products with fp16 hi/lo splits (22 significant bits,

@@ -78,20 +78,23 @@ template <> struct Cx<zf> {
 
 // 16-bit split w = v * scale = hi + lo (each rounded to nearest): fmt 1 bf16,
 // fmt 0 fp16 (scale keeps w inside the fp16 range); returns false when |w|
-// exceeds the fp16 range
-#define TC_FP16_MAX 65000.0
+// exceeds the fp16 range.  The split keeps 16 (bf16) or 22 (fp16) significant
+// bits, fewer than FP32's 24, so it is taken from w rounded once to FP32 with
+// FP32 arithmetic: one conversion on the slow FP64 path per value instead of
+// five (scale is a power of two, exact in FP32).
+#define TC_FP16_MAX 65000.0f
 __device__ __forceinline__ bool split16(double v, int fmt, double scale, unsigned short& hi, unsigned short& lo) {
-    const double w = v * scale;
+    const float w = __double2float_rn(v) * (float)scale;
     if (fmt) {
-        const __nv_bfloat16 h = __double2bfloat16(w);
+        const __nv_bfloat16 h = __float2bfloat16_rn(w);
         hi = __bfloat16_as_ushort(h);
-        lo = __bfloat16_as_ushort(__double2bfloat16(w - (double)__bfloat162float(h)));
+        lo = __bfloat16_as_ushort(__float2bfloat16_rn(w - __bfloat162float(h)));
         return true;
     }
-    const __half h = __double2half(w);
+    const __half h = __float2half_rn(w);
     hi = __half_as_ushort(h);
-    lo = __half_as_ushort(__double2half(w - (double)__half2float(h)));
-    return fabs(w) <= TC_FP16_MAX;
+    lo = __half_as_ushort(__float2half_rn(w - __half2float(h)));
+    return fabsf(w) <= TC_FP16_MAX;
 }
 // the split packed as hi | lo << 16
 __device__ __forceinline__ uint32_t split16_bits(double v, int fmt, double scale, bool& ok) {

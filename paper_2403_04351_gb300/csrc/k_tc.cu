@@ -1040,7 +1040,7 @@ __global__ void k_tc_pack_z(const KDev* __restrict__ kd, int ns, int ma, int Kp,
     put16(-z.y, fmt, sz, bh, bl, re_row + 32 + o, flag);
 }
 
-// Sum of the K slices in FP64: interstitial rows into K.th (ng x ns),
+// Sum of the K slices (two-sum pairs, FP64 results): interstitial rows into K.th (ng x ns),
 // matching rows into K.Q (ma x ns).
 struct TcRedParams {
     int ns, ma, Dn, kbps_t, splits_t, kbps_a, splits_a, Rt, Ra;
@@ -1053,11 +1053,24 @@ struct TcRedParams {
     const float* Da;
     const float* Db;
 };
+// Sum of FP32 values kept as an unevaluated pair s + e (Knuth's two-sum on each
+// addition, the rounding errors collected in e): FP32 arithmetic throughout, so
+// a sum of a few slices costs no FP64 instructions until the pair is widened
+// once; it carries about 48 significant bits, more than the slices' own.
+struct Sum2f {
+    float s = 0.f, e = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x, bp = t - s;
+        e += (s - (t - bp)) + (x - bp);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)e; }
+};
 // A tile of TC_RT output rows of one product: the FP32 slice partials
 // D[s][row][Dn] (real columns c < nc: Re, nc + c: Im) summed over the nsp
-// slices in slice order in FP64, staged in shared memory so that the loads
-// run along the rows of D and the stores along the columns of the
-// column-major output out[row + c ld].
+// slices in slice order (two-sum pairs, widened to FP64 once), staged in
+// shared memory so that the loads run along the rows of D and the stores
+// along the columns of the column-major output out[row + c ld].
 #define TC_RT 16
 __device__ void tc_red_tile(const float* __restrict__ D, size_t sstride, int nsp, int Dn, int nc, int row0,
                             int nrow, double scale, zd* __restrict__ out, size_t ld, double (*tile)[257]) {
@@ -1067,7 +1080,7 @@ __device__ void tc_red_tile(const float* __restrict__ D, size_t sstride, int nsp
         const int q4 = n2 >> 2;
         for (int e = threadIdx.x; e < TC_RT * q4; e += blockDim.x) {
             const int r = e / q4, c = (e % q4) * 4, row = row0 + r;
-            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+            Sum2f v0, v1, v2, v3;
             if (row < nrow) {
                 const float* d = D + (size_t)row * Dn + c;
                 for (int s0 = 0; s0 < nsp; s0 += 4) {
@@ -1078,22 +1091,22 @@ __device__ void tc_red_tile(const float* __restrict__ D, size_t sstride, int nsp
                                               : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        v0 += (double)a[u].x;
-                        v1 += (double)a[u].y;
-                        v2 += (double)a[u].z;
-                        v3 += (double)a[u].w;
+                        v0.add(a[u].x);
+                        v1.add(a[u].y);
+                        v2.add(a[u].z);
+                        v3.add(a[u].w);
                     }
                 }
             }
-            tile[r][c] = v0;
-            tile[r][c + 1] = v1;
-            tile[r][c + 2] = v2;
-            tile[r][c + 3] = v3;
+            tile[r][c] = v0.value();
+            tile[r][c + 1] = v1.value();
+            tile[r][c + 2] = v2.value();
+            tile[r][c + 3] = v3.value();
         }
     } else {
         for (int e = threadIdx.x; e < TC_RT * n2; e += blockDim.x) {
             const int r = e / n2, c = e % n2, row = row0 + r;
-            double v = 0.0;
+            Sum2f v;
             if (row < nrow) {
                 const float* d = D + (size_t)row * Dn + c;
                 for (int s0 = 0; s0 < nsp; s0 += 4) {
@@ -1101,10 +1114,10 @@ __device__ void tc_red_tile(const float* __restrict__ D, size_t sstride, int nsp
 #pragma unroll
                     for (int u = 0; u < 4; ++u) a[u] = (s0 + u < nsp) ? d[(size_t)(s0 + u) * sstride] : 0.f;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) v += (double)a[u];
+                    for (int u = 0; u < 4; ++u) v.add(a[u]);
                 }
             }
-            tile[r][c] = v;
+            tile[r][c] = v.value();
         }
     }
     __syncthreads();

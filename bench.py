@@ -63,8 +63,8 @@ TRAFFIC = {
     # k-points (8x, every k-point has the same N_aux), the interstitial and matching-
     # row products by sum_k N_G (6.833x; their streams are the matching coefficients
     # and the packed C_G, both proportional to N_G).
-    ("chebyshev_series", "bf16x3", "mos2_16k", "d0352726545c4245"): 27918336.0,
-    ("tc_interstitial_and_forward", "bf16x3", "mos2_16k", "d0352726545c4245"): 4535055194.0,
+    ("chebyshev_series", "bf16x3", "mos2_16k", "7a742d39b168f133"): 27926528.0,
+    ("tc_interstitial_and_forward", "bf16x3", "mos2_16k", "7a742d39b168f133"): 4533407514.0,
 }
 
 

@@ -45,7 +45,7 @@ def ref(tiny):
     return a, Oracle(tiny).run(a, tiny["dt"], hartree=True)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
 def test_hartree_feedback_matches_oracle(tiny, ref, prec):
     a, r = ref
     ctx = Context(tiny, precision=prec, interstitial="fft", hartree=True, graph_steps=10)
@@ -57,9 +57,12 @@ def test_hartree_feedback_matches_oracle(tiny, ref, prec):
         assert np.max(obs["norm_dev"]) < 1e-10
         assert np.max(np.abs(obs["n_exc"] - r["n_exc"])) < 1e-10
     else:
+        # split-BF16: the interstitial sum by the FP32 FFT route, the matching-
+        # coefficient products on the tensor cores; the density and its potential
+        # are FP64 in every form
         assert rel(obs["dmu"], r["dmu"]) < 1e-6
-        assert rel(obs["energy"], r["E"]) < 1e-5
-        assert np.max(obs["norm_dev"]) < 1e-5
+        assert rel(obs["energy"], r["E"]) < (1e-5 if prec == "fp32" else 1e-4)
+        assert np.max(obs["norm_dev"]) < (1e-5 if prec == "fp32" else 1e-4)
     ctx.close()
 
 

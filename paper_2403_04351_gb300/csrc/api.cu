@@ -1255,8 +1255,9 @@ int rttddft_setup(const rttddft_system* s, const rttddft_options* opt_in, void* 
                 }
             }
             ctx->gd_mt1 = upload_descs(ctx, m1);
-            if (o->precision == RTTDDFT_PREC_BF16X3 && 2 * ns <= 128) {
-                // split-BF16 form: the same products as one batch on the tensor cores
+            if (o->precision == RTTDDFT_PREC_BF16X3 && 2 * ns <= 128 && (long long)nk * at.n <= 65535) {
+                // split-BF16 form: the same products as one batch on the tensor cores (one
+                // grid slice per (k, atom), within the grid's z limit)
                 std::string why;
                 const int e = tc_mt_create(&ctx->tcmt, nk, at.n, ctx->maxm, ns, ctx->d_flag, ctx->stream, &why);
                 if (e) fail(ctx, e, why);

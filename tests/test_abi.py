@@ -133,14 +133,17 @@ def test_polarizability_arguments_checked_on_the_host(lib):
 
 
 def test_hartree_options_checked_on_the_host(lib, small):
-    """The density feedback needs the FFT route, the reciprocal vectors and a
-    positive bound; all refused before any device work."""
+    """The density feedback needs the FFT route, the reciprocal vectors, a
+    positive bound and a finite muffin-tin coupling; all refused before any
+    device work."""
     _expect("ERR_UNSUPPORTED", small, hartree=True)
     _expect("ERR_ARG", small, interstitial="fft", hartree=True, hartree_bound=-1.0)
     s = dict(small)
     del s["recip"]
     _expect("ERR_ARG", s, interstitial="fft", hartree=True)
+    _expect("ERR_NONFINITE", small, interstitial="fft", hartree=True, hartree_mt_u=float("nan"))
     assert rttddft.rttddft_default_options().hartree == 0
+    assert rttddft.rttddft_default_options().hartree_mt_u == 0.0
 
 
 def _header_fields(name):

@@ -563,6 +563,16 @@ def time_forms(timer, s, forms, a_all, sc_all, nsteps, nwarm, have=None):
     return entries, recs
 
 
+def shard_refusal(form, world, k_subset):
+    """Why a form cannot run on a subset of the k-points, or None: the density
+    feedback sums the density over every k-point each step, so a k-point shard
+    or subset would feed back a partial density."""
+    if parse_form(form)[2] and (world > 1 or k_subset):
+        return ("%s: the density feedback couples the k-points through the density and is "
+                "not sharded (run it on one GPU, all k-points)" % form)
+    return None
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from synth import CONFIGS, make_system
@@ -770,6 +780,9 @@ def main():
         p.error("--warmup must be >= 3")
     parse_form(args.precision)
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    why = shard_refusal(args.precision, world, args.k_subset)
+    if why:
+        p.error(why)
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":

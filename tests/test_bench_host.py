@@ -48,3 +48,14 @@ def test_roofline_entry_of_the_fft_slot():
     assert np.isclose(roof["achieved"], fl / 0.03e-3 / 1e12)
     roof64 = bench.roofline_of("fft_interstitial", tr, s, "fp64+fft", 14)
     assert roof64["peak"] == bench.FP64_PEAK_TFLOPS
+
+
+def test_density_feedback_is_not_sharded():
+    """A k-point shard or subset of a density-feedback run would feed back a
+    partial density: the benchmark refuses it before any GPU work; the forms
+    without feedback shard freely."""
+    assert bench.shard_refusal("fp64+fft+hartree", 2, "") is not None
+    assert bench.shard_refusal("fp32+fft+hartree", 1, "0,1") is not None
+    assert bench.shard_refusal("fp64+fft+hartree", 1, "") is None
+    for form in ("fp64", "bf16x3", "fp32+fft+dv"):
+        assert bench.shard_refusal(form, 8, "0,1") is None
